@@ -1,0 +1,186 @@
+"""FP64 CPU oracle of the symmetric free-energy multicomponent LB update.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only code allowed to import this
+package.  The CUDA library never imports it and shares no code with it.
+
+The lattice update itself is plain C (``mclb_oracle.c``), built with gcc on
+first use into ``oracle/_build``; this module marshals numpy arrays to it.
+``oracle.thermo`` holds the Flory-Huggins thermodynamics (binodals, critical
+points) the paper compares its simulations against.
+
+Parity unpinned: none of the lattice-update functions; every stage is pinned
+by tests against moment conditions, closed forms and an independent D1Q3
+transcription.  The paper's printed ternary critical points are not
+reproduced by the symmetric-chi reading and are reported, not asserted.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mclb_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NMAX = 8
+
+
+class OracleParams(ctypes.Structure):
+    _fields_ = [("ncomp", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("tau", ctypes.c_double), ("theta", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
+                ("chi", ctypes.c_double * (NMAX * NMAX)), ("m", ctypes.c_double * NMAX)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP, no FP contraction so that x86 and
+    Arm hosts round identically).  Returns the shared-library path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            pp = ctypes.POINTER(OracleParams)
+            lib.oracle_nthreads.restype = ctypes.c_int
+            lib.oracle_equilibrium.argtypes = [ctypes.c_double] * 3 + [dp]
+            lib.oracle_forcing.argtypes = [ctypes.c_double] * 5 + [dp]
+            lib.oracle_psi.argtypes = [pp, dp]
+            lib.oracle_psi.restype = ctypes.c_double
+            lib.oracle_mu_bulk.argtypes = [pp, dp, dp]
+            lib.oracle_init.argtypes = [pp, dp, dp, dp]
+            lib.oracle_run.argtypes = [pp, dp, ctypes.c_long]
+            lib.oracle_fields.argtypes = [pp, dp] + [dp] * 6
+            lib.oracle_moments.argtypes = [pp, dp] + [dp] * 4
+            lib.oracle_conservation.argtypes = [pp, dp, dp, dp, dp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def nthreads() -> int:
+    return _load().oracle_nthreads()
+
+
+class Oracle:
+    """One oracle simulation: parameters plus the FP64 distribution array.
+
+    ``f`` has shape (N, 9, ny, nx): pre-collision distributions at the current
+    time, D2Q9 velocity order (0,0), (1,0), (0,1), (-1,0), (0,-1), (1,1),
+    (-1,1), (-1,-1), (1,-1).
+    """
+
+    def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
+                 force=(0.0, 0.0)):
+        self.lib = _load()
+        p = OracleParams()
+        p.ncomp, p.nx, p.ny = int(ncomp), int(nx), int(ny)
+        p.tau, p.theta, p.kappa = float(tau), float(theta), float(kappa)
+        p.gx, p.gy = float(force[0]), float(force[1])
+        chi = np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp)
+        for a in range(ncomp):
+            for b in range(ncomp):
+                p.chi[a * ncomp + b] = chi[a, b]
+        m = np.ones(ncomp) if m is None else np.asarray(m, dtype=np.float64)
+        for a in range(ncomp):
+            p.m[a] = m[a]
+        self.p = p
+        self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
+        self.f = np.zeros((ncomp, 9, ny, nx))
+
+    @classmethod
+    def from_problem(cls, prob):
+        o = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
+                prob.kappa, prob.force)
+        o.init(prob.rho, prob.u)
+        return o
+
+    @property
+    def _pp(self):
+        return ctypes.byref(self.p)
+
+    def init(self, rho, u=None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        rc = self.lib.oracle_init(self._pp, _ptr(rho), _ptr(uu), _ptr(self.f))
+        if rc:
+            raise ValueError(f"oracle_init failed ({rc})")
+
+    def set_state(self, f):
+        self.f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(
+            self.ncomp, 9, self.ny, self.nx)).copy()
+
+    def run(self, nsteps: int) -> int:
+        rc = self.lib.oracle_run(self._pp, _ptr(self.f), int(nsteps))
+        if rc < 0:
+            raise ValueError(f"oracle_run failed ({rc})")
+        return rc
+
+    def fields(self):
+        N, S = self.ncomp, (self.ny, self.nx)
+        rs, nu, ax, ay = (np.zeros((N,) + S) for _ in range(4))
+        ux, uy = np.zeros(S), np.zeros(S)
+        self.lib.oracle_fields(self._pp, _ptr(self.f), _ptr(rs), _ptr(ux), _ptr(uy), _ptr(nu),
+                               _ptr(ax), _ptr(ay))
+        return dict(rho=rs, ux=ux, uy=uy, nu=nu, ax=ax, ay=ay)
+
+    def moments(self):
+        N, S = self.ncomp, (self.ny, self.nx)
+        rho, U, mu, P = np.zeros((N,) + S), np.zeros((2,) + S), np.zeros((N,) + S), np.zeros((3,) + S)
+        self.lib.oracle_moments(self._pp, _ptr(self.f), _ptr(rho), _ptr(U), _ptr(mu), _ptr(P))
+        return dict(rho=rho, U=U, mu=mu, P=P)
+
+    def conservation(self):
+        mass, mom, fs = np.zeros(self.ncomp), np.zeros(2), np.zeros(2)
+        self.lib.oracle_conservation(self._pp, _ptr(self.f), _ptr(mass), _ptr(mom), _ptr(fs))
+        return dict(mass=mass, mom=mom, force=fs)
+
+    # per-site helpers used by the pins
+    def psi(self, rs) -> float:
+        rs = np.ascontiguousarray(rs, dtype=np.float64)
+        return self.lib.oracle_psi(self._pp, _ptr(rs))
+
+    def mu_bulk(self, rs):
+        rs = np.ascontiguousarray(rs, dtype=np.float64)
+        out = np.zeros(self.ncomp)
+        self.lib.oracle_mu_bulk(self._pp, _ptr(rs), _ptr(out))
+        return out
+
+
+def equilibrium(rho_s, ux, uy):
+    out = np.zeros(9)
+    _load().oracle_equilibrium(float(rho_s), float(ux), float(uy), _ptr(out))
+    return out
+
+
+def forcing(rho_s, jx, jy, ax, ay):
+    out = np.zeros(9)
+    _load().oracle_forcing(float(rho_s), float(jx), float(jy), float(ax), float(ay), _ptr(out))
+    return out

@@ -1,0 +1,486 @@
+/*
+ * mclb_oracle.c -- plain FP64 CPU oracle for one timestep of the symmetric
+ * free-energy multicomponent lattice Boltzmann method (Li & Wagner,
+ * arXiv:0704.3444, "A Symmetric Free Energy Based Multi-Component Lattice
+ * Boltzmann Method").
+ *
+ * TEST INFRASTRUCTURE ONLY.  The test suite, the smoke check and the
+ * benchmark's CPU-baseline leg are the only callers.  This file shares no code,
+ * header, table or constant generator with the CUDA library; the two meet only
+ * through the seeded input generators and through arrays compared in tests.
+ *
+ * The step follows the paper in its own order, one plain loop per stage, FP64
+ * throughout, fixed summation orders (velocities i = 0..8, components
+ * sigma = 0..N-1), two buffers and periodic wrap:
+ *
+ *   1. moments        rho^s = sum_i f^s_i, rho^s u^s = sum_i f^s_i v_i,
+ *                     rho = sum_s rho^s, rho u = sum_s rho^s u^s       (Sec. 3)
+ *   2. potentials     Flory-Huggins chemical potential (Eq. lgf, Eq.
+ *                     chemicalpotential) plus the gradient term, and
+ *                     nu^s = mu^s - (1/3) ln rho^s                     (Eq. definef)
+ *   3. forces         rho^s a^s = -(1 - 1/(2 tau)) rho^s grad nu^s     (Eq. definef)
+ *                     plus the body acceleration g of the momentum
+ *                     equation (Eq. NSEeq)
+ *   4. collision      f* = f + (f^e - f)/tau + F                       (Eq. ssLB)
+ *                     with f^e and F the D2Q9 polynomials whose moments
+ *                     are the ones listed in Sec. 3
+ *   5. streaming      f(r + v_i, t + 1) = f*(r, t)                     (Eq. ssLB)
+ *
+ * Readings of points the paper leaves open (each is listed in the design doc):
+ *   - mu is used per unit mass, mu^s / m^s = d psi / d rho^s, so that
+ *     rho^s grad(mu^s/m^s) = n^s grad mu^s (identical for m = 1);
+ *   - theta, the Flory-Huggins temperature, is a free parameter;
+ *   - gradient term: psi += sum_s (kappa/2) |grad rho^s|^2, hence
+ *     mu^s gains -kappa lap rho^s;
+ *   - discrete operators: grad g = 3 sum_i w_i v_i g(r + v_i),
+ *     lap g = 6 sum_i w_i (g(r + v_i) - g(r));
+ *   - the logarithms of nu^s are combined as
+ *     (theta/m^s - 1/3) ln rho^s - (theta/m^s) ln rho, the first term is
+ *     dropped when its coefficient is exactly zero and otherwise uses
+ *     max(rho^s, 1e-12 rho);
+ *   - f^e is built with the bare barycentric u, F with rho^s u^s = j^s;
+ *     the output velocity is U = u + a/2 with rho a = sum_s rho^s a^s;
+ *   - initial distributions are the equilibria of the given fields.
+ *
+ * Layout: f[((s * 9 + i) * ny + y) * nx + x], the pre-collision distribution
+ * of component s, velocity i at site (x, y) at the current time.
+ * D2Q9 velocities: v_0 = (0,0); v_1..4 = (1,0), (0,1), (-1,0), (0,-1);
+ * v_5..8 = (1,1), (-1,1), (-1,-1), (1,-1).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_QMAX 9
+#define OR_NMAX 8
+
+typedef struct {
+    int ncomp, nx, ny;
+    double tau, theta, kappa, gx, gy;
+    double chi[OR_NMAX * OR_NMAX];
+    double m[OR_NMAX];
+} oracle_params;
+
+static const int VX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int VY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WT[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double LOG_FLOOR = 1e-12;
+
+int oracle_nthreads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int check(const oracle_params* p)
+{
+    if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1 || p->ny < 1) return -1;
+    if (!(p->tau > 0.5)) return -1;
+    return 0;
+}
+
+static inline long wrap(long a, long n) { a %= n; return a < 0 ? a + n : a; }
+
+/* ---------------------------------------------------------------- per site */
+
+/* f^e_i with sum f^e = rho^s, sum f^e v = rho^s u, sum f^e v v = rho^s/3 I + rho^s u u
+ * (Sec. 3, equilibrium moments of one component; the D2Q9 second-order polynomial). */
+void oracle_equilibrium(double rho_s, double ux, double uy, double* fe)
+{
+    double uu = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        double cu = VX[i] * ux + VY[i] * uy;
+        fe[i] = WT[i] * rho_s * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+/* F_i with sum F = 0, sum F v = rho^s a^s, sum F v v = rho^s (a^s u^s + u^s a^s)
+ * (Eqs. ff1-ff3), rho^s u^s = j^s. */
+void oracle_forcing(double rho_s, double jx, double jy, double ax, double ay, double* F)
+{
+    double aj = ax * jx + ay * jy;
+    for (int i = 0; i < 9; ++i) {
+        double ca = VX[i] * ax + VY[i] * ay;
+        double cj = VX[i] * jx + VY[i] * jy;
+        F[i] = WT[i] * (3.0 * rho_s * ca + 9.0 * ca * cj - 3.0 * aj);
+    }
+}
+
+/* Flory-Huggins free energy density of Eq. lgf with n^s = rho^s / m^s and
+ * phi^s = rho^s / rho:  psi = theta [ -sum n m + sum n ln phi + 1/2 sum chi m n phi' ]. */
+double oracle_psi(const oracle_params* p, const double* rs)
+{
+    int N = p->ncomp;
+    double rho = 0.0;
+    for (int s = 0; s < N; ++s) rho += rs[s];
+    double psi = 0.0;
+    for (int s = 0; s < N; ++s) {
+        double n = rs[s] / p->m[s];
+        double phi = rs[s] / rho;
+        psi += -p->theta * n * p->m[s];
+        psi += n * p->theta * log(phi);
+        for (int t = 0; t < N; ++t)
+            psi += 0.5 * p->chi[s * N + t] * p->theta * p->m[s] * n * (rs[t] / rho);
+    }
+    return psi;
+}
+
+/* Mass-specific bulk chemical potential mu^s/m^s = d psi / d rho^s of Eq. lgf:
+ * theta [ (ln phi^s + 1)/m^s - 1 - sum_t phi^t/m^t + sum_t chi^{st} phi^t
+ *         - 1/2 sum_{t,t'} chi^{tt'} phi^t phi^t' ]. */
+void oracle_mu_bulk(const oracle_params* p, const double* rs, double* mu)
+{
+    int N = p->ncomp;
+    double rho = 0.0;
+    for (int s = 0; s < N; ++s) rho += rs[s];
+    double phi[OR_NMAX], chiphi[OR_NMAX];
+    double sum_phi_m = 0.0, quad = 0.0;
+    for (int s = 0; s < N; ++s) phi[s] = rs[s] / rho;
+    for (int s = 0; s < N; ++s) sum_phi_m += phi[s] / p->m[s];
+    for (int s = 0; s < N; ++s) {
+        chiphi[s] = 0.0;
+        for (int t = 0; t < N; ++t) chiphi[s] += p->chi[s * N + t] * phi[t];
+    }
+    for (int s = 0; s < N; ++s) quad += 0.5 * phi[s] * chiphi[s];
+    for (int s = 0; s < N; ++s) {
+        double ph = phi[s] > LOG_FLOOR ? phi[s] : LOG_FLOOR;
+        mu[s] = p->theta * ((log(ph) + 1.0) / p->m[s] - 1.0 - sum_phi_m + chiphi[s] - quad);
+    }
+}
+
+/* ------------------------------------------------------------- whole field */
+
+typedef struct {
+    long S;
+    double *rs, *jx, *jy;      /* per component: rho^s, j^s = rho^s u^s   (N*S) */
+    double *rho, *ux, *uy;     /* total density and barycentric velocity  (S)   */
+    double *nu;                /* mu^s - 1/3 ln rho^s                     (N*S) */
+    double *ax, *ay;           /* a^s                                     (N*S) */
+} work_t;
+
+static int work_alloc(const oracle_params* p, work_t* w)
+{
+    long S = (long)p->nx * p->ny, N = p->ncomp;
+    w->S = S;
+    w->rs = malloc(sizeof(double) * N * S);
+    w->jx = malloc(sizeof(double) * N * S);
+    w->jy = malloc(sizeof(double) * N * S);
+    w->rho = malloc(sizeof(double) * S);
+    w->ux = malloc(sizeof(double) * S);
+    w->uy = malloc(sizeof(double) * S);
+    w->nu = malloc(sizeof(double) * N * S);
+    w->ax = malloc(sizeof(double) * N * S);
+    w->ay = malloc(sizeof(double) * N * S);
+    return (w->rs && w->jx && w->jy && w->rho && w->ux && w->uy && w->nu && w->ax && w->ay) ? 0 : -2;
+}
+
+static void work_free(work_t* w)
+{
+    free(w->rs); free(w->jx); free(w->jy); free(w->rho); free(w->ux); free(w->uy);
+    free(w->nu); free(w->ax); free(w->ay);
+}
+
+/* Discrete lap g = 6 sum_i w_i (g(r + v_i) - g(r)) of one scalar field. */
+static double lap_at(const double* g, int nx, int ny, int x, int y)
+{
+    double c = g[(long)y * nx + x], acc = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        long xx = wrap(x + VX[i], nx), yy = wrap(y + VY[i], ny);
+        acc += WT[i] * (g[yy * nx + xx] - c);
+    }
+    return 6.0 * acc;
+}
+
+/* Discrete grad g = 3 sum_i w_i v_i g(r + v_i). */
+static void grad_at(const double* g, int nx, int ny, int x, int y, double* gx, double* gy)
+{
+    double ax = 0.0, ay = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        long xx = wrap(x + VX[i], nx), yy = wrap(y + VY[i], ny);
+        double v = g[yy * nx + xx];
+        ax += WT[i] * VX[i] * v;
+        ay += WT[i] * VY[i] * v;
+    }
+    *gx = 3.0 * ax;
+    *gy = 3.0 * ay;
+}
+
+/* Stage 1: moments of the pre-collision distributions (Sec. 3). */
+static void stage_moments(const oracle_params* p, const double* f, work_t* w)
+{
+    int N = p->ncomp, nx = p->nx, ny = p->ny;
+    long S = w->S;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            long c = (long)y * nx + x;
+            double rho = 0.0, jxt = 0.0, jyt = 0.0;
+            for (int s = 0; s < N; ++s) {
+                double r = 0.0, jx = 0.0, jy = 0.0;
+                for (int i = 0; i < 9; ++i) {
+                    double v = f[(long)(s * 9 + i) * S + c];
+                    r += v;
+                    jx += v * VX[i];
+                    jy += v * VY[i];
+                }
+                w->rs[s * S + c] = r;
+                w->jx[s * S + c] = jx;
+                w->jy[s * S + c] = jy;
+                rho += r;
+                jxt += jx;
+                jyt += jy;
+            }
+            w->rho[c] = rho;
+            w->ux[c] = jxt / rho;
+            w->uy[c] = jyt / rho;
+        }
+    }
+}
+
+/* Stage 2: nu^s = mu^s/m^s - kappa lap rho^s - (1/3) ln rho^s (Eq. lgf, Eq.
+ * chemicalpotential, Eq. definef), logarithms combined as described above. */
+static void stage_potentials(const oracle_params* p, work_t* w)
+{
+    int N = p->ncomp, nx = p->nx, ny = p->ny;
+    long S = w->S;
+    double th = p->theta;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            long c = (long)y * nx + x;
+            double rho = w->rho[c];
+            double phi[OR_NMAX], chiphi[OR_NMAX];
+            double sum_phi_m = 0.0, quad = 0.0;
+            for (int s = 0; s < N; ++s) phi[s] = w->rs[s * S + c] / rho;
+            for (int s = 0; s < N; ++s) sum_phi_m += phi[s] / p->m[s];
+            for (int s = 0; s < N; ++s) {
+                chiphi[s] = 0.0;
+                for (int t = 0; t < N; ++t) chiphi[s] += p->chi[s * N + t] * phi[t];
+            }
+            for (int s = 0; s < N; ++s) quad += 0.5 * phi[s] * chiphi[s];
+            double lnrho = log(rho);
+            for (int s = 0; s < N; ++s) {
+                double rs = w->rs[s * S + c];
+                double coef = th / p->m[s] - 1.0 / 3.0;
+                double logs = -(th / p->m[s]) * lnrho;
+                if (coef != 0.0) {
+                    double r = rs > LOG_FLOOR * rho ? rs : LOG_FLOOR * rho;
+                    logs += coef * log(r);
+                }
+                double bulk = th * (1.0 / p->m[s] - 1.0 - sum_phi_m + chiphi[s] - quad);
+                double grad_term = -p->kappa * lap_at(w->rs + s * S, nx, ny, x, y);
+                w->nu[s * S + c] = logs + bulk + grad_term;
+            }
+        }
+    }
+}
+
+/* Stage 3: a^s = -(1 - 1/(2 tau)) grad nu^s + g (Eq. definef; g from Eq. NSEeq). */
+static void stage_forces(const oracle_params* p, work_t* w)
+{
+    int N = p->ncomp, nx = p->nx, ny = p->ny;
+    long S = w->S;
+    double coef = 1.0 - 1.0 / (2.0 * p->tau);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            long c = (long)y * nx + x;
+            for (int s = 0; s < N; ++s) {
+                double gx, gy;
+                grad_at(w->nu + s * S, nx, ny, x, y, &gx, &gy);
+                w->ax[s * S + c] = -coef * gx + p->gx;
+                w->ay[s * S + c] = -coef * gy + p->gy;
+            }
+        }
+    }
+}
+
+/* Stages 4 and 5: BGK collision with forcing, then streaming (Eq. ssLB). */
+static void stage_collide_stream(const oracle_params* p, const double* f, const work_t* w,
+                                 double* fnew)
+{
+    int N = p->ncomp, nx = p->nx, ny = p->ny;
+    long S = w->S;
+    double tau = p->tau;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            long c = (long)y * nx + x;
+            for (int s = 0; s < N; ++s) {
+                double fe[9], F[9];
+                double rs = w->rs[s * S + c];
+                oracle_equilibrium(rs, w->ux[c], w->uy[c], fe);
+                oracle_forcing(rs, w->jx[s * S + c], w->jy[s * S + c], w->ax[s * S + c],
+                               w->ay[s * S + c], F);
+                for (int i = 0; i < 9; ++i) {
+                    double fi = f[(long)(s * 9 + i) * S + c];
+                    double post = fi + (fe[i] - fi) / tau + F[i];
+                    long xx = wrap(x + VX[i], nx), yy = wrap(y + VY[i], ny);
+                    fnew[(long)(s * 9 + i) * S + yy * nx + xx] = post;
+                }
+            }
+        }
+    }
+}
+
+static void compute_fields(const oracle_params* p, const double* f, work_t* w)
+{
+    stage_moments(p, f, w);
+    stage_potentials(p, w);
+    stage_forces(p, w);
+}
+
+/* f(r, 0) = f^e(rho^s(r), u(r)) for every component. */
+int oracle_init(const oracle_params* p, const double* rho, const double* u, double* f)
+{
+    if (check(p)) return -1;
+    int N = p->ncomp;
+    long S = (long)p->nx * p->ny;
+    for (int s = 0; s < N; ++s)
+        for (long c = 0; c < S; ++c) {
+            double fe[9];
+            oracle_equilibrium(rho[s * S + c], u ? u[c] : 0.0, u ? u[S + c] : 0.0, fe);
+            for (int i = 0; i < 9; ++i) f[(long)(s * 9 + i) * S + c] = fe[i];
+        }
+    return 0;
+}
+
+/* Advance f (in place) by nsteps timesteps.  Returns 0, -1 for invalid
+ * parameters, -2 if memory ran out, 1 if a non-finite value appeared. */
+int oracle_run(const oracle_params* p, double* f, long nsteps)
+{
+    if (check(p)) return -1;
+    work_t w;
+    if (work_alloc(p, &w)) { work_free(&w); return -2; }
+    long total = (long)9 * p->ncomp * w.S;
+    double* g = malloc(sizeof(double) * total);
+    if (!g) { work_free(&w); return -2; }
+    double *cur = f, *nxt = g;
+    for (long t = 0; t < nsteps; ++t) {
+        compute_fields(p, cur, &w);
+        stage_collide_stream(p, cur, &w, nxt);
+        double* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (cur != f) memcpy(f, cur, sizeof(double) * total);
+    free(g);
+    work_free(&w);
+    for (long k = 0; k < total; ++k)
+        if (!isfinite(f[k])) return 1;
+    return 0;
+}
+
+/* Intermediate fields of one step from state f: rho^s, u, nu^s, a^s (any may be NULL). */
+int oracle_fields(const oracle_params* p, const double* f, double* rs, double* ux, double* uy,
+                  double* nu, double* ax, double* ay)
+{
+    if (check(p)) return -1;
+    work_t w;
+    if (work_alloc(p, &w)) { work_free(&w); return -2; }
+    compute_fields(p, f, &w);
+    long S = w.S, N = p->ncomp;
+    if (rs) memcpy(rs, w.rs, sizeof(double) * N * S);
+    if (ux) memcpy(ux, w.ux, sizeof(double) * S);
+    if (uy) memcpy(uy, w.uy, sizeof(double) * S);
+    if (nu) memcpy(nu, w.nu, sizeof(double) * N * S);
+    if (ax) memcpy(ax, w.ax, sizeof(double) * N * S);
+    if (ay) memcpy(ay, w.ay, sizeof(double) * N * S);
+    work_free(&w);
+    return 0;
+}
+
+/* Macroscopic output fields of state f (any pointer may be NULL):
+ *   rho (N*S)  rho^s
+ *   U   (2*S)  U = u + a/2, rho a = sum_s rho^s a^s         (Eq. scon)
+ *   mu  (N*S)  mu^s/m^s - kappa lap rho^s                    (Eq. lgf + gradient term)
+ *   P   (3*S)  P_xx, P_xy, P_yy with
+ *              P = (sum_s rho^s mu^s - psi) I + kappa sum_s grad rho^s grad rho^s,
+ *              psi the Eq. lgf density plus sum_s (kappa/2)|grad rho^s|^2. */
+int oracle_moments(const oracle_params* p, const double* f, double* rho_out, double* U,
+                   double* mu, double* P)
+{
+    if (check(p)) return -1;
+    work_t w;
+    if (work_alloc(p, &w)) { work_free(&w); return -2; }
+    compute_fields(p, f, &w);
+    int N = p->ncomp, nx = p->nx, ny = p->ny;
+    long S = w.S;
+    if (rho_out) memcpy(rho_out, w.rs, sizeof(double) * N * S);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            long c = (long)y * nx + x;
+            if (U) {
+                double fx = 0.0, fy = 0.0;
+                for (int s = 0; s < N; ++s) {
+                    fx += w.rs[s * S + c] * w.ax[s * S + c];
+                    fy += w.rs[s * S + c] * w.ay[s * S + c];
+                }
+                U[c] = w.ux[c] + 0.5 * fx / w.rho[c];
+                U[S + c] = w.uy[c] + 0.5 * fy / w.rho[c];
+            }
+            if (mu || P) {
+                double rsl[OR_NMAX], mub[OR_NMAX], muf[OR_NMAX];
+                for (int s = 0; s < N; ++s) rsl[s] = w.rs[s * S + c];
+                oracle_mu_bulk(p, rsl, mub);
+                for (int s = 0; s < N; ++s)
+                    muf[s] = mub[s] - p->kappa * lap_at(w.rs + s * S, nx, ny, x, y);
+                if (mu)
+                    for (int s = 0; s < N; ++s) mu[s * S + c] = muf[s];
+                if (P) {
+                    double psi = oracle_psi(p, rsl), rmu = 0.0, gg = 0.0;
+                    double pxx = 0.0, pxy = 0.0, pyy = 0.0;
+                    for (int s = 0; s < N; ++s) {
+                        double gx, gy;
+                        grad_at(w.rs + s * S, nx, ny, x, y, &gx, &gy);
+                        rmu += rsl[s] * muf[s];
+                        gg += 0.5 * p->kappa * (gx * gx + gy * gy);
+                        pxx += p->kappa * gx * gx;
+                        pxy += p->kappa * gx * gy;
+                        pyy += p->kappa * gy * gy;
+                    }
+                    double iso = rmu - (psi + gg);
+                    P[c] = iso + pxx;
+                    P[S + c] = pxy;
+                    P[2 * S + c] = iso + pyy;
+                }
+            }
+        }
+    work_free(&w);
+    return 0;
+}
+
+/* Global sums of state f: mass^s = sum_r rho^s (N), momentum sum_r rho u (2),
+ * force sum_r sum_s rho^s a^s (2).  Plain sums in site order. */
+int oracle_conservation(const oracle_params* p, const double* f, double* mass, double* mom,
+                        double* force_sum)
+{
+    if (check(p)) return -1;
+    work_t w;
+    if (work_alloc(p, &w)) { work_free(&w); return -2; }
+    compute_fields(p, f, &w);
+    int N = p->ncomp;
+    long S = w.S;
+    for (int s = 0; s < N; ++s) {
+        double acc = 0.0;
+        for (long c = 0; c < S; ++c) acc += w.rs[s * S + c];
+        if (mass) mass[s] = acc;
+    }
+    double mx = 0.0, my = 0.0, fx = 0.0, fy = 0.0;
+    for (long c = 0; c < S; ++c)
+        for (int s = 0; s < N; ++s) {
+            mx += w.jx[s * S + c];
+            my += w.jy[s * S + c];
+            fx += w.rs[s * S + c] * w.ax[s * S + c];
+            fy += w.rs[s * S + c] * w.ay[s * S + c];
+        }
+    if (mom) { mom[0] = mx; mom[1] = my; }
+    if (force_sum) { force_sum[0] = fx; force_sum[1] = fy; }
+    work_free(&w);
+    return 0;
+}

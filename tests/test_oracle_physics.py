@@ -1,0 +1,185 @@
+"""Pins of the oracle against closed forms and the thermodynamics the paper compares to.
+
+* Eq. woche for an ideal mixture (chi = kappa = 0): a concentration mode decays
+  at D k^2 with D = (tau - 1/2) theta.  theta != 1/3 makes the rate depend on
+  the force coefficient 1 - 1/(2 tau) of Eq. definef.
+* Linearised Eq. woche for a binary Flory-Huggins mixture: growth rate
+  -(tau - 1/2) [theta (1 - 2 chi phi (1 - phi)) k^2 + 2 kappa phi (1 - phi) k^4].
+  Both converge at O(k^2) as the lattice is refined.
+* Sec. 4: a flat interface relaxes to the coexisting compositions of the
+  Flory-Huggins free energy (common tangent), with nearly uniform total density.
+* The thermodynamics module itself is pinned by closed-form critical points, the
+  printed critical volume fraction 0.24 of the m = (10, 1) binary, and two
+  independent routes (Newton on the tangent conditions, brute-force hull).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle, thermo
+from paper_0704_3444_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def _mode_rate(nx, theta, tau, chi, kappa, t_span, amp=1e-5, t0=200):
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    d = amp * np.sin(k * x)
+    rho = np.stack([(0.5 + d)[None, :], (0.5 - d)[None, :]])
+    o = Oracle(2, nx, 1, tau, np.array([[0.0, chi], [chi, 0.0]]), theta=theta, kappa=kappa)
+    o.init(rho, np.zeros((2, 1, nx)))
+
+    def amplitude():
+        r = o.moments()["rho"][0, 0]
+        return 2.0 * np.mean((r - r.mean()) * np.sin(k * x))
+
+    o.run(t0)
+    a0 = amplitude()
+    o.run(t_span)
+    return math.log(amplitude() / a0) / t_span, k
+
+
+def test_ideal_mixture_diffusion_rate():
+    theta, tau = 0.5, 0.8
+    D = (tau - 0.5) * theta
+    errs = []
+    for nx in (32, 64):
+        k = 2 * math.pi / nx
+        rate, _ = _mode_rate(nx, theta, tau, 0.0, 0.0, int(3 / (D * k * k)))
+        errs.append(rate / (-D * k * k) - 1.0)
+    assert abs(errs[0]) < 1e-3 and abs(errs[1]) < 3e-4
+    assert 3.0 < errs[0] / errs[1] < 5.0  # O(k^2) convergence
+
+
+def test_ideal_diffusion_sees_force_coefficient():
+    """With the force coefficient 1 instead of 1 - 1/(2 tau) the rate would be
+    tau (theta - 1/3) + (tau - 1/2)/3 instead of (tau - 1/2) theta."""
+    theta, tau, nx = 0.6, 0.7, 64
+    k = 2 * math.pi / nx
+    rate, _ = _mode_rate(nx, theta, tau, 0.0, 0.0, 4000)
+    right = (tau - 0.5) * theta
+    wrong = tau * (theta - 1 / 3) + (tau - 0.5) / 3
+    assert abs(-rate / (k * k) - right) < 0.1 * abs(wrong - right)
+
+
+def test_spinodal_growth_rate():
+    theta, tau, chi, kappa = 0.4, 0.9, 2.6, 0.5
+    w = tau - 0.5
+    errs = []
+    for nx in (32, 64):
+        k = 2 * math.pi / nx
+        pred = -w * (theta * (1 - 2 * chi * 0.25) * k * k + 2 * kappa * 0.25 * k ** 4)
+        rate, _ = _mode_rate(nx, theta, tau, chi, kappa, int(3 / abs(pred)))
+        errs.append(rate / pred - 1.0)
+    assert abs(errs[0]) < 0.06 and abs(errs[1]) < 0.015
+    assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_flat_interface_binary_coexistence():
+    """Binary monomer, chi = 2.2, kappa = 0, 1/tau = 0.9, sinusoid of amplitude 0.1 over
+    the lattice (Sec. 4), 64 sites so that one domain forms.  Bulk compositions within
+    0.015 of the common tangent and total density uniform to 2 %.  The remaining gap
+    (about 0.011 here) is the sharp-interface discretisation: the stationary state keeps
+    a small jump of the exchange potential across the interface, and it shrinks as
+    kappa widens the interface."""
+    chi = np.array([[0.0, 2.2], [2.2, 0.0]])
+    lo, hi = thermo.binodal_binary(2.2)
+    p = inputs.flat_interface([0.5, 0.5], chi=chi, nx=64, ny=1, kappa=0.0, tau=1 / 0.9)
+    o = Oracle.from_problem(p)
+    o.run(40000)
+    m = o.moments()
+    rho = m["rho"].sum(0)
+    phi = m["rho"][0] / rho
+    assert np.sum(np.diff(np.sign(phi[0] - 0.5)) != 0) <= 2  # a single domain
+    assert abs(phi.min() - lo) < 0.015 and abs(phi.max() - hi) < 0.015
+    assert np.ptp(rho) / rho.mean() < 0.02
+    # stationary: the exchange potential is flat across each bulk plateau
+    ex = m["mu"][0] - m["mu"][1]
+    for ext in (phi.min(), phi.max()):
+        plateau = np.abs(phi - ext) < 1e-3
+        assert plateau.sum() >= 3 and np.ptp(ex[plateau]) < 1e-3
+    assert abs(ex[phi == phi.max()][0] - ex[phi == phi.min()][0]) < 1e-2
+
+
+def test_flat_interface_ternary_coexistence():
+    """Ternary monomer with the paper's chi set (chi_AB = 3, chi_AC = 0.5, chi_BC = 0.2,
+    1/tau = 0.9) started on the path from the critical region toward (0.5, 0.5, 0):
+    two phases near the Flory-Huggins tie line through the mean composition."""
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    pb = [0.4, 0.4, 0.2]
+    q1, q2 = thermo.tie_line(chi, np.ones(3), pb)
+    p = inputs.flat_interface(pb, chi=chi, nx=128, ny=1, kappa=0.0, tau=1 / 0.9)
+    o = Oracle.from_problem(p)
+    o.run(30000)
+    m = o.moments()
+    phi = m["rho"] / m["rho"].sum(0)
+    a_rich = phi[:, 0, np.argmax(phi[0, 0])]
+    b_rich = phi[:, 0, np.argmin(phi[0, 0])]
+    hi, lo = (q1, q2) if q1[0] > q2[0] else (q2, q1)
+    assert np.max(np.abs(a_rich - hi)) < 0.05 and np.max(np.abs(b_rich - lo)) < 0.05
+
+
+# ---------------------------------------------------------------- thermodynamics
+
+def test_paper_binary_critical_points():
+    g = json.load(open(GOLDEN))["binary_critical_phiA"]
+    for case in ("monomer", "polymer"):
+        mA, mB = g[case]["m"]
+        phic, chic = thermo.critical_binary(mA, mB)
+        assert round(phic, 2) == g[case]["phiA"]
+        # at the critical point the spinodal touches: chi_spinodal(phi_c) = chi_c, minimal there
+        assert abs(thermo.spinodal_chi_binary(phic, mA, mB) - chic) < 1e-12
+        for d in (1e-3, -1e-3):
+            assert thermo.spinodal_chi_binary(phic + d, mA, mB) > chic
+    # the polymer run of Sec. 4 (chi = 0.94) lies above the critical chi 0.866
+    run = json.load(open(GOLDEN))["binary_polymer_run"]
+    assert thermo.critical_binary(*run["m"])[1] < run["chi"]
+
+
+@pytest.mark.parametrize("chi,m", [(2.2, (1, 1)), (2.8, (1, 1)), (0.94, (10, 1)), (1.3, (10, 1)),
+                                   (1.0, (3, 2))])
+def test_binodal_newton_vs_hull(chi, m):
+    lo, hi = thermo.binodal_binary(chi, *m)
+    hlo, hhi = thermo.hull_binary(chi, *m)
+    assert abs(lo - hlo) < 2e-5 and abs(hi - hhi) < 2e-5
+    if m == (1, 1):
+        assert abs(hi - thermo.symmetric_binary_binodal(chi)) < 1e-12
+        assert abs(lo + hi - 1.0) < 1e-12
+
+
+def test_ternary_tie_line_conditions():
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    m = np.ones(3)
+    pb = np.array([0.4, 0.4, 0.2])
+    q1, q2 = thermo.tie_line(chi, m, pb)
+    np.testing.assert_allclose(thermo.exchange_potentials(q1, chi, m),
+                               thermo.exchange_potentials(q2, chi, m), atol=1e-10)
+    # pb lies on the segment
+    t = np.dot(pb - q2, q1 - q2) / np.dot(q1 - q2, q1 - q2)
+    np.testing.assert_allclose(t * q1 + (1 - t) * q2, pb, atol=1e-10)
+    # brute-force hull facet vertices sit next to the two phases
+    tri, _ = thermo.hull_ternary(chi, m, pb, n=300)
+    for q in (q1, q2):
+        assert np.min(np.linalg.norm(tri - q, axis=1)) < 0.02
+
+
+def test_symmetric_three_phase():
+    """Uniform chi = 3.6 ternary: phases (a, b, b) and permutations with ln(a/b) = chi (a-b);
+    the equimolar mixture sits on a three-phase facet of the hull."""
+    a, b = thermo.symmetric_three_phase(3.6)
+    assert abs(math.log(a / b) - 3.6 * (a - b)) < 1e-12
+    chi = inputs.uniform_chi(3, 3.6)
+    tri, lam = thermo.hull_ternary(chi, np.ones(3), [1 / 3, 1 / 3, 1 / 3], n=300)
+    assert np.all(lam > 0.2)  # phibar deep inside a large facet: three phases
+    for perm in ([a, b, b], [b, a, b], [b, b, a]):
+        assert np.min(np.linalg.norm(tri - np.array(perm), axis=1)) < 0.02
