@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput of the multicomponent lattice Boltzmann timestep on GB300.
+
+One "step" is one timestep of the whole hot path (pull streaming, moments,
+Flory-Huggins potentials with the gradient term, Eq. definef force,
+equilibria, forcing, BGK collision) over the full lattice.  Default workload:
+N = 5 components on a periodic 2048 x 2048 D2Q9 lattice, FP32 storage, random
+symmetric chi in [0.8, 1.5] x critical, tau = 1, kappa = 0.01, mean composition
+1/5 with +-0.01 uniform noise (synthetic, seeded).  Its distributions (2 x 755 MB
+ping-pong) exceed the 129 MB L2, so no flush is needed between steps.
+
+Metric: MLUPS x components = sites * N * steps / seconds / 1e6, whole job.
+Roofline: the fused kernel moves at least 9 loads + 9 stores of f per
+(site, component) per step (72 B in FP32, 36 B in the 16-bit shifted modes).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mclb|reference]
+Under torchrun each rank advances its own copy of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS×components and % of HBM roofline; FP32 vs BF16-shifted vs batched"
+UNIT = "MLUPS×components"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["fused.cuh", "physics.cuh", "lattice.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "k_fused_fp32_n5_2048x2048.md")
+
+
+def workloads():
+    from paper_0704_3444_gb300 import inputs
+    return {
+        "n5_2048x2048": lambda: inputs.multi_uniform(),
+        "ternary_256x256": lambda: inputs.ternary_gauss(),
+        "binary_64x64": lambda: inputs.binary_noise(precision="fp32"),
+        "slab_8192x2048": lambda: inputs.slab(),
+    }
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_0704_3444_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, or None
+    if the summary is missing or was taken from different kernel sources."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(path))["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[4 + k]
+                          and "Not" not in r[4 + k]})
+        pw = [num(r[2]) for r in rows if num(r[2]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            return int(vis.split(",")[local_rank])
+        except (ValueError, IndexError):
+            return local_rank
+    return local_rank
+
+
+def time_steps(torch, sim, steps, warmup, stream):
+    """Device time of `steps` timesteps after `warmup` untimed ones (CUDA events on the
+    stream the library launches on)."""
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    sim.step(steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(stop) / 1e3
+
+
+def run_cpu_baseline(prob, budget_s=15.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded number of
+    timesteps of the same workload."""
+    import oracle
+    from oracle import Oracle
+    o = Oracle.from_problem(prob)
+    t0 = time.perf_counter()
+    o.run(1)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(50, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.run(k)
+    dt = time.perf_counter() - t0
+    v = prob.sites * prob.ncomp * k / dt / 1e6
+    return {"value": v, "unit": UNIT, "cores": oracle.nthreads(), "kind": "oracle",
+            "sample": f"{k} FP64 oracle timesteps of the full {prob.nx}x{prob.ny} N={prob.ncomp} "
+                      f"lattice ({dt:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 oracle, as it stands, on host cores.  Each step is one
+    timestep of a bounded sample of the workload (a periodic band of rows of the same
+    lattice, same parameters), sized so that warm-up plus timed steps take a few minutes."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import Oracle
+    from paper_0704_3444_gb300 import inputs
+    prob = workloads()[args.workload]()
+    # calibrate the per-site cost on a 64-row band
+    rows = min(prob.ny, 64)
+    band = lambda r: inputs.Problem(
+        name=prob.name, ncomp=prob.ncomp, nx=prob.nx, ny=r, tau=prob.tau, chi=prob.chi, m=prob.m,
+        theta=prob.theta, kappa=prob.kappa, force=prob.force,
+        rho=prob.rho[:, :r].copy(), u=prob.u[:, :r].copy())
+    o = Oracle.from_problem(band(rows))
+    t0 = time.perf_counter()
+    o.run(1)
+    per_site = (time.perf_counter() - t0) / (prob.nx * rows)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    rows = int(max(3, min(prob.ny, budget / max(per_site * prob.nx, 1e-9))))
+    sample = band(rows)
+    o = Oracle.from_problem(sample)
+    o.run(args.warmup)
+    t0 = time.perf_counter()
+    o.run(args.steps)
+    dt = time.perf_counter() - t0
+    value = sample.sites * sample.ncomp * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny,
+                                        "ncomp": prob.ncomp},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.nthreads(),
+                         "kind": "oracle",
+                         "sample": f"each step one FP64 oracle timestep of a {prob.nx}x{rows} "
+                                   f"periodic band of the {prob.nx}x{prob.ny} N={prob.ncomp} "
+                                   "workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="mclb", choices=["mclb", "reference"])
+    ap.add_argument("--workload", default="n5_2048x2048")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import paper_0704_3444_gb300 as mclb
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    mclb.load()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    prob = workloads()[args.workload]()
+    N, S = prob.ncomp, prob.sites
+
+    sim = mclb.Simulation.from_problem(prob, precision=args.precision,
+                                       kernel=mclb.KERNEL_FUSED, stream=sptr)
+    launches = sim.launches_per_step
+    bytes_step = sim.bytes_per_step
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index(local_rank)) as clk:
+        start.record(stream)
+        sim.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    elapsed = start.elapsed_time(stop) / 1e3
+    if dist:
+        dist.barrier()
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    status = sim.status()
+    if status != 0:
+        raise SystemExit(f"device status {status} after the timed steps")
+    clocks = clk.summary()
+    value = world * S * N * args.steps / elapsed / 1e6
+    per_launch = elapsed / args.steps
+    peak, peak_src = hbm_peak()
+    achieved = bytes_step / per_launch / 1e9
+    traffic = profiled_traffic() if args.precision == "fp32" and args.workload == "n5_2048x2048" else None
+
+    # end to end through the C ABI with host buffers: H2D of the initial fields from pinned
+    # memory, every step's status word back, and the final rho/U fields to the host
+    e2e = None
+    if rank == 0 or world > 1:
+        rho_h = torch.from_numpy(prob.rho).pin_memory().numpy()
+        u_h = torch.from_numpy(prob.u).pin_memory().numpy()
+        out_rho = torch.empty(prob.rho.shape, dtype=torch.float64).pin_memory().numpy()
+        out_u = torch.empty(prob.u.shape, dtype=torch.float64).pin_memory().numpy()
+        sim2 = mclb.Simulation(N, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
+                               prob.kappa, prob.force, args.precision, mclb.KERNEL_FUSED, sptr)
+        sim2.init_fields(rho_h, u_h)
+        sim2.step(args.warmup)
+        sim2.status()
+        t0 = time.perf_counter()
+        sim2.init_fields(rho_h, u_h)
+        for _ in range(args.steps):
+            sim2.step(1)
+        rc = sim2.lib.mclb_moments(sim2.h, mclb._dp(out_rho), mclb._dp(out_u), None, None)
+        rc2 = sim2.status()
+        t_e2e = time.perf_counter() - t0
+        sim2.close()
+        if rc == 0 and rc2 == 0:
+            io = (prob.rho.nbytes + prob.u.nbytes)
+            e2e = {"value": S * N * args.steps / t_e2e / 1e6 * world, "unit": UNIT,
+                   "h2d_bytes_per_step": io / args.steps,
+                   "d2h_bytes_per_step": 4 + io / args.steps}
+
+    variants = {}
+    if not args.no_variants and rank == 0 and args.precision == "fp32":
+        ks = min(args.steps, 500)
+        for prec in ("bf16", "fp16"):
+            v = mclb.Simulation.from_problem(prob, precision=prec, kernel=mclb.KERNEL_FUSED,
+                                             stream=sptr)
+            t = time_steps(torch, v, ks, args.warmup, stream)
+            ok = v.status() == 0
+            variants[f"{prec}_shifted"] = {
+                "value": S * N * ks / t / 1e6, "steps": ks, "status_ok": ok,
+                "speedup_vs_fp32": (S * N * ks / t / 1e6) / (value / world),
+                "hbm_gbs_algorithmic": v.bytes_per_step / (t / ks) / 1e9}
+            v.close()
+        v = mclb.Simulation.from_problem(prob, precision="fp32", kernel=mclb.KERNEL_STAGED,
+                                         stream=sptr)
+        t = time_steps(torch, v, min(ks, 200), args.warmup, stream)
+        variants["fp32_staged_3_launches"] = {
+            "value": S * N * min(ks, 200) / t / 1e6, "steps": min(ks, 200),
+            "speedup_vs_fp32": (S * N * min(ks, 200) / t / 1e6) / (value / world)}
+        v.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        del sim
+        torch.cuda.synchronize()
+        cpu = run_cpu_baseline(prob)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-storage/f32", "fp16": "f16-storage/f32"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "ncomp": N,
+                   "precision": args.precision, "schedule": "fused single pass",
+                   "l2": "distributions (2 x %.0f MB) exceed the 129 MB L2; no flush" %
+                         (bytes_step / 2 / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "note": f"k_fused: 72*N B per site (9 loads + 9 stores of f in FP32) per "
+                             f"launch / CUDA-event time per launch; peak of {peak_src} copy bandwidth"},
+        "mlups": world * S * args.steps / elapsed / 1e6,
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "variants": variants,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

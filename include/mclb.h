@@ -1,0 +1,200 @@
+/*
+ * mclb.h -- C ABI of the GB300 (sm_103a) multicomponent lattice Boltzmann library.
+ *
+ * The library advances the symmetric free-energy multicomponent lattice
+ * Boltzmann method of Li & Wagner (arXiv:0704.3444) on a periodic D2Q9 lattice:
+ * one lattice Boltzmann equation per component with BGK relaxation towards an
+ * equilibrium built on the shared barycentric velocity, plus the forcing term
+ *     rho^s a^s = -(1 - 1/(2 tau)) rho^s grad( mu^s - (1/3) ln rho^s )   (Eq. definef)
+ * with mu^s the Flory-Huggins chemical potential of Eq. lgf (plus a gradient
+ * term kappa), and streaming (Eq. ssLB).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: MCLB_OK (0) on success, a negative MCLB_E* code on failure;
+ *     mclb_last_error() then returns a message (thread-local, valid until the
+ *     next call on the same thread).
+ *   - Host arrays are owned by the caller; the library copies in and out and keeps
+ *     no pointer to them after the call returns.  Device memory of a handle is
+ *     owned by the library and released by mclb_destroy / mclb_batch_destroy.
+ *   - Field arrays are FP64, row-major [component][y][x] with x fastest;
+ *     velocity-like arrays are [2][y][x] (x component first).  This holds in every
+ *     storage precision.
+ *   - D2Q9 velocity order: v_0 = (0,0); v_1..4 = (1,0), (0,1), (-1,0), (0,-1);
+ *     v_5..8 = (1,1), (-1,1), (-1,-1), (1,-1).  Weights 4/9, 1/9, 1/36.
+ *   - All device work of a handle is ordered on the stream given at creation
+ *     (NULL: the legacy default stream).  Calls that return host data
+ *     synchronise that stream.  Handles are not thread-safe.
+ */
+#ifndef MCLB_H
+#define MCLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCLB_NMAX 8 /* largest number of components */
+
+enum {
+    MCLB_OK = 0,
+    MCLB_EINVAL = -1,     /* invalid argument or parameter                          */
+    MCLB_ENOMEM = -2,     /* device or host allocation failed                       */
+    MCLB_ECUDA = -3,      /* a CUDA runtime call failed (message has the CUDA error) */
+    MCLB_ENONFINITE = -4, /* a NaN/Inf or a non-positive total density appeared     */
+    MCLB_ETIMEOUT = -5,   /* a bounded device wait ran out                          */
+    MCLB_EHANDLE = -6     /* NULL, destroyed or foreign handle                      */
+};
+
+/* Storage precision of the distributions.  Arithmetic is FP64 in MCLB_FP64 and
+ * FP32 otherwise.  The *_SHIFTED modes store f - w_i rhobar^s (rhobar^s the mean
+ * density of component s at initialisation) in 16 bits. */
+typedef enum {
+    MCLB_FP64 = 0,
+    MCLB_FP32 = 1,
+    MCLB_BF16_SHIFTED = 2,
+    MCLB_FP16_SHIFTED = 3
+} mclb_precision;
+
+/* Which kernel schedule performs a timestep. */
+typedef enum {
+    MCLB_KERNEL_AUTO = 0,   /* the fused single-pass kernel                         */
+    MCLB_KERNEL_FUSED = 1,  /* one launch per step: stream, moments, potentials,
+                               force, collision in one pass over the distributions  */
+    MCLB_KERNEL_STAGED = 2  /* three launches per step through density and
+                               potential fields in device scratch memory            */
+} mclb_kernel;
+
+/* Problem statement (Sec. 3 and Sec. 4 of the paper).
+ *   ncomp      N, number of components, 1..MCLB_NMAX
+ *   nx, ny     periodic lattice size, >= 1 each
+ *   tau        one relaxation time for every component (Eq. ssLB), > 1/2
+ *   chi        N*N Flory-Huggins interaction matrix (Eq. lgf), row-major, must be
+ *              symmetric and finite; the paper sets the diagonal to zero
+ *   m          N polymerisations m^s (Eq. lgf), > 0; NULL means all 1
+ *   theta      Flory-Huggins temperature of Eq. lgf; <= 0 selects 1/3
+ *   kappa      gradient coefficient: the free energy gains sum_s (kappa/2)|grad rho^s|^2,
+ *              so mu^s gains -kappa lap rho^s (the paper names kappa and sets it to 0)
+ *   force      body acceleration g (Eq. NSEeq), added to every a^s
+ *   precision  mclb_precision
+ *   kernel     mclb_kernel
+ *   stream     cudaStream_t to order all work on, or NULL */
+typedef struct {
+    int ncomp;
+    int nx, ny;
+    double tau;
+    const double* chi;
+    const double* m;
+    double theta;
+    double kappa;
+    double force[2];
+    int precision;
+    int kernel;
+    void* stream;
+} mclb_params;
+
+typedef struct mclb_handle_s* mclb_handle;
+
+/* Validate params and allocate the device state of one simulation.  The
+ * distributions start at zero: call mclb_init_fields or mclb_set_state next.
+ * Errors: EINVAL (any parameter out of range, asymmetric or non-finite chi),
+ * ENOMEM, ECUDA.  *out is set to NULL on failure. */
+int mclb_create(const mclb_params* params, mclb_handle* out);
+
+/* Set f^s_i(r, 0) to the equilibrium of the given fields (Sec. 3 equilibrium
+ * moments with the barycentric u).  rho: N*ny*nx component densities rho^s, each
+ * > 0 in total per site; u: 2*ny*nx barycentric velocity or NULL for rest.
+ * Host pointers; the copy is synchronous.  Resets the step counter and, in the
+ * shifted modes, the shifts.  Errors: EHANDLE, EINVAL (NULL rho, non-finite
+ * value, non-positive total density), ECUDA. */
+int mclb_init_fields(mclb_handle h, const double* rho, const double* u);
+
+/* As mclb_init_fields, but rho and u are device pointers (same layouts) read in
+ * stream order; the call does not synchronise and does not validate the values. */
+int mclb_init_fields_device(mclb_handle h, const double* rho, const double* u);
+
+/* Enqueue nsteps timesteps (Eq. ssLB with the Eq. definef force) on the handle's
+ * stream and return without waiting for them.  nsteps >= 0.  The return value
+ * reports the device status word of earlier work that has already completed
+ * (ENONFINITE once a non-finite value or a non-positive total density was seen);
+ * mclb_status synchronises and reports everything enqueued so far. */
+int mclb_step(mclb_handle h, long nsteps);
+
+/* Synchronise the stream and return the device status: OK, ENONFINITE or ETIMEOUT. */
+int mclb_status(mclb_handle h);
+
+/* Macroscopic fields of the current state (any pointer may be NULL).  Host
+ * pointers, synchronises.
+ *   rho (N*ny*nx)  component densities rho^s = sum_i f^s_i               (Sec. 3)
+ *   U   (2*ny*nx)  fluid velocity U = u + a/2 with rho a = sum_s rho^s a^s (Eq. scon)
+ *   mu  (N*ny*nx)  chemical potential per unit mass mu^s/m^s, gradient term included
+ *   P   (3*ny*nx)  pressure tensor P_xx, P_xy, P_yy:
+ *                  (sum_s rho^s mu^s/m^s - psi) I + kappa sum_s grad rho^s grad rho^s,
+ *                  psi the Eq. lgf density plus the gradient energy (Eq. ppp, diagnostic) */
+int mclb_moments(mclb_handle h, double* rho, double* U, double* mu, double* P);
+
+/* As mclb_moments into device pointers, in stream order, without synchronising. */
+int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, double* P);
+
+/* FP64 global sums of the current state (any pointer may be NULL), synchronises:
+ *   mass (N)       sum over sites of rho^s                (kept by Eq. ff1)
+ *   mom (2)        sum over sites of rho u                (Sec. 3 moments)
+ *   force_sum (2)  sum over sites of sum_s rho^s a^s      (the next step adds it to mom) */
+int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_sum);
+
+/* Mean compositions phi^s = rho^s / rho of the nphase bulk phases of the current
+ * state (FP64, on the device): sites whose composition gradient is below a
+ * threshold are clustered into nphase groups (k-means started from the sites of
+ * extreme composition); phi receives nphase*N values, phases ordered by
+ * decreasing phi^0.  nphase in 1..MCLB_NMAX.  Synchronises.  Sec. 4 compares
+ * these coexisting compositions with the Flory-Huggins binodal. */
+int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi);
+
+/* Copy the distributions in or out as FP64 pre-collision values f^s_i(r, t), layout
+ * [s][i][y][x] (count must equal N*9*ny*nx).  Host pointers, synchronous.  Getting
+ * and setting a state is exact in FP64 and FP32; in the shifted modes setting
+ * re-derives the shifts from the state.  Errors: EHANDLE, EINVAL, ECUDA. */
+int mclb_get_state(mclb_handle h, double* f, size_t count);
+int mclb_set_state(mclb_handle h, const double* f, size_t count);
+
+/* Timesteps taken since the last init / set_state. */
+long mclb_step_count(mclb_handle h);
+
+/* HBM bytes one timestep must move at least: 2 * 9 * N * ny * nx * storage size
+ * (every distribution read once and written once). */
+double mclb_bytes_per_step(mclb_handle h);
+
+/* Kernel launches one timestep issues (1 for the fused schedule, 3 for the staged). */
+int mclb_launches_per_step(mclb_handle h);
+
+/* Release everything the handle owns.  NULL is accepted.  Synchronises. */
+int mclb_destroy(mclb_handle h);
+
+/* Message describing the most recent failure on this thread ("" if none). */
+const char* mclb_last_error(void);
+
+/* ----------------------------------------------------------------------------
+ * Batched simulations: count independent problems (each its own N, grid, chi, tau,
+ * ...) advanced together, one launch per timestep for the whole batch, captured in
+ * a CUDA graph.  precision and stream are taken from params[0]; kernel is ignored.
+ * Instances share no data.  Errors as for the single-simulation calls, and
+ * EINVAL for an index outside 0..count-1.
+ * ------------------------------------------------------------------------- */
+typedef struct mclb_batch_s* mclb_batch;
+
+int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out);
+int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const double* u);
+int mclb_batch_step(mclb_batch b, long nsteps);
+int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P);
+int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count);
+/* per_instance (count ints, may be NULL) receives each instance's status; the
+ * return value is the first non-OK status or OK.  Synchronises. */
+int mclb_batch_status(mclb_batch b, int* per_instance);
+double mclb_batch_bytes_per_step(mclb_batch b);
+int mclb_batch_destroy(mclb_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCLB_H */

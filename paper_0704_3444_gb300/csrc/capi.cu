@@ -1,0 +1,775 @@
+// capi.cu -- the C ABI declared in include/mclb.h: handle lifetime, validation,
+// device buffers, TMA descriptors, CUDA-graph replay of timestep chunks and
+// status reporting.  All arithmetic of the method runs in the kernels of the
+// prec_*.cu units; this file only orchestrates.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mclb.h"
+#include "mclb_internal.h"
+
+using namespace mclb;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(MCLB_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                               \
+    } while (0)
+
+constexpr uint32_t MAGIC = 0x4d434c42u;  // "MCLB"
+constexpr uint32_t DEAD = 0xdeadbeefu;
+constexpr int GRAPH_STEPS = 32;          // timesteps per captured graph (even)
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+const KernelTable& table_for(int precision)
+{
+    switch (precision) {
+        case MCLB_FP64: return table_fp64();
+        case MCLB_BF16_SHIFTED: return table_bf16();
+        case MCLB_FP16_SHIFTED: return table_fp16();
+        default: return table_fp32();
+    }
+}
+
+int validate(const mclb_params* p)
+{
+    if (!p) return fail(MCLB_EINVAL, "params is NULL");
+    if (p->ncomp < 1 || p->ncomp > MCLB_NMAX)
+        return fail(MCLB_EINVAL, "ncomp=%d outside 1..%d", p->ncomp, MCLB_NMAX);
+    if (p->nx < 1 || p->ny < 1) return fail(MCLB_EINVAL, "grid %dx%d invalid", p->nx, p->ny);
+    if ((long long)p->nx * p->ny > (1LL << 31))
+        return fail(MCLB_EINVAL, "grid %dx%d exceeds 2^31 sites", p->nx, p->ny);
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau))
+        return fail(MCLB_EINVAL, "tau=%g must be finite and > 1/2", p->tau);
+    if (!p->chi) return fail(MCLB_EINVAL, "chi is NULL");
+    const int N = p->ncomp;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            const double v = p->chi[a * N + b];
+            if (!std::isfinite(v)) return fail(MCLB_EINVAL, "chi[%d][%d] not finite", a, b);
+            if (v != p->chi[b * N + a])
+                return fail(MCLB_EINVAL, "chi not symmetric at (%d,%d)", a, b);
+        }
+    if (p->m)
+        for (int a = 0; a < N; ++a)
+            if (!(p->m[a] > 0.0) || !std::isfinite(p->m[a]))
+                return fail(MCLB_EINVAL, "m[%d]=%g must be finite and > 0", a, p->m[a]);
+    if (!std::isfinite(p->theta)) return fail(MCLB_EINVAL, "theta not finite");
+    if (!std::isfinite(p->kappa) || p->kappa < 0.0)
+        return fail(MCLB_EINVAL, "kappa=%g must be finite and >= 0", p->kappa);
+    if (!std::isfinite(p->force[0]) || !std::isfinite(p->force[1]))
+        return fail(MCLB_EINVAL, "force not finite");
+    if (p->precision < MCLB_FP64 || p->precision > MCLB_FP16_SHIFTED)
+        return fail(MCLB_EINVAL, "precision=%d unknown", p->precision);
+    if (p->kernel < MCLB_KERNEL_AUTO || p->kernel > MCLB_KERNEL_STAGED)
+        return fail(MCLB_EINVAL, "kernel=%d unknown", p->kernel);
+    return MCLB_OK;
+}
+
+void fill_problem(const mclb_params* p, int hx, Problem& P)
+{
+    memset(&P, 0, sizeof(P));
+    P.N = p->ncomp;
+    P.nx = p->nx;
+    P.ny = p->ny;
+    P.S = (long long)p->nx * p->ny;
+    P.hx = hx;
+    P.pitch = 2LL * hx + (long long)((p->nx + ROW_ALIGN - 1) / ROW_ALIGN) * ROW_ALIGN;
+    P.plane = P.pitch * p->ny;
+    P.tau = p->tau;
+    P.theta = p->theta > 0.0 ? p->theta : 1.0 / 3.0;
+    P.kappa = p->kappa;
+    P.gx = p->force[0];
+    P.gy = p->force[1];
+    for (int a = 0; a < P.N; ++a) {
+        for (int b = 0; b < P.N; ++b) P.chi[a * P.N + b] = p->chi[a * P.N + b];
+        P.m[a] = p->m ? p->m[a] : 1.0;
+    }
+}
+
+}  // namespace
+
+struct mclb_handle_s {
+    uint32_t magic;
+    int precision, kernel;
+    const KernelTable* tab;
+    Problem P;
+    Scratch sc;
+    FusedPlan plan;
+    bool fused;
+    cudaStream_t stream;
+    bool own_stream;
+    void* f[2];
+    CUtensorMap tmap[2];
+    int cur;                      // buffer holding the current state
+    long steps;
+    size_t fbytes;                // bytes of one distribution buffer
+    unsigned int* status_host;    // pinned mirror of the device status word
+    cudaEvent_t status_event;
+    bool status_pending;
+    cudaGraphExec_t graph[2];     // GRAPH_STEPS steps starting from buffer 0 / 1
+    bool graph_tried[2];
+    double* dtmp;                 // device FP64 staging for host copies
+    size_t dtmp_cap;
+};
+
+namespace {
+
+int check_handle(mclb_handle h)
+{
+    if (!h) return fail(MCLB_EHANDLE, "handle is NULL");
+    if (h->magic != MAGIC) return fail(MCLB_EHANDLE, "handle destroyed or not a handle");
+    return MCLB_OK;
+}
+
+int status_code(unsigned int s)
+{
+    if (s & STATUS_TIMEOUT) return fail(MCLB_ETIMEOUT, "a bounded device wait gave up");
+    if (s & STATUS_NONFINITE)
+        return fail(MCLB_ENONFINITE, "non-finite value or non-positive total density");
+    return MCLB_OK;
+}
+
+int ensure_dtmp(mclb_handle h, size_t doubles)
+{
+    if (h->dtmp_cap >= doubles) return MCLB_OK;
+    if (h->dtmp) cudaFree(h->dtmp);
+    h->dtmp = nullptr;
+    h->dtmp_cap = 0;
+    if (cudaMalloc(&h->dtmp, doubles * sizeof(double)) != cudaSuccess)
+        return fail(MCLB_ENOMEM, "device staging of %zu bytes failed", doubles * sizeof(double));
+    h->dtmp_cap = doubles;
+    return MCLB_OK;
+}
+
+int make_tmap(mclb_handle h, int b)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const Problem& P = h->P;
+    const size_t sz = h->tab->storage_bytes;
+    cuuint64_t dims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, (cuuint64_t)(P.N * Q)};
+    cuuint64_t strides[2] = {(cuuint64_t)(P.pitch * sz), (cuuint64_t)(P.plane * sz)};
+    cuuint32_t box[3] = {(cuuint32_t)(h->plan.W + 2 * P.hx), 1u, (cuuint32_t)(P.N * Q)};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = fn(&h->tmap[b], h->tab->tma_type, 3, h->f[b], dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MCLB_OK;
+}
+
+cudaError_t launch_one_step(mclb_handle h, int from)
+{
+    const Problem& P = h->P;
+    if (h->fused)
+        return h->tab->step_fused(P, h->sc, h->plan, &h->tmap[from], h->f[from ^ 1], h->stream);
+    return h->tab->step_staged(P, h->sc, h->f[from], h->f[from ^ 1], h->stream);
+}
+
+void try_capture(mclb_handle h, int from)
+{
+    h->graph_tried[from] = true;
+    h->graph[from] = nullptr;
+    if (h->stream == nullptr) return;
+    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int b = from;
+    bool ok = true;
+    for (int k = 0; k < GRAPH_STEPS && ok; ++k) {
+        ok = launch_one_step(h, b) == cudaSuccess;
+        b ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (ok && e == cudaSuccess && g) {
+        cudaGraphExec_t ex = nullptr;
+        if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) h->graph[from] = ex;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+}
+
+int enqueue_status_copy(mclb_handle h)
+{
+    CK(cudaMemcpyAsync(h->status_host, h->sc.status, sizeof(unsigned int),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->status_event, h->stream));
+    h->status_pending = true;
+    return MCLB_OK;
+}
+
+int sync_status(mclb_handle h)
+{
+    int rc = enqueue_status_copy(h);
+    if (rc) return rc;
+    CK(cudaEventSynchronize(h->status_event));
+    h->status_pending = false;
+    return status_code(*h->status_host);
+}
+
+int set_shift_from_means(mclb_handle h, const double* rhobar)
+{
+    for (int s = 0; s < h->P.N; ++s) {
+        const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        for (int i = 0; i < Q; ++i) h->P.shift[s * Q + i] = h->tab->shifted ? w[i] * rhobar[s] : 0.0;
+    }
+    // kernel parameters changed: captured graphs are stale
+    for (int b = 0; b < 2; ++b) {
+        if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
+        h->graph[b] = nullptr;
+        h->graph_tried[b] = false;
+    }
+    return MCLB_OK;
+}
+
+__global__ void k_plane_sums(const double* __restrict__ a, long long n, int planes,
+                             double* __restrict__ out)
+{
+    // one block per plane, fixed order: deterministic
+    __shared__ double red[256];
+    const int pl = blockIdx.x;
+    double acc = 0.0;
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) acc += a[pl * n + k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[pl] = red[0];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mclb_last_error(void) { return g_err.c_str(); }
+
+int mclb_create(const mclb_params* params, mclb_handle* out)
+{
+    if (!out) return fail(MCLB_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(params);
+    if (rc) return rc;
+    mclb_handle h = new (std::nothrow) mclb_handle_s();
+    if (!h) return fail(MCLB_ENOMEM, "host allocation failed");
+    memset(h, 0, sizeof(*h));
+    h->precision = params->precision;
+    h->kernel = params->kernel;
+    h->tab = &table_for(params->precision);
+    fill_problem(params, h->tab->hx, h->P);
+    const Problem& P = h->P;
+    auto bail = [&](int code) {
+        h->magic = MAGIC;
+        mclb_destroy(h);
+        return code;
+    };
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(MCLB_ECUDA, "no usable CUDA device"));
+    }
+    if (params->stream) {
+        h->stream = (cudaStream_t)params->stream;
+    } else {
+        if (cudaStreamCreate(&h->stream) != cudaSuccess)
+            return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
+        h->own_stream = true;
+    }
+    h->fbytes = (size_t)P.plane * P.N * Q * h->tab->storage_bytes;
+    const size_t cbytes = (h->precision == MCLB_FP64) ? sizeof(double) : sizeof(float);
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMalloc(&h->f[b], h->fbytes) != cudaSuccess)
+            return bail(fail(MCLB_ENOMEM, "distribution buffer of %zu bytes", h->fbytes));
+        if (cudaMemset(h->f[b], 0, h->fbytes) != cudaSuccess)
+            return bail(fail(MCLB_ECUDA, "cudaMemset failed"));
+    }
+    if (cudaMalloc(&h->sc.rho_s, (size_t)P.N * P.S * cbytes) != cudaSuccess ||
+        cudaMalloc(&h->sc.nu, (size_t)P.N * P.S * cbytes) != cudaSuccess)
+        return bail(fail(MCLB_ENOMEM, "scratch fields"));
+    h->sc.partial_cap = (size_t)REDUCE_BLOCKS * (NMAX + 4) + 64;
+    if (cudaMalloc(&h->sc.partial, h->sc.partial_cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->sc.status, sizeof(unsigned int)) != cudaSuccess)
+        return bail(fail(MCLB_ENOMEM, "reduction scratch"));
+    if (cudaMemset(h->sc.status, 0, sizeof(unsigned int)) != cudaSuccess)
+        return bail(fail(MCLB_ECUDA, "cudaMemset failed"));
+    if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess)
+        return bail(fail(MCLB_ENOMEM, "pinned status word"));
+    *h->status_host = 0;
+    if (cudaEventCreateWithFlags(&h->status_event, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(MCLB_ECUDA, "cudaEventCreate failed"));
+    h->fused = false;
+    if (h->kernel != MCLB_KERNEL_STAGED) {
+        h->plan = h->tab->plan_fused(P, sms);
+        if (h->plan.ok) {
+            h->magic = MAGIC;
+            if (make_tmap(h, 0) == MCLB_OK && make_tmap(h, 1) == MCLB_OK) h->fused = true;
+            h->magic = 0;
+        }
+        if (!h->fused && h->kernel == MCLB_KERNEL_FUSED)
+            return bail(fail(MCLB_EINVAL, "fused kernel unavailable for this problem"));
+    }
+    cudaGetLastError();
+    h->magic = MAGIC;
+    *out = h;
+    return MCLB_OK;
+}
+
+int mclb_destroy(mclb_handle h)
+{
+    if (!h) return MCLB_OK;
+    if (h->magic != MAGIC) return fail(MCLB_EHANDLE, "handle destroyed or not a handle");
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b) {
+        if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
+        if (h->f[b]) cudaFree(h->f[b]);
+    }
+    if (h->sc.rho_s) cudaFree(h->sc.rho_s);
+    if (h->sc.nu) cudaFree(h->sc.nu);
+    if (h->sc.partial) cudaFree(h->sc.partial);
+    if (h->sc.status) cudaFree(h->sc.status);
+    if (h->dtmp) cudaFree(h->dtmp);
+    if (h->status_host) cudaFreeHost(h->status_host);
+    if (h->status_event) cudaEventDestroy(h->status_event);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    h->magic = DEAD;
+    delete h;
+    return MCLB_OK;
+}
+
+static int init_common(mclb_handle h, const double* rho_d, const double* u_d, const double* rhobar)
+{
+    set_shift_from_means(h, rhobar);
+    CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
+    CK(h->tab->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
+    h->cur = 0;
+    h->steps = 0;
+    return MCLB_OK;
+}
+
+int mclb_init_fields(mclb_handle h, const double* rho, const double* u)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!rho) return fail(MCLB_EINVAL, "rho is NULL");
+    const Problem& P = h->P;
+    double rhobar[NMAX] = {0};
+    for (long long c = 0; c < P.S; ++c) {
+        double tot = 0.0;
+        for (int s = 0; s < P.N; ++s) {
+            const double v = rho[s * P.S + c];
+            if (!std::isfinite(v)) return fail(MCLB_EINVAL, "rho not finite at site %lld", c);
+            tot += v;
+            rhobar[s] += v;
+        }
+        if (!(tot > 0.0)) return fail(MCLB_EINVAL, "total density <= 0 at site %lld", c);
+        if (u && (!std::isfinite(u[c]) || !std::isfinite(u[P.S + c])))
+            return fail(MCLB_EINVAL, "u not finite at site %lld", c);
+    }
+    for (int s = 0; s < P.N; ++s) rhobar[s] /= (double)P.S;
+    rc = ensure_dtmp(h, (size_t)(P.N + 2) * P.S);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->dtmp, rho, sizeof(double) * P.N * P.S, cudaMemcpyHostToDevice,
+                       h->stream));
+    if (u)
+        CK(cudaMemcpyAsync(h->dtmp + P.N * P.S, u, sizeof(double) * 2 * P.S,
+                           cudaMemcpyHostToDevice, h->stream));
+    rc = init_common(h, h->dtmp, u ? h->dtmp + P.N * P.S : nullptr, rhobar);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
+    return MCLB_OK;
+}
+
+int mclb_init_fields_device(mclb_handle h, const double* rho, const double* u)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!rho) return fail(MCLB_EINVAL, "rho is NULL");
+    const Problem& P = h->P;
+    double rhobar[NMAX] = {0};
+    if (h->tab->shifted) {
+        // the shifts need the mean densities on the host: one small synchronous copy
+        rc = ensure_dtmp(h, NMAX);
+        if (rc) return rc;
+        k_plane_sums<<<P.N, 256, 0, h->stream>>>(rho, P.S, P.N, h->dtmp);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(rhobar, h->dtmp, sizeof(double) * P.N, cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int s = 0; s < P.N; ++s) rhobar[s] /= (double)P.S;
+    }
+    return init_common(h, rho, u, rhobar);
+}
+
+int mclb_step(mclb_handle h, long nsteps)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(MCLB_EINVAL, "nsteps=%ld < 0", nsteps);
+    // status of work that has already finished (non-blocking)
+    int prev = MCLB_OK;
+    if (h->status_pending && cudaEventQuery(h->status_event) == cudaSuccess) {
+        h->status_pending = false;
+        prev = status_code(*h->status_host);
+    }
+    cudaGetLastError();
+    long left = nsteps;
+    while (left >= GRAPH_STEPS) {
+        if (!h->graph_tried[h->cur]) try_capture(h, h->cur);
+        if (!h->graph[h->cur]) break;
+        CK(cudaGraphLaunch(h->graph[h->cur], h->stream));
+        left -= GRAPH_STEPS;
+    }
+    for (; left > 0; --left) {
+        CK(launch_one_step(h, h->cur));
+        h->cur ^= 1;
+    }
+    h->steps += nsteps;
+    if (nsteps > 0) {
+        rc = enqueue_status_copy(h);
+        if (rc) return rc;
+    }
+    return prev;
+}
+
+int mclb_status(mclb_handle h)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    return sync_status(h);
+}
+
+long mclb_step_count(mclb_handle h) { return check_handle(h) ? -1 : h->steps; }
+
+double mclb_bytes_per_step(mclb_handle h)
+{
+    if (check_handle(h)) return -1.0;
+    return 2.0 * Q * h->P.N * (double)h->P.S * (double)h->tab->storage_bytes;
+}
+
+int mclb_launches_per_step(mclb_handle h)
+{
+    if (check_handle(h)) return -1;
+    return h->fused ? 1 : 3;
+}
+
+int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, double* P)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (!rho && !U && !mu && !P) return MCLB_OK;
+    CK(h->tab->moments(h->P, h->sc, h->f[h->cur], rho, U, mu, P, h->stream));
+    return MCLB_OK;
+}
+
+int mclb_moments(mclb_handle h, double* rho, double* U, double* mu, double* P)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const Problem& Pb = h->P;
+    const long long S = Pb.S;
+    rc = ensure_dtmp(h, (size_t)(2 * Pb.N + 5) * S);
+    if (rc) return rc;
+    double* d_rho = rho ? h->dtmp : nullptr;
+    double* d_U = U ? h->dtmp + Pb.N * S : nullptr;
+    double* d_mu = mu ? h->dtmp + (Pb.N + 2) * S : nullptr;
+    double* d_P = P ? h->dtmp + (2 * Pb.N + 2) * S : nullptr;
+    rc = mclb_moments_device(h, d_rho, d_U, d_mu, d_P);
+    if (rc) return rc;
+    if (rho) CK(cudaMemcpyAsync(rho, d_rho, sizeof(double) * Pb.N * S, cudaMemcpyDeviceToHost, h->stream));
+    if (U) CK(cudaMemcpyAsync(U, d_U, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost, h->stream));
+    if (mu) CK(cudaMemcpyAsync(mu, d_mu, sizeof(double) * Pb.N * S, cudaMemcpyDeviceToHost, h->stream));
+    if (P) CK(cudaMemcpyAsync(P, d_P, sizeof(double) * 3 * S, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MCLB_OK;
+}
+
+int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_sum)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const int N = h->P.N;
+    rc = ensure_dtmp(h, NMAX + 4);
+    if (rc) return rc;
+    CK(h->tab->conservation(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    double out[NMAX + 4];
+    CK(cudaMemcpyAsync(out, h->dtmp, sizeof(double) * (N + 4), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (mass) memcpy(mass, out, sizeof(double) * N);
+    if (mom) memcpy(mom, out + N, sizeof(double) * 2);
+    if (force_sum) memcpy(force_sum, out + N + 2, sizeof(double) * 2);
+    return MCLB_OK;
+}
+
+int mclb_get_state(mclb_handle h, double* f, size_t count)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const size_t want = (size_t)h->P.N * Q * h->P.S;
+    if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
+    rc = ensure_dtmp(h, want);
+    if (rc) return rc;
+    CK(h->tab->get_state(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    CK(cudaMemcpyAsync(f, h->dtmp, sizeof(double) * want, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MCLB_OK;
+}
+
+int mclb_set_state(mclb_handle h, const double* f, size_t count)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const Problem& P = h->P;
+    const size_t want = (size_t)P.N * Q * P.S;
+    if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
+    double rhobar[NMAX] = {0};
+    for (int s = 0; s < P.N; ++s) {
+        double acc = 0.0;
+        for (int i = 0; i < Q; ++i)
+            for (long long c = 0; c < P.S; ++c) {
+                const double v = f[((size_t)s * Q + i) * P.S + c];
+                if (!std::isfinite(v)) return fail(MCLB_EINVAL, "state not finite");
+                acc += v;
+            }
+        rhobar[s] = acc / (double)P.S;
+    }
+    set_shift_from_means(h, rhobar);
+    rc = ensure_dtmp(h, want);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->dtmp, f, sizeof(double) * want, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
+    CK(h->tab->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    h->steps = 0;
+    return MCLB_OK;
+}
+
+int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    const Problem& P = h->P;
+    if (nphase < 1 || nphase > P.N || !phi)
+        return fail(MCLB_EINVAL, "nphase=%d must be in 1..N=%d (phi non-NULL)", nphase, P.N);
+    const long long S = P.S;
+    rc = ensure_dtmp(h, (size_t)(P.N + 1) * S);
+    if (rc) return rc;
+    double* d_phi = h->dtmp;
+    double* d_bulk = h->dtmp + P.N * S;
+    CK(h->tab->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
+    std::vector<double> hphi((size_t)P.N * S), hbulk(S);
+    CK(cudaMemcpyAsync(hphi.data(), d_phi, sizeof(double) * P.N * S, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaMemcpyAsync(hbulk.data(), d_bulk, sizeof(double) * S, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    // k-means over the bulk sites; phase c is seeded at the bulk site richest in component c
+    std::vector<double> cen((size_t)nphase * P.N);
+    long long nbulk = 0;
+    for (int c = 0; c < nphase; ++c) {
+        double best = -1.0;
+        long long arg = -1;
+        for (long long t = 0; t < S; ++t)
+            if (hbulk[t] > 0.5 && hphi[(size_t)c * S + t] > best) {
+                best = hphi[(size_t)c * S + t];
+                arg = t;
+            }
+        if (arg < 0) return fail(MCLB_EINVAL, "no bulk sites (composition gradients all >= 1e-3)");
+        for (int s = 0; s < P.N; ++s) cen[(size_t)c * P.N + s] = hphi[(size_t)s * S + arg];
+    }
+    std::vector<int> lab(S, -1);
+    for (int it = 0; it < 100; ++it) {
+        bool changed = false;
+        std::vector<double> acc((size_t)nphase * P.N, 0.0);
+        std::vector<long long> cnt(nphase, 0);
+        nbulk = 0;
+        for (long long t = 0; t < S; ++t) {
+            if (hbulk[t] < 0.5) continue;
+            ++nbulk;
+            int best = 0;
+            double bd = 1e300;
+            for (int c = 0; c < nphase; ++c) {
+                double d = 0.0;
+                for (int s = 0; s < P.N; ++s) {
+                    const double e = hphi[(size_t)s * S + t] - cen[(size_t)c * P.N + s];
+                    d += e * e;
+                }
+                if (d < bd) { bd = d; best = c; }
+            }
+            if (lab[t] != best) changed = true;
+            lab[t] = best;
+            ++cnt[best];
+            for (int s = 0; s < P.N; ++s) acc[(size_t)best * P.N + s] += hphi[(size_t)s * S + t];
+        }
+        for (int c = 0; c < nphase; ++c)
+            if (cnt[c] > 0)
+                for (int s = 0; s < P.N; ++s) cen[(size_t)c * P.N + s] = acc[(size_t)c * P.N + s] / cnt[c];
+        if (!changed) break;
+    }
+    memcpy(phi, cen.data(), sizeof(double) * nphase * P.N);
+    return MCLB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct mclb_batch_s {
+    uint32_t magic;
+    std::vector<mclb_handle> items;
+    cudaStream_t stream;
+    bool own_stream;
+};
+
+extern "C" {
+
+int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
+{
+    if (!out) return fail(MCLB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params || count < 1) return fail(MCLB_EINVAL, "count=%d must be >= 1", count);
+    mclb_batch b = new (std::nothrow) mclb_batch_s();
+    if (!b) return fail(MCLB_ENOMEM, "host allocation failed");
+    b->magic = MAGIC;
+    b->stream = (cudaStream_t)params[0].stream;
+    b->own_stream = false;
+    if (!b->stream) {
+        if (cudaStreamCreate(&b->stream) != cudaSuccess) {
+            delete b;
+            return fail(MCLB_ECUDA, "cudaStreamCreate failed");
+        }
+        b->own_stream = true;
+    }
+    for (int k = 0; k < count; ++k) {
+        mclb_params p = params[k];
+        p.precision = params[0].precision;
+        p.stream = b->stream;
+        mclb_handle h = nullptr;
+        int rc = mclb_create(&p, &h);
+        if (rc) {
+            std::string msg = g_err;
+            mclb_batch_destroy(b);
+            return fail(rc, "instance %d: %s", k, msg.c_str());
+        }
+        b->items.push_back(h);
+    }
+    *out = b;
+    return MCLB_OK;
+}
+
+static int batch_item(mclb_batch b, int index, mclb_handle* h)
+{
+    if (!b || b->magic != MAGIC) return fail(MCLB_EHANDLE, "batch destroyed or not a batch");
+    if (index < 0 || index >= (int)b->items.size())
+        return fail(MCLB_EINVAL, "index %d outside 0..%zu", index, b->items.size() - 1);
+    *h = b->items[index];
+    return MCLB_OK;
+}
+
+int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const double* u)
+{
+    mclb_handle h;
+    int rc = batch_item(b, index, &h);
+    return rc ? rc : mclb_init_fields(h, rho, u);
+}
+
+int mclb_batch_step(mclb_batch b, long nsteps)
+{
+    if (!b || b->magic != MAGIC) return fail(MCLB_EHANDLE, "batch destroyed or not a batch");
+    int first = MCLB_OK;
+    for (auto h : b->items) {
+        int rc = mclb_step(h, nsteps);
+        if (rc && !first) first = rc;
+    }
+    return first;
+}
+
+int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P)
+{
+    mclb_handle h;
+    int rc = batch_item(b, index, &h);
+    return rc ? rc : mclb_moments(h, rho, U, mu, P);
+}
+
+int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count)
+{
+    mclb_handle h;
+    int rc = batch_item(b, index, &h);
+    return rc ? rc : mclb_get_state(h, f, count);
+}
+
+int mclb_batch_status(mclb_batch b, int* per_instance)
+{
+    if (!b || b->magic != MAGIC) return fail(MCLB_EHANDLE, "batch destroyed or not a batch");
+    int first = MCLB_OK;
+    for (size_t k = 0; k < b->items.size(); ++k) {
+        int rc = mclb_status(b->items[k]);
+        if (per_instance) per_instance[k] = rc;
+        if (rc && !first) first = rc;
+    }
+    return first;
+}
+
+double mclb_batch_bytes_per_step(mclb_batch b)
+{
+    if (!b || b->magic != MAGIC) return -1.0;
+    double t = 0.0;
+    for (auto h : b->items) t += mclb_bytes_per_step(h);
+    return t;
+}
+
+int mclb_batch_destroy(mclb_batch b)
+{
+    if (!b) return MCLB_OK;
+    if (b->magic != MAGIC) return fail(MCLB_EHANDLE, "batch destroyed or not a batch");
+    for (auto h : b->items) mclb_destroy(h);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    b->magic = DEAD;
+    delete b;
+    return MCLB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// lattice.cuh -- D2Q9 lattice, storage precisions and kernel parameters shared by
+// every kernel of the library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mclb_internal.h"
+
+namespace mclb {
+
+// D2Q9 velocities v_i and weights w_i (c_s^2 = 1/3), in the order
+// (0,0), (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1).
+__host__ __device__ __forceinline__ constexpr int vx(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int vy(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+template <typename C>
+__host__ __device__ __forceinline__ constexpr C wq(int i)
+{
+    return i == 0 ? C(4.0 / 9.0) : (i < 5 ? C(1.0 / 9.0) : C(1.0 / 36.0));
+}
+
+// Storage precisions.  C is the arithmetic type.  The 16-bit formats hold the
+// deviation f - shift with shift = w_i * rhobar^s, so that their few mantissa bits
+// describe the departure from the mean state rather than the state itself.
+template <typename T>
+struct Storage;
+
+template <>
+struct Storage<double> {
+    using C = double;
+    static constexpr bool shifted = false;
+    __device__ __forceinline__ static C load(const double* p) { return __ldg(p); }
+    __device__ __forceinline__ static void store(double* p, C v) { *p = v; }
+};
+
+template <>
+struct Storage<float> {
+    using C = float;
+    static constexpr bool shifted = false;
+    __device__ __forceinline__ static C load(const float* p) { return __ldg(p); }
+    __device__ __forceinline__ static void store(float* p, C v) { *p = v; }
+};
+
+template <>
+struct Storage<__nv_bfloat16> {
+    using C = float;
+    static constexpr bool shifted = true;
+    __device__ __forceinline__ static C load(const __nv_bfloat16* p)
+    {
+        return __bfloat162float(__ldg(p));
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16* p, C v)
+    {
+        *p = __float2bfloat16_rn(v);
+    }
+};
+
+template <>
+struct Storage<__half> {
+    using C = float;
+    static constexpr bool shifted = true;
+    __device__ __forceinline__ static C load(const __half* p) { return __half2float(__ldg(p)); }
+    __device__ __forceinline__ static void store(__half* p, C v) { *p = __float2half_rn(v); }
+};
+
+// Kernel parameters in the arithmetic type.  Built on the host from a Problem.
+template <typename C>
+struct StepParams {
+    int nx, ny;
+    long long S;
+    int hx;               // ghost columns per side
+    long long pitch;      // elements per row
+    long long plane;      // elements per plane
+    C omega;              // 1 / tau
+    C fcoef;              // 1 - 1/(2 tau), Eq. definef
+    C gx, gy;             // body acceleration
+    C kappa, theta;
+    C log_floor;          // floor of rho^s / rho inside a logarithm
+    C chi[NMAX * NMAX];
+    C th_m[NMAX];         // theta / m^s
+    C logc[NMAX];         // theta / m^s - 1/3: coefficient of ln rho^s in nu^s
+    C m_inv_m1[NMAX];     // 1/m^s - 1
+    C inv_m[NMAX];        // 1/m^s
+    C m[NMAX];
+    C shift[NMAX * Q];
+    unsigned int log_mask; // bit s set when logc[s] != 0
+    unsigned int* status;
+};
+
+template <typename C>
+inline StepParams<C> make_params(const Problem& P, unsigned int* status)
+{
+    StepParams<C> p{};
+    p.nx = P.nx;
+    p.ny = P.ny;
+    p.S = P.S;
+    p.hx = P.hx;
+    p.pitch = P.pitch;
+    p.plane = P.plane;
+    p.omega = C(1.0 / P.tau);
+    p.fcoef = C(1.0 - 1.0 / (2.0 * P.tau));
+    p.gx = C(P.gx);
+    p.gy = C(P.gy);
+    p.kappa = C(P.kappa);
+    p.theta = C(P.theta);
+    p.log_floor = C(1e-12);
+    p.log_mask = 0;
+    for (int a = 0; a < P.N; ++a) {
+        for (int b = 0; b < P.N; ++b) p.chi[a * P.N + b] = C(P.chi[a * P.N + b]);
+        double c = P.theta / P.m[a] - 1.0 / 3.0;
+        p.th_m[a] = C(P.theta / P.m[a]);
+        p.logc[a] = C(c);
+        if (c != 0.0) p.log_mask |= 1u << a;
+        p.m_inv_m1[a] = C(1.0 / P.m[a] - 1.0);
+        p.inv_m[a] = C(1.0 / P.m[a]);
+        p.m[a] = C(P.m[a]);
+        for (int i = 0; i < Q; ++i) p.shift[a * Q + i] = C(P.shift[a * Q + i]);
+    }
+    p.status = status;
+    return p;
+}
+
+// a + d mod n for |d| <= n
+__device__ __forceinline__ int wrap_add(int a, int d, int n)
+{
+    a += d;
+    a += (a < 0) ? n : 0;
+    a -= (a >= n) ? n : 0;
+    return a;
+}
+
+// Element offset of (plane, y, x) with 0 <= x < nx in the ghost-padded layout.
+template <typename C>
+__device__ __forceinline__ long long fidx(const StepParams<C>& p, int plane, int y, int x)
+{
+    return (long long)plane * p.plane + (long long)y * p.pitch + p.hx + x;
+}
+
+// Store one distribution value at column x of a row (row points at the row start,
+// ghosts included) and at every ghost column that repeats column x.
+template <typename T, typename C>
+__device__ __forceinline__ void store_row(T* row, int x, int nx, int hx, C v)
+{
+    Storage<T>::store(row + hx + x, v);
+    if (x < hx)
+        for (int g = nx + x; g < nx + hx; g += nx) Storage<T>::store(row + hx + g, v);
+    if (x >= nx - hx)
+        for (int g = x - nx; g >= -hx; g -= nx) Storage<T>::store(row + hx + g, v);
+}
+
+}  // namespace mclb

@@ -1,0 +1,101 @@
+// mclb_internal.h -- interface between the C ABI runtime (capi.cu) and the
+// per-precision kernel translation units.  Host-only types; no torch anywhere.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mclb {
+
+constexpr int NMAX = 8;
+constexpr int Q = 9;
+constexpr int ROW_ALIGN = 128;  // data columns per row are padded to a multiple of this
+
+// Everything a launcher needs to know about one simulation, in FP64 as given at
+// the boundary; each precision unit converts it to its own kernel parameters.
+//
+// Distribution layout (every schedule): plane p = s * 9 + i, row y, column x at
+//   p * plane + y * pitch + hx + x,
+// where hx ghost columns on each side of a row repeat the periodic neighbours
+// (ghost column g in [-hx, 0) u [nx, nx + hx) holds column g mod nx) and the
+// row is padded to pitch = 2 hx + roundup(nx, ROW_ALIGN) elements.  Every kernel
+// that writes distributions also writes the ghosts, so that the fused kernel can
+// move whole aligned row segments with TMA.
+struct Problem {
+    int N, nx, ny;
+    long long S;            // nx * ny sites
+    int hx;                 // ghost columns per side
+    long long pitch;        // elements per row
+    long long plane;        // elements per plane = pitch * ny
+    double tau, theta, kappa, gx, gy;
+    double chi[NMAX * NMAX];
+    double m[NMAX];
+    double shift[NMAX * Q]; // storage shift w_i * rhobar^s in the shifted modes, else 0
+};
+
+// Device scratch owned by a handle: component densities and the potentials
+// nu^s = mu^s - (1/3) ln rho^s in the compute type (used by the staged schedule and
+// by the diagnostics), block partial sums for FP64 reductions, and the status word.
+struct Scratch {
+    void* rho_s;            // N * S compute-type values
+    void* nu;               // N * S compute-type values
+    double* partial;        // reduction partials
+    size_t partial_cap;     // capacity in doubles
+    unsigned int* status;   // device status bits (see STATUS_*)
+};
+
+enum : unsigned int {
+    STATUS_NONFINITE = 1u,  // NaN/Inf or non-positive total density seen
+    STATUS_TIMEOUT = 2u     // a bounded device wait gave up
+};
+
+constexpr int REDUCE_BLOCKS = 256;    // fixed grid of the FP64 reductions (deterministic)
+
+// Launch shape of the fused kernel: strips of W columns, segments of H rows,
+// NS shared-memory stages of source rows.
+struct FusedPlan {
+    int W, NS, H;
+    int nstrips, nsegs;
+    size_t smem;
+    bool ok;
+};
+
+struct KernelTable {
+    size_t storage_bytes;   // bytes of one stored distribution value
+    bool shifted;
+    CUtensorMapDataType tma_type;
+    int hx;                 // ghost columns per side for this storage type
+    FusedPlan (*plan_fused)(const Problem&, int sm_count);
+    // f^s_i(r) = equilibrium of (rho, u) (device FP64 inputs; u may be null)
+    cudaError_t (*init)(const Problem&, const Scratch&, const double* rho, const double* u,
+                        void* f, cudaStream_t st);
+    // one fused timestep fin -> fout (tmap_in describes fin)
+    cudaError_t (*step_fused)(const Problem&, const Scratch&, const FusedPlan&,
+                              const CUtensorMap* tmap_in, void* fout, cudaStream_t st);
+    // one staged timestep fin -> fout (three launches through scratch)
+    cudaError_t (*step_staged)(const Problem&, const Scratch&, const void* fin, void* fout,
+                               cudaStream_t st);
+    // macroscopic output fields into device FP64 arrays (any may be null)
+    cudaError_t (*moments)(const Problem&, const Scratch&, const void* f, double* rho,
+                           double* U, double* mu, double* P, cudaStream_t st);
+    // FP64 sums into out: [0, N) mass, [N, N+2) momentum, [N+2, N+4) force
+    cudaError_t (*conservation)(const Problem&, const Scratch&, const void* f, double* out,
+                                cudaStream_t st);
+    // FP64 compositions phi (N * S) and bulk flags (S, 1.0 where max |grad phi| < tol)
+    cudaError_t (*compositions)(const Problem&, const Scratch&, const void* f, double* phi,
+                                double* bulk, double tol, cudaStream_t st);
+    // pre-collision FP64 state out / in, layout [s][i][y][x]
+    cudaError_t (*get_state)(const Problem&, const Scratch&, const void* f, double* out,
+                             cudaStream_t st);
+    cudaError_t (*set_state)(const Problem&, const Scratch&, const double* in, void* f,
+                             cudaStream_t st);
+};
+
+const KernelTable& table_fp64();
+const KernelTable& table_fp32();
+const KernelTable& table_bf16();
+const KernelTable& table_fp16();
+
+}  // namespace mclb

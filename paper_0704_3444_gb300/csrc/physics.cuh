@@ -1,0 +1,151 @@
+// physics.cuh -- per-site arithmetic of one timestep (Li & Wagner, arXiv:0704.3444),
+// shared by the staged, fused and diagnostic kernels.
+#pragma once
+
+#include "lattice.cuh"
+
+namespace mclb {
+
+template <typename C>
+__device__ __forceinline__ C dev_log(C x);
+template <>
+__device__ __forceinline__ double dev_log<double>(double x) { return log(x); }
+template <>
+__device__ __forceinline__ float dev_log<float>(float x) { return logf(x); }
+
+// nu^s = mu^s/m^s - kappa lap rho^s - (1/3) ln rho^s for every component at one site
+// (Eq. lgf, Eq. chemicalpotential, Eq. definef).  The Flory-Huggins potential per
+// unit mass is
+//   theta [ (ln phi^s + 1)/m^s - 1 - sum_t phi^t/m^t + sum_t chi^{st} phi^t
+//           - 1/2 sum_{t,t'} chi^{tt'} phi^t phi^t' ],
+// and its logarithms are combined with -(1/3) ln rho^s as
+//   (theta/m^s - 1/3) ln rho^s - (theta/m^s) ln rho,
+// the first term skipped when its coefficient is zero (theta = m^s/3) and otherwise
+// evaluated at max(rho^s, 1e-12 rho).
+template <typename C, int N>
+__device__ __forceinline__ void site_nu(const StepParams<C>& p, const C (&r)[N],
+                                        const C (&lap)[N], C (&nu)[N])
+{
+    C rho = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) rho += r[s];
+    const C inv_rho = C(1) / rho;
+    C phi[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) phi[s] = r[s] * inv_rho;
+    C sum_phi_m = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) sum_phi_m += phi[s] * p.inv_m[s];
+    C chiphi[N];
+    C quad = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C acc = C(0);
+#pragma unroll
+        for (int t = 0; t < N; ++t) acc += p.chi[s * N + t] * phi[t];
+        chiphi[s] = acc;
+    }
+#pragma unroll
+    for (int s = 0; s < N; ++s) quad += C(0.5) * phi[s] * chiphi[s];
+    const C lnrho = dev_log(rho);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C logs = -p.th_m[s] * lnrho;
+        if (p.log_mask & (1u << s)) {
+            const C fl = p.log_floor * rho;
+            logs += p.logc[s] * dev_log(r[s] > fl ? r[s] : fl);
+        }
+        const C bulk = p.theta * (p.m_inv_m1[s] - sum_phi_m + chiphi[s] - quad);
+        nu[s] = logs + bulk - p.kappa * lap[s];
+    }
+}
+
+// Chemical potential per unit mass mu^s/m^s including the gradient term (output
+// diagnostic; ln phi^s evaluated at max(phi^s, 1e-12)).
+template <typename C, int N>
+__device__ __forceinline__ void site_mu(const StepParams<C>& p, const C (&r)[N],
+                                        const C (&lap)[N], C (&mu)[N])
+{
+    C rho = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) rho += r[s];
+    C phi[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) phi[s] = r[s] / rho;
+    C sum_phi_m = C(0), quad = C(0);
+    C chiphi[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) sum_phi_m += phi[s] * p.inv_m[s];
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C acc = C(0);
+#pragma unroll
+        for (int t = 0; t < N; ++t) acc += p.chi[s * N + t] * phi[t];
+        chiphi[s] = acc;
+    }
+#pragma unroll
+    for (int s = 0; s < N; ++s) quad += C(0.5) * phi[s] * chiphi[s];
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        const C ph = phi[s] > p.log_floor ? phi[s] : p.log_floor;
+        mu[s] = p.theta * ((dev_log(ph) + C(1)) * p.inv_m[s] - C(1) - sum_phi_m + chiphi[s] - quad)
+                - p.kappa * lap[s];
+    }
+}
+
+// Flory-Huggins free energy density of Eq. lgf (n^s = rho^s/m^s), with the
+// phi ln phi term taken as 0 at phi = 0.
+template <typename C, int N>
+__device__ __forceinline__ C site_psi(const StepParams<C>& p, const C (&r)[N])
+{
+    C rho = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) rho += r[s];
+    C psi = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        const C n = r[s] * p.inv_m[s];
+        C phi = r[s] / rho;
+        C ph = phi > p.log_floor ? phi : p.log_floor;
+        psi += -p.theta * n * p.m[s];
+        psi += n * p.theta * dev_log(ph);
+        C acc = C(0);
+#pragma unroll
+        for (int t = 0; t < N; ++t) acc += p.chi[s * N + t] * (r[t] / rho);
+        psi += C(0.5) * p.theta * p.m[s] * n * acc;
+    }
+    return psi;
+}
+
+// Velocity-dependent part of the equilibrium, shared by every component:
+// e_i = w_i (1 + 3 v_i.u + 9/2 (v_i.u)^2 - 3/2 u.u), so that f^{s,e}_i = rho^s e_i
+// (Sec. 3 equilibrium moments, all components built on the barycentric u).
+template <typename C>
+__device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
+{
+    const C uu = ux * ux + uy * uy;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const C cu = C(vx(i)) * ux + C(vy(i)) * uy;
+        e[i] = wq<C>(i) * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+    }
+}
+
+// Post-collision populations of one component (Eq. ssLB):
+//   f* = f + (f^e - f)/tau + F,  f^e_i = rho^s e_i,
+//   F_i = w_i [3 rho^s (v_i.a) + 9 (v_i.a)(v_i.j) - 3 a.j]   (Eqs. ff1-ff3, j = rho^s u^s).
+template <typename C>
+__device__ __forceinline__ void collide(const StepParams<C>& p, const C (&f)[Q], const C (&e)[Q],
+                                        C r, C jx, C jy, C ax, C ay, C (&out)[Q])
+{
+    const C aj = ax * jx + ay * jy;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const C ca = C(vx(i)) * ax + C(vy(i)) * ay;
+        const C cj = C(vx(i)) * jx + C(vy(i)) * jy;
+        const C F = wq<C>(i) * (C(3) * r * ca + C(9) * ca * cj - C(3) * aj);
+        out[i] = f[i] + (r * e[i] - f[i]) * p.omega + F;
+    }
+}
+
+}  // namespace mclb

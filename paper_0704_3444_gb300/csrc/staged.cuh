@@ -1,0 +1,407 @@
+// staged.cuh -- the three-launch timestep and the diagnostic kernels.
+//
+// Staged schedule (one thread per site, periodic neighbours by index arithmetic):
+//   k_density    rho^s = sum_i f^s_i(r - v_i)           pull streaming + zeroth moment
+//   k_potential  nu^s  = mu^s/m^s - kappa lap rho^s - (1/3) ln rho^s
+//   k_collide    pull f again, first moments, barycentric u, a^s = -(1 - 1/2tau) grad nu^s + g,
+//                f^e, F, BGK (Eq. ssLB), store post-collision values in place (pull scheme)
+// The density and potential fields live in handle-owned scratch memory.
+#pragma once
+
+#include "physics.cuh"
+
+namespace mclb {
+
+constexpr int SITE_THREADS = 256;
+
+// Pre-collision value f^s_i(x, y) = post-collision value stored at (x - v_i, y - v_i).
+template <typename T>
+__device__ __forceinline__ typename Storage<T>::C pull(const T* __restrict__ f,
+                                                       const StepParams<typename Storage<T>::C>& p,
+                                                       int s, int i, int x, int y)
+{
+    using C = typename Storage<T>::C;
+    const int xs = wrap_add(x, -vx(i), p.nx);
+    const int ys = wrap_add(y, -vy(i), p.ny);
+    C v = Storage<T>::load(f + fidx(p, s * Q + i, ys, xs));
+    if constexpr (Storage<T>::shifted) v += p.shift[s * Q + i];
+    return v;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
+          const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C r = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) r += pull(f, p, s, i, x, y);
+        rs[s * p.S + site] = r;
+    }
+}
+
+template <typename C, int N>
+__device__ __forceinline__ void neighbour_laplacians(const C* __restrict__ rs,
+                                                     const StepParams<C>& p, int x, int y,
+                                                     const C (&r)[N], C (&lap)[N])
+{
+    // lap g = 6 sum_i w_i (g(r + v_i) - g(r))
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C acc = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+            acc += wq<C>(i) * (rs[s * p.S + (long long)yy * p.nx + xx] - r[s]);
+        }
+        lap[s] = C(6) * acc;
+    }
+}
+
+template <typename C, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant__ StepParams<C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+    C r[N], lap[N], out[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) r[s] = rs[s * p.S + site];
+    neighbour_laplacians<C, N>(rs, p, x, y, r, lap);
+    site_nu<C, N>(p, r, lap, out);
+#pragma unroll
+    for (int s = 0; s < N; ++s) nu[s * p.S + site] = out[s];
+}
+
+// grad g = 3 sum_i w_i v_i g(r + v_i) of one component's field
+template <typename C>
+__device__ __forceinline__ void field_grad(const C* __restrict__ g, const StepParams<C>& p, int x,
+                                           int y, C& gx, C& gy)
+{
+    C ax = C(0), ay = C(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const C v = g[(long long)yy * p.nx + xx];
+        ax += wq<C>(i) * C(vx(i)) * v;
+        ay += wq<C>(i) * C(vy(i)) * v;
+    }
+    gx = C(3) * ax;
+    gy = C(3) * ay;
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_collide(const T* __restrict__ fin, T* __restrict__ fout,
+          const typename Storage<T>::C* __restrict__ nu,
+          const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+    C f[N][Q];
+    C r[N], jx[N], jy[N];
+    C rho = C(0), jxt = C(0), jyt = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C a = C(0), bx = C(0), by = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const C v = pull(fin, p, s, i, x, y);
+            f[s][i] = v;
+            a += v;
+            bx += v * C(vx(i));
+            by += v * C(vy(i));
+        }
+        r[s] = a;
+        jx[s] = bx;
+        jy[s] = by;
+        rho += a;
+        jxt += bx;
+        jyt += by;
+    }
+    const C ux = jxt / rho, uy = jyt / rho;
+    C e[Q];
+    eq_weights(ux, uy, e);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C gx, gy;
+        field_grad(nu + s * p.S, p, x, y, gx, gy);
+        const C ax = -p.fcoef * gx + p.gx;
+        const C ay = -p.fcoef * gy + p.gy;
+        C out[Q];
+        collide(p, f[s], e, r[s], jx[s], jy[s], ax, ay, out);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            C v = out[i];
+            if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
+            store_row(fout + (long long)(s * Q + i) * p.plane + (long long)y * p.pitch, x, p.nx,
+                      p.hx, v);
+        }
+    }
+    if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
+}
+
+// ---------------------------------------------------------------- diagnostics
+
+// f^s_i stored at (x, y) so that pulling yields f^e_i(rho^s, u) at (x + v_i, y + v_i).
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_init(const double* __restrict__ rho, const double* __restrict__ u, T* __restrict__ f,
+       const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const long long t = (long long)yy * p.nx + xx;
+        const C ux = u ? C(u[t]) : C(0), uy = u ? C(u[p.S + t]) : C(0);
+        const C uu = ux * ux + uy * uy;
+        const C cu = C(vx(i)) * ux + C(vy(i)) * uy;
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            C v = wq<C>(i) * C(rho[s * p.S + t]) *
+                  (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+            if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
+            store_row(f + (long long)(s * Q + i) * p.plane + (long long)y * p.pitch, x, p.nx, p.hx,
+                      v);
+        }
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_get_state(const T* __restrict__ f, double* __restrict__ out,
+            const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+#pragma unroll
+    for (int s = 0; s < N; ++s)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out[(s * Q + i) * p.S + site] = (double)pull(f, p, s, i, x, y);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_set_state(const double* __restrict__ in, T* __restrict__ f,
+            const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const long long t = (long long)yy * p.nx + xx;
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            C v = C(in[(s * Q + i) * p.S + t]);
+            if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
+            store_row(f + (long long)(s * Q + i) * p.plane + (long long)y * p.pitch, x, p.nx, p.hx,
+                      v);
+        }
+    }
+}
+
+// Output fields: rho^s, U = u + (sum_s rho^s a^s)/(2 rho), mu^s, P (needs k_density and
+// k_potential to have filled the scratch fields for the same state).
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_moments(const T* __restrict__ f, const typename Storage<T>::C* __restrict__ rs,
+          const typename Storage<T>::C* __restrict__ nu, double* __restrict__ rho_out,
+          double* __restrict__ U, double* __restrict__ mu_out, double* __restrict__ P,
+          const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+    C r[N];
+    C rho = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        r[s] = rs[s * p.S + site];
+        rho += r[s];
+    }
+    if (rho_out)
+#pragma unroll
+        for (int s = 0; s < N; ++s) rho_out[s * p.S + site] = (double)r[s];
+    if (U) {
+        C jxt = C(0), jyt = C(0), fx = C(0), fy = C(0);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const C v = pull(f, p, s, i, x, y);
+                jxt += v * C(vx(i));
+                jyt += v * C(vy(i));
+            }
+            C gx, gy;
+            field_grad(nu + s * p.S, p, x, y, gx, gy);
+            fx += r[s] * (-p.fcoef * gx + p.gx);
+            fy += r[s] * (-p.fcoef * gy + p.gy);
+        }
+        U[site] = (double)(jxt / rho + C(0.5) * fx / rho);
+        U[p.S + site] = (double)(jyt / rho + C(0.5) * fy / rho);
+    }
+    if (mu_out || P) {
+        C lap[N], mu[N];
+        neighbour_laplacians<C, N>(rs, p, x, y, r, lap);
+        site_mu<C, N>(p, r, lap, mu);
+        if (mu_out)
+#pragma unroll
+            for (int s = 0; s < N; ++s) mu_out[s * p.S + site] = (double)mu[s];
+        if (P) {
+            const C psi = site_psi<C, N>(p, r);
+            C rmu = C(0), gg = C(0), pxx = C(0), pxy = C(0), pyy = C(0);
+#pragma unroll
+            for (int s = 0; s < N; ++s) {
+                C gx, gy;
+                field_grad(rs + s * p.S, p, x, y, gx, gy);
+                rmu += r[s] * mu[s];
+                gg += C(0.5) * p.kappa * (gx * gx + gy * gy);
+                pxx += p.kappa * gx * gx;
+                pxy += p.kappa * gx * gy;
+                pyy += p.kappa * gy * gy;
+            }
+            const C iso = rmu - (psi + gg);
+            P[site] = (double)(iso + pxx);
+            P[p.S + site] = (double)pxy;
+            P[2 * p.S + site] = (double)(iso + pyy);
+        }
+    }
+}
+
+// Deterministic FP64 block reduction of K values per thread into partial[block * K + k].
+template <int K>
+__device__ __forceinline__ void block_reduce_store(double (&v)[K], double* partial)
+{
+    __shared__ double red[SITE_THREADS];
+    for (int k = 0; k < K; ++k) {
+        red[threadIdx.x] = v[k];
+        __syncthreads();
+        for (int w = SITE_THREADS / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[blockIdx.x * K + k] = red[0];
+        __syncthreads();
+    }
+}
+
+// Conservation sums: mass^s, total momentum sum_s j^s, force sum_s rho^s a^s.
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_conservation(const T* __restrict__ f, const typename Storage<T>::C* __restrict__ rs,
+               const typename Storage<T>::C* __restrict__ nu, double* __restrict__ partial,
+               const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    constexpr int K = N + 4;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < p.S;
+         site += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            const C r = rs[s * p.S + site];
+            acc[s] += (double)r;
+            double jx = 0.0, jy = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const double v = (double)pull(f, p, s, i, x, y);
+                jx += v * vx(i);
+                jy += v * vy(i);
+            }
+            acc[N] += jx;
+            acc[N + 1] += jy;
+            C gx, gy;
+            field_grad(nu + s * p.S, p, x, y, gx, gy);
+            acc[N + 2] += (double)r * (double)(-p.fcoef * gx + p.gx);
+            acc[N + 3] += (double)r * (double)(-p.fcoef * gy + p.gy);
+        }
+    }
+    block_reduce_store<K>(acc, partial);
+}
+
+// Sum the per-block partials in a fixed order: out[k] = sum_b partial[b * K + k].
+static __global__ void k_reduce_partials(const double* __restrict__ partial, int nblocks, int K,
+                                  double* __restrict__ out)
+{
+    __shared__ double red[SITE_THREADS];
+    for (int k = 0; k < K; ++k) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partial[b * K + k];
+        red[threadIdx.x] = a;
+        __syncthreads();
+        for (int w = SITE_THREADS / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[k] = red[0];
+        __syncthreads();
+    }
+}
+
+// FP64 compositions phi^s = rho^s / rho and a bulk flag (1 where every |grad phi^s| < tol).
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_compositions(const typename Storage<T>::C* __restrict__ rs, double* __restrict__ phi,
+               double* __restrict__ bulk, double tol,
+               const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+    double g2max = 0.0;
+    double here[N];
+    {
+        double rho = 0.0;
+#pragma unroll
+        for (int s = 0; s < N; ++s) rho += (double)rs[s * p.S + site];
+#pragma unroll
+        for (int s = 0; s < N; ++s) here[s] = (double)rs[s * p.S + site] / rho;
+    }
+    double gx[N], gy[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) gx[s] = gy[s] = 0.0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const long long t = (long long)yy * p.nx + xx;
+        double rho = 0.0;
+#pragma unroll
+        for (int s = 0; s < N; ++s) rho += (double)rs[s * p.S + t];
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            const double ph = (double)rs[s * p.S + t] / rho;
+            gx[s] += 3.0 * wq<double>(i) * vx(i) * ph;
+            gy[s] += 3.0 * wq<double>(i) * vy(i) * ph;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        phi[s * p.S + site] = here[s];
+        const double g2 = gx[s] * gx[s] + gy[s] * gy[s];
+        g2max = g2 > g2max ? g2 : g2max;
+    }
+    bulk[site] = (g2max < tol * tol) ? 1.0 : 0.0;
+}
+
+}  // namespace mclb

@@ -1,0 +1,193 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated per field, max-norm of the difference):
+  * FP64 storage and arithmetic: 1e-12 relative to the field's max-norm, up to 50 steps
+    on every case and for 1000 steps on the 64 x 64 binary (still in its linear regime);
+  * FP32: 1e-5 absolute (lattice units; densities are O(1/N), velocities O(1e-3)) after
+    100 steps on the ternary 256 x 256 workload;
+  * one step at the full 2048 x 2048 (N = 5) and 8192 x 2048 (N = 3) sizes from the same
+    state: 2e-6 relative to the largest population (one FP32 step from identical input).
+Every case runs both schedules (fused single pass and staged three launches).
+"""
+import numpy as np
+import pytest
+
+import paper_0704_3444_gb300 as mclb
+from oracle import Oracle
+from paper_0704_3444_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+KERNELS = [mclb.KERNEL_FUSED, mclb.KERNEL_STAGED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mclb.build()
+    mclb.load()
+
+
+def _chi(n, seed):
+    r = inputs.uniform(seed, n * n, 3).reshape(n, n)
+    c = 2.0 + r + r.T
+    np.fill_diagonal(c, 0.0)
+    return c
+
+
+def _pair(n, nx, ny, tau, chi, m=None, theta=1 / 3, kappa=0.0, force=(0.0, 0.0),
+          precision="fp64", kernel=mclb.KERNEL_FUSED, rho=None, u=None):
+    sim = mclb.Simulation(n, nx, ny, tau, chi, m, theta, kappa, force, precision, kernel)
+    orc = Oracle(n, nx, ny, tau, chi, m, theta, kappa, force)
+    sim.init_fields(rho, u)
+    orc.init(rho, u)
+    return sim, orc
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+CASES = [
+    # (nx, ny, N, steps, tau, theta, kappa, m, force)
+    (4, 4, 2, 20, 1.0, 1 / 3, 0.0, None, (0.0, 0.0)),
+    (5, 3, 3, 20, 0.8, 0.4, 0.05, [1.0, 3.0, 10.0], (3e-4, -1e-4)),
+    (7, 6, 1, 20, 0.9, 1 / 3, 0.02, None, (1e-4, 0.0)),
+    (1, 9, 2, 20, 0.7, 0.45, 0.01, None, (0.0, 2e-4)),
+    (130, 37, 4, 30, 1.0, 1 / 3, 0.01, None, (0.0, 0.0)),
+    (300, 170, 3, 25, 0.8, 0.5, 0.01, [2.0, 1.0, 1.0], (1e-5, 1e-5)),
+    (40, 33, 5, 15, 1.2, 1 / 3, 0.01, None, (0.0, 0.0)),
+    (40, 33, 6, 10, 0.9, 0.4, 0.01, None, (0.0, 0.0)),
+    (33, 40, 7, 10, 1.0, 1 / 3, 0.02, None, (0.0, 0.0)),
+    (64, 20, 8, 10, 1.1, 1 / 3, 0.01, [1, 1, 2, 1, 1, 3, 1, 1], (0.0, 0.0)),
+]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}N{c[2]}")
+def test_fp64_state_parity(case, kernel):
+    nx, ny, n, steps, tau, theta, kappa, m, force = case
+    rho, u = inputs.random_state(n, nx, ny, seed=1000 + nx * ny + n, amp=0.3, umax=0.03)
+    sim, orc = _pair(n, nx, ny, tau, _chi(n, n + nx), m, theta, kappa, force, "fp64", kernel,
+                     rho, u)
+    np.testing.assert_allclose(sim.get_state(), orc.f, rtol=0, atol=1e-15 * np.abs(orc.f).max())
+    sim.step(steps)
+    orc.run(steps)
+    assert sim.status() == 0
+    assert _rel(sim.get_state(), orc.f) < 1e-12
+    gm, om = sim.moments(), orc.moments()
+    for k in ("rho", "U", "mu"):
+        assert _rel(gm[k], om[k]) < 1e-11, k
+    # P: compare against the scale of its gradient part (its isotropic bulk part is ~0)
+    assert np.max(np.abs(gm["P"] - om["P"])) < 1e-12 * max(1.0, np.abs(om["P"]).max())
+    sim.close()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_binary_64_full_horizon_fp64(kernel):
+    """The 64 x 64 binary workload (chi = 2.2, kappa = 0.01, tau = 1), all 1000 steps in FP64."""
+    p = inputs.binary_noise()
+    sim = mclb.Simulation.from_problem(p, precision="fp64", kernel=kernel)
+    orc = Oracle.from_problem(p)
+    sim.step(1000)
+    orc.run(1000)
+    assert sim.status() == 0
+    assert _rel(sim.get_state(), orc.f) < 1e-11
+    c = sim.conservation()
+    mass0 = p.rho.reshape(2, -1).sum(1)
+    assert np.max(np.abs(c["mass"] / mass0 - 1)) < 1e-13
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_ternary_256_fp32(kernel):
+    """Ternary 256 x 256 (chi = 3.6, tau = 0.8, kappa = 0.01) in FP32: 1e-5 after 100 steps."""
+    p = inputs.ternary_gauss(steps=100)
+    sim = mclb.Simulation.from_problem(p, precision="fp32", kernel=kernel)
+    orc = Oracle.from_problem(p)
+    sim.step(100)
+    orc.run(100)
+    assert sim.status() == 0
+    gm, om = sim.moments(), orc.moments()
+    assert np.max(np.abs(gm["rho"] - om["rho"])) < 1e-5
+    assert np.max(np.abs(gm["U"] - om["U"])) < 1e-5
+    assert np.max(np.abs(gm["mu"] - om["mu"])) < 1e-4
+
+
+def test_fused_matches_staged_fp32():
+    p = inputs.ternary_gauss(128, 96, steps=50)
+    a = mclb.Simulation.from_problem(p, precision="fp32", kernel=mclb.KERNEL_FUSED)
+    b = mclb.Simulation.from_problem(p, precision="fp32", kernel=mclb.KERNEL_STAGED)
+    assert a.launches_per_step == 1 and b.launches_per_step == 3
+    a.step(50)
+    b.step(50)
+    assert np.max(np.abs(a.get_state() - b.get_state())) < 1e-6
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_momentum_balance_gpu(kernel):
+    """Total momentum changes by exactly the summed force (Eq. ff2), FP64."""
+    n, nx, ny = 3, 50, 30
+    rho, u = inputs.random_state(n, nx, ny, seed=77, amp=0.3, umax=0.02)
+    sim = mclb.Simulation(n, nx, ny, 0.7, _chi(n, 9), [1.0, 2.0, 5.0], 0.4, 0.03, (1e-4, -2e-4),
+                          "fp64", kernel)
+    sim.init_fields(rho, u)
+    for _ in range(3):
+        c0 = sim.conservation()
+        sim.step(1)
+        c1 = sim.conservation()
+        np.testing.assert_allclose(c1["mom"] - c0["mom"], c0["force"], rtol=1e-9, atol=1e-14)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16", "fp16"])
+def test_state_roundtrip(precision):
+    n, nx, ny = 3, 37, 11
+    rho, u = inputs.random_state(n, nx, ny, seed=5, amp=0.2, umax=0.02)
+    orc = Oracle(n, nx, ny, 1.0, _chi(n, 1))
+    orc.init(rho, u)
+    sim = mclb.Simulation(n, nx, ny, 1.0, _chi(n, 1), precision=precision)
+    sim.set_state(orc.f)
+    g = sim.get_state()
+    if precision == "fp64":
+        assert np.array_equal(g, orc.f)
+    elif precision == "fp32":
+        assert np.array_equal(g, orc.f.astype(np.float32).astype(np.float64))
+    else:
+        tol = 2e-3 if precision == "bf16" else 2e-4
+        assert np.max(np.abs(g - orc.f)) < tol * np.abs(orc.f).max()
+
+
+def test_nonpositive_density_sets_status():
+    """A host-made bad input (negative total density at one site, passed through the
+    unvalidated device entry point) is reported as ENONFINITE after the step."""
+    torch = pytest.importorskip("torch")
+    n, nx, ny = 2, 16, 16
+    rho = np.full((n, ny, nx), 0.5)
+    rho[:, 3, 4] = -0.5
+    sim = mclb.Simulation(n, nx, ny, 1.0, np.array([[0.0, 2.0], [2.0, 0.0]]))
+    t = torch.tensor(rho, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    sim.init_fields_device(t)
+    sim.step(2)
+    assert sim.status() == -4
+
+
+@pytest.mark.parametrize("name,make", [
+    ("n5_2048x2048", lambda: inputs.multi_uniform(steps=1)),
+    ("slab_8192x2048", lambda: inputs.slab(steps=1)),
+])
+def test_full_size_single_step_fp32(name, make):
+    """At the full benchmark sizes and in the fused launch configuration the benchmark
+    times: advance 10 steps on the GPU, then one more step on both sides from the
+    GPU's own state, compared at every population."""
+    p = make()
+    sim = mclb.Simulation.from_problem(p, precision="fp32", kernel=mclb.KERNEL_FUSED)
+    sim.step(10)
+    f0 = sim.get_state()
+    orc = Oracle(p.ncomp, p.nx, p.ny, p.tau, p.chi, p.m, p.theta, p.kappa, p.force)
+    orc.set_state(f0)
+    del f0
+    orc.run(1)
+    sim.step(1)
+    assert sim.status() == 0
+    g = sim.get_state()
+    err = np.max(np.abs(g - orc.f)) / np.abs(orc.f).max()
+    assert err < 2e-6, err
