@@ -142,7 +142,7 @@ def ternary_gauss(nx=256, ny=256, *, chi=3.6, tau=0.8, kappa=0.01, sigma=0.005, 
     Defaults: 256 x 256, chi_ij = 3.6 (1.2 x the uniform critical 3), tau = 0.8.
     """
     s = nx * ny
-    noise = np.stack([gaussian(seed, s, k) for k in range(3)])
+    noise = np.stack([sigma * gaussian(seed, s, k) for k in range(3)])
     phi = (1.0 / 3.0 + _mass_neutral(noise)).reshape(3, ny, nx)
     return _problem(name, 3, nx, ny, tau, uniform_chi(3, chi), phi, kappa=kappa, steps=steps,
                     precision=precision)
