@@ -95,14 +95,17 @@ def uniform_chi(n: int, value: float) -> np.ndarray:
     return chi
 
 
-def chi_critical_uniform(n: int) -> float:
-    """Critical pair interaction of the equimolar N-component mixture with uniform chi.
+def chi_critical_pair(ma: float = 1.0, mb: float = 1.0) -> float:
+    """Critical Flory-Huggins interaction of a binary pair with polymerisations ma, mb:
+    (1/sqrt(ma) + 1/sqrt(mb))^2 / 2, i.e. 2 for two monomers.
 
-    This is a *reading* used to turn "k x critical" into a number (chi_c(N) = N
-    for theta-scaled Flory-Huggins with m = 1): the value at which the Hessian
-    of the mixing free energy at phi = 1/N loses positivity on the simplex.
+    This is the *reading* used to turn "k x critical" into a number for every
+    workload: k times the critical interaction of a pair of components.  (The
+    equimolar-spinodal reading chi_c = N would put the five-component pairs up to
+    chi = 7.5, far beyond the largest chi the paper runs, and there the method
+    diverges within a few hundred steps.)
     """
-    return float(n)
+    return 0.5 * (1.0 / math.sqrt(ma) + 1.0 / math.sqrt(mb)) ** 2
 
 
 def _mass_neutral(noise: np.ndarray) -> np.ndarray:
@@ -135,11 +138,11 @@ def binary_noise(nx=64, ny=64, *, chi=2.2, tau=1.0, kappa=0.01, amp=0.01, seed=1
                     precision=precision)
 
 
-def ternary_gauss(nx=256, ny=256, *, chi=3.6, tau=0.8, kappa=0.01, sigma=0.005, seed=2,
+def ternary_gauss(nx=256, ny=256, *, chi=2.4, tau=0.8, kappa=0.01, sigma=0.005, seed=2,
                   steps=5000, precision="fp32", name="ternary_256x256") -> Problem:
     """Ternary mixture, phi = 1/3 + N(0, sigma^2) made mass neutral per site.
 
-    Defaults: 256 x 256, chi_ij = 3.6 (1.2 x the uniform critical 3), tau = 0.8.
+    Defaults: 256 x 256, chi_ij = 2.4 (1.2 x the pair critical 2), tau = 0.8.
     """
     s = nx * ny
     noise = np.stack([sigma * gaussian(seed, s, k) for k in range(3)])
@@ -149,13 +152,14 @@ def ternary_gauss(nx=256, ny=256, *, chi=3.6, tau=0.8, kappa=0.01, sigma=0.005, 
 
 
 def random_chi(n: int, lo: float, hi: float, seed: int) -> np.ndarray:
-    """Symmetric matrix chi_ij = chi_c(n) * U[lo, hi] for i != j, zero diagonal."""
+    """Symmetric matrix chi_ij = chi_c * U[lo, hi] for i != j (chi_c the monomer pair
+    critical value 2), zero diagonal."""
     r = uniform(seed, n * n, 77)
     chi = np.zeros((n, n))
     k = 0
     for i in range(n):
         for j in range(i + 1, n):
-            v = chi_critical_uniform(n) * (lo + (hi - lo) * r[k])
+            v = chi_critical_pair() * (lo + (hi - lo) * r[k])
             chi[i, j] = chi[j, i] = v
             k += 1
     return chi
@@ -226,7 +230,8 @@ def batch(count=512, *, seed=4, lo=32, hi=512, steps=1000, precision="fp32") -> 
     """Independent binary/ternary instances of uneven size.
 
     N uniform in {2, 3}; nx, ny independent uniform integers in [lo, hi];
-    chi = s * chi_c(N) with s ~ U[0.9, 1.6]; tau ~ U[0.6, 1.5]; kappa = 0.01;
+    chi = s * chi_c with s ~ U[0.9, 1.6] (chi_c = 2, the pair critical value);
+    tau ~ U[0.6, 1.5]; kappa = 0.01;
     initial fields as the binary (uniform noise 0.01) and ternary (Gaussian
     noise 0.005) recipes, each instance with its own seed.
     """
@@ -238,7 +243,7 @@ def batch(count=512, *, seed=4, lo=32, hi=512, steps=1000, precision="fp32") -> 
         ny = lo + int(r[k, 2] * (hi - lo + 1))
         s = 0.9 + 0.7 * r[k, 3]
         tau = 0.6 + 0.9 * r[k, 4]
-        chi = s * chi_critical_uniform(n)
+        chi = s * chi_critical_pair()
         iseed = seed * 100003 + k
         if n == 2:
             p = binary_noise(nx, ny, chi=chi, tau=tau, kappa=0.01, seed=iseed, steps=steps,

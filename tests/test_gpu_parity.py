@@ -99,7 +99,7 @@ def test_binary_64_full_horizon_fp64(kernel):
 
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_ternary_256_fp32(kernel):
-    """Ternary 256 x 256 (chi = 3.6, tau = 0.8, kappa = 0.01) in FP32: 1e-5 after 100 steps."""
+    """Ternary 256 x 256 (chi = 2.4, tau = 0.8, kappa = 0.01) in FP32: 1e-5 after 100 steps."""
     p = inputs.ternary_gauss(steps=100)
     sim = mclb.Simulation.from_problem(p, precision="fp32", kernel=kernel)
     orc = Oracle.from_problem(p)
@@ -110,6 +110,21 @@ def test_ternary_256_fp32(kernel):
     assert np.max(np.abs(gm["rho"] - om["rho"])) < 1e-5
     assert np.max(np.abs(gm["U"] - om["U"])) < 1e-5
     assert np.max(np.abs(gm["mu"] - om["mu"])) < 1e-4
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_slab_phase_separating_fp32(kernel):
+    """A phase-separating case in FP32: the polymer/solvent | non-solvent slab (paper's
+    ternary chi set, sharp initial contacts) on 256 x 64, 300 steps."""
+    p = inputs.slab(256, 64, steps=300)
+    sim = mclb.Simulation.from_problem(p, precision="fp32", kernel=kernel)
+    orc = Oracle.from_problem(p)
+    sim.step(300)
+    orc.run(300)
+    assert sim.status() == 0
+    gm, om = sim.moments(), orc.moments()
+    assert np.max(np.abs(gm["rho"] - om["rho"])) < 1e-5
+    assert np.max(np.abs(gm["U"] - om["U"])) < 1e-5
 
 
 def test_fused_matches_staged_fp32():
