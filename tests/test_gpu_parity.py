@@ -29,7 +29,7 @@ def built():
 
 def _chi(n, seed):
     r = inputs.uniform(seed, n * n, 3).reshape(n, n)
-    c = 2.0 + r + r.T
+    c = 2.0 + (r + r.T)
     np.fill_diagonal(c, 0.0)
     return c
 
