@@ -45,6 +45,7 @@ def workloads():
     from paper_0704_3444_gb300 import inputs
     return {
         "n5_2048x2048": lambda: inputs.multi_uniform(),
+        "n5_1024x1024": lambda: inputs.multi_uniform(1024, 1024, name="n5_1024x1024"),
         "ternary_256x256": lambda: inputs.ternary_gauss(),
         "binary_64x64": lambda: inputs.binary_noise(precision="fp32"),
         "slab_8192x2048": lambda: inputs.slab(),
