@@ -241,7 +241,9 @@ def main():
     ap.add_argument("--impl", default="mclb", choices=["mclb", "reference"])
     ap.add_argument("--workload", default="n5_2048x2048")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
+    ap.add_argument("--kernel", default="fused", choices=["fused", "staged"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -267,8 +269,8 @@ def main():
     prob = workloads()[args.workload]()
     N, S = prob.ncomp, prob.sites
 
-    sim = mclb.Simulation.from_problem(prob, precision=args.precision,
-                                       kernel=mclb.KERNEL_FUSED, stream=sptr)
+    kern = mclb.KERNEL_FUSED if args.kernel == "fused" else mclb.KERNEL_STAGED
+    sim = mclb.Simulation.from_problem(prob, precision=args.precision, kernel=kern, stream=sptr)
     launches = sim.launches_per_step
     bytes_step = sim.bytes_per_step
     sim.step(args.warmup)
@@ -301,13 +303,13 @@ def main():
     # end to end through the C ABI with host buffers: H2D of the initial fields from pinned
     # memory, every step's status word back, and the final rho/U fields to the host
     e2e = None
-    if rank == 0 or world > 1:
+    if not args.no_e2e:
         rho_h = torch.from_numpy(prob.rho).pin_memory().numpy()
         u_h = torch.from_numpy(prob.u).pin_memory().numpy()
         out_rho = torch.empty(prob.rho.shape, dtype=torch.float64).pin_memory().numpy()
         out_u = torch.empty(prob.u.shape, dtype=torch.float64).pin_memory().numpy()
         sim2 = mclb.Simulation(N, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
-                               prob.kappa, prob.force, args.precision, mclb.KERNEL_FUSED, sptr)
+                               prob.kappa, prob.force, args.precision, kern, sptr)
         sim2.init_fields(rho_h, u_h)
         sim2.step(args.warmup)
         sim2.status()
@@ -359,7 +361,8 @@ def main():
         "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-storage/f32", "fp16": "f16-storage/f32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "ncomp": N,
-                   "precision": args.precision, "schedule": "fused single pass",
+                   "precision": args.precision,
+                   "schedule": "fused single pass" if args.kernel == "fused" else "staged, 3 launches",
                    "l2": "distributions (2 x %.0f MB) exceed the 129 MB L2; no flush" %
                          (bytes_step / 2 / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
