@@ -113,7 +113,7 @@ void fill_problem(const mclb_params* p, int hx, Problem& P)
     P.S = (long long)p->nx * p->ny;
     P.hx = hx;
     P.pitch = 2LL * hx + (long long)((p->nx + ROW_ALIGN - 1) / ROW_ALIGN) * ROW_ALIGN;
-    P.plane = P.pitch * p->ny;
+    P.plane = P.pitch * Q * p->ny;
     P.tau = p->tau;
     P.theta = p->theta > 0.0 ? p->theta : 1.0 / 3.0;
     P.kappa = p->kappa;
@@ -186,11 +186,13 @@ int make_tmap(mclb_handle h, int b)
     if (!fn) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled unavailable");
     const Problem& P = h->P;
     const size_t sz = h->tab->storage_bytes;
-    cuuint64_t dims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, (cuuint64_t)(P.N * Q)};
-    cuuint64_t strides[2] = {(cuuint64_t)(P.pitch * sz), (cuuint64_t)(P.plane * sz)};
-    cuuint32_t box[3] = {(cuuint32_t)(h->plan.W + 2 * P.hx), 1u, (cuuint32_t)(P.N * Q)};
-    cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = fn(&h->tmap[b], h->tab->tma_type, 3, h->f[b], dims, strides, box, estr,
+    // 4-D view (x, velocity, row, component); one box = one source row of every line
+    cuuint64_t dims[4] = {(cuuint64_t)P.pitch, (cuuint64_t)Q, (cuuint64_t)P.ny, (cuuint64_t)P.N};
+    cuuint64_t strides[3] = {(cuuint64_t)(P.pitch * sz), (cuuint64_t)(Q * P.pitch * sz),
+                             (cuuint64_t)(P.plane * sz)};
+    cuuint32_t box[4] = {(cuuint32_t)(h->plan.W + 2 * P.hx), (cuuint32_t)Q, 1u, (cuuint32_t)P.N};
+    cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    CUresult r = fn(&h->tmap[b], h->tab->tma_type, 4, h->f[b], dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -319,7 +321,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
             return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
         h->own_stream = true;
     }
-    h->fbytes = (size_t)P.plane * P.N * Q * h->tab->storage_bytes;
+    h->fbytes = (size_t)P.plane * P.N * h->tab->storage_bytes;
     const size_t cbytes = (h->precision == MCLB_FP64) ? sizeof(double) : sizeof(float);
     for (int b = 0; b < 2; ++b) {
         if (cudaMalloc(&h->f[b], h->fbytes) != cudaSuccess)

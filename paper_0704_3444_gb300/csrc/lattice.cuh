@@ -77,8 +77,8 @@ struct StepParams {
     int nx, ny;
     long long S;
     int hx;               // ghost columns per side
-    long long pitch;      // elements per row
-    long long plane;      // elements per plane
+    long long pitch;      // elements per (row, velocity) line
+    long long plane;      // elements per component (ny * 9 * pitch)
     C omega;              // 1 / tau
     C fcoef;              // 1 - 1/(2 tau), Eq. definef
     C gx, gy;             // body acceleration
@@ -137,14 +137,21 @@ __device__ __forceinline__ int wrap_add(int a, int d, int n)
     return a;
 }
 
-// Element offset of (plane, y, x) with 0 <= x < nx in the ghost-padded layout.
+// Offset of the start (ghosts included) of the line of component s, row y, velocity i.
 template <typename C>
-__device__ __forceinline__ long long fidx(const StepParams<C>& p, int plane, int y, int x)
+__device__ __forceinline__ long long line_off(const StepParams<C>& p, int s, int y, int i)
 {
-    return (long long)plane * p.plane + (long long)y * p.pitch + p.hx + x;
+    return ((long long)s * p.ny + y) * (Q * p.pitch) + (long long)i * p.pitch;
 }
 
-// Store one distribution value at column x of a row (row points at the row start,
+// Element offset of (s, i, y, x) with 0 <= x < nx in the ghost-padded layout.
+template <typename C>
+__device__ __forceinline__ long long fidx(const StepParams<C>& p, int s, int i, int y, int x)
+{
+    return line_off(p, s, y, i) + p.hx + x;
+}
+
+// Store one distribution value at column x of a line (row points at the line start,
 // ghosts included) and at every ghost column that repeats column x.
 template <typename T, typename C>
 __device__ __forceinline__ void store_row(T* row, int x, int nx, int hx, C v)

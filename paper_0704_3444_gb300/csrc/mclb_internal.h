@@ -16,19 +16,21 @@ constexpr int ROW_ALIGN = 128;  // data columns per row are padded to a multiple
 // Everything a launcher needs to know about one simulation, in FP64 as given at
 // the boundary; each precision unit converts it to its own kernel parameters.
 //
-// Distribution layout (every schedule): plane p = s * 9 + i, row y, column x at
-//   p * plane + y * pitch + hx + x,
-// where hx ghost columns on each side of a row repeat the periodic neighbours
-// (ghost column g in [-hx, 0) u [nx, nx + hx) holds column g mod nx) and the
-// row is padded to pitch = 2 hx + roundup(nx, ROW_ALIGN) elements.  Every kernel
-// that writes distributions also writes the ghosts, so that the fused kernel can
-// move whole aligned row segments with TMA.
+// Distribution layout (every schedule): component s, row y, velocity i, column x at
+//   ((s * ny + y) * 9 + i) * pitch + hx + x,
+// i.e. the nine velocity lines of one component row are adjacent, so that they
+// sit at small constant offsets from one address and one source row of every
+// component is a single 4-D TMA box.  hx ghost columns on each side of a line
+// repeat the periodic neighbours (ghost column g in [-hx, 0) u [nx, nx + hx)
+// holds column g mod nx) and a line is padded to pitch = 2 hx + roundup(nx,
+// ROW_ALIGN) elements.  Every kernel that writes distributions also writes the
+// ghosts, so that the fused kernel moves whole aligned row segments with TMA.
 struct Problem {
     int N, nx, ny;
     long long S;            // nx * ny sites
     int hx;                 // ghost columns per side
-    long long pitch;        // elements per row
-    long long plane;        // elements per plane = pitch * ny
+    long long pitch;        // elements per (row, velocity) line
+    long long plane;        // elements per component = ny * 9 * pitch
     double tau, theta, kappa, gx, gy;
     double chi[NMAX * NMAX];
     double m[NMAX];

@@ -117,34 +117,65 @@ __device__ __forceinline__ C site_psi(const StepParams<C>& p, const C (&r)[N])
     return psi;
 }
 
+// The nine products v_i . (x, y) of one vector, formed without multiplying by 0 or
+// +-1 (i is a compile-time constant once the direction loops are unrolled).
+template <typename C>
+struct VDots {
+    C x, y, sp, sm;  // x, y, x + y, x - y
+    __device__ __forceinline__ VDots(C x_, C y_) : x(x_), y(y_), sp(x_ + y_), sm(x_ - y_) {}
+    __device__ __forceinline__ C operator()(int i) const
+    {
+        switch (i) {
+            case 1: return x;
+            case 2: return y;
+            case 3: return -x;
+            case 4: return -y;
+            case 5: return sp;
+            case 6: return -sm;
+            case 7: return -sp;
+            case 8: return sm;
+            default: return C(0);
+        }
+    }
+};
+
 // Velocity-dependent part of the equilibrium, shared by every component:
 // e_i = w_i (1 + 3 v_i.u + 9/2 (v_i.u)^2 - 3/2 u.u), so that f^{s,e}_i = rho^s e_i
 // (Sec. 3 equilibrium moments, all components built on the barycentric u).
 template <typename C>
 __device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
 {
-    const C uu = ux * ux + uy * uy;
+    const C base = C(1) - C(1.5) * (ux * ux + uy * uy);
+    const VDots<C> du(ux, uy);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const C cu = C(vx(i)) * ux + C(vy(i)) * uy;
-        e[i] = wq<C>(i) * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+        if (i == 0) {
+            e[0] = wq<C>(0) * base;
+        } else {
+            const C cu = du(i);
+            e[i] = wq<C>(i) * fma(cu, fma(C(4.5), cu, C(3)), base);
+        }
     }
 }
 
 // Post-collision populations of one component (Eq. ssLB):
 //   f* = f + (f^e - f)/tau + F,  f^e_i = rho^s e_i,
-//   F_i = w_i [3 rho^s (v_i.a) + 9 (v_i.a)(v_i.j) - 3 a.j]   (Eqs. ff1-ff3, j = rho^s u^s).
+//   F_i = w_i [3 rho^s (v_i.a) + 9 (v_i.a)(v_i.j) - 3 a.j]   (Eqs. ff1-ff3, j = rho^s u^s),
+// evaluated as f (1 - 1/tau) + (rho^s/tau) e_i + w_i [(v_i.a)(9 v_i.j + 3 rho^s) - 3 a.j].
 template <typename C>
 __device__ __forceinline__ void collide(const StepParams<C>& p, const C (&f)[Q], const C (&e)[Q],
                                         C r, C jx, C jy, C ax, C ay, C (&out)[Q])
 {
-    const C aj = ax * jx + ay * jy;
+    const VDots<C> da(ax, ay), dj(jx, jy);
+    const C m3aj = C(-3) * (ax * jx + ay * jy);
+    const C r3 = C(3) * r;
+    const C omr = p.omega * r;
+    const C keep = C(1) - p.omega;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const C ca = C(vx(i)) * ax + C(vy(i)) * ay;
-        const C cj = C(vx(i)) * jx + C(vy(i)) * jy;
-        const C F = wq<C>(i) * (C(3) * r * ca + C(9) * ca * cj - C(3) * aj);
-        out[i] = f[i] + (r * e[i] - f[i]) * p.omega + F;
+        const C F = (i == 0) ? wq<C>(0) * m3aj
+                             : wq<C>(i) * fma(da(i), fma(C(9), dj(i), r3), m3aj);
+        out[i] = fma(keep, f[i], fma(omr, e[i], F));
     }
 }
 

@@ -23,7 +23,7 @@ __device__ __forceinline__ typename Storage<T>::C pull(const T* __restrict__ f,
     using C = typename Storage<T>::C;
     const int xs = wrap_add(x, -vx(i), p.nx);
     const int ys = wrap_add(y, -vy(i), p.ny);
-    C v = Storage<T>::load(f + fidx(p, s * Q + i, ys, xs));
+    C v = Storage<T>::load(f + fidx(p, s, i, ys, xs));
     if constexpr (Storage<T>::shifted) v += p.shift[s * Q + i];
     return v;
 }
@@ -143,8 +143,7 @@ k_collide(const T* __restrict__ fin, T* __restrict__ fout,
         for (int i = 0; i < Q; ++i) {
             C v = out[i];
             if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
-            store_row(fout + (long long)(s * Q + i) * p.plane + (long long)y * p.pitch, x, p.nx,
-                      p.hx, v);
+            store_row(fout + line_off(p, s, y, i), x, p.nx, p.hx, v);
         }
     }
     if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
@@ -174,8 +173,7 @@ k_init(const double* __restrict__ rho, const double* __restrict__ u, T* __restri
             C v = wq<C>(i) * C(rho[s * p.S + t]) *
                   (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
             if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
-            store_row(f + (long long)(s * Q + i) * p.plane + (long long)y * p.pitch, x, p.nx, p.hx,
-                      v);
+            store_row(f + line_off(p, s, y, i), x, p.nx, p.hx, v);
         }
     }
 }
@@ -211,8 +209,7 @@ k_set_state(const double* __restrict__ in, T* __restrict__ f,
         for (int s = 0; s < N; ++s) {
             C v = C(in[(s * Q + i) * p.S + t]);
             if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
-            store_row(f + (long long)(s * Q + i) * p.plane + (long long)y * p.pitch, x, p.nx, p.hx,
-                      v);
+            store_row(f + line_off(p, s, y, i), x, p.nx, p.hx, v);
         }
     }
 }

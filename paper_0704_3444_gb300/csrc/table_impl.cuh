@@ -63,40 +63,53 @@ struct Launch {
     template <int N>
     static FusedPlan plan_n(const Problem& P, int sm_count)
     {
-        FusedPlan pl{};
-        pl.ok = false;
-        const size_t limit = 227 * 1024;
-        const int wmax = std::min(FUSED_MAX_W, (P.nx + 31) / 32 * 32);
-        for (int W = 128; W >= 32; W /= 2) {
-            if (W > wmax && W > 32) continue;
+        // Pick the strip width W and stage count NS that keep the most warps resident
+        // per SM (shared memory and the 2048-thread limit decide), preferring at least
+        // two rows of copy lookahead (NS >= 7) and then the wider strip.
+        FusedPlan best{};
+        best.ok = false;
+        const size_t limit = 227 * 1024, per_sm_smem = 228 * 1024;
+        const int wcap = std::max(32, (P.nx + 31) / 32 * 32);
+        int best_score = -1;
+        for (int W = 32; W <= FUSED_MAX_W; W *= 2) {
+            if (W > wcap && W > 32) break;
+            const int threads = N * W + 32;
+            if (threads > FUSED_MAX_THREADS) break;
             for (int NS = 8; NS >= 6; --NS) {
                 const size_t sm = fused_smem_bytes<T, N>(W, NS, P.hx);
-                if (sm <= limit) {
-                    pl.W = W;
-                    pl.NS = NS;
-                    pl.smem = sm;
-                    pl.ok = true;
-                    break;
+                if (sm > limit) continue;
+                const int by_smem = (int)(per_sm_smem / (sm + 1024));
+                const int by_threads = 2048 / threads;
+                const int ctas = std::min(by_smem, by_threads);
+                if (ctas < 1) continue;
+                const int warps = ctas * ((threads + 31) / 32);
+                const int score = warps * 64 + (NS >= 7 ? 32 : 0) + W / 4 + NS;
+                if (score > best_score) {
+                    best_score = score;
+                    best.W = W;
+                    best.NS = NS;
+                    best.smem = sm;
+                    best.ok = true;
                 }
             }
-            if (pl.ok) break;
         }
-        if (!pl.ok) return pl;
+        if (!best.ok) return best;
         if (cudaFuncSetAttribute(k_fused<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)limit) != cudaSuccess) {
-            pl.ok = false;
-            return pl;
+            best.ok = false;
+            return best;
         }
-        pl.nstrips = (P.nx + pl.W - 1) / pl.W;
-        // resident CTAs per SM from shared memory, then about two waves of tiles with
-        // segments no shorter than 16 rows
-        const int per_sm = std::max(1, (int)((228 * 1024) / (pl.smem + 1024)));
+        best.nstrips = (P.nx + best.W - 1) / best.W;
+        const int threads = N * best.W + 32;
+        const int per_sm = std::max(1, std::min((int)(per_sm_smem / (best.smem + 1024)),
+                                                2048 / threads));
+        // about two waves of tiles, segments no shorter than 16 rows
         const int target = 2 * per_sm * std::max(1, sm_count);
-        int nsegs = std::max(1, (target + pl.nstrips - 1) / pl.nstrips);
+        int nsegs = std::max(1, (target + best.nstrips - 1) / best.nstrips);
         nsegs = std::min(nsegs, std::max(1, P.ny / 16));
-        pl.H = (P.ny + nsegs - 1) / nsegs;
-        pl.nsegs = (P.ny + pl.H - 1) / pl.H;
-        return pl;
+        best.H = (P.ny + nsegs - 1) / nsegs;
+        best.nsegs = (P.ny + best.H - 1) / best.H;
+        return best;
     }
 
     static FusedPlan plan_fused(const Problem& P, int sm_count)
@@ -122,8 +135,8 @@ struct Launch {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
         MCLB_DISPATCH_N(P.N, {
-            k_fused<T, NN><<<grid, pl.W + 32, pl.smem, st>>>(*tmap_in, (T*)fout, p, pl.W, pl.NS,
-                                                             pl.H);
+            k_fused<T, NN><<<grid, NN * pl.W + 32, pl.smem, st>>>(*tmap_in, (T*)fout, p, pl.W,
+                                                                  pl.NS, pl.H);
             return cudaGetLastError();
         });
     }
