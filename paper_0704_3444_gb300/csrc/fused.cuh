@@ -19,9 +19,11 @@
 // index modulo ny.
 //
 // Threads.  One warp group of W threads per component: thread (s, c) handles
-// component s at column x0 + c in every phase, so a CTA runs N*W threads on the
-// interior plus one helper warp, whose lanes compute the halo columns of the
-// moment and nu rings and whose lane 0 issues the TMA copies.  Every wait on an
+// component s at column x0 + c in every phase.  W "site" threads compute, once per
+// site and one row ahead, what all components share: rho, 1/rho, ln rho, the
+// common part of the Flory-Huggins potential and the nine equilibrium weights e_i.
+// One helper warp computes the halo columns of the rings and its last lane issues
+// the TMA copies.  Every wait on an
 // mbarrier is bounded; on expiry the CTA sets STATUS_TIMEOUT, drains the copies it
 // issued (again bounded) and returns.
 #pragma once
@@ -108,142 +110,158 @@ __device__ __forceinline__ float to_c<__half>(__half v) { return __half2float(v)
 
 __host__ __device__ constexpr size_t round_up_sz(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
-template <typename T, int N>
-__host__ __device__ constexpr size_t fused_stage_bytes(int W, int hx)
-{
-    return round_up_sz((size_t)N * Q * (W + 2 * hx) * sizeof(T), 128);
-}
-
-template <typename T, int N>
-__host__ __device__ constexpr size_t fused_smem_bytes(int W, int NS, int hx)
-{
+// Compile-time geometry of one CTA: W columns per strip, NS stages, hx ghost columns.
+template <typename T, int N, int W>
+struct FusedGeom {
     using C = typename Storage<T>::C;
-    return FUSED_HDR + (size_t)NS * fused_stage_bytes<T, N>(W, hx) +
-           (size_t)4 * 3 * N * (W + 4) * sizeof(C) + (size_t)4 * N * (W + 2) * sizeof(C);
-}
+    static constexpr int NS = 6;                       // source-row stages
+    static constexpr int HX = (16 / (int)sizeof(T)) < 4 ? 4 : 16 / (int)sizeof(T);
+    static constexpr int WI = W + 2 * HX;              // staged columns per line
+    static constexpr int RW = W + 4;                   // moment ring: x0-2 .. x0+W+1
+    static constexpr int VW = W + 2;                   // nu ring:     x0-1 .. x0+W
+    static constexpr int NCT = N * W;                  // component threads
+    static constexpr int THREADS = NCT + W + 32;       // + site threads + helper warp
+    static constexpr int PRODUCER = THREADS - 1;       // helper lane issuing the copies
+    static constexpr size_t STAGE_BYTES = round_up_sz((size_t)N * Q * WI * sizeof(T), 128);
+    static constexpr size_t STAGE_ELEMS = STAGE_BYTES / sizeof(T);
+    // rings (elements of C)
+    static constexpr int MOM = 4 * 3 * N * RW;         // slot, (rho, jx, jy), component, column
+    static constexpr int NU = 4 * N * VW;              // slot, component, column
+    static constexpr int SH = 4 * 4 * VW;              // slot, (rho, 1/rho, ln rho, G), column
+    static constexpr int EQ = 4 * Q * W;               // slot, velocity, column
+    static constexpr size_t SMEM = FUSED_HDR + NS * STAGE_BYTES + (size_t)(MOM + NU + SH + EQ) * sizeof(C);
+};
 
 constexpr int FUSED_MAX_THREADS = 1024;
 
-template <typename T, int N>
-__global__ void __launch_bounds__(FUSED_MAX_THREADS, 1)
+template <typename T, int N, int W>
+__global__ void __launch_bounds__(FusedGeom<T, N, W>::THREADS, 1)
 k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
-        const __grid_constant__ StepParams<typename Storage<T>::C> p, const int W, const int NS,
-        const int H)
+        const __grid_constant__ StepParams<typename Storage<T>::C> p, const int H)
 {
+    using G = FusedGeom<T, N, W>;
     using C = typename Storage<T>::C;
-    const int hx = p.hx;
-    const int WI = W + 2 * hx;   // staged columns per line
-    const int RW = W + 4;        // moment ring columns: x0-2 .. x0+W+1
-    const int VW = W + 2;        // nu ring columns:     x0-1 .. x0+W
+    constexpr int NS = G::NS, HX = G::HX, WI = G::WI, RW = G::RW, VW = G::VW, NCT = G::NCT;
     const int x0 = blockIdx.x * W;
     const int y0 = blockIdx.y * H;
     const int Hc = min(H, p.ny - y0);
     const int nrows = Hc + 6;    // source rows k <-> global row y0 - 3 + k (mod ny)
     const int tid = threadIdx.x;
-    const int nct = N * W;
-    const bool helper = tid >= nct;
-    const int g = helper ? 0 : tid / W;   // component of this thread
-    const int c = helper ? 0 : tid - g * W;
-    const int lane = tid - nct;           // helper lane
+    const bool comp = tid < NCT;
+    const bool site = !comp && tid < NCT + W;
+    const int g = comp ? tid / W : 0;                  // component of a component thread
+    const int c = comp ? tid % W : (site ? tid - NCT : 0);
+    const int lane = tid - NCT - W;                    // helper lane (>= 0 in the helper warp)
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 8 * FUSED_MAX_NS);
-    const size_t stage_elems = fused_stage_bytes<T, N>(W, hx) / sizeof(T);
     T* stages = reinterpret_cast<T*>(smem + FUSED_HDR);
-    C* mom = reinterpret_cast<C*>(smem + FUSED_HDR + NS * stage_elems * sizeof(T));
-    C* nur = mom + 4 * 3 * N * RW;
-    // moment ring: slot, quantity (rho, jx, jy), component, column
-    auto mom_at = [&](int slot, int q, int s, int col) -> C& {
-        return mom[((slot * 3 + q) * N + s) * RW + col];
-    };
+    C* mom = reinterpret_cast<C*>(smem + FUSED_HDR + NS * G::STAGE_BYTES);
+    C* nur = mom + G::MOM;
+    C* shr = nur + G::NU;
+    C* eqr = shr + G::SH;
+    auto MOMI = [](int slot, int q, int s, int col) { return ((slot * 3 + q) * N + s) * RW + col; };
+    auto SHI = [](int slot, int q, int col) { return (slot * 4 + q) * VW + col; };
+    constexpr int SH_RHO = 0, SH_INV = 1, SH_LN = 2, SH_G = 3;
 
-    const uint32_t tx_bytes = (uint32_t)(N * Q * WI * sizeof(T));
-    if (tid == nct) {
+    if (tid == G::PRODUCER) {
         for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
+    constexpr uint32_t TX = (uint32_t)(N * Q * WI * sizeof(T));
     auto issue = [&](int k) {
         const int st = k % NS;
         int row = (y0 - 3 + k) % p.ny;
         row += row < 0 ? p.ny : 0;
-        mbar_arrive_expect_tx(&full[st], tx_bytes);
-        tma_load_row(stages + st * stage_elems, &tmap, &full[st], x0, row);
+        mbar_arrive_expect_tx(&full[st], TX);
+        tma_load_row(stages + st * G::STAGE_ELEMS, &tmap, &full[st], x0, row);
     };
     int issued = 0;
-    if (tid == nct) {
+    if (tid == G::PRODUCER) {
         const int pre = min(NS, nrows);
         for (int k = 0; k < pre; ++k) issue(k);
         issued = pre;
     }
     auto wait_row = [&](int k) -> bool { return mbar_wait(&full[k % NS], (k / NS) & 1); };
-    auto stage_of = [&](int k) -> const T* { return stages + (k % NS) * stage_elems; };
+    auto stage_of = [&](int k) -> const T* { return stages + (k % NS) * G::STAGE_ELEMS; };
 
-    // per-thread constants of its component
+    // constants of this thread's component, kept in registers
     C shift[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) shift[i] = Storage<T>::shifted ? p.shift[g * Q + i] : C(0);
+    C chi_row[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) chi_row[u] = p.chi[g * N + u];
+    const C th_m = p.th_m[g], logc = p.logc[g], minv1 = p.m_inv_m1[g];
+    const bool has_log = (p.log_mask >> g) & 1u;
 
-    // moments rho, jx, jy of component s at ring column cc of the row whose source
-    // rows are sr[0..2] (dy = -1, 0, +1)
-    auto moments_at = [&](const T* const (&sr)[3], int s, int cc, int slot, const C* sh) {
+    // zeroth and first moments of component s at moment-ring column cc (row from sr)
+    auto moments_at = [&](const T* const (&sr)[3], int s, int cc, int slot, const C (&sh)[Q]) {
         C v[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            v[i] = to_c<T>(sr[vy(i) + 1][(s * Q + i) * WI + cc - 2 + hx - vx(i)]);
+            v[i] = to_c<T>(sr[vy(i) + 1][(s * Q + i) * WI + cc - 2 + HX - vx(i)]);
             if constexpr (Storage<T>::shifted) v[i] += sh[i];
         }
         C r = C(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) r += v[i];
-        mom_at(slot, 0, s, cc) = r;
-        mom_at(slot, 1, s, cc) = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
-        mom_at(slot, 2, s, cc) = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
+        mom[MOMI(slot, 0, s, cc)] = r;
+        mom[MOMI(slot, 1, s, cc)] = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
+        mom[MOMI(slot, 2, s, cc)] = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
     };
 
-    // nu^s at nu-ring column vc of row r (moment slots rs[0..2] for rows r-1, r, r+1)
-    auto nu_at = [&](const int (&rs)[3], int s, int vc) -> C {
+    // per-site terms of nu shared by all components at nu column vc (moment slot ms):
+    // rho, 1/rho, ln rho and G = -theta (sum_t phi^t/m^t + 1/2 sum chi phi phi)
+    auto site_terms = [&](int ms, int vc, int ss) {
         const int cc = vc + 1;
         C r[N];
         C rho = C(0);
 #pragma unroll
         for (int t = 0; t < N; ++t) {
-            r[t] = mom_at(rs[1], 0, t, cc);
+            r[t] = mom[MOMI(ms, 0, t, cc)];
             rho += r[t];
         }
-        const C inv_rho = C(1) / rho;
-        C phi[N];
-#pragma unroll
-        for (int t = 0; t < N; ++t) phi[t] = r[t] * inv_rho;
-        C sum_phi_m = C(0);
-#pragma unroll
-        for (int t = 0; t < N; ++t) sum_phi_m += phi[t] * p.inv_m[t];
-        C quad = C(0);
+        const C inv = C(1) / rho;
+        C sm = C(0), quad = C(0);
 #pragma unroll
         for (int t = 0; t < N; ++t) {
+            sm += r[t] * p.inv_m[t];
             C acc = C(0);
 #pragma unroll
-            for (int u = 0; u < N; ++u) acc += p.chi[t * N + u] * phi[u];
-            quad += C(0.5) * phi[t] * acc;
+            for (int u = 0; u < N; ++u) acc += p.chi[t * N + u] * r[u];
+            quad += r[t] * acc;
         }
-        C chiphi = C(0);
-#pragma unroll
-        for (int u = 0; u < N; ++u) chiphi += p.chi[s * N + u] * phi[u];
-        C rs_own = mom_at(rs[1], 0, s, cc);
+        shr[SHI(ss, SH_RHO, vc)] = rho;
+        shr[SHI(ss, SH_INV, vc)] = inv;
+        shr[SHI(ss, SH_LN, vc)] = dev_log(rho);
+        shr[SHI(ss, SH_G, vc)] = -p.theta * (sm * inv + C(0.5) * quad * inv * inv);
+        return inv;
+    };
+
+    // nu^s at nu column vc of the row whose moments sit in slots rs[0..2] (rows r-1, r, r+1)
+    // and whose site terms sit in slot ss
+    auto nu_comp = [&](const int (&rs)[3], int ss, int s, int vc, const C (&chi_s)[N], C thm,
+                       C lc, C mi1, bool lg) -> C {
+        const int cc = vc + 1;
         C acc = C(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) acc += wq<C>(i) * (mom_at(rs[vy(i) + 1], 0, s, cc + vx(i)) - rs_own);
-        const C lap = C(6) * acc;
-        C logs = -p.th_m[s] * dev_log(rho);
-        if (p.log_mask & (1u << s)) {
-            const C fl = p.log_floor * rho;
-            logs += p.logc[s] * dev_log(rs_own > fl ? rs_own : fl);
+        for (int u = 0; u < N; ++u) acc += chi_s[u] * mom[MOMI(rs[1], 0, u, cc)];
+        const C inv = shr[SHI(ss, SH_INV, vc)];
+        const C own = mom[MOMI(rs[1], 0, s, cc)];
+        C lap = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) lap += wq<C>(i) * (mom[MOMI(rs[vy(i) + 1], 0, s, cc + vx(i))] - own);
+        C logs = -thm * shr[SHI(ss, SH_LN, vc)];
+        if (lg) {
+            const C fl = p.log_floor * shr[SHI(ss, SH_RHO, vc)];
+            logs += lc * dev_log(own > fl ? own : fl);
         }
-        const C bulk = p.theta * (p.m_inv_m1[s] - sum_phi_m + chiphi - quad);
-        return logs + bulk - p.kappa * lap;
+        return logs + p.theta * (mi1 + acc * inv) + shr[SHI(ss, SH_G, vc)] - p.kappa * (C(6) * lap);
     };
 
     bool ok = wait_row(0);
@@ -257,9 +275,9 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         // ---- phase A: moments of row j-2 into ring slot j&3 (source rows j .. j+2)
         {
             const T* const sr[3] = {stage_of(j + 2), stage_of(j + 1), stage_of(j)};
-            if (!helper) {
+            if (comp) {
                 moments_at(sr, g, c + 2, j & 3, shift);
-            } else if (lane < 4 * N) {
+            } else if (lane >= 0 && lane < 4 * N) {
                 const int hc = lane / N, s = lane - hc * N;
                 C sh[Q];
 #pragma unroll
@@ -269,7 +287,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         }
         __syncthreads();
         if (*abort_flag) break;
-        if (tid == nct && j >= 3) {
+        if (tid == G::PRODUCER && j >= 3) {
             const int k = j - 3 + NS;  // reuse the stage of row j-3, last read by phase C of j-1
             if (k < nrows) {
                 issue(k);
@@ -277,47 +295,67 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             }
         }
 
-        // ---- phase B: nu of row j-3 into ring slot j&3 (moment rows j-4 .. j-2)
-        if (j >= 2) {
-            const int rs[3] = {(j - 2) & 3, (j - 1) & 3, j & 3};
-            C* nn = nur + (j & 3) * N * VW;
-            if (!helper) {
-                nn[g * VW + c + 1] = nu_at(rs, g, c + 1);
-            } else if (lane < 2 * N) {
+        // ---- phase B: nu of row j-3 (slot j&3); site terms and equilibrium weights of
+        //      row j-2 (slot j&3) for the next iterations
+        if (comp) {
+            if (j >= 2) {
+                const int rs[3] = {(j - 2) & 3, (j - 1) & 3, j & 3};
+                nur[(j & 3) * N * VW + g * VW + c + 1] =
+                    nu_comp(rs, (j - 1) & 3, g, c + 1, chi_row, th_m, logc, minv1, has_log);
+            }
+        } else if (site) {
+            const int ms = j & 3;
+            const C inv = site_terms(ms, c + 1, ms);
+            C jx = C(0), jy = C(0);
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                jx += mom[MOMI(ms, 1, t, c + 2)];
+                jy += mom[MOMI(ms, 2, t, c + 2)];
+            }
+            C e[Q];
+            eq_weights(jx * inv, jy * inv, e);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) eqr[(ms * Q + i) * W + c] = e[i];
+            const int r = j - 2;
+            if (r >= 0 && r < Hc && x0 + c < p.nx) {
+                const C rho = shr[SHI(ms, SH_RHO, c + 1)];
+                if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
+            }
+        } else if (lane < 2 * N) {
+            if (j >= 2) {
                 const int hv = lane / N, s = lane - hv * N;
                 const int vc = hv == 0 ? 0 : W + 1;
-                nn[s * VW + vc] = nu_at(rs, s, vc);
+                const int rs[3] = {(j - 2) & 3, (j - 1) & 3, j & 3};
+                C chi_s[N];
+#pragma unroll
+                for (int u = 0; u < N; ++u) chi_s[u] = p.chi[s * N + u];
+                nur[(j & 3) * N * VW + s * VW + vc] =
+                    nu_comp(rs, (j - 1) & 3, s, vc, chi_s, p.th_m[s], p.logc[s], p.m_inv_m1[s],
+                            (p.log_mask >> s) & 1u);
             }
+        } else if (lane < 2 * N + 2) {
+            site_terms(j & 3, lane == 2 * N ? 0 : W + 1, j & 3);
         }
         __syncthreads();
 
         // ---- phase C: collide row j-4 (source rows j-2 .. j, nu rows j-5 .. j-3)
-        if (j >= 4 && !helper) {
+        if (comp && j >= 4) {
             const int x = x0 + c;
-            const int r = j - 4;
             if (x < p.nx) {
                 const T* const sr[3] = {stage_of(j), stage_of(j - 1), stage_of(j - 2)};
                 C f[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    f[i] = to_c<T>(sr[vy(i) + 1][(g * Q + i) * WI + c + hx - vx(i)]);
+                    f[i] = to_c<T>(sr[vy(i) + 1][(g * Q + i) * WI + c + HX - vx(i)]);
                     if constexpr (Storage<T>::shifted) f[i] += shift[i];
                 }
-                const int ms = (j - 2) & 3;  // moment slot of row j-4
-                const int cc = c + 2;
-                C rho = C(0), jxt = C(0), jyt = C(0);
-#pragma unroll
-                for (int t = 0; t < N; ++t) {
-                    rho += mom_at(ms, 0, t, cc);
-                    jxt += mom_at(ms, 1, t, cc);
-                    jyt += mom_at(ms, 2, t, cc);
-                }
-                const C rg = mom_at(ms, 0, g, cc);
-                const C jxg = mom_at(ms, 1, g, cc);
-                const C jyg = mom_at(ms, 2, g, cc);
-                const C inv_rho = C(1) / rho;
+                const int ms = (j - 2) & 3;  // moment / equilibrium slot of row j-4
+                const C rg = mom[MOMI(ms, 0, g, c + 2)];
+                const C jxg = mom[MOMI(ms, 1, g, c + 2)];
+                const C jyg = mom[MOMI(ms, 2, g, c + 2)];
                 C e[Q];
-                eq_weights(jxt * inv_rho, jyt * inv_rho, e);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) e[i] = eqr[(ms * Q + i) * W + c];
                 // grad nu = 3 sum_i w_i v_i nu(r + v_i)
                 const C* vrow[3] = {nur + ((j - 2) & 3) * N * VW + g * VW,
                                     nur + ((j - 1) & 3) * N * VW + g * VW,
@@ -333,14 +371,13 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
                 const C ay = -p.fcoef * (C(3) * gy) + p.gy;
                 C out[Q];
                 collide(p, f, e, rg, jxg, jyg, ax, ay, out);
-                T* line = fout + line_off(p, g, y0 + r, 0);
+                T* line = fout + line_off(p, g, y0 + j - 4, 0);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     C v = out[i];
                     if constexpr (Storage<T>::shifted) v -= shift[i];
-                    store_row(line + i * p.pitch, x, p.nx, hx, v);
+                    store_row(line + i * p.pitch, x, p.nx, HX, v);
                 }
-                if (g == 0 && (!(rho > C(0)) || !isfinite(rho))) atomicOr(p.status, STATUS_NONFINITE);
             }
         }
     }
@@ -348,7 +385,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     if (*abort_flag) {
         if (tid == 0) atomicOr(p.status, STATUS_TIMEOUT);
         // drain the copies still in flight before the shared memory is released
-        if (tid == nct)
+        if (tid == G::PRODUCER)
             for (int k = j + 2; k < issued; ++k) wait_row(k);
     }
 }

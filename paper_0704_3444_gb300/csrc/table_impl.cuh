@@ -60,55 +60,45 @@ struct Launch {
         });
     }
 
+    template <int N, int W>
+    static void consider(FusedPlan& best, int& best_score, const Problem& P, int sm_count)
+    {
+        using G = FusedGeom<T, N, W>;
+        const size_t limit = 227 * 1024, per_sm_smem = 228 * 1024;
+        if (G::SMEM > limit || G::THREADS > FUSED_MAX_THREADS) return;
+        const int wcap = std::max(32, (P.nx + 31) / 32 * 32);
+        if (W > wcap && W > 32) return;
+        const int ctas = std::min((int)(per_sm_smem / (G::SMEM + 1024)), 2048 / G::THREADS);
+        if (ctas < 1) return;
+        const int warps = ctas * ((G::THREADS + 31) / 32);
+        const int score = warps * 4 + W / 32;  // most resident warps, then the wider strip
+        if (score <= best_score) return;
+        if (cudaFuncSetAttribute(k_fused<T, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)G::SMEM) != cudaSuccess)
+            return;
+        best_score = score;
+        best.W = W;
+        best.NS = G::NS;
+        best.smem = G::SMEM;
+        best.ok = true;
+        best.nstrips = (P.nx + W - 1) / W;
+        // one wave of tiles: as many row segments as resident CTAs allow, each as tall
+        // as possible (every segment re-reads 6 halo rows), at least 8 rows
+        const int slots = ctas * std::max(1, sm_count);
+        int nsegs = std::max(1, slots / best.nstrips);
+        nsegs = std::min(nsegs, std::max(1, P.ny / 8));
+        best.H = (P.ny + nsegs - 1) / nsegs;
+        best.nsegs = (P.ny + best.H - 1) / best.H;
+    }
+
     template <int N>
     static FusedPlan plan_n(const Problem& P, int sm_count)
     {
-        // Pick the strip width W and stage count NS that keep the most warps resident
-        // per SM (shared memory and the 2048-thread limit decide), preferring at least
-        // two rows of copy lookahead (NS >= 7) and then the wider strip.
         FusedPlan best{};
         best.ok = false;
-        const size_t limit = 227 * 1024, per_sm_smem = 228 * 1024;
-        const int wcap = std::max(32, (P.nx + 31) / 32 * 32);
-        int best_score = -1;
-        for (int W = 32; W <= FUSED_MAX_W; W *= 2) {
-            if (W > wcap && W > 32) break;
-            const int threads = N * W + 32;
-            if (threads > FUSED_MAX_THREADS) break;
-            for (int NS = 8; NS >= 6; --NS) {
-                const size_t sm = fused_smem_bytes<T, N>(W, NS, P.hx);
-                if (sm > limit) continue;
-                const int by_smem = (int)(per_sm_smem / (sm + 1024));
-                const int by_threads = 2048 / threads;
-                const int ctas = std::min(by_smem, by_threads);
-                if (ctas < 1) continue;
-                const int warps = ctas * ((threads + 31) / 32);
-                const int score = warps * 64 + (NS >= 7 ? 32 : 0) + W / 4 + NS;
-                if (score > best_score) {
-                    best_score = score;
-                    best.W = W;
-                    best.NS = NS;
-                    best.smem = sm;
-                    best.ok = true;
-                }
-            }
-        }
-        if (!best.ok) return best;
-        if (cudaFuncSetAttribute(k_fused<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)limit) != cudaSuccess) {
-            best.ok = false;
-            return best;
-        }
-        best.nstrips = (P.nx + best.W - 1) / best.W;
-        const int threads = N * best.W + 32;
-        const int per_sm = std::max(1, std::min((int)(per_sm_smem / (best.smem + 1024)),
-                                                2048 / threads));
-        // about two waves of tiles, segments no shorter than 16 rows
-        const int target = 2 * per_sm * std::max(1, sm_count);
-        int nsegs = std::max(1, (target + best.nstrips - 1) / best.nstrips);
-        nsegs = std::min(nsegs, std::max(1, P.ny / 16));
-        best.H = (P.ny + nsegs - 1) / nsegs;
-        best.nsegs = (P.ny + best.H - 1) / best.H;
+        int score = -1;
+        consider<N, 32>(best, score, P, sm_count);
+        consider<N, 64>(best, score, P, sm_count);
         return best;
     }
 
@@ -135,8 +125,13 @@ struct Launch {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
         MCLB_DISPATCH_N(P.N, {
-            k_fused<T, NN><<<grid, NN * pl.W + 32, pl.smem, st>>>(*tmap_in, (T*)fout, p, pl.W,
-                                                                  pl.NS, pl.H);
+            if (pl.W == 32) {
+                k_fused<T, NN, 32><<<grid, FusedGeom<T, NN, 32>::THREADS, pl.smem, st>>>(
+                    *tmap_in, (T*)fout, p, pl.H);
+            } else {
+                k_fused<T, NN, 64><<<grid, FusedGeom<T, NN, 64>::THREADS, pl.smem, st>>>(
+                    *tmap_in, (T*)fout, p, pl.H);
+            }
             return cudaGetLastError();
         });
     }
