@@ -124,18 +124,27 @@ struct FusedGeom {
     static constexpr int PRODUCER = THREADS - 1;       // helper lane issuing the copies
     static constexpr size_t STAGE_BYTES = round_up_sz((size_t)N * Q * WI * sizeof(T), 128);
     static constexpr size_t STAGE_ELEMS = STAGE_BYTES / sizeof(T);
-    // rings (elements of C)
-    static constexpr int MOM = 4 * 3 * N * RW;         // slot, (rho, jx, jy), component, column
-    static constexpr int NU = 4 * N * VW;              // slot, component, column
-    static constexpr int SH = 4 * 4 * VW;              // slot, (rho, 1/rho, ln rho, G), column
-    static constexpr int EQ = 4 * Q * W;               // slot, velocity, column
+    // rings (elements of C).  Slot counts follow from who reads a row after the barrier
+    // that follows its write: moments of row r are read until phase C two iterations
+    // later and are overwritten by the next phase A without a barrier in between (4);
+    // nu of row r is read by three collisions (3); the equilibrium weights of row r are
+    // written two iterations before their collision (3); the site terms of row r are
+    // read by the next phase B only (2).
+    static constexpr int MOM_SLOTS = 4, NU_SLOTS = 3, EQ_SLOTS = 3, SH_SLOTS = 2;
+    static constexpr int MOM = MOM_SLOTS * 3 * N * RW; // slot, (rho, jx, jy), component, column
+    static constexpr int NU = NU_SLOTS * N * VW;       // slot, component, column
+    static constexpr int SH = SH_SLOTS * 4 * VW;       // slot, (rho, 1/rho, ln rho, G), column
+    static constexpr int EQ = EQ_SLOTS * Q * W;        // slot, velocity, column
     static constexpr size_t SMEM = FUSED_HDR + NS * STAGE_BYTES + (size_t)(MOM + NU + SH + EQ) * sizeof(C);
+    // two CTAs per SM when both fit (shared memory incl. the per-CTA reserve, and
+    // registers: the launch bound then caps a thread at 65536 / (2 THREADS))
+    static constexpr int MIN_CTAS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
 };
 
 constexpr int FUSED_MAX_THREADS = 1024;
 
 template <typename T, int N, int W>
-__global__ void __launch_bounds__(FusedGeom<T, N, W>::THREADS, 1)
+__global__ void __launch_bounds__(FusedGeom<T, N, W>::THREADS, FusedGeom<T, N, W>::MIN_CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         const __grid_constant__ StepParams<typename Storage<T>::C> p, const int H)
 {
@@ -163,6 +172,8 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     C* eqr = shr + G::SH;
     auto MOMI = [](int slot, int q, int s, int col) { return ((slot * 3 + q) * N + s) * RW + col; };
     auto SHI = [](int slot, int q, int col) { return (slot * 4 + q) * VW + col; };
+    // ring slots of row r (relative): moments (r+2)&3, nu (r+3)%3, equilibrium (r+2)%3,
+    // site terms (r+2)&1
     constexpr int SH_RHO = 0, SH_INV = 1, SH_LN = 2, SH_G = 3;
 
     if (tid == G::PRODUCER) {
@@ -264,13 +275,24 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         return logs + p.theta * (mi1 + acc * inv) + shr[SHI(ss, SH_G, vc)] - p.kappa * (C(6) * lap);
     };
 
-    bool ok = wait_row(0);
-    ok = wait_row(1) && ok;
+    // columns whose value is repeated in a ghost column (one copy each when nx >= HX)
+    const bool simple_ghosts = p.nx >= HX;
+    const bool ghost_r = (x0 + c) < HX;
+    const bool ghost_l = (x0 + c) >= p.nx - HX;
+
+    bool ok = true;
+    if (!site) {
+        ok = wait_row(0);
+        ok = wait_row(1) && ok;
+    }
     if (!ok) *abort_flag = 1;
 
     int j = 0;
     for (; j < Hc + 4; ++j) {
-        if (!wait_row(j + 2)) *abort_flag = 1;
+        if (!site && !wait_row(j + 2)) *abort_flag = 1;
+        const int nu_w = j % 3, nu_m1 = (j + 1) % 3, nu_m2 = (j + 2) % 3;  // rows j-3, j-5, j-4
+        const int eq_w = j % 3, eq_r = (j + 1) % 3;                       // rows j-2, j-4
+        const int sh_w = j & 1, sh_r = (j + 1) & 1;                         // rows j-2, j-3
 
         // ---- phase A: moments of row j-2 into ring slot j&3 (source rows j .. j+2)
         {
@@ -300,12 +322,12 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         if (comp) {
             if (j >= 2) {
                 const int rs[3] = {(j - 2) & 3, (j - 1) & 3, j & 3};
-                nur[(j & 3) * N * VW + g * VW + c + 1] =
-                    nu_comp(rs, (j - 1) & 3, g, c + 1, chi_row, th_m, logc, minv1, has_log);
+                nur[nu_w * N * VW + g * VW + c + 1] =
+                    nu_comp(rs, sh_r, g, c + 1, chi_row, th_m, logc, minv1, has_log);
             }
         } else if (site) {
             const int ms = j & 3;
-            const C inv = site_terms(ms, c + 1, ms);
+            const C inv = site_terms(ms, c + 1, sh_w);
             C jx = C(0), jy = C(0);
 #pragma unroll
             for (int t = 0; t < N; ++t) {
@@ -315,10 +337,10 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             C e[Q];
             eq_weights(jx * inv, jy * inv, e);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) eqr[(ms * Q + i) * W + c] = e[i];
+            for (int i = 0; i < Q; ++i) eqr[(eq_w * Q + i) * W + c] = e[i];
             const int r = j - 2;
             if (r >= 0 && r < Hc && x0 + c < p.nx) {
-                const C rho = shr[SHI(ms, SH_RHO, c + 1)];
+                const C rho = shr[SHI(sh_w, SH_RHO, c + 1)];
                 if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
             }
         } else if (lane < 2 * N) {
@@ -329,12 +351,12 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
                 C chi_s[N];
 #pragma unroll
                 for (int u = 0; u < N; ++u) chi_s[u] = p.chi[s * N + u];
-                nur[(j & 3) * N * VW + s * VW + vc] =
-                    nu_comp(rs, (j - 1) & 3, s, vc, chi_s, p.th_m[s], p.logc[s], p.m_inv_m1[s],
+                nur[nu_w * N * VW + s * VW + vc] =
+                    nu_comp(rs, sh_r, s, vc, chi_s, p.th_m[s], p.logc[s], p.m_inv_m1[s],
                             (p.log_mask >> s) & 1u);
             }
         } else if (lane < 2 * N + 2) {
-            site_terms(j & 3, lane == 2 * N ? 0 : W + 1, j & 3);
+            site_terms(j & 3, lane == 2 * N ? 0 : W + 1, sh_w);
         }
         __syncthreads();
 
@@ -349,17 +371,16 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
                     f[i] = to_c<T>(sr[vy(i) + 1][(g * Q + i) * WI + c + HX - vx(i)]);
                     if constexpr (Storage<T>::shifted) f[i] += shift[i];
                 }
-                const int ms = (j - 2) & 3;  // moment / equilibrium slot of row j-4
+                const int ms = (j - 2) & 3;  // moment slot of row j-4
                 const C rg = mom[MOMI(ms, 0, g, c + 2)];
                 const C jxg = mom[MOMI(ms, 1, g, c + 2)];
                 const C jyg = mom[MOMI(ms, 2, g, c + 2)];
                 C e[Q];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) e[i] = eqr[(ms * Q + i) * W + c];
+                for (int i = 0; i < Q; ++i) e[i] = eqr[(eq_r * Q + i) * W + c];
                 // grad nu = 3 sum_i w_i v_i nu(r + v_i)
-                const C* vrow[3] = {nur + ((j - 2) & 3) * N * VW + g * VW,
-                                    nur + ((j - 1) & 3) * N * VW + g * VW,
-                                    nur + (j & 3) * N * VW + g * VW};
+                const C* vrow[3] = {nur + nu_m1 * N * VW + g * VW, nur + nu_m2 * N * VW + g * VW,
+                                    nur + nu_w * N * VW + g * VW};
                 C gx = C(0), gy = C(0);
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
@@ -371,12 +392,25 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
                 const C ay = -p.fcoef * (C(3) * gy) + p.gy;
                 C out[Q];
                 collide(p, f, e, rg, jxg, jyg, ax, ay, out);
-                T* line = fout + line_off(p, g, y0 + j - 4, 0);
+                T* line = fout + line_off(p, g, y0 + j - 4, 0) + HX + x;
+                if (simple_ghosts) {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    C v = out[i];
-                    if constexpr (Storage<T>::shifted) v -= shift[i];
-                    store_row(line + i * p.pitch, x, p.nx, HX, v);
+                    for (int i = 0; i < Q; ++i) {
+                        C v = out[i];
+                        if constexpr (Storage<T>::shifted) v -= shift[i];
+                        Storage<T>::store(line, v);
+                        if (ghost_r) Storage<T>::store(line + p.nx, v);
+                        if (ghost_l) Storage<T>::store(line - p.nx, v);
+                        line += p.pitch;
+                    }
+                } else {
+                    T* row0 = line - HX - x;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        C v = out[i];
+                        if constexpr (Storage<T>::shifted) v -= shift[i];
+                        store_row(row0 + i * p.pitch, x, p.nx, HX, v);
+                    }
                 }
             }
         }

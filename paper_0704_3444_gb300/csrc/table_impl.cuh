@@ -64,18 +64,20 @@ struct Launch {
     static void consider(FusedPlan& best, int& best_score, const Problem& P, int sm_count)
     {
         using G = FusedGeom<T, N, W>;
-        const size_t limit = 227 * 1024, per_sm_smem = 228 * 1024;
+        const size_t limit = 227 * 1024;
         if (G::SMEM > limit || G::THREADS > FUSED_MAX_THREADS) return;
         const int wcap = std::max(32, (P.nx + 31) / 32 * 32);
         if (W > wcap && W > 32) return;
-        const int ctas = std::min((int)(per_sm_smem / (G::SMEM + 1024)), 2048 / G::THREADS);
-        if (ctas < 1) return;
-        const int warps = ctas * ((G::THREADS + 31) / 32);
-        const int score = warps * 4 + W / 32;  // most resident warps, then the wider strip
-        if (score <= best_score) return;
         if (cudaFuncSetAttribute(k_fused<T, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)G::SMEM) != cudaSuccess)
             return;
+        int ctas = 0;  // resident CTAs per SM as the runtime computes them (smem, registers)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_fused<T, N, W>, G::THREADS,
+                                                          G::SMEM) != cudaSuccess || ctas < 1)
+            return;
+        const int warps = ctas * ((G::THREADS + 31) / 32);
+        const int score = warps * 4 + W / 32;  // most resident warps, then the wider strip
+        if (score <= best_score) return;
         best_score = score;
         best.W = W;
         best.NS = G::NS;
