@@ -20,10 +20,11 @@
 //
 // Threads.  One warp group of W threads per component: thread (s, c) handles
 // component s at column x0 + c in every phase.  W "site" threads compute, once per
-// site and one row ahead, what all components share: rho, 1/rho, ln rho, the
-// common part of the Flory-Huggins potential and the nine equilibrium weights e_i.
-// One helper warp computes the halo columns of the rings and its last lane issues
-// the TMA copies.  Every wait on an
+// site, what all components share: rho, 1/rho, ln rho and the common part of the
+// Flory-Huggins potential (phase A, for the nu of the same iteration) and the nine
+// equilibrium weights e_i (phase B, two iterations before their collision).  One
+// helper warp computes the halo columns of the rings and its last lane issues the
+// TMA copies, plus an L2 prefetch of the row two beyond the staged window.  Every wait on an
 // mbarrier is bounded; on expiry the CTA sets STATUS_TIMEOUT, drains the copies it
 // issued (again bounded) and returns.
 #pragma once
@@ -97,6 +98,15 @@ __device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, 
         : "memory");
 }
 
+// Prefetch the same 4-D box into L2 only (no shared memory, no barrier).
+__device__ __forceinline__ void tma_prefetch_row(const CUtensorMap* map, int col, int row)
+{
+    const uint64_t desc = reinterpret_cast<uint64_t>(map);
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global [%0, {%1, %2, %3, %4}];" ::"l"(desc),
+                 "r"(col), "r"(0), "r"(row), "r"(0)
+                 : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ typename Storage<T>::C to_c(T v);
 template <>
@@ -115,6 +125,7 @@ template <typename T, int N, int W>
 struct FusedGeom {
     using C = typename Storage<T>::C;
     static constexpr int NS = 6;                       // source-row stages
+    static constexpr int PF = 2;                       // rows prefetched into L2 beyond the stages
     static constexpr int HX = (16 / (int)sizeof(T)) < 4 ? 4 : 16 / (int)sizeof(T);
     static constexpr int WI = W + 2 * HX;              // staged columns per line
     static constexpr int RW = W + 4;                   // moment ring: x0-2 .. x0+W+1
@@ -129,12 +140,15 @@ struct FusedGeom {
     // later and are overwritten by the next phase A without a barrier in between (4);
     // nu of row r is read by three collisions (3); the equilibrium weights of row r are
     // written two iterations before their collision (3); the site terms of row r are
-    // read by the next phase B only (2).
-    static constexpr int MOM_SLOTS = 4, NU_SLOTS = 3, EQ_SLOTS = 3, SH_SLOTS = 2;
-    static constexpr int MOM = MOM_SLOTS * 3 * N * RW; // slot, (rho, jx, jy), component, column
-    static constexpr int NU = NU_SLOTS * N * VW;       // slot, component, column
-    static constexpr int SH = SH_SLOTS * 4 * VW;       // slot, (rho, 1/rho, ln rho, G), column
-    static constexpr int EQ = EQ_SLOTS * Q * W;        // slot, velocity, column
+    // written in phase A and read in phase B of the same iteration (1).
+    static constexpr int MOM_SLOTS = 4, NU_SLOTS = 3, EQ_SLOTS = 3;
+    static constexpr int MOM_SLOT = 3 * N * RW;        // (rho, jx, jy), component, column
+    static constexpr int MOM = MOM_SLOTS * MOM_SLOT;
+    static constexpr int NU_SLOT = N * VW;             // component, column
+    static constexpr int NU = NU_SLOTS * NU_SLOT;
+    static constexpr int SH = 4 * W;                   // (rho, 1/rho, ln rho, G), column
+    static constexpr int EQ_SLOT = Q * W;              // velocity, column
+    static constexpr int EQ = EQ_SLOTS * EQ_SLOT;
     static constexpr size_t SMEM = FUSED_HDR + NS * STAGE_BYTES + (size_t)(MOM + NU + SH + EQ) * sizeof(C);
     // two CTAs per SM when both fit (shared memory incl. the per-CTA reserve, and
     // registers: the launch bound then caps a thread at 65536 / (2 THREADS))
@@ -170,11 +184,6 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     C* nur = mom + G::MOM;
     C* shr = nur + G::NU;
     C* eqr = shr + G::SH;
-    auto MOMI = [](int slot, int q, int s, int col) { return ((slot * 3 + q) * N + s) * RW + col; };
-    auto SHI = [](int slot, int q, int col) { return (slot * 4 + q) * VW + col; };
-    // ring slots of row r (relative): moments (r+2)&3, nu (r+3)%3, equilibrium (r+2)%3,
-    // site terms (r+2)&1
-    constexpr int SH_RHO = 0, SH_INV = 1, SH_LN = 2, SH_G = 3;
 
     if (tid == G::PRODUCER) {
         for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
@@ -184,12 +193,15 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     __syncthreads();
 
     constexpr uint32_t TX = (uint32_t)(N * Q * WI * sizeof(T));
+    auto grow = [&](int k) {
+        int row = (y0 - 3 + k) % p.ny;
+        return row + (row < 0 ? p.ny : 0);
+    };
     auto issue = [&](int k) {
         const int st = k % NS;
-        int row = (y0 - 3 + k) % p.ny;
-        row += row < 0 ? p.ny : 0;
         mbar_arrive_expect_tx(&full[st], TX);
-        tma_load_row(stages + st * G::STAGE_ELEMS, &tmap, &full[st], x0, row);
+        tma_load_row(stages + st * G::STAGE_ELEMS, &tmap, &full[st], x0, grow(k));
+        if (k + G::PF < nrows) tma_prefetch_row(&tmap, x0, grow(k + G::PF));
     };
     int issued = 0;
     if (tid == G::PRODUCER) {
@@ -198,7 +210,6 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         issued = pre;
     }
     auto wait_row = [&](int k) -> bool { return mbar_wait(&full[k % NS], (k / NS) & 1); };
-    auto stage_of = [&](int k) -> const T* { return stages + (k % NS) * G::STAGE_ELEMS; };
 
     // constants of this thread's component, kept in registers
     C shift[Q];
@@ -210,31 +221,32 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     const C th_m = p.th_m[g], logc = p.logc[g], minv1 = p.m_inv_m1[g];
     const bool has_log = (p.log_mask >> g) & 1u;
 
-    // zeroth and first moments of component s at moment-ring column cc (row from sr)
-    auto moments_at = [&](const T* const (&sr)[3], int s, int cc, int slot, const C (&sh)[Q]) {
+    // zeroth and first moments of one line triple: rows[dy+1] point at the component's
+    // velocity-0 element of the source rows for the pulled site (column offset applied)
+    auto moments_to = [&](const T* const (&rows)[3], C* dst, const C (&sh)[Q]) {
         C v[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            v[i] = to_c<T>(sr[vy(i) + 1][(s * Q + i) * WI + cc - 2 + HX - vx(i)]);
+            v[i] = to_c<T>(rows[vy(i) + 1][i * WI - vx(i)]);
             if constexpr (Storage<T>::shifted) v[i] += sh[i];
         }
         C r = C(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) r += v[i];
-        mom[MOMI(slot, 0, s, cc)] = r;
-        mom[MOMI(slot, 1, s, cc)] = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
-        mom[MOMI(slot, 2, s, cc)] = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
+        dst[0] = r;
+        dst[N * RW] = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
+        dst[2 * N * RW] = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
     };
 
-    // per-site terms of nu shared by all components at nu column vc (moment slot ms):
-    // rho, 1/rho, ln rho and G = -theta (sum_t phi^t/m^t + 1/2 sum chi phi phi)
-    auto site_terms = [&](int ms, int vc, int ss) {
-        const int cc = vc + 1;
+    // site terms from the densities of all components at one column (pointer at
+    // component 0, stride RW): rho, 1/rho, ln rho, G = -theta (sum phi/m + 1/2 sum chi phi phi)
+    struct SiteTerms { C rho, inv, ln, G; };
+    auto site_terms = [&](const C* r0) -> SiteTerms {
         C r[N];
         C rho = C(0);
 #pragma unroll
         for (int t = 0; t < N; ++t) {
-            r[t] = mom[MOMI(ms, 0, t, cc)];
+            r[t] = r0[t * RW];
             rho += r[t];
         }
         const C inv = C(1) / rho;
@@ -247,38 +259,33 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             for (int u = 0; u < N; ++u) acc += p.chi[t * N + u] * r[u];
             quad += r[t] * acc;
         }
-        shr[SHI(ss, SH_RHO, vc)] = rho;
-        shr[SHI(ss, SH_INV, vc)] = inv;
-        shr[SHI(ss, SH_LN, vc)] = dev_log(rho);
-        shr[SHI(ss, SH_G, vc)] = -p.theta * (sm * inv + C(0.5) * quad * inv * inv);
-        return inv;
+        return SiteTerms{rho, inv, dev_log(rho), -p.theta * (sm * inv + C(0.5) * quad * inv * inv)};
     };
 
-    // nu^s at nu column vc of the row whose moments sit in slots rs[0..2] (rows r-1, r, r+1)
-    // and whose site terms sit in slot ss
-    auto nu_comp = [&](const int (&rs)[3], int ss, int s, int vc, const C (&chi_s)[N], C thm,
-                       C lc, C mi1, bool lg) -> C {
-        const int cc = vc + 1;
+    // nu^s at one column: mrow[dy+1] point at the density of component s at that column
+    // in the moment rows r-1, r, r+1; dens points at component 0 of row r (stride RW)
+    auto nu_of = [&](const C* const (&mrow)[3], const C* dens, const SiteTerms& st,
+                     const C (&chi_s)[N], C thm, C lc, C mi1, bool lg) -> C {
         C acc = C(0);
 #pragma unroll
-        for (int u = 0; u < N; ++u) acc += chi_s[u] * mom[MOMI(rs[1], 0, u, cc)];
-        const C inv = shr[SHI(ss, SH_INV, vc)];
-        const C own = mom[MOMI(rs[1], 0, s, cc)];
+        for (int u = 0; u < N; ++u) acc += chi_s[u] * dens[u * RW];
+        const C own = mrow[1][0];
         C lap = C(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) lap += wq<C>(i) * (mom[MOMI(rs[vy(i) + 1], 0, s, cc + vx(i))] - own);
-        C logs = -thm * shr[SHI(ss, SH_LN, vc)];
+        for (int i = 0; i < Q; ++i) lap += wq<C>(i) * (mrow[vy(i) + 1][vx(i)] - own);
+        C logs = -thm * st.ln;
         if (lg) {
-            const C fl = p.log_floor * shr[SHI(ss, SH_RHO, vc)];
+            const C fl = p.log_floor * st.rho;
             logs += lc * dev_log(own > fl ? own : fl);
         }
-        return logs + p.theta * (mi1 + acc * inv) + shr[SHI(ss, SH_G, vc)] - p.kappa * (C(6) * lap);
+        return logs + p.theta * (mi1 + acc * st.inv) + st.G - p.kappa * (C(6) * lap);
     };
 
     // columns whose value is repeated in a ghost column (one copy each when nx >= HX)
     const bool simple_ghosts = p.nx >= HX;
     const bool ghost_r = (x0 + c) < HX;
     const bool ghost_l = (x0 + c) >= p.nx - HX;
+    const bool any_ghost = ghost_r || ghost_l || !simple_ghosts;
 
     bool ok = true;
     if (!site) {
@@ -288,24 +295,49 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     if (!ok) *abort_flag = 1;
 
     int j = 0;
-    for (; j < Hc + 4; ++j) {
+    int sj = 0;  // stage of source row j (= j mod NS)
+    for (; j < Hc + 4; ++j, sj = (sj + 1 == NS) ? 0 : sj + 1) {
         if (!site && !wait_row(j + 2)) *abort_flag = 1;
-        const int nu_w = j % 3, nu_m1 = (j + 1) % 3, nu_m2 = (j + 2) % 3;  // rows j-3, j-5, j-4
-        const int eq_w = j % 3, eq_r = (j + 1) % 3;                       // rows j-2, j-4
-        const int sh_w = j & 1, sh_r = (j + 1) & 1;                         // rows j-2, j-3
+        auto stage = [&](int d) -> const T* {  // stage of source row j + d, -2 <= d <= 2
+            int s_ = sj + d;
+            s_ += (s_ < 0) ? NS : 0;
+            s_ -= (s_ >= NS) ? NS : 0;
+            return stages + s_ * G::STAGE_ELEMS;
+        };
+        C* momA = mom + (j & 3) * G::MOM_SLOT;           // row j-2
+        const C* momB0 = mom + ((j - 1) & 3) * G::MOM_SLOT;  // row j-3
+        const C* momBm = mom + ((j - 2) & 3) * G::MOM_SLOT;  // row j-4
+        C* nuw = nur + (j % 3) * G::NU_SLOT;                 // nu row j-3
+        const C* nuA = nur + ((j + 1) % 3) * G::NU_SLOT;     // nu row j-5
+        const C* nuB = nur + ((j + 2) % 3) * G::NU_SLOT;     // nu row j-4
+        C* eqw = eqr + (j % 3) * G::EQ_SLOT;                 // equilibrium row j-2
+        const C* eqc = eqr + ((j + 1) % 3) * G::EQ_SLOT;     // equilibrium row j-4
 
-        // ---- phase A: moments of row j-2 into ring slot j&3 (source rows j .. j+2)
-        {
-            const T* const sr[3] = {stage_of(j + 2), stage_of(j + 1), stage_of(j)};
-            if (comp) {
-                moments_at(sr, g, c + 2, j & 3, shift);
-            } else if (lane >= 0 && lane < 4 * N) {
-                const int hc = lane / N, s = lane - hc * N;
-                C sh[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) sh[i] = Storage<T>::shifted ? p.shift[s * Q + i] : C(0);
-                moments_at(sr, s, hc < 2 ? hc : W + hc, j & 3, sh);
+        // ---- phase A: moments of row j-2 (source rows j .. j+2); site terms of row j-3
+        if (comp) {
+            const T* const rows[3] = {stage(2) + g * Q * WI + c + HX, stage(1) + g * Q * WI + c + HX,
+                                      stage(0) + g * Q * WI + c + HX};
+            moments_to(rows, momA + g * RW + c + 2, shift);
+        } else if (site) {
+            if (j >= 1) {
+                const SiteTerms st = site_terms(momB0 + c + 2);
+                shr[c] = st.rho;
+                shr[W + c] = st.inv;
+                shr[2 * W + c] = st.ln;
+                shr[3 * W + c] = st.G;
+                const int r = j - 3;
+                if (r >= 0 && r < Hc && x0 + c < p.nx && (!(st.rho > C(0)) || !isfinite(st.rho)))
+                    atomicOr(p.status, STATUS_NONFINITE);
             }
+        } else if (lane < 4 * N) {
+            const int hc = lane / N, s = lane - hc * N;
+            const int cc = hc < 2 ? hc : W + hc;     // moment-ring column of the halo site
+            C sh[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) sh[i] = Storage<T>::shifted ? p.shift[s * Q + i] : C(0);
+            const int col = s * Q * WI + cc - 2 + HX;
+            const T* const rows[3] = {stage(2) + col, stage(1) + col, stage(0) + col};
+            moments_to(rows, momA + s * RW + cc, sh);
         }
         __syncthreads();
         if (*abort_flag) break;
@@ -317,101 +349,85 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             }
         }
 
-        // ---- phase B: nu of row j-3 (slot j&3); site terms and equilibrium weights of
-        //      row j-2 (slot j&3) for the next iterations
+        // ---- phase B: nu of row j-3; equilibrium weights of row j-2
         if (comp) {
             if (j >= 2) {
-                const int rs[3] = {(j - 2) & 3, (j - 1) & 3, j & 3};
-                nur[nu_w * N * VW + g * VW + c + 1] =
-                    nu_comp(rs, sh_r, g, c + 1, chi_row, th_m, logc, minv1, has_log);
+                const C* mc = momB0 + g * RW + c + 2;
+                const C* const mrow[3] = {momBm + g * RW + c + 2, mc, momA + g * RW + c + 2};
+                const SiteTerms st{shr[c], shr[W + c], shr[2 * W + c], shr[3 * W + c]};
+                nuw[g * VW + c + 1] = nu_of(mrow, momB0 + c + 2, st, chi_row, th_m, logc, minv1, has_log);
             }
         } else if (site) {
-            const int ms = j & 3;
-            const C inv = site_terms(ms, c + 1, sh_w);
-            C jx = C(0), jy = C(0);
+            const C* m = momA + c + 2;
+            C rho = C(0), jx = C(0), jy = C(0);
 #pragma unroll
             for (int t = 0; t < N; ++t) {
-                jx += mom[MOMI(ms, 1, t, c + 2)];
-                jy += mom[MOMI(ms, 2, t, c + 2)];
+                rho += m[t * RW];
+                jx += m[N * RW + t * RW];
+                jy += m[2 * N * RW + t * RW];
             }
+            const C inv = C(1) / rho;
             C e[Q];
             eq_weights(jx * inv, jy * inv, e);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) eqr[(eq_w * Q + i) * W + c] = e[i];
-            const int r = j - 2;
-            if (r >= 0 && r < Hc && x0 + c < p.nx) {
-                const C rho = shr[SHI(sh_w, SH_RHO, c + 1)];
-                if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
-            }
+            for (int i = 0; i < Q; ++i) eqw[i * W + c] = e[i];
         } else if (lane < 2 * N) {
             if (j >= 2) {
                 const int hv = lane / N, s = lane - hv * N;
+                const int cc = hv == 0 ? 1 : W + 2;  // moment-ring column of the halo nu site
                 const int vc = hv == 0 ? 0 : W + 1;
-                const int rs[3] = {(j - 2) & 3, (j - 1) & 3, j & 3};
+                const C* const mrow[3] = {momBm + s * RW + cc, momB0 + s * RW + cc, momA + s * RW + cc};
+                const SiteTerms st = site_terms(momB0 + cc);
                 C chi_s[N];
 #pragma unroll
                 for (int u = 0; u < N; ++u) chi_s[u] = p.chi[s * N + u];
-                nur[nu_w * N * VW + s * VW + vc] =
-                    nu_comp(rs, sh_r, s, vc, chi_s, p.th_m[s], p.logc[s], p.m_inv_m1[s],
-                            (p.log_mask >> s) & 1u);
+                nuw[s * VW + vc] = nu_of(mrow, momB0 + cc, st, chi_s, p.th_m[s], p.logc[s],
+                                         p.m_inv_m1[s], (p.log_mask >> s) & 1u);
             }
-        } else if (lane < 2 * N + 2) {
-            site_terms(j & 3, lane == 2 * N ? 0 : W + 1, sh_w);
         }
         __syncthreads();
 
         // ---- phase C: collide row j-4 (source rows j-2 .. j, nu rows j-5 .. j-3)
-        if (comp && j >= 4) {
+        if (comp && j >= 4 && x0 + c < p.nx) {
+            const int off = g * Q * WI + c + HX;
+            const T* const rows[3] = {stage(0) + off, stage(-1) + off, stage(-2) + off};
+            C f[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                f[i] = to_c<T>(rows[vy(i) + 1][i * WI - vx(i)]);
+                if constexpr (Storage<T>::shifted) f[i] += shift[i];
+            }
+            const C* mg = momBm + g * RW + c + 2;
+            const C rg = mg[0], jxg = mg[N * RW], jyg = mg[2 * N * RW];
+            C e[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) e[i] = eqc[i * W + c];
+            // grad nu = 3 sum_i w_i v_i nu(r + v_i)
+            const C* const vrow[3] = {nuA + g * VW + c + 1, nuB + g * VW + c + 1, nuw + g * VW + c + 1};
+            C gx = C(0), gy = C(0);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const C v = vrow[vy(i) + 1][vx(i)];
+                if (vx(i) != 0) gx += wq<C>(i) * C(vx(i)) * v;
+                if (vy(i) != 0) gy += wq<C>(i) * C(vy(i)) * v;
+            }
+            const C ax = -p.fcoef * (C(3) * gx) + p.gx;
+            const C ay = -p.fcoef * (C(3) * gy) + p.gy;
+            C out[Q];
+            collide(p, f, e, rg, jxg, jyg, ax, ay, out);
+            if constexpr (Storage<T>::shifted) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) out[i] -= shift[i];
+            }
             const int x = x0 + c;
-            if (x < p.nx) {
-                const T* const sr[3] = {stage_of(j), stage_of(j - 1), stage_of(j - 2)};
-                C f[Q];
+            T* line = fout + line_off(p, g, y0 + j - 4, 0);
+            if (!any_ghost) {
+                T* q = line + HX + x;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    f[i] = to_c<T>(sr[vy(i) + 1][(g * Q + i) * WI + c + HX - vx(i)]);
-                    if constexpr (Storage<T>::shifted) f[i] += shift[i];
-                }
-                const int ms = (j - 2) & 3;  // moment slot of row j-4
-                const C rg = mom[MOMI(ms, 0, g, c + 2)];
-                const C jxg = mom[MOMI(ms, 1, g, c + 2)];
-                const C jyg = mom[MOMI(ms, 2, g, c + 2)];
-                C e[Q];
+                for (int i = 0; i < Q; ++i) Storage<T>::store(q + i * p.pitch, out[i]);
+            } else {
 #pragma unroll
-                for (int i = 0; i < Q; ++i) e[i] = eqr[(eq_r * Q + i) * W + c];
-                // grad nu = 3 sum_i w_i v_i nu(r + v_i)
-                const C* vrow[3] = {nur + nu_m1 * N * VW + g * VW, nur + nu_m2 * N * VW + g * VW,
-                                    nur + nu_w * N * VW + g * VW};
-                C gx = C(0), gy = C(0);
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const C v = vrow[vy(i) + 1][c + 1 + vx(i)];
-                    if (vx(i) != 0) gx += wq<C>(i) * C(vx(i)) * v;
-                    if (vy(i) != 0) gy += wq<C>(i) * C(vy(i)) * v;
-                }
-                const C ax = -p.fcoef * (C(3) * gx) + p.gx;
-                const C ay = -p.fcoef * (C(3) * gy) + p.gy;
-                C out[Q];
-                collide(p, f, e, rg, jxg, jyg, ax, ay, out);
-                T* line = fout + line_off(p, g, y0 + j - 4, 0) + HX + x;
-                if (simple_ghosts) {
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        C v = out[i];
-                        if constexpr (Storage<T>::shifted) v -= shift[i];
-                        Storage<T>::store(line, v);
-                        if (ghost_r) Storage<T>::store(line + p.nx, v);
-                        if (ghost_l) Storage<T>::store(line - p.nx, v);
-                        line += p.pitch;
-                    }
-                } else {
-                    T* row0 = line - HX - x;
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        C v = out[i];
-                        if constexpr (Storage<T>::shifted) v -= shift[i];
-                        store_row(row0 + i * p.pitch, x, p.nx, HX, v);
-                    }
-                }
+                for (int i = 0; i < Q; ++i) store_row(line + i * p.pitch, x, p.nx, HX, out[i]);
             }
         }
     }
