@@ -61,17 +61,21 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: a thread whose phase is not complete sleeps in
+// hardware (up to the hint) instead of re-polling.
+constexpr uint32_t WAIT_SUSPEND_NS = 200000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n"
         ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         "selp.u32 %0, 1, 0, p;\n"
         "}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(WAIT_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -125,7 +129,7 @@ template <typename T, int N, int W>
 struct FusedGeom {
     using C = typename Storage<T>::C;
     static constexpr int NS = 6;                       // source-row stages
-    static constexpr int PF = 2;                       // rows prefetched into L2 beyond the stages
+    static constexpr int PF = 4;                       // L2 prefetch distance (rows) of a copy
     static constexpr int HX = (16 / (int)sizeof(T)) < 4 ? 4 : 16 / (int)sizeof(T);
     static constexpr int WI = W + 2 * HX;              // staged columns per line
     static constexpr int RW = W + 4;                   // moment ring: x0-2 .. x0+W+1
