@@ -18,13 +18,13 @@
 // TMA box an in-bounds, 16-byte aligned row segment; periodicity in y is the row
 // index modulo ny.
 //
-// Threads.  One warp group of W threads per component: thread (s, c) handles
-// component s at column x0 + c in every phase.  W "site" threads compute, once per
-// site, what all components share: rho, 1/rho, ln rho and the common part of the
-// Flory-Huggins potential (phase A, for the nu of the same iteration) and the nine
-// equilibrium weights e_i (phase B, two iterations before their collision).  One
-// helper warp computes the halo columns of the rings and its last lane issues the
-// TMA copies, plus an L2 prefetch of the row two beyond the staged window.  Every wait on an
+// Threads.  One warp per component: lane c handles that component at columns
+// x0 + c and x0 + c + 32 of a 64-column strip in every phase, which halves the
+// per-thread index and control work per site.  Two "site" warps (one column per
+// thread) compute, once per site, what all components share: rho, 1/rho, ln rho,
+// the common part of the Flory-Huggins potential and the nine equilibrium weights
+// e_i.  One helper warp computes the halo columns of the rings; its last lane issues
+// the TMA copies plus an L2 prefetch four rows beyond each copy.  Every wait on an
 // mbarrier is bounded; on expiry the CTA sets STATUS_TIMEOUT, drains the copies it
 // issued (again bounded) and returns.
 #pragma once
@@ -124,66 +124,69 @@ __device__ __forceinline__ float to_c<__half>(__half v) { return __half2float(v)
 
 __host__ __device__ constexpr size_t round_up_sz(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
-// Compile-time geometry of one CTA: W columns per strip, NS stages, hx ghost columns.
-template <typename T, int N, int W>
+// Compile-time geometry of one CTA: a strip of W = 64 columns; each component thread
+// handles the two columns c and c + 32 of its component; two site warps handle one
+// column per thread; one helper warp does the halo columns and issues the copies.
+template <typename T, int N>
 struct FusedGeom {
     using C = typename Storage<T>::C;
+    static constexpr int W = 64;
     static constexpr int NS = 6;                       // source-row stages
     static constexpr int PF = 4;                       // L2 prefetch distance (rows) of a copy
     static constexpr int HX = (16 / (int)sizeof(T)) < 4 ? 4 : 16 / (int)sizeof(T);
     static constexpr int WI = W + 2 * HX;              // staged columns per line
     static constexpr int RW = W + 4;                   // moment ring: x0-2 .. x0+W+1
     static constexpr int VW = W + 2;                   // nu ring:     x0-1 .. x0+W
-    static constexpr int NCT = N * W;                  // component threads
-    static constexpr int THREADS = NCT + W + 32;       // + site threads + helper warp
+    static constexpr int NCT = N * 32;                 // component threads (2 columns each)
+    static constexpr int NST = W;                      // site threads (1 column each)
+    static constexpr int THREADS = NCT + NST + 32;     // + helper warp
     static constexpr int PRODUCER = THREADS - 1;       // helper lane issuing the copies
     static constexpr size_t STAGE_BYTES = round_up_sz((size_t)N * Q * WI * sizeof(T), 128);
-    static constexpr size_t STAGE_ELEMS = STAGE_BYTES / sizeof(T);
+    static constexpr int STAGE_ELEMS = (int)(STAGE_BYTES / sizeof(T));
     // rings (elements of C).  Slot counts follow from who reads a row after the barrier
     // that follows its write: moments of row r are read until phase C two iterations
     // later and are overwritten by the next phase A without a barrier in between (4);
-    // nu of row r is read by three collisions (3); the equilibrium weights of row r are
-    // written two iterations before their collision (3); the site terms of row r are
-    // written in phase A and read in phase B of the same iteration (1).
-    static constexpr int MOM_SLOTS = 4, NU_SLOTS = 3, EQ_SLOTS = 3;
+    // nu of row r is read by three collisions (3); site terms and equilibrium weights
+    // of row r are written in phase A one iteration before the collision of row r, and
+    // the next phase A may run before that collision ends (3 for the weights; the site
+    // terms are read only by the phase B of the iteration that wrote them (1)).
     static constexpr int MOM_SLOT = 3 * N * RW;        // (rho, jx, jy), component, column
-    static constexpr int MOM = MOM_SLOTS * MOM_SLOT;
+    static constexpr int MOM = 4 * MOM_SLOT;
     static constexpr int NU_SLOT = N * VW;             // component, column
-    static constexpr int NU = NU_SLOTS * NU_SLOT;
-    static constexpr int SH = 4 * W;                   // (rho, 1/rho, ln rho, G), column
+    static constexpr int NU = 3 * NU_SLOT;
+    static constexpr int SH = 4 * VW;                  // (rho, 1/rho, ln rho, G), nu column
     static constexpr int EQ_SLOT = Q * W;              // velocity, column
-    static constexpr int EQ = EQ_SLOTS * EQ_SLOT;
+    static constexpr int EQ = 3 * EQ_SLOT;
     static constexpr size_t SMEM = FUSED_HDR + NS * STAGE_BYTES + (size_t)(MOM + NU + SH + EQ) * sizeof(C);
-    // two CTAs per SM when both fit (shared memory incl. the per-CTA reserve, and
-    // registers: the launch bound then caps a thread at 65536 / (2 THREADS))
     static constexpr int MIN_CTAS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
 };
 
 constexpr int FUSED_MAX_THREADS = 1024;
 
-template <typename T, int N, int W>
-__global__ void __launch_bounds__(FusedGeom<T, N, W>::THREADS, FusedGeom<T, N, W>::MIN_CTAS)
+template <typename T, int N>
+__global__ void __launch_bounds__(FusedGeom<T, N>::THREADS, FusedGeom<T, N>::MIN_CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         const __grid_constant__ StepParams<typename Storage<T>::C> p, const int H)
 {
-    using G = FusedGeom<T, N, W>;
+    using G = FusedGeom<T, N>;
     using C = typename Storage<T>::C;
-    constexpr int NS = G::NS, HX = G::HX, WI = G::WI, RW = G::RW, VW = G::VW, NCT = G::NCT;
+    constexpr int W = G::W, NS = G::NS, HX = G::HX, WI = G::WI, RW = G::RW, VW = G::VW;
+    constexpr int NCT = G::NCT, NST = G::NST;
     const int x0 = blockIdx.x * W;
     const int y0 = blockIdx.y * H;
     const int Hc = min(H, p.ny - y0);
     const int nrows = Hc + 6;    // source rows k <-> global row y0 - 3 + k (mod ny)
     const int tid = threadIdx.x;
     const bool comp = tid < NCT;
-    const bool site = !comp && tid < NCT + W;
-    const int g = comp ? tid / W : 0;                  // component of a component thread
-    const int c = comp ? tid % W : (site ? tid - NCT : 0);
-    const int lane = tid - NCT - W;                    // helper lane (>= 0 in the helper warp)
+    const bool site = !comp && tid < NCT + NST;
+    const int g = comp ? (tid >> 5) : 0;               // component of a component thread
+    const int c = comp ? (tid & 31) : (site ? tid - NCT : 0);  // first column
+    const int lane = tid - NCT - NST;                  // helper lane (>= 0 in the helper warp)
 
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 8 * FUSED_MAX_NS);
-    T* stages = reinterpret_cast<T*>(smem + FUSED_HDR);
+    T* stg = reinterpret_cast<T*>(smem + FUSED_HDR);
     C* mom = reinterpret_cast<C*>(smem + FUSED_HDR + NS * G::STAGE_BYTES);
     C* nur = mom + G::MOM;
     C* shr = nur + G::NU;
@@ -204,7 +207,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     auto issue = [&](int k) {
         const int st = k % NS;
         mbar_arrive_expect_tx(&full[st], TX);
-        tma_load_row(stages + st * G::STAGE_ELEMS, &tmap, &full[st], x0, grow(k));
+        tma_load_row(stg + st * G::STAGE_ELEMS, &tmap, &full[st], x0, grow(k));
         if (k + G::PF < nrows) tma_prefetch_row(&tmap, x0, grow(k + G::PF));
     };
     int issued = 0;
@@ -225,32 +228,33 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     const C th_m = p.th_m[g], logc = p.logc[g], minv1 = p.m_inv_m1[g];
     const bool has_log = (p.log_mask >> g) & 1u;
 
-    // zeroth and first moments of one line triple: rows[dy+1] point at the component's
-    // velocity-0 element of the source rows for the pulled site (column offset applied)
-    auto moments_to = [&](const T* const (&rows)[3], C* dst, const C (&sh)[Q]) {
+    // moments of one component at one column: a0/a1/a2 are the stage element offsets of
+    // the velocity-0 line (column applied) in the source rows for dy = -1, 0, +1
+    auto moments_to = [&](int a0, int a1, int a2, int dst, const C (&sh)[Q]) {
+        const int ar[3] = {a0, a1, a2};
         C v[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            v[i] = to_c<T>(rows[vy(i) + 1][i * WI - vx(i)]);
+            v[i] = to_c<T>(stg[ar[vy(i) + 1] + i * WI - vx(i)]);
             if constexpr (Storage<T>::shifted) v[i] += sh[i];
         }
         C r = C(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) r += v[i];
-        dst[0] = r;
-        dst[N * RW] = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
-        dst[2 * N * RW] = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
+        mom[dst] = r;
+        mom[dst + N * RW] = (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]);
+        mom[dst + 2 * N * RW] = (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]);
     };
 
-    // site terms from the densities of all components at one column (pointer at
-    // component 0, stride RW): rho, 1/rho, ln rho, G = -theta (sum phi/m + 1/2 sum chi phi phi)
-    struct SiteTerms { C rho, inv, ln, G; };
-    auto site_terms = [&](const C* r0) -> SiteTerms {
+    // site terms from the densities of all components at one column (offset of
+    // component 0, stride RW): returns rho and 1/rho, stores rho, 1/rho, ln rho and
+    // G = -theta (sum phi/m + 1/2 sum chi phi phi) at nu column vc
+    auto site_terms = [&](int m0, int vc, C& inv_out) -> C {
         C r[N];
         C rho = C(0);
 #pragma unroll
         for (int t = 0; t < N; ++t) {
-            r[t] = r0[t * RW];
+            r[t] = mom[m0 + t * RW];
             rho += r[t];
         }
         const C inv = C(1) / rho;
@@ -263,33 +267,83 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             for (int u = 0; u < N; ++u) acc += p.chi[t * N + u] * r[u];
             quad += r[t] * acc;
         }
-        return SiteTerms{rho, inv, dev_log(rho), -p.theta * (sm * inv + C(0.5) * quad * inv * inv)};
+        shr[vc] = rho;
+        shr[VW + vc] = inv;
+        shr[2 * VW + vc] = dev_log(rho);
+        shr[3 * VW + vc] = -p.theta * (sm * inv + C(0.5) * quad * inv * inv);
+        inv_out = inv;
+        return rho;
     };
 
-    // nu^s at one column: mrow[dy+1] point at the density of component s at that column
-    // in the moment rows r-1, r, r+1; dens points at component 0 of row r (stride RW)
-    auto nu_of = [&](const C* const (&mrow)[3], const C* dens, const SiteTerms& st,
-                     const C (&chi_s)[N], C thm, C lc, C mi1, bool lg) -> C {
+    // nu^s at one column: m[dy+1] = moment offsets of component s at the column in rows
+    // r-1, r, r+1; d0 = offset of component 0 in row r; site terms at nu column vc
+    auto nu_of = [&](int mm, int m0, int mp, int d0, int vc, int s, const C (&chi_s)[N], C thm,
+                     C lc, C mi1, bool lg) -> C {
+        const int mr[3] = {mm, m0, mp};
         C acc = C(0);
 #pragma unroll
-        for (int u = 0; u < N; ++u) acc += chi_s[u] * dens[u * RW];
-        const C own = mrow[1][0];
+        for (int u = 0; u < N; ++u) acc += chi_s[u] * mom[d0 + u * RW];
+        const C own = mom[m0];
         C lap = C(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) lap += wq<C>(i) * (mrow[vy(i) + 1][vx(i)] - own);
-        C logs = -thm * st.ln;
+        for (int i = 0; i < Q; ++i) lap += wq<C>(i) * (mom[mr[vy(i) + 1] + vx(i)] - own);
+        C logs = -thm * shr[2 * VW + vc];
         if (lg) {
-            const C fl = p.log_floor * st.rho;
+            const C fl = p.log_floor * shr[vc];
             logs += lc * dev_log(own > fl ? own : fl);
         }
-        return logs + p.theta * (mi1 + acc * st.inv) + st.G - p.kappa * (C(6) * lap);
+        (void)s;
+        return logs + p.theta * (mi1 + acc * shr[VW + vc]) + shr[3 * VW + vc] - p.kappa * (C(6) * lap);
     };
 
-    // columns whose value is repeated in a ghost column (one copy each when nx >= HX)
-    const bool simple_ghosts = p.nx >= HX;
-    const bool ghost_r = (x0 + c) < HX;
-    const bool ghost_l = (x0 + c) >= p.nx - HX;
-    const bool any_ghost = ghost_r || ghost_l || !simple_ghosts;
+    // collision of component g at first-column offset cc (0 or 32) of the strip
+    auto collide_col = [&](int cc, int s0, int s1, int s2, int momr, int eqo, int n0, int n1, int n2,
+                           T* line, bool ghost) {
+        const int x = x0 + c + cc;
+        if (x >= p.nx) return;
+        const int col = g * Q * WI + c + cc + HX;
+        const int ar[3] = {s0 + col, s1 + col, s2 + col};
+        C f[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            f[i] = to_c<T>(stg[ar[vy(i) + 1] + i * WI - vx(i)]);
+            if constexpr (Storage<T>::shifted) f[i] += shift[i];
+        }
+        const int mg = momr + g * RW + c + cc + 2;
+        const C rg = mom[mg], jxg = mom[mg + N * RW], jyg = mom[mg + 2 * N * RW];
+        C e[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) e[i] = eqr[eqo + i * W + c + cc];
+        const int vo = g * VW + c + cc + 1;
+        const int nr[3] = {n0 + vo, n1 + vo, n2 + vo};
+        C gx = C(0), gy = C(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const C v = nur[nr[vy(i) + 1] + vx(i)];
+            if (vx(i) != 0) gx += wq<C>(i) * C(vx(i)) * v;
+            if (vy(i) != 0) gy += wq<C>(i) * C(vy(i)) * v;
+        }
+        const C ax = -p.fcoef * (C(3) * gx) + p.gx;
+        const C ay = -p.fcoef * (C(3) * gy) + p.gy;
+        C out[Q];
+        collide(p, f, e, rg, jxg, jyg, ax, ay, out);
+        if constexpr (Storage<T>::shifted) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[i] -= shift[i];
+        }
+        if (!ghost) {
+            T* q = line + HX + x;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Storage<T>::store(q + i * p.pitch, out[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) store_row(line + i * p.pitch, x, p.nx, HX, out[i]);
+        }
+    };
+
+    // columns whose value is repeated in a ghost column
+    auto has_ghost = [&](int x) { return p.nx < HX || x < HX || x >= p.nx - HX; };
+    const bool ghost0 = has_ghost(x0 + c), ghost1 = has_ghost(x0 + c + 32);
 
     bool ok = true;
     if (!site) {
@@ -299,49 +353,70 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     if (!ok) *abort_flag = 1;
 
     int j = 0;
-    int sj = 0;  // stage of source row j (= j mod NS)
-    for (; j < Hc + 4; ++j, sj = (sj + 1 == NS) ? 0 : sj + 1) {
+    int sj = 0;   // stage of source row j
+    int j3 = 0;   // j mod 3
+    for (; j < Hc + 4; ++j) {
         if (!site && !wait_row(j + 2)) *abort_flag = 1;
-        auto stage = [&](int d) -> const T* {  // stage of source row j + d, -2 <= d <= 2
+        auto stage_off = [&](int d) -> int {  // element offset of the stage of row j + d
             int s_ = sj + d;
             s_ += (s_ < 0) ? NS : 0;
             s_ -= (s_ >= NS) ? NS : 0;
-            return stages + s_ * G::STAGE_ELEMS;
+            return s_ * G::STAGE_ELEMS;
         };
-        C* momA = mom + (j & 3) * G::MOM_SLOT;           // row j-2
-        const C* momB0 = mom + ((j - 1) & 3) * G::MOM_SLOT;  // row j-3
-        const C* momBm = mom + ((j - 2) & 3) * G::MOM_SLOT;  // row j-4
-        C* nuw = nur + (j % 3) * G::NU_SLOT;                 // nu row j-3
-        const C* nuA = nur + ((j + 1) % 3) * G::NU_SLOT;     // nu row j-5
-        const C* nuB = nur + ((j + 2) % 3) * G::NU_SLOT;     // nu row j-4
-        C* eqw = eqr + (j % 3) * G::EQ_SLOT;                 // equilibrium row j-2
-        const C* eqc = eqr + ((j + 1) % 3) * G::EQ_SLOT;     // equilibrium row j-4
+        const int st0 = stage_off(0), stp1 = stage_off(1), stp2 = stage_off(2);
+        const int stm1 = stage_off(-1), stm2 = stage_off(-2);
+        const int momA = (j & 3) * G::MOM_SLOT;        // row j-2
+        const int momB = ((j - 1) & 3) * G::MOM_SLOT;  // row j-3
+        const int momC = ((j - 2) & 3) * G::MOM_SLOT;  // row j-4
+        const int j3p1 = (j3 == 2) ? 0 : j3 + 1, j3p2 = (j3 == 0) ? 2 : j3 - 1;
+        const int nuw = j3 * G::NU_SLOT;               // nu row j-3
+        const int nuA = j3p1 * G::NU_SLOT;             // nu row j-5
+        const int nuB = j3p2 * G::NU_SLOT;             // nu row j-4
+        const int eqw = j3 * G::EQ_SLOT;               // equilibrium row j-3
+        const int eqc = j3p2 * G::EQ_SLOT;             // equilibrium row j-4
 
-        // ---- phase A: moments of row j-2 (source rows j .. j+2); site terms of row j-3
+        // ---- phase A: moments of row j-2 (source rows j .. j+2); site terms and
+        //      equilibrium weights of row j-3 (moments complete since the last phase A)
         if (comp) {
-            const T* const rows[3] = {stage(2) + g * Q * WI + c + HX, stage(1) + g * Q * WI + c + HX,
-                                      stage(0) + g * Q * WI + c + HX};
-            moments_to(rows, momA + g * RW + c + 2, shift);
+            const int col = g * Q * WI + c + HX;
+            moments_to(stp2 + col, stp1 + col, st0 + col, momA + g * RW + c + 2, shift);
+            moments_to(stp2 + col + 32, stp1 + col + 32, st0 + col + 32, momA + g * RW + c + 34, shift);
         } else if (site) {
             if (j >= 1) {
-                const SiteTerms st = site_terms(momB0 + c + 2);
-                shr[c] = st.rho;
-                shr[W + c] = st.inv;
-                shr[2 * W + c] = st.ln;
-                shr[3 * W + c] = st.G;
+                C inv;
+                const C rho = site_terms(momB + c + 2, c + 1, inv);
+                const int mj = momB + N * RW + c + 2;
+                C jx = C(0), jy = C(0);
+#pragma unroll
+                for (int t = 0; t < N; ++t) {
+                    jx += mom[mj + t * RW];
+                    jy += mom[mj + N * RW + t * RW];
+                }
+                C e[Q];
+                eq_weights(jx * inv, jy * inv, e);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) eqr[eqw + i * W + c] = e[i];
                 const int r = j - 3;
-                if (r >= 0 && r < Hc && x0 + c < p.nx && (!(st.rho > C(0)) || !isfinite(st.rho)))
+                if (r >= 0 && r < Hc && x0 + c < p.nx && (!(rho > C(0)) || !isfinite(rho)))
                     atomicOr(p.status, STATUS_NONFINITE);
             }
-        } else if (lane < 4 * N) {
-            const int hc = lane / N, s = lane - hc * N;
-            const int cc = hc < 2 ? hc : W + hc;     // moment-ring column of the halo site
-            C sh[Q];
+        } else {
+            if (lane < 4 * N) {
+                const int hc = lane / N, s = lane - hc * N;
+                const int cc = hc < 2 ? hc : W + hc;     // moment-ring column of the halo site
+                C sh[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) sh[i] = Storage<T>::shifted ? p.shift[s * Q + i] : C(0);
-            const int col = s * Q * WI + cc - 2 + HX;
-            const T* const rows[3] = {stage(2) + col, stage(1) + col, stage(0) + col};
-            moments_to(rows, momA + s * RW + cc, sh);
+                for (int i = 0; i < Q; ++i) sh[i] = Storage<T>::shifted ? p.shift[s * Q + i] : C(0);
+                const int col = s * Q * WI + cc - 2 + HX;
+                moments_to(stp2 + col, stp1 + col, st0 + col, momA + s * RW + cc, sh);
+            }
+            // halo site terms of row j-3 on two lanes (the last two when they are free)
+            const int hl = (4 * N + 2 <= 32) ? 4 * N : 0;
+            if (j >= 1 && (lane == hl || lane == hl + 1)) {
+                C inv;
+                const int vc = lane == hl ? 0 : W + 1;
+                site_terms(momB + vc + 1, vc, inv);
+            }
         }
         __syncthreads();
         if (*abort_flag) break;
@@ -353,87 +428,37 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             }
         }
 
-        // ---- phase B: nu of row j-3; equilibrium weights of row j-2
-        if (comp) {
-            if (j >= 2) {
-                const C* mc = momB0 + g * RW + c + 2;
-                const C* const mrow[3] = {momBm + g * RW + c + 2, mc, momA + g * RW + c + 2};
-                const SiteTerms st{shr[c], shr[W + c], shr[2 * W + c], shr[3 * W + c]};
-                nuw[g * VW + c + 1] = nu_of(mrow, momB0 + c + 2, st, chi_row, th_m, logc, minv1, has_log);
-            }
-        } else if (site) {
-            const C* m = momA + c + 2;
-            C rho = C(0), jx = C(0), jy = C(0);
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                rho += m[t * RW];
-                jx += m[N * RW + t * RW];
-                jy += m[2 * N * RW + t * RW];
-            }
-            const C inv = C(1) / rho;
-            C e[Q];
-            eq_weights(jx * inv, jy * inv, e);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) eqw[i * W + c] = e[i];
-        } else if (lane < 2 * N) {
-            if (j >= 2) {
+        // ---- phase B: nu of row j-3 (moment rows j-4 .. j-2)
+        if (j >= 2) {
+            if (comp) {
+                const int o = g * RW + c + 2;
+                nur[nuw + g * VW + c + 1] = nu_of(momC + o, momB + o, momA + o, momB + c + 2, c + 1, g,
+                                                  chi_row, th_m, logc, minv1, has_log);
+                nur[nuw + g * VW + c + 33] = nu_of(momC + o + 32, momB + o + 32, momA + o + 32,
+                                                   momB + c + 34, c + 33, g, chi_row, th_m, logc,
+                                                   minv1, has_log);
+            } else if (!site && lane < 2 * N) {
                 const int hv = lane / N, s = lane - hv * N;
-                const int cc = hv == 0 ? 1 : W + 2;  // moment-ring column of the halo nu site
                 const int vc = hv == 0 ? 0 : W + 1;
-                const C* const mrow[3] = {momBm + s * RW + cc, momB0 + s * RW + cc, momA + s * RW + cc};
-                const SiteTerms st = site_terms(momB0 + cc);
+                const int o = s * RW + vc + 1;
                 C chi_s[N];
 #pragma unroll
                 for (int u = 0; u < N; ++u) chi_s[u] = p.chi[s * N + u];
-                nuw[s * VW + vc] = nu_of(mrow, momB0 + cc, st, chi_s, p.th_m[s], p.logc[s],
-                                         p.m_inv_m1[s], (p.log_mask >> s) & 1u);
+                nur[nuw + s * VW + vc] = nu_of(momC + o, momB + o, momA + o, momB + vc + 1, vc, s, chi_s,
+                                               p.th_m[s], p.logc[s], p.m_inv_m1[s],
+                                               (p.log_mask >> s) & 1u);
             }
         }
         __syncthreads();
 
         // ---- phase C: collide row j-4 (source rows j-2 .. j, nu rows j-5 .. j-3)
-        if (comp && j >= 4 && x0 + c < p.nx) {
-            const int off = g * Q * WI + c + HX;
-            const T* const rows[3] = {stage(0) + off, stage(-1) + off, stage(-2) + off};
-            C f[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                f[i] = to_c<T>(rows[vy(i) + 1][i * WI - vx(i)]);
-                if constexpr (Storage<T>::shifted) f[i] += shift[i];
-            }
-            const C* mg = momBm + g * RW + c + 2;
-            const C rg = mg[0], jxg = mg[N * RW], jyg = mg[2 * N * RW];
-            C e[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) e[i] = eqc[i * W + c];
-            // grad nu = 3 sum_i w_i v_i nu(r + v_i)
-            const C* const vrow[3] = {nuA + g * VW + c + 1, nuB + g * VW + c + 1, nuw + g * VW + c + 1};
-            C gx = C(0), gy = C(0);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const C v = vrow[vy(i) + 1][vx(i)];
-                if (vx(i) != 0) gx += wq<C>(i) * C(vx(i)) * v;
-                if (vy(i) != 0) gy += wq<C>(i) * C(vy(i)) * v;
-            }
-            const C ax = -p.fcoef * (C(3) * gx) + p.gx;
-            const C ay = -p.fcoef * (C(3) * gy) + p.gy;
-            C out[Q];
-            collide(p, f, e, rg, jxg, jyg, ax, ay, out);
-            if constexpr (Storage<T>::shifted) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) out[i] -= shift[i];
-            }
-            const int x = x0 + c;
+        if (comp && j >= 4) {
             T* line = fout + line_off(p, g, y0 + j - 4, 0);
-            if (!any_ghost) {
-                T* q = line + HX + x;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) Storage<T>::store(q + i * p.pitch, out[i]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) store_row(line + i * p.pitch, x, p.nx, HX, out[i]);
-            }
+            collide_col(0, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, ghost0);
+            collide_col(32, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, ghost1);
         }
+        sj = (sj + 1 == NS) ? 0 : sj + 1;
+        j3 = j3p1;
     }
 
     if (*abort_flag) {

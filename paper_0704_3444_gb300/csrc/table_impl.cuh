@@ -60,48 +60,33 @@ struct Launch {
         });
     }
 
-    template <int N, int W>
-    static void consider(FusedPlan& best, int& best_score, const Problem& P, int sm_count)
-    {
-        using G = FusedGeom<T, N, W>;
-        const size_t limit = 227 * 1024;
-        if (G::SMEM > limit || G::THREADS > FUSED_MAX_THREADS) return;
-        const int wcap = std::max(32, (P.nx + 31) / 32 * 32);
-        if (W > wcap && W > 32) return;
-        if (cudaFuncSetAttribute(k_fused<T, N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)G::SMEM) != cudaSuccess)
-            return;
-        int ctas = 0;  // resident CTAs per SM as the runtime computes them (smem, registers)
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_fused<T, N, W>, G::THREADS,
-                                                          G::SMEM) != cudaSuccess || ctas < 1)
-            return;
-        const int warps = ctas * ((G::THREADS + 31) / 32);
-        const int score = warps * 4 + W / 32;  // most resident warps, then the wider strip
-        if (score <= best_score) return;
-        best_score = score;
-        best.W = W;
-        best.NS = G::NS;
-        best.smem = G::SMEM;
-        best.ok = true;
-        best.nstrips = (P.nx + W - 1) / W;
-        // one wave of tiles: as many row segments as resident CTAs allow, each as tall
-        // as possible (every segment re-reads 6 halo rows), at least 8 rows
-        const int slots = ctas * std::max(1, sm_count);
-        int nsegs = std::max(1, slots / best.nstrips);
-        nsegs = std::min(nsegs, std::max(1, P.ny / 8));
-        best.H = (P.ny + nsegs - 1) / nsegs;
-        best.nsegs = (P.ny + best.H - 1) / best.H;
-    }
-
     template <int N>
     static FusedPlan plan_n(const Problem& P, int sm_count)
     {
-        FusedPlan best{};
-        best.ok = false;
-        int score = -1;
-        consider<N, 32>(best, score, P, sm_count);
-        consider<N, 64>(best, score, P, sm_count);
-        return best;
+        using G = FusedGeom<T, N>;
+        FusedPlan pl{};
+        pl.ok = false;
+        if (G::SMEM > 227 * 1024 || G::THREADS > FUSED_MAX_THREADS) return pl;
+        if (cudaFuncSetAttribute(k_fused<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)G::SMEM) != cudaSuccess)
+            return pl;
+        int ctas = 0;  // resident CTAs per SM as the runtime computes them (smem, registers)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_fused<T, N>, G::THREADS,
+                                                          G::SMEM) != cudaSuccess || ctas < 1)
+            return pl;
+        pl.W = G::W;
+        pl.NS = G::NS;
+        pl.smem = G::SMEM;
+        pl.ok = true;
+        pl.nstrips = (P.nx + G::W - 1) / G::W;
+        // one wave of tiles: as many row segments as resident CTAs allow, each as tall
+        // as possible (every segment re-reads 6 halo rows), at least 8 rows
+        const int slots = ctas * std::max(1, sm_count);
+        int nsegs = std::max(1, slots / pl.nstrips);
+        nsegs = std::min(nsegs, std::max(1, P.ny / 8));
+        pl.H = (P.ny + nsegs - 1) / nsegs;
+        pl.nsegs = (P.ny + pl.H - 1) / pl.H;
+        return pl;
     }
 
     static FusedPlan plan_fused(const Problem& P, int sm_count)
@@ -127,13 +112,8 @@ struct Launch {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
         MCLB_DISPATCH_N(P.N, {
-            if (pl.W == 32) {
-                k_fused<T, NN, 32><<<grid, FusedGeom<T, NN, 32>::THREADS, pl.smem, st>>>(
-                    *tmap_in, (T*)fout, p, pl.H);
-            } else {
-                k_fused<T, NN, 64><<<grid, FusedGeom<T, NN, 64>::THREADS, pl.smem, st>>>(
-                    *tmap_in, (T*)fout, p, pl.H);
-            }
+            k_fused<T, NN><<<grid, FusedGeom<T, NN>::THREADS, pl.smem, st>>>(*tmap_in, (T*)fout, p,
+                                                                             pl.H);
             return cudaGetLastError();
         });
     }
