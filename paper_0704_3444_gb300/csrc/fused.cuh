@@ -124,13 +124,14 @@ __device__ __forceinline__ float to_c<__half>(__half v) { return __half2float(v)
 
 __host__ __device__ constexpr size_t round_up_sz(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
-// Compile-time geometry of one CTA: a strip of W = 64 columns; each component thread
-// handles the two columns c and c + 32 of its component; two site warps handle one
-// column per thread; one helper warp does the halo columns and issues the copies.
-template <typename T, int N>
+// Compile-time geometry of one CTA: a strip of W = 32 COLS columns; each component
+// thread handles the COLS columns c, c + 32, ... of its component; COLS site warps
+// handle one column per thread; one helper warp does the halo columns and issues the
+// copies.
+template <typename T, int N, int COLS>
 struct FusedGeom {
     using C = typename Storage<T>::C;
-    static constexpr int W = 64;
+    static constexpr int W = 32 * COLS;
     static constexpr int NS = 6;                       // source-row stages
     static constexpr int PF = 4;                       // L2 prefetch distance (rows) of a copy
     static constexpr int HX = (16 / (int)sizeof(T)) < 4 ? 4 : 16 / (int)sizeof(T);
@@ -163,12 +164,12 @@ struct FusedGeom {
 
 constexpr int FUSED_MAX_THREADS = 1024;
 
-template <typename T, int N>
-__global__ void __launch_bounds__(FusedGeom<T, N>::THREADS, FusedGeom<T, N>::MIN_CTAS)
+template <typename T, int N, int COLS>
+__global__ void __launch_bounds__(FusedGeom<T, N, COLS>::THREADS, FusedGeom<T, N, COLS>::MIN_CTAS)
 k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         const __grid_constant__ StepParams<typename Storage<T>::C> p, const int H)
 {
-    using G = FusedGeom<T, N>;
+    using G = FusedGeom<T, N, COLS>;
     using C = typename Storage<T>::C;
     constexpr int W = G::W, NS = G::NS, HX = G::HX, WI = G::WI, RW = G::RW, VW = G::VW;
     constexpr int NCT = G::NCT, NST = G::NST;
@@ -343,7 +344,9 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
 
     // columns whose value is repeated in a ghost column
     auto has_ghost = [&](int x) { return p.nx < HX || x < HX || x >= p.nx - HX; };
-    const bool ghost0 = has_ghost(x0 + c), ghost1 = has_ghost(x0 + c + 32);
+    bool ghost[COLS];
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) ghost[k] = has_ghost(x0 + c + 32 * k);
 
     bool ok = true;
     if (!site) {
@@ -378,9 +381,11 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         // ---- phase A: moments of row j-2 (source rows j .. j+2); site terms and
         //      equilibrium weights of row j-3 (moments complete since the last phase A)
         if (comp) {
-            const int col = g * Q * WI + c + HX;
-            moments_to(stp2 + col, stp1 + col, st0 + col, momA + g * RW + c + 2, shift);
-            moments_to(stp2 + col + 32, stp1 + col + 32, st0 + col + 32, momA + g * RW + c + 34, shift);
+#pragma unroll
+            for (int k = 0; k < COLS; ++k) {
+                const int col = g * Q * WI + c + 32 * k + HX;
+                moments_to(stp2 + col, stp1 + col, st0 + col, momA + g * RW + c + 32 * k + 2, shift);
+            }
         } else if (site) {
             if (j >= 1) {
                 C inv;
@@ -431,12 +436,13 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         // ---- phase B: nu of row j-3 (moment rows j-4 .. j-2)
         if (j >= 2) {
             if (comp) {
-                const int o = g * RW + c + 2;
-                nur[nuw + g * VW + c + 1] = nu_of(momC + o, momB + o, momA + o, momB + c + 2, c + 1, g,
-                                                  chi_row, th_m, logc, minv1, has_log);
-                nur[nuw + g * VW + c + 33] = nu_of(momC + o + 32, momB + o + 32, momA + o + 32,
-                                                   momB + c + 34, c + 33, g, chi_row, th_m, logc,
-                                                   minv1, has_log);
+#pragma unroll
+                for (int k = 0; k < COLS; ++k) {
+                    const int o = g * RW + c + 32 * k + 2;
+                    nur[nuw + g * VW + c + 32 * k + 1] =
+                        nu_of(momC + o, momB + o, momA + o, momB + c + 32 * k + 2, c + 32 * k + 1, g,
+                              chi_row, th_m, logc, minv1, has_log);
+                }
             } else if (!site && lane < 2 * N) {
                 const int hv = lane / N, s = lane - hv * N;
                 const int vc = hv == 0 ? 0 : W + 1;
@@ -454,8 +460,9 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         // ---- phase C: collide row j-4 (source rows j-2 .. j, nu rows j-5 .. j-3)
         if (comp && j >= 4) {
             T* line = fout + line_off(p, g, y0 + j - 4, 0);
-            collide_col(0, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, ghost0);
-            collide_col(32, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, ghost1);
+#pragma unroll
+            for (int k = 0; k < COLS; ++k)
+                collide_col(32 * k, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, ghost[k]);
         }
         sj = (sj + 1 == NS) ? 0 : sj + 1;
         j3 = j3p1;

@@ -60,20 +60,18 @@ struct Launch {
         });
     }
 
-    template <int N>
-    static FusedPlan plan_n(const Problem& P, int sm_count)
+    template <int N, int COLS>
+    static bool plan_cols(const Problem& P, int sm_count, FusedPlan& pl)
     {
-        using G = FusedGeom<T, N>;
-        FusedPlan pl{};
-        pl.ok = false;
-        if (G::SMEM > 227 * 1024 || G::THREADS > FUSED_MAX_THREADS) return pl;
-        if (cudaFuncSetAttribute(k_fused<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        using G = FusedGeom<T, N, COLS>;
+        if (G::SMEM > 227 * 1024 || G::THREADS > FUSED_MAX_THREADS) return false;
+        if (cudaFuncSetAttribute(k_fused<T, N, COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)G::SMEM) != cudaSuccess)
-            return pl;
+            return false;
         int ctas = 0;  // resident CTAs per SM as the runtime computes them (smem, registers)
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_fused<T, N>, G::THREADS,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_fused<T, N, COLS>, G::THREADS,
                                                           G::SMEM) != cudaSuccess || ctas < 1)
-            return pl;
+            return false;
         pl.W = G::W;
         pl.NS = G::NS;
         pl.smem = G::SMEM;
@@ -86,6 +84,17 @@ struct Launch {
         nsegs = std::min(nsegs, std::max(1, P.ny / 8));
         pl.H = (P.ny + nsegs - 1) / nsegs;
         pl.nsegs = (P.ny + pl.H - 1) / pl.H;
+        return true;
+    }
+
+    // two columns per component thread (64-column strips) when shared memory allows,
+    // else one (32-column strips)
+    template <int N>
+    static FusedPlan plan_n(const Problem& P, int sm_count)
+    {
+        FusedPlan pl{};
+        pl.ok = false;
+        if (!plan_cols<N, 2>(P, sm_count, pl)) plan_cols<N, 1>(P, sm_count, pl);
         return pl;
     }
 
@@ -112,8 +121,12 @@ struct Launch {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
         MCLB_DISPATCH_N(P.N, {
-            k_fused<T, NN><<<grid, FusedGeom<T, NN>::THREADS, pl.smem, st>>>(*tmap_in, (T*)fout, p,
-                                                                             pl.H);
+            if (pl.W == 64)
+                k_fused<T, NN, 2><<<grid, FusedGeom<T, NN, 2>::THREADS, pl.smem, st>>>(
+                    *tmap_in, (T*)fout, p, pl.H);
+            else
+                k_fused<T, NN, 1><<<grid, FusedGeom<T, NN, 1>::THREADS, pl.smem, st>>>(
+                    *tmap_in, (T*)fout, p, pl.H);
             return cudaGetLastError();
         });
     }
