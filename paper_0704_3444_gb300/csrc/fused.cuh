@@ -229,64 +229,8 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     const C th_m = p.th_m[g], logc = p.logc[g], minv1 = p.m_inv_m1[g];
     const bool has_log = (p.log_mask >> g) & 1u;
 
-    // columns whose value is repeated in a ghost column
-    auto has_ghost = [&](int x) { return p.nx < HX || x < HX || x >= p.nx - HX; };
-    bool ghost[COLS];
-#pragma unroll
-    for (int k = 0; k < COLS; ++k) ghost[k] = has_ghost(x0 + c + 32 * k);
-
-    // The component threads compute their COLS columns (c, c + 32, ...) together in CV.
-    using CV = typename ColsOf<C, COLS>::type;
-    auto pack = [](const C (&x)[COLS]) -> CV {
-        if constexpr (COLS == 2) return CV(x[0], x[1]);
-        else return CV(x[0]);
-    };
-    auto unpack = [](CV v, C (&x)[COLS]) {
-        if constexpr (COLS == 2) { x[0] = v.lo(); x[1] = v.hi(); }
-        else x[0] = v;
-    };
-    // COLS stage values at element offset off (columns 32 apart)
-    auto ld_stage = [&](int off) -> CV {
-        C x[COLS];
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) x[k] = to_c<T>(stg[off + 32 * k]);
-        return pack(x);
-    };
-    auto ld_c = [&](const C* a, int off) -> CV {
-        C x[COLS];
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) x[k] = a[off + 32 * k];
-        return pack(x);
-    };
-    auto st_c = [&](C* a, int off, CV v) {
-        C x[COLS];
-        unpack(v, x);
-#pragma unroll
-        for (int k = 0; k < COLS; ++k) a[off + 32 * k] = x[k];
-    };
-    CV shiftv[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) shiftv[i] = CV(shift[i]);
-
-    // moments of component g at the thread's columns: a0/a1/a2 are the stage offsets of
-    // the velocity-0 line (first column applied) for source rows dy = -1, 0, +1
-    auto moments_comp = [&](int a0, int a1, int a2, int dst) {
-        const int ar[3] = {a0, a1, a2};
-        CV v[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            v[i] = ld_stage(ar[vy(i) + 1] + i * WI - vx(i));
-            if constexpr (Storage<T>::shifted) v[i] = v[i] + shiftv[i];
-        }
-        CV r = v[0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) r = r + v[i];
-        st_c(mom, dst, r);
-        st_c(mom, dst + N * RW, (v[1] + v[5] + v[8]) - (v[3] + v[6] + v[7]));
-        st_c(mom, dst + 2 * N * RW, (v[2] + v[5] + v[6]) - (v[4] + v[7] + v[8]));
-    };
-
-    // scalar moments of component s at one halo column (helper warp)
+    // moments of one component at one column: a0/a1/a2 are the stage element offsets of
+    // the velocity-0 line (column applied) in the source rows for dy = -1, 0, +1
     auto moments_to = [&](int a0, int a1, int a2, int dst, const C (&sh)[Q]) {
         const int ar[3] = {a0, a1, a2};
         C v[Q];
@@ -332,10 +276,10 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         return rho;
     };
 
-    // nu^s at one halo column (scalar, helper warp): m* = moment offsets of component s
-    // at the column in rows r-1, r, r+1; d0 = offset of component 0 in row r
-    auto nu_of = [&](int mm, int m0, int mp, int d0, int vc, const C (&chi_s)[N], C thm, C lc,
-                     C mi1, bool lg) -> C {
+    // nu^s at one column: m[dy+1] = moment offsets of component s at the column in rows
+    // r-1, r, r+1; d0 = offset of component 0 in row r; site terms at nu column vc
+    auto nu_of = [&](int mm, int m0, int mp, int d0, int vc, int s, const C (&chi_s)[N], C thm,
+                     C lc, C mi1, bool lg) -> C {
         const int mr[3] = {mm, m0, mp};
         C acc = C(0);
 #pragma unroll
@@ -349,88 +293,60 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             const C fl = p.log_floor * shr[vc];
             logs += lc * dev_log(own > fl ? own : fl);
         }
+        (void)s;
         return logs + p.theta * (mi1 + acc * shr[VW + vc]) + shr[3 * VW + vc] - p.kappa * (C(6) * lap);
     };
 
-    // nu^g at the thread's columns (first nu column vc): same formula in CV
-    const CV thmv(th_m), minv1v(minv1), thetav(p.theta), kappa6v(C(6) * p.kappa);
-    CV chiv[N];
-#pragma unroll
-    for (int u = 0; u < N; ++u) chiv[u] = CV(chi_row[u]);
-    auto nu_comp = [&](int mm, int m0, int mp, int d0, int vc) -> CV {
-        const int mr[3] = {mm, m0, mp};
-        CV acc = chiv[0] * ld_c(mom, d0);
-#pragma unroll
-        for (int u = 1; u < N; ++u) acc = fma(chiv[u], ld_c(mom, d0 + u * RW), acc);
-        const CV own = ld_c(mom, m0);
-        CV lap = wv<CV>(0) * (ld_c(mom, mr[1]) - own);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) lap = fma(wv<CV>(i), ld_c(mom, mr[vy(i) + 1] + vx(i)) - own, lap);
-        CV logs = -thmv * ld_c(shr, 2 * VW + vc);
-        if (has_log) {
-            C o[COLS], fr[COLS], lgv[COLS];
-            unpack(own, o);
-            unpack(ld_c(shr, vc), fr);
-#pragma unroll
-            for (int k = 0; k < COLS; ++k) {
-                const C fl = p.log_floor * fr[k];
-                lgv[k] = logc * dev_log(o[k] > fl ? o[k] : fl);
-            }
-            logs = logs + pack(lgv);
-        }
-        const CV bulk = thetav * fma(acc, ld_c(shr, VW + vc), minv1v);
-        return (logs + bulk) + ld_c(shr, 3 * VW + vc) - kappa6v * lap;
-    };
-
-    // collision of component g at the thread's columns (all valid: x0 + c + 32 k < nx)
-    const CV fcoef3v(C(-3) * p.fcoef), gxv(p.gx), gyv(p.gy);
-    auto collide_comp = [&](int s0, int s1, int s2, int momr, int eqo, int n0, int n1, int n2,
-                            T* line) {
-        const int col = g * Q * WI + c + HX;
+    // collision of component g at first-column offset cc (0 or 32) of the strip
+    auto collide_col = [&](int cc, int s0, int s1, int s2, int momr, int eqo, int n0, int n1, int n2,
+                           T* line, bool ghost) {
+        const int x = x0 + c + cc;
+        if (x >= p.nx) return;
+        const int col = g * Q * WI + c + cc + HX;
         const int ar[3] = {s0 + col, s1 + col, s2 + col};
-        CV f[Q];
+        C f[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = ld_stage(ar[vy(i) + 1] + i * WI - vx(i));
-            if constexpr (Storage<T>::shifted) f[i] = f[i] + shiftv[i];
+            f[i] = to_c<T>(stg[ar[vy(i) + 1] + i * WI - vx(i)]);
+            if constexpr (Storage<T>::shifted) f[i] += shift[i];
         }
-        const int mg = momr + g * RW + c + 2;
-        const CV rg = ld_c(mom, mg), jxg = ld_c(mom, mg + N * RW), jyg = ld_c(mom, mg + 2 * N * RW);
-        CV e[Q];
+        const int mg = momr + g * RW + c + cc + 2;
+        const C rg = mom[mg], jxg = mom[mg + N * RW], jyg = mom[mg + 2 * N * RW];
+        C e[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) e[i] = ld_c(eqr, eqo + i * W + c);
-        const int vo = g * VW + c + 1;
+        for (int i = 0; i < Q; ++i) e[i] = eqr[eqo + i * W + c + cc];
+        const int vo = g * VW + c + cc + 1;
         const int nr[3] = {n0 + vo, n1 + vo, n2 + vo};
-        // grad nu = 3 sum_i w_i v_i nu(r + v_i):
-        //   x: (E - W)/9 + (NE + SE - NW - SW)/36, and likewise in y
-        const CV nE = ld_c(nur, nr[1] + 1), nW = ld_c(nur, nr[1] - 1);
-        const CV nN = ld_c(nur, nr[2]), nS = ld_c(nur, nr[0]);
-        const CV nNE = ld_c(nur, nr[2] + 1), nNW = ld_c(nur, nr[2] - 1);
-        const CV nSE = ld_c(nur, nr[0] + 1), nSW = ld_c(nur, nr[0] - 1);
-        const CV d1 = nNE - nSW, d2 = nSE - nNW;  // the diagonals enter x as d1 + d2, y as d1 - d2
-        const CV gx = fma(CV(C(1) / C(9)), nE - nW, CV(C(1) / C(36)) * (d1 + d2));
-        const CV gy = fma(CV(C(1) / C(9)), nN - nS, CV(C(1) / C(36)) * (d1 - d2));
-        // a = -(1 - 1/(2 tau)) grad nu + g, grad = 3 (gx, gy)
-        const CV ax = fma(fcoef3v, gx, gxv), ay = fma(fcoef3v, gy, gyv);
-        CV out[Q];
+        C gx = C(0), gy = C(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const C v = nur[nr[vy(i) + 1] + vx(i)];
+            if (vx(i) != 0) gx += wq<C>(i) * C(vx(i)) * v;
+            if (vy(i) != 0) gy += wq<C>(i) * C(vy(i)) * v;
+        }
+        const C ax = -p.fcoef * (C(3) * gx) + p.gx;
+        const C ay = -p.fcoef * (C(3) * gy) + p.gy;
+        C out[Q];
         collide(p, f, e, rg, jxg, jyg, ax, ay, out);
-        const int pitch = (int)p.pitch;
+        if constexpr (Storage<T>::shifted) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            CV v = out[i];
-            if constexpr (Storage<T>::shifted) v = v - shiftv[i];
-            C x[COLS];
-            unpack(v, x);
+            for (int i = 0; i < Q; ++i) out[i] -= shift[i];
+        }
+        if (!ghost) {
+            T* q = line + HX + x;
 #pragma unroll
-            for (int k = 0; k < COLS; ++k) {
-                const int xx = x0 + c + 32 * k;
-                if (xx >= p.nx) continue;
-                if (!ghost[k]) Storage<T>::store(line + HX + xx + i * pitch, x[k]);
-                else store_row(line + i * pitch, xx, p.nx, HX, x[k]);
-            }
+            for (int i = 0; i < Q; ++i) Storage<T>::store(q + i * p.pitch, out[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) store_row(line + i * p.pitch, x, p.nx, HX, out[i]);
         }
     };
 
+    // columns whose value is repeated in a ghost column
+    auto has_ghost = [&](int x) { return p.nx < HX || x < HX || x >= p.nx - HX; };
+    bool ghost[COLS];
+#pragma unroll
+    for (int k = 0; k < COLS; ++k) ghost[k] = has_ghost(x0 + c + 32 * k);
 
     bool ok = true;
     if (!site) {
@@ -465,8 +381,11 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         // ---- phase A: moments of row j-2 (source rows j .. j+2); site terms and
         //      equilibrium weights of row j-3 (moments complete since the last phase A)
         if (comp) {
-            const int col = g * Q * WI + c + HX;
-            moments_comp(stp2 + col, stp1 + col, st0 + col, momA + g * RW + c + 2);
+#pragma unroll
+            for (int k = 0; k < COLS; ++k) {
+                const int col = g * Q * WI + c + 32 * k + HX;
+                moments_to(stp2 + col, stp1 + col, st0 + col, momA + g * RW + c + 32 * k + 2, shift);
+            }
         } else if (site) {
             if (j >= 1) {
                 C inv;
@@ -517,8 +436,13 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         // ---- phase B: nu of row j-3 (moment rows j-4 .. j-2)
         if (j >= 2) {
             if (comp) {
-                const int o = g * RW + c + 2;
-                st_c(nur, nuw + g * VW + c + 1, nu_comp(momC + o, momB + o, momA + o, momB + c + 2, c + 1));
+#pragma unroll
+                for (int k = 0; k < COLS; ++k) {
+                    const int o = g * RW + c + 32 * k + 2;
+                    nur[nuw + g * VW + c + 32 * k + 1] =
+                        nu_of(momC + o, momB + o, momA + o, momB + c + 32 * k + 2, c + 32 * k + 1, g,
+                              chi_row, th_m, logc, minv1, has_log);
+                }
             } else if (!site && lane < 2 * N) {
                 const int hv = lane / N, s = lane - hv * N;
                 const int vc = hv == 0 ? 0 : W + 1;
@@ -526,7 +450,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
                 C chi_s[N];
 #pragma unroll
                 for (int u = 0; u < N; ++u) chi_s[u] = p.chi[s * N + u];
-                nur[nuw + s * VW + vc] = nu_of(momC + o, momB + o, momA + o, momB + vc + 1, vc, chi_s,
+                nur[nuw + s * VW + vc] = nu_of(momC + o, momB + o, momA + o, momB + vc + 1, vc, s, chi_s,
                                                p.th_m[s], p.logc[s], p.m_inv_m1[s],
                                                (p.log_mask >> s) & 1u);
             }
@@ -534,9 +458,11 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         __syncthreads();
 
         // ---- phase C: collide row j-4 (source rows j-2 .. j, nu rows j-5 .. j-3)
-        if (comp && j >= 4 && x0 + c < p.nx) {
+        if (comp && j >= 4) {
             T* line = fout + line_off(p, g, y0 + j - 4, 0);
-            collide_comp(st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line);
+#pragma unroll
+            for (int k = 0; k < COLS; ++k)
+                collide_col(32 * k, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, ghost[k]);
         }
         sj = (sj + 1 == NS) ? 0 : sj + 1;
         j3 = j3p1;

@@ -13,62 +13,6 @@ __device__ __forceinline__ double dev_log<double>(double x) { return log(x); }
 template <>
 __device__ __forceinline__ float dev_log<float>(float x) { return logf(x); }
 
-// Scalar fused multiply-add under the same name as the pair overloads below.
-__device__ __forceinline__ float fma(float a, float b, float c) { return ::fmaf(a, b, c); }
-__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
-
-// Two columns computed together.  For FP32 every operation is one packed FP32x2
-// instruction (add/mul/fma with round-to-nearest, as the scalar path); for FP64 the
-// pair is plain element-wise arithmetic.
-struct F2 {
-    float2 v;
-    __device__ __forceinline__ F2() {}
-    __device__ __forceinline__ explicit F2(float s) : v(make_float2(s, s)) {}
-    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
-    __device__ __forceinline__ explicit F2(float2 x) : v(x) {}
-    __device__ __forceinline__ float lo() const { return v.x; }
-    __device__ __forceinline__ float hi() const { return v.y; }
-};
-__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
-// a - b = (-1) b + a, one rounding as the scalar subtraction
-__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
-__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
-__device__ __forceinline__ F2& operator+=(F2& a, F2 b) { a = a + b; return a; }
-__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
-
-struct D2 {
-    double x, y;
-    __device__ __forceinline__ D2() {}
-    __device__ __forceinline__ explicit D2(double s) : x(s), y(s) {}
-    __device__ __forceinline__ D2(double a, double b) : x(a), y(b) {}
-    __device__ __forceinline__ double lo() const { return x; }
-    __device__ __forceinline__ double hi() const { return y; }
-};
-__device__ __forceinline__ D2 operator+(D2 a, D2 b) { return D2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ D2 operator-(D2 a) { return D2(-a.x, -a.y); }
-__device__ __forceinline__ D2 operator-(D2 a, D2 b) { return D2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ D2 operator*(D2 a, D2 b) { return D2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ D2& operator+=(D2& a, D2 b) { a = a + b; return a; }
-__device__ __forceinline__ D2 fma(D2 a, D2 b, D2 c) { return D2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
-
-// Arithmetic type for K columns at once, and the scalar type underneath.
-template <typename C, int K>
-struct ColsOf { using type = C; };
-template <typename V>
-struct ScalarOf { using type = V; };
-template <>
-struct ScalarOf<F2> { using type = float; };
-template <>
-struct ScalarOf<D2> { using type = double; };
-// lattice weight w_i in any arithmetic type
-template <typename V>
-__device__ __forceinline__ V wv(int i) { return V(wq<typename ScalarOf<V>::type>(i)); }
-template <>
-struct ColsOf<float, 2> { using type = F2; };
-template <>
-struct ColsOf<double, 2> { using type = D2; };
-
 // nu^s = mu^s/m^s - kappa lap rho^s - (1/3) ln rho^s for every component at one site
 // (Eq. lgf, Eq. chemicalpotential, Eq. definef).  The Flory-Huggins potential per
 // unit mass is
@@ -206,10 +150,10 @@ __device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (i == 0) {
-            e[0] = wv<C>(0) * base;
+            e[0] = wq<C>(0) * base;
         } else {
             const C cu = du(i);
-            e[i] = wv<C>(i) * fma(cu, fma(C(4.5), cu, C(3)), base);
+            e[i] = wq<C>(i) * fma(cu, fma(C(4.5), cu, C(3)), base);
         }
     }
 }
@@ -218,19 +162,19 @@ __device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
 //   f* = f + (f^e - f)/tau + F,  f^e_i = rho^s e_i,
 //   F_i = w_i [3 rho^s (v_i.a) + 9 (v_i.a)(v_i.j) - 3 a.j]   (Eqs. ff1-ff3, j = rho^s u^s),
 // evaluated as f (1 - 1/tau) + (rho^s/tau) e_i + w_i [(v_i.a)(9 v_i.j + 3 rho^s) - 3 a.j].
-template <typename C, typename P>
-__device__ __forceinline__ void collide(const StepParams<P>& p, const C (&f)[Q], const C (&e)[Q],
+template <typename C>
+__device__ __forceinline__ void collide(const StepParams<C>& p, const C (&f)[Q], const C (&e)[Q],
                                         C r, C jx, C jy, C ax, C ay, C (&out)[Q])
 {
     const VDots<C> da(ax, ay), dj(jx, jy);
     const C m3aj = C(-3) * (ax * jx + ay * jy);
     const C r3 = C(3) * r;
-    const C omr = C(p.omega) * r;
-    const C keep = C(P(1) - p.omega);
+    const C omr = p.omega * r;
+    const C keep = C(1) - p.omega;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const C F = (i == 0) ? wv<C>(0) * m3aj
-                             : wv<C>(i) * fma(da(i), fma(C(9), dj(i), r3), m3aj);
+        const C F = (i == 0) ? wq<C>(0) * m3aj
+                             : wq<C>(i) * fma(da(i), fma(C(9), dj(i), r3), m3aj);
         out[i] = fma(keep, f[i], fma(omr, e[i], F));
     }
 }
