@@ -174,6 +174,33 @@ int mclb_destroy(mclb_handle h);
 const char* mclb_last_error(void);
 
 /* ----------------------------------------------------------------------------
+ * Allocation-free timestep.  (The paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory: code that runs inside a host
+ * application which owns a fixed, pre-reserved device memory budget, or code that must
+ * not call cudaMalloc/cudaFree because those calls synchronise the device and would
+ * break the caller's own overlap of work.)
+ *
+ * mclb_step_noalloc advances the distributions by one timestep with the staged
+ * schedule in FP64 (params->precision must be MCLB_FP64; params->kernel is ignored).
+ * Its two scratch fields live in one fixed array inside the library (a static device
+ * array of 2 * MCLB_NOALLOC_MAX_COMP_SITES doubles, 8 MiB, which every GPU that loads
+ * the library holds until the process exits); the call allocates nothing.
+ *   f_in   device array, N*9*ny*nx doubles, pre-collision f^s_i(r, t) in the layout of
+ *          mclb_get_state ([s][i][y][x]); read only
+ *   f_out  device array of the same size, distinct from f_in; receives f^s_i(r, t + 1)
+ * Work is enqueued on params->stream (NULL: the legacy default stream) and the call
+ * returns without waiting.  Errors: EINVAL for invalid params, a precision other than
+ * FP64, NULL or identical arrays, or N*nx*ny above MCLB_NOALLOC_MAX_COMP_SITES; ECUDA
+ * if no device is usable or a launch fails.  Non-finite values are not reported.
+ * The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the one array,
+ * so calls that overlap on the GPU (on different streams, or from several threads)
+ * race with each other; serialise them.
+ * ------------------------------------------------------------------------- */
+#define MCLB_NOALLOC_MAX_COMP_SITES 524288 /* largest N * nx * ny */
+int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_out);
+
+/* ----------------------------------------------------------------------------
  * Batched simulations: count independent problems (each its own N, grid, chi, tau,
  * ...) advanced together, one launch per timestep for the whole batch, captured in
  * a CUDA graph.  precision and stream are taken from params[0]; kernel is ignored.

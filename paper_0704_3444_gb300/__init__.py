@@ -93,6 +93,8 @@ def load():
             "mclb_batch_status": ([H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "mclb_batch_bytes_per_step": ([H], ctypes.c_double),
             "mclb_batch_destroy": ([H], ctypes.c_int),
+            "mclb_step_noalloc": ([ctypes.POINTER(mclb_params), ctypes.c_void_p, ctypes.c_void_p],
+                                  ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

@@ -127,6 +127,12 @@ void fill_problem(const mclb_params* p, int hx, Problem& P)
 
 }  // namespace
 
+namespace mclb {
+// Parameter validation and error reporting shared with the allocation-free entry point.
+int check_params(const mclb_params* p) { return validate(p); }
+int report(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace mclb
+
 struct mclb_handle_s {
     uint32_t magic;
     int precision, kernel;
