@@ -202,16 +202,22 @@ int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_o
 
 /* ----------------------------------------------------------------------------
  * Batched simulations: count independent problems (each its own N, grid, chi, tau,
- * ...) advanced together, one launch per timestep for the whole batch, captured in
- * a CUDA graph.  precision and stream are taken from params[0]; kernel is ignored.
- * Instances share no data.  Errors as for the single-simulation calls, and
- * EINVAL for an index outside 0..count-1.
+ * ...) advanced together by the staged schedule: per timestep, three launches for
+ * each distinct N in the batch cover every instance (each block works on one
+ * instance, found through a block-to-instance table), replayed from a CUDA graph in
+ * chunks of 32 steps.  precision and stream are taken from params[0]; kernel is
+ * ignored.  Instances share no data.  Every instance must be initialised
+ * (mclb_batch_init_fields) before the first mclb_batch_step.  Errors as for the
+ * single-simulation calls, and EINVAL for an index outside 0..count-1.
  * ------------------------------------------------------------------------- */
 typedef struct mclb_batch_s* mclb_batch;
 
 int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out);
 int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const double* u);
+/* Enqueue nsteps timesteps of every instance; returns without waiting. */
 int mclb_batch_step(mclb_batch b, long nsteps);
+/* Kernel launches one batched timestep issues (3 per distinct N). */
+int mclb_batch_launches_per_step(mclb_batch b);
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P);
 int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count);
 /* per_instance (count ints, may be NULL) receives each instance's status; the

@@ -92,6 +92,7 @@ def load():
             "mclb_batch_get_state": ([H, ctypes.c_int, dp, ctypes.c_size_t], ctypes.c_int),
             "mclb_batch_status": ([H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "mclb_batch_bytes_per_step": ([H], ctypes.c_double),
+            "mclb_batch_launches_per_step": ([H], ctypes.c_int),
             "mclb_batch_destroy": ([H], ctypes.c_int),
             "mclb_step_noalloc": ([ctypes.POINTER(mclb_params), ctypes.c_void_p, ctypes.c_void_p],
                                   ctypes.c_int),
@@ -310,3 +311,7 @@ class Batch:
     @property
     def bytes_per_step(self):
         return self.lib.mclb_batch_bytes_per_step(self.h)
+
+    @property
+    def launches_per_step(self):
+        return self.lib.mclb_batch_launches_per_step(self.h)

@@ -667,10 +667,91 @@ int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi)
 
 struct mclb_batch_s {
     uint32_t magic;
-    std::vector<mclb_handle> items;
+    std::vector<mclb_handle> items;   // one handle per instance (buffers, scratch, status)
     cudaStream_t stream;
     bool own_stream;
+    const KernelTable* tab;
+    std::vector<void*> groups;        // batched launches, one group per distinct N
+    bool dirty;                       // groups must be rebuilt (new shifts after init)
+    int parity;                       // buffer holding every instance's current state
+    cudaGraphExec_t graph[2];
+    bool graph_tried[2];
 };
+
+namespace {
+
+void batch_drop(mclb_batch b)
+{
+    for (void* g : b->groups) b->tab->batch_destroy(g);
+    b->groups.clear();
+    for (int k = 0; k < 2; ++k) {
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+        b->graph[k] = nullptr;
+        b->graph_tried[k] = false;
+    }
+}
+
+int batch_build(mclb_batch b)
+{
+    batch_drop(b);
+    for (int n = 1; n <= NMAX; ++n) {
+        std::vector<Problem> probs;
+        std::vector<Scratch> scs;
+        std::vector<void*> fa, fb;
+        for (auto h : b->items)
+            if (h->P.N == n) {
+                probs.push_back(h->P);
+                scs.push_back(h->sc);
+                fa.push_back(h->f[0]);
+                fb.push_back(h->f[1]);
+            }
+        if (probs.empty()) continue;
+        void* g = b->tab->batch_create(n, (int)probs.size(), probs.data(), scs.data(), fa.data(),
+                                       fb.data(), b->stream);
+        if (!g) {
+            batch_drop(b);
+            return fail(MCLB_ENOMEM, "batched launch tables for N=%d could not be built", n);
+        }
+        b->groups.push_back(g);
+    }
+    b->dirty = false;
+    return MCLB_OK;
+}
+
+cudaError_t batch_launch(mclb_batch b, int parity)
+{
+    for (void* g : b->groups) {
+        const cudaError_t e = b->tab->batch_step(g, parity, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void batch_capture(mclb_batch b, int from)
+{
+    b->graph_tried[from] = true;
+    b->graph[from] = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    int par = from;
+    bool ok = true;
+    for (int k = 0; k < GRAPH_STEPS && ok; ++k) {
+        ok = batch_launch(b, par) == cudaSuccess;
+        par ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (ok && e == cudaSuccess && g) {
+        cudaGraphExec_t ex = nullptr;
+        if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) b->graph[from] = ex;
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -682,8 +763,11 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
     mclb_batch b = new (std::nothrow) mclb_batch_s();
     if (!b) return fail(MCLB_ENOMEM, "host allocation failed");
     b->magic = MAGIC;
+    b->tab = &table_for(params[0].precision);
     b->stream = (cudaStream_t)params[0].stream;
     b->own_stream = false;
+    b->dirty = true;
+    b->parity = 0;
     if (!b->stream) {
         if (cudaStreamCreate(&b->stream) != cudaSuccess) {
             delete b;
@@ -694,6 +778,7 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
     for (int k = 0; k < count; ++k) {
         mclb_params p = params[k];
         p.precision = params[0].precision;
+        p.kernel = MCLB_KERNEL_STAGED;
         p.stream = b->stream;
         mclb_handle h = nullptr;
         int rc = mclb_create(&p, &h);
@@ -721,18 +806,50 @@ int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const dou
 {
     mclb_handle h;
     int rc = batch_item(b, index, &h);
-    return rc ? rc : mclb_init_fields(h, rho, u);
+    if (rc) return rc;
+    rc = mclb_init_fields(h, rho, u);  // writes buffer 0
+    if (rc) return rc;
+    if (b->parity == 1) {              // every instance's state lives in the batch's buffer
+        CK(cudaMemcpyAsync(h->f[1], h->f[0], h->fbytes, cudaMemcpyDeviceToDevice, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        h->cur = 1;
+    }
+    b->dirty = true;                   // the instance's shifts may have changed
+    return MCLB_OK;
 }
 
 int mclb_batch_step(mclb_batch b, long nsteps)
 {
     if (!b || b->magic != MAGIC) return fail(MCLB_EHANDLE, "batch destroyed or not a batch");
-    int first = MCLB_OK;
-    for (auto h : b->items) {
-        int rc = mclb_step(h, nsteps);
-        if (rc && !first) first = rc;
+    if (nsteps < 0) return fail(MCLB_EINVAL, "nsteps=%ld < 0", nsteps);
+    if (b->dirty) {
+        int rc = batch_build(b);
+        if (rc) return rc;
     }
-    return first;
+    cudaGetLastError();
+    long left = nsteps;
+    while (left >= GRAPH_STEPS) {
+        if (!b->graph_tried[b->parity]) batch_capture(b, b->parity);
+        if (!b->graph[b->parity]) break;
+        CK(cudaGraphLaunch(b->graph[b->parity], b->stream));
+        left -= GRAPH_STEPS;  // an even number of steps: the parity is unchanged
+    }
+    for (; left > 0; --left) {
+        CK(batch_launch(b, b->parity));
+        b->parity ^= 1;
+    }
+    for (auto h : b->items) {
+        h->cur = b->parity;
+        h->steps += nsteps;
+    }
+    return MCLB_OK;
+}
+
+int mclb_batch_launches_per_step(mclb_batch b)
+{
+    if (!b || b->magic != MAGIC) return -1;
+    if (b->dirty && batch_build(b)) return -1;
+    return 3 * (int)b->groups.size();
 }
 
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P)
@@ -773,6 +890,8 @@ int mclb_batch_destroy(mclb_batch b)
 {
     if (!b) return MCLB_OK;
     if (b->magic != MAGIC) return fail(MCLB_EHANDLE, "batch destroyed or not a batch");
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop(b);
     for (auto h : b->items) mclb_destroy(h);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     b->magic = DEAD;

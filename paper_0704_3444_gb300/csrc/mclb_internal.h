@@ -93,6 +93,12 @@ struct KernelTable {
                              cudaStream_t st);
     cudaError_t (*set_state)(const Problem&, const Scratch&, const double* in, void* f,
                              cudaStream_t st);
+    // batches: a group of `count` instances with the same N (buffers fa/fb, scratch scs);
+    // one staged step of the whole group reads buffer `parity` and writes the other
+    void* (*batch_create)(int N, int count, const Problem* probs, const Scratch* scs,
+                          void* const* fa, void* const* fb, cudaStream_t st);
+    cudaError_t (*batch_step)(void* group, int parity, cudaStream_t st);
+    void (*batch_destroy)(void* group);
 };
 
 const KernelTable& table_fp64();

@@ -28,14 +28,13 @@ __device__ __forceinline__ typename Storage<T>::C pull(const T* __restrict__ f,
     return v;
 }
 
+// rho^s at one site (pull streaming + zeroth moment).
 template <typename T, int N>
-__global__ void __launch_bounds__(SITE_THREADS)
-k_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
-          const __grid_constant__ StepParams<typename Storage<T>::C> p)
+__device__ __forceinline__ void density_site(const T* __restrict__ f,
+                                             typename Storage<T>::C* __restrict__ rs,
+                                             const StepParams<typename Storage<T>::C>& p, long long site)
 {
     using C = typename Storage<T>::C;
-    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= p.S) return;
     const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
 #pragma unroll
     for (int s = 0; s < N; ++s) {
@@ -44,6 +43,16 @@ k_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
         for (int i = 0; i < Q; ++i) r += pull(f, p, s, i, x, y);
         rs[s * p.S + site] = r;
     }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
+          const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    density_site<T, N>(f, rs, p, site);
 }
 
 template <typename C, int N>
@@ -64,12 +73,11 @@ __device__ __forceinline__ void neighbour_laplacians(const C* __restrict__ rs,
     }
 }
 
+// nu^s at one site from the density fields.
 template <typename C, int N>
-__global__ void __launch_bounds__(SITE_THREADS)
-k_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant__ StepParams<C> p)
+__device__ __forceinline__ void potential_site(const C* __restrict__ rs, C* __restrict__ nu,
+                                               const StepParams<C>& p, long long site)
 {
-    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= p.S) return;
     const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
     C r[N], lap[N], out[N];
 #pragma unroll
@@ -78,6 +86,15 @@ k_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant_
     site_nu<C, N>(p, r, lap, out);
 #pragma unroll
     for (int s = 0; s < N; ++s) nu[s * p.S + site] = out[s];
+}
+
+template <typename C, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant__ StepParams<C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    potential_site<C, N>(rs, nu, p, site);
 }
 
 // grad g = 3 sum_i w_i v_i g(r + v_i) of one component's field
@@ -97,15 +114,15 @@ __device__ __forceinline__ void field_grad(const C* __restrict__ g, const StepPa
     gy = C(3) * ay;
 }
 
+// Collision at one site from the pulled populations and the potential fields; the
+// post-collision values are stored in place (pull scheme), ghosts included.
 template <typename T, int N>
-__global__ void __launch_bounds__(SITE_THREADS)
-k_collide(const T* __restrict__ fin, T* __restrict__ fout,
-          const typename Storage<T>::C* __restrict__ nu,
-          const __grid_constant__ StepParams<typename Storage<T>::C> p)
+__device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __restrict__ fout,
+                                             const typename Storage<T>::C* __restrict__ nu,
+                                             const StepParams<typename Storage<T>::C>& p,
+                                             long long site)
 {
     using C = typename Storage<T>::C;
-    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= p.S) return;
     const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
     C f[N][Q];
     C r[N], jx[N], jy[N];
@@ -147,6 +164,17 @@ k_collide(const T* __restrict__ fin, T* __restrict__ fout,
         }
     }
     if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k_collide(const T* __restrict__ fin, T* __restrict__ fout,
+          const typename Storage<T>::C* __restrict__ nu,
+          const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    collide_site<T, N>(fin, fout, nu, p, site);
 }
 
 // ---------------------------------------------------------------- diagnostics

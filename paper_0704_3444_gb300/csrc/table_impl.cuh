@@ -3,6 +3,7 @@
 
 #include <algorithm>
 
+#include "batch.cuh"
 #include "fused.cuh"
 #include "staged.cuh"
 
@@ -210,6 +211,9 @@ inline KernelTable make_table(CUtensorMapDataType tt)
     t.compositions = &Launch<T>::compositions;
     t.get_state = &Launch<T>::get_state;
     t.set_state = &Launch<T>::set_state;
+    t.batch_create = &batch_group_create<T>;
+    t.batch_step = &batch_group_step<T>;
+    t.batch_destroy = &batch_group_destroy<T>;
     return t;
 }
 

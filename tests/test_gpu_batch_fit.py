@@ -1,0 +1,82 @@
+"""GPU: batched simulations and the equilibrium fit, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import paper_0704_3444_gb300 as mclb
+from oracle import Oracle, thermo
+from paper_0704_3444_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mclb.build()
+    mclb.load()
+
+
+def _instances():
+    probs = []
+    shapes = [(40, 33, 2), (67, 29, 3), (32, 32, 2), (91, 45, 3), (16, 70, 2), (50, 50, 3)]
+    for k, (nx, ny, n) in enumerate(shapes):
+        rho, u = inputs.random_state(n, nx, ny, seed=500 + k, amp=0.3, umax=0.02)
+        chi = inputs.uniform_chi(n, 1.8 + 0.15 * k)
+        p = inputs.Problem(name=f"b{k}", ncomp=n, nx=nx, ny=ny, tau=0.7 + 0.1 * k, chi=chi,
+                           m=np.ones(n), theta=1 / 3, kappa=0.01, force=(0.0, 0.0), rho=rho, u=u)
+        probs.append(p)
+    return probs
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_batch_matches_oracle(precision, tol):
+    """Mixed N and ragged grids; 45 steps = one 32-step graph chunk plus 13 single steps."""
+    probs = _instances()
+    b = mclb.Batch(probs, precision=precision)
+    b.init_all()
+    assert b.launches_per_step == 6  # three per distinct N (2 and 3)
+    b.step(45)
+    rc, per = b.status()
+    assert rc == 0 and all(v == 0 for v in per)
+    for k, p in enumerate(probs):
+        o = Oracle.from_problem(p)
+        o.run(45)
+        g = b.get_state(k)
+        err = np.max(np.abs(g - o.f)) / np.abs(o.f).max()
+        assert err < tol, (k, err)
+    b.close()
+
+
+def test_batch_reinit_at_odd_parity():
+    probs = _instances()[:3]
+    b = mclb.Batch(probs, precision="fp64")
+    b.init_all()
+    b.step(3)                      # every instance now lives in the second buffer
+    b.init_fields(1, probs[1].rho, probs[1].u)
+    b.step(4)
+    o = Oracle.from_problem(probs[1])
+    o.run(4)
+    assert np.max(np.abs(b.get_state(1) - o.f)) < 1e-12 * np.abs(o.f).max()
+    o0 = Oracle.from_problem(probs[0])
+    o0.run(7)
+    assert np.max(np.abs(b.get_state(0) - o0.f)) < 1e-12 * np.abs(o0.f).max()
+    b.close()
+
+
+def test_fit_equilibrium_flat_interface():
+    """Binary flat interface (chi = 2.2, kappa = 0) run to stationarity in FP64 on the GPU:
+    the fitted bulk compositions equal the oracle's plateau values and sit within 0.015 of
+    the Flory-Huggins binodal (Sec. 4)."""
+    chi = np.array([[0.0, 2.2], [2.2, 0.0]])
+    p = inputs.flat_interface([0.5, 0.5], chi=chi, nx=64, ny=4, kappa=0.0, tau=1 / 0.9)
+    sim = mclb.Simulation.from_problem(p, precision="fp64", kernel=mclb.KERNEL_FUSED)
+    sim.step(40000)
+    assert sim.status() == 0
+    fit = sim.fit_equilibrium(2)        # phase 0 richest in component 0
+    o = Oracle.from_problem(p)
+    o.run(40000)
+    m = o.moments()
+    phi = m["rho"][0] / m["rho"].sum(0)
+    assert abs(fit[0, 0] - phi.max()) < 1e-3 and abs(fit[1, 0] - phi.min()) < 1e-3
+    lo, hi = thermo.binodal_binary(2.2)
+    assert abs(fit[0, 0] - hi) < 0.015 and abs(fit[1, 0] - lo) < 0.015
+    np.testing.assert_allclose(fit.sum(1), 1.0, atol=1e-12)
