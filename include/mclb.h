@@ -47,8 +47,11 @@ enum {
 };
 
 /* Storage precision of the distributions.  Arithmetic is FP64 in MCLB_FP64 and
- * FP32 otherwise.  The *_SHIFTED modes store f - w_i rhobar^s (rhobar^s the mean
- * density of component s at initialisation) in 16 bits. */
+ * FP32 otherwise.  The *_SHIFTED modes store, per site and component, a reference
+ * density R in FP32 and the deviations d_i = f_i - w_i M (M = sum_i f_i after the
+ * collision) in 16 bits, with R = M - sum_i d_i so that the stored site mass is M to
+ * FP32 rounding: f_i is read back as d_i + w_i R.  This needs 9*2 + 4 = 22 bytes per
+ * site and component instead of 36 (FP32) or 72 (FP64). */
 typedef enum {
     MCLB_FP64 = 0,
     MCLB_FP32 = 1,
@@ -104,9 +107,8 @@ int mclb_create(const mclb_params* params, mclb_handle* out);
 /* Set f^s_i(r, 0) to the equilibrium of the given fields (Sec. 3 equilibrium
  * moments with the barycentric u).  rho: N*ny*nx component densities rho^s, each
  * > 0 in total per site; u: 2*ny*nx barycentric velocity or NULL for rest.
- * Host pointers; the copy is synchronous.  Resets the step counter and, in the
- * shifted modes, the shifts.  Errors: EHANDLE, EINVAL (NULL rho, non-finite
- * value, non-positive total density), ECUDA. */
+ * Host pointers; the copy is synchronous.  Resets the step counter.  Errors:
+ * EHANDLE, EINVAL (NULL rho, non-finite value, non-positive total density), ECUDA. */
 int mclb_init_fields(mclb_handle h, const double* rho, const double* u);
 
 /* As mclb_init_fields, but rho and u are device pointers (same layouts) read in
@@ -143,25 +145,30 @@ int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, doubl
 int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_sum);
 
 /* Mean compositions phi^s = rho^s / rho of the nphase bulk phases of the current
- * state (FP64, on the device): sites whose composition gradient is below a
- * threshold are clustered into nphase groups (k-means started from the sites of
- * extreme composition); phi receives nphase*N values, phases ordered by
- * decreasing phi^0.  nphase in 1..MCLB_NMAX.  Synchronises.  Sec. 4 compares
- * these coexisting compositions with the Flory-Huggins binodal. */
+ * state: the compositions and the bulk mask (sites whose largest composition
+ * difference to a neighbour is below 1e-3) are computed on the device in FP64; the
+ * bulk sites are clustered on the host into nphase groups by k-means, group c
+ * started at the bulk site richest in component c.  phi receives nphase*N values,
+ * group c first.  nphase in 1..N.  Synchronises.  Errors: EHANDLE, EINVAL (nphase out
+ * of range, no bulk site), ENOMEM, ECUDA.  Sec. 4 compares these coexisting
+ * compositions with the Flory-Huggins binodal. */
 int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi);
 
 /* Copy the distributions in or out as FP64 pre-collision values f^s_i(r, t), layout
  * [s][i][y][x] (count must equal N*9*ny*nx).  Host pointers, synchronous.  Getting
  * and setting a state is exact in FP64 and FP32; in the shifted modes setting
- * re-derives the shifts from the state.  Errors: EHANDLE, EINVAL, ECUDA. */
+ * stores the state as R and 16-bit deviations (see mclb_precision), so a state
+ * read back differs by the rounding of the deviations.  Errors: EHANDLE, EINVAL,
+ * ECUDA. */
 int mclb_get_state(mclb_handle h, double* f, size_t count);
 int mclb_set_state(mclb_handle h, const double* f, size_t count);
 
 /* Timesteps taken since the last init / set_state. */
 long mclb_step_count(mclb_handle h);
 
-/* HBM bytes one timestep must move at least: 2 * 9 * N * ny * nx * storage size
- * (every distribution read once and written once). */
+/* HBM bytes one timestep must move at least: every stored value read once and
+ * written once, 2 * N * ny * nx * (9 * storage size) in FP64 and FP32 and
+ * 2 * N * ny * nx * (9 * 2 + 4) in the shifted modes. */
 double mclb_bytes_per_step(mclb_handle h);
 
 /* Kernel launches one timestep issues (1 for the fused schedule, 3 for the staged). */

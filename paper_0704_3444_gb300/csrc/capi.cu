@@ -104,8 +104,9 @@ int validate(const mclb_params* p)
     return MCLB_OK;
 }
 
-void fill_problem(const mclb_params* p, int hx, Problem& P)
+void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
 {
+    const int hx = tab.hx;
     memset(&P, 0, sizeof(P));
     P.N = p->ncomp;
     P.nx = p->nx;
@@ -114,6 +115,8 @@ void fill_problem(const mclb_params* p, int hx, Problem& P)
     P.hx = hx;
     P.pitch = 2LL * hx + (long long)((p->nx + ROW_ALIGN - 1) / ROW_ALIGN) * ROW_ALIGN;
     P.plane = P.pitch * Q * p->ny;
+    // 16-bit formats: the FP32 density lines follow the deviations, 256-byte aligned
+    P.rbytes = tab.shifted ? (long long)((P.plane * P.N * (long long)tab.storage_bytes + 255) / 256 * 256) : 0;
     P.tau = p->tau;
     P.theta = p->theta > 0.0 ? p->theta : 1.0 / 3.0;
     P.kappa = p->kappa;
@@ -145,6 +148,7 @@ struct mclb_handle_s {
     bool own_stream;
     void* f[2];
     CUtensorMap tmap[2];
+    CUtensorMap tmapr[2];         // density lines of the 16-bit formats
     int cur;                      // buffer holding the current state
     long steps;
     size_t fbytes;                // bytes of one distribution buffer
@@ -202,6 +206,19 @@ int make_tmap(mclb_handle h, int b)
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if (h->tab->shifted) {
+        // 3-D view (x, row, component) of the FP32 density lines; same columns per box
+        cuuint64_t rdims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, (cuuint64_t)P.N};
+        cuuint64_t rstrides[2] = {(cuuint64_t)(P.pitch * sizeof(float)),
+                                  (cuuint64_t)(P.ny * P.pitch * sizeof(float))};
+        cuuint32_t rbox[3] = {(cuuint32_t)(h->plan.W + 2 * P.hx), 1u, (cuuint32_t)P.N};
+        r = fn(&h->tmapr[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+               static_cast<char*>(h->f[b]) + P.rbytes, rdims, rstrides, rbox, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled (density lines) failed (%d)", (int)r);
+    }
     return MCLB_OK;
 }
 
@@ -209,7 +226,8 @@ cudaError_t launch_one_step(mclb_handle h, int from)
 {
     const Problem& P = h->P;
     if (h->fused)
-        return h->tab->step_fused(P, h->sc, h->plan, &h->tmap[from], h->f[from ^ 1], h->stream);
+        return h->tab->step_fused(P, h->sc, h->plan, &h->tmap[from], &h->tmapr[from], h->f[from ^ 1],
+                                  h->stream);
     return h->tab->step_staged(P, h->sc, h->f[from], h->f[from ^ 1], h->stream);
 }
 
@@ -256,39 +274,6 @@ int sync_status(mclb_handle h)
     return status_code(*h->status_host);
 }
 
-int set_shift_from_means(mclb_handle h, const double* rhobar)
-{
-    for (int s = 0; s < h->P.N; ++s) {
-        const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-        for (int i = 0; i < Q; ++i) h->P.shift[s * Q + i] = h->tab->shifted ? w[i] * rhobar[s] : 0.0;
-    }
-    // kernel parameters changed: captured graphs are stale
-    for (int b = 0; b < 2; ++b) {
-        if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
-        h->graph[b] = nullptr;
-        h->graph_tried[b] = false;
-    }
-    return MCLB_OK;
-}
-
-__global__ void k_plane_sums(const double* __restrict__ a, long long n, int planes,
-                             double* __restrict__ out)
-{
-    // one block per plane, fixed order: deterministic
-    __shared__ double red[256];
-    const int pl = blockIdx.x;
-    double acc = 0.0;
-    for (long long k = threadIdx.x; k < n; k += blockDim.x) acc += a[pl * n + k];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[pl] = red[0];
-}
-
 }  // namespace
 
 extern "C" {
@@ -307,7 +292,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     h->precision = params->precision;
     h->kernel = params->kernel;
     h->tab = &table_for(params->precision);
-    fill_problem(params, h->tab->hx, h->P);
+    fill_problem(params, *h->tab, h->P);
     const Problem& P = h->P;
     auto bail = [&](int code) {
         h->magic = MAGIC;
@@ -328,6 +313,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
         h->own_stream = true;
     }
     h->fbytes = (size_t)P.plane * P.N * h->tab->storage_bytes;
+    if (h->tab->shifted) h->fbytes = (size_t)P.rbytes + (size_t)P.N * P.ny * P.pitch * sizeof(float);
     const size_t cbytes = (h->precision == MCLB_FP64) ? sizeof(double) : sizeof(float);
     for (int b = 0; b < 2; ++b) {
         if (cudaMalloc(&h->f[b], h->fbytes) != cudaSuccess)
@@ -388,9 +374,8 @@ int mclb_destroy(mclb_handle h)
     return MCLB_OK;
 }
 
-static int init_common(mclb_handle h, const double* rho_d, const double* u_d, const double* rhobar)
+static int init_common(mclb_handle h, const double* rho_d, const double* u_d)
 {
-    set_shift_from_means(h, rhobar);
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
     CK(h->tab->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
     h->cur = 0;
@@ -404,20 +389,17 @@ int mclb_init_fields(mclb_handle h, const double* rho, const double* u)
     if (rc) return rc;
     if (!rho) return fail(MCLB_EINVAL, "rho is NULL");
     const Problem& P = h->P;
-    double rhobar[NMAX] = {0};
     for (long long c = 0; c < P.S; ++c) {
         double tot = 0.0;
         for (int s = 0; s < P.N; ++s) {
             const double v = rho[s * P.S + c];
             if (!std::isfinite(v)) return fail(MCLB_EINVAL, "rho not finite at site %lld", c);
             tot += v;
-            rhobar[s] += v;
         }
         if (!(tot > 0.0)) return fail(MCLB_EINVAL, "total density <= 0 at site %lld", c);
         if (u && (!std::isfinite(u[c]) || !std::isfinite(u[P.S + c])))
             return fail(MCLB_EINVAL, "u not finite at site %lld", c);
     }
-    for (int s = 0; s < P.N; ++s) rhobar[s] /= (double)P.S;
     rc = ensure_dtmp(h, (size_t)(P.N + 2) * P.S);
     if (rc) return rc;
     CK(cudaMemcpyAsync(h->dtmp, rho, sizeof(double) * P.N * P.S, cudaMemcpyHostToDevice,
@@ -425,7 +407,7 @@ int mclb_init_fields(mclb_handle h, const double* rho, const double* u)
     if (u)
         CK(cudaMemcpyAsync(h->dtmp + P.N * P.S, u, sizeof(double) * 2 * P.S,
                            cudaMemcpyHostToDevice, h->stream));
-    rc = init_common(h, h->dtmp, u ? h->dtmp + P.N * P.S : nullptr, rhobar);
+    rc = init_common(h, h->dtmp, u ? h->dtmp + P.N * P.S : nullptr);
     if (rc) return rc;
     CK(cudaStreamSynchronize(h->stream));
     return MCLB_OK;
@@ -436,20 +418,7 @@ int mclb_init_fields_device(mclb_handle h, const double* rho, const double* u)
     int rc = check_handle(h);
     if (rc) return rc;
     if (!rho) return fail(MCLB_EINVAL, "rho is NULL");
-    const Problem& P = h->P;
-    double rhobar[NMAX] = {0};
-    if (h->tab->shifted) {
-        // the shifts need the mean densities on the host: one small synchronous copy
-        rc = ensure_dtmp(h, NMAX);
-        if (rc) return rc;
-        k_plane_sums<<<P.N, 256, 0, h->stream>>>(rho, P.S, P.N, h->dtmp);
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(rhobar, h->dtmp, sizeof(double) * P.N, cudaMemcpyDeviceToHost,
-                           h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        for (int s = 0; s < P.N; ++s) rhobar[s] /= (double)P.S;
-    }
-    return init_common(h, rho, u, rhobar);
+    return init_common(h, rho, u);
 }
 
 int mclb_step(mclb_handle h, long nsteps)
@@ -495,7 +464,8 @@ long mclb_step_count(mclb_handle h) { return check_handle(h) ? -1 : h->steps; }
 double mclb_bytes_per_step(mclb_handle h)
 {
     if (check_handle(h)) return -1.0;
-    return 2.0 * Q * h->P.N * (double)h->P.S * (double)h->tab->storage_bytes;
+    const double per = Q * (double)h->tab->storage_bytes + (h->tab->shifted ? sizeof(float) : 0.0);
+    return 2.0 * h->P.N * (double)h->P.S * per;
 }
 
 int mclb_launches_per_step(mclb_handle h)
@@ -573,18 +543,8 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
     const Problem& P = h->P;
     const size_t want = (size_t)P.N * Q * P.S;
     if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
-    double rhobar[NMAX] = {0};
-    for (int s = 0; s < P.N; ++s) {
-        double acc = 0.0;
-        for (int i = 0; i < Q; ++i)
-            for (long long c = 0; c < P.S; ++c) {
-                const double v = f[((size_t)s * Q + i) * P.S + c];
-                if (!std::isfinite(v)) return fail(MCLB_EINVAL, "state not finite");
-                acc += v;
-            }
-        rhobar[s] = acc / (double)P.S;
-    }
-    set_shift_from_means(h, rhobar);
+    for (size_t k = 0; k < want; ++k)
+        if (!std::isfinite(f[k])) return fail(MCLB_EINVAL, "state not finite");
     rc = ensure_dtmp(h, want);
     if (rc) return rc;
     CK(cudaMemcpyAsync(h->dtmp, f, sizeof(double) * want, cudaMemcpyHostToDevice, h->stream));
@@ -672,7 +632,7 @@ struct mclb_batch_s {
     bool own_stream;
     const KernelTable* tab;
     std::vector<void*> groups;        // batched launches, one group per distinct N
-    bool dirty;                       // groups must be rebuilt (new shifts after init)
+    bool dirty;                       // groups must be rebuilt before the next step
     int parity;                       // buffer holding every instance's current state
     cudaGraphExec_t graph[2];
     bool graph_tried[2];
@@ -814,7 +774,7 @@ int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const dou
         CK(cudaStreamSynchronize(b->stream));
         h->cur = 1;
     }
-    b->dirty = true;                   // the instance's shifts may have changed
+    b->dirty = true;
     return MCLB_OK;
 }
 

@@ -102,6 +102,18 @@ __device__ __forceinline__ void tma_load_row(void* dst, const CUtensorMap* map, 
         : "memory");
 }
 
+// One 3-D TMA box (columns, 1 row, all components) of the FP32 density lines.
+__device__ __forceinline__ void tma_load_rline(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                               int col, int row)
+{
+    const uint64_t desc = reinterpret_cast<uint64_t>(map);
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(desc), "r"(smem_u32(bar)), "r"(col), "r"(row), "r"(0)
+        : "memory");
+}
+
 // Prefetch the same 4-D box into L2 only (no shared memory, no barrier).
 __device__ __forceinline__ void tma_prefetch_row(const CUtensorMap* map, int col, int row)
 {
@@ -142,8 +154,16 @@ struct FusedGeom {
     static constexpr int NST = W;                      // site threads (1 column each)
     static constexpr int THREADS = NCT + NST + 32;     // + helper warp
     static constexpr int PRODUCER = THREADS - 1;       // helper lane issuing the copies
-    static constexpr size_t STAGE_BYTES = round_up_sz((size_t)N * Q * WI * sizeof(T), 128);
+    // one stage: the 9 N lines of a source row, then (16-bit formats) its N FP32
+    // density lines at byte offset DEV_BYTES
+    static constexpr bool SHIFTED = Storage<T>::shifted;
+    static constexpr size_t DEV_BYTES = round_up_sz((size_t)N * Q * WI * sizeof(T), 128);
+    static constexpr size_t R_BYTES = SHIFTED ? (size_t)N * WI * sizeof(float) : 0;
+    static constexpr size_t STAGE_BYTES = round_up_sz(DEV_BYTES + R_BYTES, 128);
     static constexpr int STAGE_ELEMS = (int)(STAGE_BYTES / sizeof(T));
+    static constexpr int STAGE_FLOATS = (int)(STAGE_BYTES / sizeof(float));
+    static constexpr int R_FLOAT0 = (int)(DEV_BYTES / sizeof(float));
+    static constexpr uint32_t TX = (uint32_t)((size_t)N * Q * WI * sizeof(T) + R_BYTES);
     // rings (elements of C).  Slot counts follow from who reads a row after the barrier
     // that follows its write: moments of row r are read until phase C two iterations
     // later and are overwritten by the next phase A without a barrier in between (4);
@@ -166,8 +186,9 @@ constexpr int FUSED_MAX_THREADS = 1024;
 
 template <typename T, int N, int COLS>
 __global__ void __launch_bounds__(FusedGeom<T, N, COLS>::THREADS, FusedGeom<T, N, COLS>::MIN_CTAS)
-k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
-        const __grid_constant__ StepParams<typename Storage<T>::C> p, const int H)
+k_fused(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapr,
+        T* __restrict__ fout, const __grid_constant__ StepParams<typename Storage<T>::C> p,
+        const int H)
 {
     using G = FusedGeom<T, N, COLS>;
     using C = typename Storage<T>::C;
@@ -188,6 +209,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 8 * FUSED_MAX_NS);
     T* stg = reinterpret_cast<T*>(smem + FUSED_HDR);
+    const float* stgr = reinterpret_cast<const float*>(smem + FUSED_HDR) + G::R_FLOAT0;
     C* mom = reinterpret_cast<C*>(smem + FUSED_HDR + NS * G::STAGE_BYTES);
     C* nur = mom + G::MOM;
     C* shr = nur + G::NU;
@@ -200,7 +222,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     }
     __syncthreads();
 
-    constexpr uint32_t TX = (uint32_t)(N * Q * WI * sizeof(T));
+    constexpr uint32_t TX = G::TX;
     auto grow = [&](int k) {
         int row = (y0 - 3 + k) % p.ny;
         return row + (row < 0 ? p.ny : 0);
@@ -209,6 +231,9 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         const int st = k % NS;
         mbar_arrive_expect_tx(&full[st], TX);
         tma_load_row(stg + st * G::STAGE_ELEMS, &tmap, &full[st], x0, grow(k));
+        if constexpr (G::SHIFTED)
+            tma_load_rline(smem + FUSED_HDR + st * G::STAGE_BYTES + G::DEV_BYTES, &tmapr, &full[st],
+                           x0, grow(k));
         if (k + G::PF < nrows) tma_prefetch_row(&tmap, x0, grow(k + G::PF));
     };
     int issued = 0;
@@ -220,24 +245,36 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
     auto wait_row = [&](int k) -> bool { return mbar_wait(&full[k % NS], (k / NS) & 1); };
 
     // constants of this thread's component, kept in registers
-    C shift[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) shift[i] = Storage<T>::shifted ? p.shift[g * Q + i] : C(0);
     C chi_row[N];
 #pragma unroll
     for (int u = 0; u < N; ++u) chi_row[u] = p.chi[g * N + u];
     const C th_m = p.th_m[g], logc = p.logc[g], minv1 = p.m_inv_m1[g];
     const bool has_log = (p.log_mask >> g) & 1u;
 
-    // moments of one component at one column: a0/a1/a2 are the stage element offsets of
-    // the velocity-0 line (column applied) in the source rows for dy = -1, 0, +1
-    auto moments_to = [&](int a0, int a1, int a2, int dst, const C (&sh)[Q]) {
-        const int ar[3] = {a0, a1, a2};
+    // pulled value of velocity i: a = stage element offset of the velocity-0 line (column
+    // applied) of the source row; in the 16-bit formats the deviation plus w_i times the
+    // density line of the same source site (float offset ra)
+    auto pulled = [&](int i, int a, int ra) -> C {
+        C v = to_c<T>(stg[a + i * WI - vx(i)]);
+        if constexpr (G::SHIFTED) v = fma(wq<C>(i), stgr[ra - vx(i)], v);
+        return v;
+    };
+    // stage float offset of a density-line column, from the stage element offset of the
+    // stage and the component/column part
+    auto roff = [&](int st, int s, int colx) -> int {
+        return st * (int)sizeof(T) / (int)sizeof(float) + s * WI + colx;
+    };
+
+    // moments of one component at one column: s0/s1/s2 are the stage element offsets of
+    // the source rows for dy = -1, 0, +1, s the component, cx the staged column
+    auto moments_to = [&](int s0, int s1, int s2, int s, int cx, int dst) {
+        const int sr[3] = {s0, s1, s2};
+        const int col = s * Q * WI + cx;
         C v[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            v[i] = to_c<T>(stg[ar[vy(i) + 1] + i * WI - vx(i)]);
-            if constexpr (Storage<T>::shifted) v[i] += sh[i];
+            const int st = sr[vy(i) + 1];
+            v[i] = pulled(i, st + col, G::SHIFTED ? roff(st, s, cx) : 0);
         }
         C r = C(0);
 #pragma unroll
@@ -299,16 +336,17 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
 
     // collision of component g at first-column offset cc (0 or 32) of the strip
     auto collide_col = [&](int cc, int s0, int s1, int s2, int momr, int eqo, int n0, int n1, int n2,
-                           T* line, bool ghost) {
+                           T* line, float* rline, bool ghost) {
         const int x = x0 + c + cc;
         if (x >= p.nx) return;
-        const int col = g * Q * WI + c + cc + HX;
-        const int ar[3] = {s0 + col, s1 + col, s2 + col};
+        const int cx = c + cc + HX;
+        const int col = g * Q * WI + cx;
+        const int sr[3] = {s0, s1, s2};
         C f[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = to_c<T>(stg[ar[vy(i) + 1] + i * WI - vx(i)]);
-            if constexpr (Storage<T>::shifted) f[i] += shift[i];
+            const int st = sr[vy(i) + 1];
+            f[i] = pulled(i, st + col, G::SHIFTED ? roff(st, g, cx) : 0);
         }
         const int mg = momr + g * RW + c + cc + 2;
         const C rg = mom[mg], jxg = mom[mg + N * RW], jyg = mom[mg + 2 * N * RW];
@@ -328,17 +366,30 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         const C ay = -p.fcoef * (C(3) * gy) + p.gy;
         C out[Q];
         collide(p, f, e, rg, jxg, jyg, ax, ay, out);
-        if constexpr (Storage<T>::shifted) {
+        C rref = C(0);
+        if constexpr (G::SHIFTED) {
+            // deviations from w_i M, rounded to storage, and the compensated reference
+            // density R = M - sum_i d_i (the same rule as store_site)
+            C M = C(0);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) out[i] -= shift[i];
+            for (int i = 0; i < Q; ++i) M += out[i];
+            C dsum = C(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                out[i] = Storage<T>::round(out[i] - wq<C>(i) * M);
+                dsum += out[i];
+            }
+            rref = M - dsum;
         }
         if (!ghost) {
             T* q = line + HX + x;
 #pragma unroll
             for (int i = 0; i < Q; ++i) Storage<T>::store(q + i * p.pitch, out[i]);
+            if constexpr (G::SHIFTED) rline[HX + x] = rref;
         } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i) store_row(line + i * p.pitch, x, p.nx, HX, out[i]);
+            if constexpr (G::SHIFTED) store_row(rline, x, p.nx, HX, rref);
         }
     };
 
@@ -382,10 +433,8 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         //      equilibrium weights of row j-3 (moments complete since the last phase A)
         if (comp) {
 #pragma unroll
-            for (int k = 0; k < COLS; ++k) {
-                const int col = g * Q * WI + c + 32 * k + HX;
-                moments_to(stp2 + col, stp1 + col, st0 + col, momA + g * RW + c + 32 * k + 2, shift);
-            }
+            for (int k = 0; k < COLS; ++k)
+                moments_to(stp2, stp1, st0, g, c + 32 * k + HX, momA + g * RW + c + 32 * k + 2);
         } else if (site) {
             if (j >= 1) {
                 C inv;
@@ -409,11 +458,7 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
             if (lane < 4 * N) {
                 const int hc = lane / N, s = lane - hc * N;
                 const int cc = hc < 2 ? hc : W + hc;     // moment-ring column of the halo site
-                C sh[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) sh[i] = Storage<T>::shifted ? p.shift[s * Q + i] : C(0);
-                const int col = s * Q * WI + cc - 2 + HX;
-                moments_to(stp2 + col, stp1 + col, st0 + col, momA + s * RW + cc, sh);
+                moments_to(stp2, stp1, st0, s, cc - 2 + HX, momA + s * RW + cc);
             }
             // halo site terms of row j-3 on two lanes (the last two when they are free)
             const int hl = (4 * N + 2 <= 32) ? 4 * N : 0;
@@ -460,9 +505,11 @@ k_fused(const __grid_constant__ CUtensorMap tmap, T* __restrict__ fout,
         // ---- phase C: collide row j-4 (source rows j-2 .. j, nu rows j-5 .. j-3)
         if (comp && j >= 4) {
             T* line = fout + line_off(p, g, y0 + j - 4, 0);
+            float* rline = nullptr;
+            if constexpr (G::SHIFTED) rline = rho_line(fout, p, g, y0 + j - 4);
 #pragma unroll
             for (int k = 0; k < COLS; ++k)
-                collide_col(32 * k, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, ghost[k]);
+                collide_col(32 * k, st0, stm1, stm2, momC, eqc, nuA, nuB, nuw, line, rline, ghost[k]);
         }
         sj = (sj + 1 == NS) ? 0 : sj + 1;
         j3 = j3p1;

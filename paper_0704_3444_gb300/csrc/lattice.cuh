@@ -27,9 +27,11 @@ __host__ __device__ __forceinline__ constexpr C wq(int i)
     return i == 0 ? C(4.0 / 9.0) : (i < 5 ? C(1.0 / 9.0) : C(1.0 / 36.0));
 }
 
-// Storage precisions.  C is the arithmetic type.  The 16-bit formats hold the
-// deviation f - shift with shift = w_i * rhobar^s, so that their few mantissa bits
-// describe the departure from the mean state rather than the state itself.
+// Storage precisions.  C is the arithmetic type.  The 16-bit formats ("shifted") hold,
+// per site and component, the deviations f_i - w_i R in 16 bits and the reference
+// density R in FP32 (a separate line per component row), so that the few mantissa
+// bits describe the departure from the local equilibrium-like part rather than f
+// itself; R is chosen so that the stored site mass sum_i f_i is exact in FP32.
 template <typename T>
 struct Storage;
 
@@ -39,6 +41,7 @@ struct Storage<double> {
     static constexpr bool shifted = false;
     __device__ __forceinline__ static C load(const double* p) { return __ldg(p); }
     __device__ __forceinline__ static void store(double* p, C v) { *p = v; }
+    __device__ __forceinline__ static C round(C v) { return v; }
 };
 
 template <>
@@ -47,6 +50,7 @@ struct Storage<float> {
     static constexpr bool shifted = false;
     __device__ __forceinline__ static C load(const float* p) { return __ldg(p); }
     __device__ __forceinline__ static void store(float* p, C v) { *p = v; }
+    __device__ __forceinline__ static C round(C v) { return v; }
 };
 
 template <>
@@ -61,6 +65,7 @@ struct Storage<__nv_bfloat16> {
     {
         *p = __float2bfloat16_rn(v);
     }
+    __device__ __forceinline__ static C round(C v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
 template <>
@@ -69,6 +74,7 @@ struct Storage<__half> {
     static constexpr bool shifted = true;
     __device__ __forceinline__ static C load(const __half* p) { return __half2float(__ldg(p)); }
     __device__ __forceinline__ static void store(__half* p, C v) { *p = __float2half_rn(v); }
+    __device__ __forceinline__ static C round(C v) { return __half2float(__float2half_rn(v)); }
 };
 
 // Kernel parameters in the arithmetic type.  Built on the host from a Problem.
@@ -79,6 +85,7 @@ struct StepParams {
     int hx;               // ghost columns per side
     long long pitch;      // elements per (row, velocity) line
     long long plane;      // elements per component (ny * 9 * pitch)
+    long long rbytes;     // byte offset of the FP32 density lines in a buffer (16-bit formats)
     C omega;              // 1 / tau
     C fcoef;              // 1 - 1/(2 tau), Eq. definef
     C gx, gy;             // body acceleration
@@ -90,7 +97,6 @@ struct StepParams {
     C m_inv_m1[NMAX];     // 1/m^s - 1
     C inv_m[NMAX];        // 1/m^s
     C m[NMAX];
-    C shift[NMAX * Q];
     unsigned int log_mask; // bit s set when logc[s] != 0
     unsigned int* status;
 };
@@ -105,6 +111,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
     p.hx = P.hx;
     p.pitch = P.pitch;
     p.plane = P.plane;
+    p.rbytes = P.rbytes;
     p.omega = C(1.0 / P.tau);
     p.fcoef = C(1.0 - 1.0 / (2.0 * P.tau));
     p.gx = C(P.gx);
@@ -122,7 +129,6 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
         p.m_inv_m1[a] = C(1.0 / P.m[a] - 1.0);
         p.inv_m[a] = C(1.0 / P.m[a]);
         p.m[a] = C(P.m[a]);
-        for (int i = 0; i < Q; ++i) p.shift[a * Q + i] = C(P.shift[a * Q + i]);
     }
     p.status = status;
     return p;
@@ -161,6 +167,46 @@ __device__ __forceinline__ void store_row(T* row, int x, int nx, int hx, C v)
         for (int g = nx + x; g < nx + hx; g += nx) Storage<T>::store(row + hx + g, v);
     if (x >= nx - hx)
         for (int g = x - nx; g >= -hx; g -= nx) Storage<T>::store(row + hx + g, v);
+}
+
+// Start (ghosts included) of the FP32 density line of component s, row y (16-bit formats).
+template <typename T, typename C>
+__device__ __forceinline__ float* rho_line(T* f, const StepParams<C>& p, int s, int y)
+{
+    return reinterpret_cast<float*>(reinterpret_cast<char*>(f) + p.rbytes) +
+           ((long long)s * p.ny + y) * p.pitch;
+}
+template <typename T, typename C>
+__device__ __forceinline__ const float* rho_line(const T* f, const StepParams<C>& p, int s, int y)
+{
+    return reinterpret_cast<const float*>(reinterpret_cast<const char*>(f) + p.rbytes) +
+           ((long long)s * p.ny + y) * p.pitch;
+}
+
+// Store the nine post-collision values of component s at column x of row y, ghosts
+// included.  In the 16-bit formats the values become deviations d_i = f_i - w_i M
+// (M = sum_i f_i) rounded to 16 bits, and the FP32 reference R = M - sum_i d_i, so that
+// sum_i (d_i + w_i R) = M: every site keeps its mass to FP32 rounding.
+template <typename T, typename C>
+__device__ __forceinline__ void store_site(T* f, const StepParams<C>& p, int s, int y, int x,
+                                           const C (&out)[Q])
+{
+    if constexpr (!Storage<T>::shifted) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) store_row(f + line_off(p, s, y, i), x, p.nx, p.hx, out[i]);
+    } else {
+        C M = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) M += out[i];
+        C dsum = C(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const C d = Storage<T>::round(out[i] - wq<C>(i) * M);
+            dsum += d;
+            store_row(f + line_off(p, s, y, i), x, p.nx, p.hx, d);
+        }
+        store_row(rho_line(f, p, s, y), x, p.nx, p.hx, M - dsum);
+    }
 }
 
 }  // namespace mclb

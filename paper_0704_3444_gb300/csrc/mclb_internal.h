@@ -34,7 +34,8 @@ struct Problem {
     double tau, theta, kappa, gx, gy;
     double chi[NMAX * NMAX];
     double m[NMAX];
-    double shift[NMAX * Q]; // storage shift w_i * rhobar^s in the shifted modes, else 0
+    long long rbytes;       // 16-bit formats: byte offset of the FP32 density lines
+                            // ([s][y][pitch], same ghosts) after the deviations; else 0
 };
 
 // Device scratch owned by a handle: component densities and the potentials
@@ -73,9 +74,11 @@ struct KernelTable {
     // f^s_i(r) = equilibrium of (rho, u) (device FP64 inputs; u may be null)
     cudaError_t (*init)(const Problem&, const Scratch&, const double* rho, const double* u,
                         void* f, cudaStream_t st);
-    // one fused timestep fin -> fout (tmap_in describes fin)
+    // one fused timestep fin -> fout (tmap_in describes fin's lines, tmapr_in its density
+    // lines in the 16-bit formats)
     cudaError_t (*step_fused)(const Problem&, const Scratch&, const FusedPlan&,
-                              const CUtensorMap* tmap_in, void* fout, cudaStream_t st);
+                              const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in, void* fout,
+                              cudaStream_t st);
     // one staged timestep fin -> fout (three launches through scratch)
     cudaError_t (*step_staged)(const Problem&, const Scratch&, const void* fin, void* fout,
                                cudaStream_t st);

@@ -24,7 +24,7 @@ __device__ __forceinline__ typename Storage<T>::C pull(const T* __restrict__ f,
     const int xs = wrap_add(x, -vx(i), p.nx);
     const int ys = wrap_add(y, -vy(i), p.ny);
     C v = Storage<T>::load(f + fidx(p, s, i, ys, xs));
-    if constexpr (Storage<T>::shifted) v += p.shift[s * Q + i];
+    if constexpr (Storage<T>::shifted) v += wq<C>(i) * __ldg(rho_line(f, p, s, ys) + p.hx + xs);
     return v;
 }
 
@@ -156,12 +156,7 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
         const C ay = -p.fcoef * gy + p.gy;
         C out[Q];
         collide(p, f[s], e, r[s], jx[s], jy[s], ax, ay, out);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            C v = out[i];
-            if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
-            store_row(fout + line_off(p, s, y, i), x, p.nx, p.hx, v);
-        }
+        store_site(fout, p, s, y, x, out);
     }
     if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
 }
@@ -189,6 +184,7 @@ k_init(const double* __restrict__ rho, const double* __restrict__ u, T* __restri
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
     const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+    C v[N][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
@@ -197,13 +193,12 @@ k_init(const double* __restrict__ rho, const double* __restrict__ u, T* __restri
         const C uu = ux * ux + uy * uy;
         const C cu = C(vx(i)) * ux + C(vy(i)) * uy;
 #pragma unroll
-        for (int s = 0; s < N; ++s) {
-            C v = wq<C>(i) * C(rho[s * p.S + t]) *
-                  (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
-            if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
-            store_row(f + line_off(p, s, y, i), x, p.nx, p.hx, v);
-        }
+        for (int s = 0; s < N; ++s)
+            v[s][i] = wq<C>(i) * C(rho[s * p.S + t]) *
+                      (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
     }
+#pragma unroll
+    for (int s = 0; s < N; ++s) store_site(f, p, s, y, x, v[s]);
 }
 
 template <typename T, int N>
@@ -229,17 +224,16 @@ k_set_state(const double* __restrict__ in, T* __restrict__ f,
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
     const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+    C v[N][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
         const long long t = (long long)yy * p.nx + xx;
 #pragma unroll
-        for (int s = 0; s < N; ++s) {
-            C v = C(in[(s * Q + i) * p.S + t]);
-            if constexpr (Storage<T>::shifted) v -= p.shift[s * Q + i];
-            store_row(f + line_off(p, s, y, i), x, p.nx, p.hx, v);
-        }
+        for (int s = 0; s < N; ++s) v[s][i] = C(in[(s * Q + i) * p.S + t]);
     }
+#pragma unroll
+    for (int s = 0; s < N; ++s) store_site(f, p, s, y, x, v[s]);
 }
 
 // Output fields: rho^s, U = u + (sum_s rho^s a^s)/(2 rho), mu^s, P (needs k_density and

@@ -117,17 +117,19 @@ struct Launch {
     }
 
     static cudaError_t step_fused(const Problem& P, const Scratch& sc, const FusedPlan& pl,
-                                  const CUtensorMap* tmap_in, void* fout, cudaStream_t st)
+                                  const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in,
+                                  void* fout, cudaStream_t st)
     {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
+        const CUtensorMap& tr = Storage<T>::shifted ? *tmapr_in : *tmap_in;
         MCLB_DISPATCH_N(P.N, {
             if (pl.W == 64)
                 k_fused<T, NN, 2><<<grid, FusedGeom<T, NN, 2>::THREADS, pl.smem, st>>>(
-                    *tmap_in, (T*)fout, p, pl.H);
+                    *tmap_in, tr, (T*)fout, p, pl.H);
             else
                 k_fused<T, NN, 1><<<grid, FusedGeom<T, NN, 1>::THREADS, pl.smem, st>>>(
-                    *tmap_in, (T*)fout, p, pl.H);
+                    *tmap_in, tr, (T*)fout, p, pl.H);
             return cudaGetLastError();
         });
     }

@@ -1,0 +1,111 @@
+"""GPU tests of the 16-bit shifted storage formats (BF16, FP16) against the FP64 oracle.
+
+In these formats a site keeps, per component, an FP32 reference density R and the nine
+deviations d_i = f_i - w_i M (M the post-collision site mass) rounded to 16 bits, with
+R = M - sum_i d_i.  The tests check what that format promises and what it is for:
+
+  * storage: every population comes back within one 16-bit rounding (unit roundoff
+    2^-8 for BF16, 2^-11 for FP16) of its deviation |f_i - w_i M| plus w_i times the
+    roundings of all nine (carried by R), plus FP32 rounding; the site mass sum_i f_i
+    comes back to FP32 rounding (the compensation);
+  * Sec. 4 use: coexisting bulk compositions of a binary flat interface (chi = 2.2,
+    40000 steps) and the densities of the polymer/solvent/non-solvent slab after 3000
+    steps agree with the oracle to 1e-3, the accuracy asked of reduced-precision
+    storage; total mass of each component drifts by less than 1e-3 over 40000 steps.
+"""
+import numpy as np
+import pytest
+
+import paper_0704_3444_gb300 as mclb
+from oracle import Oracle
+from paper_0704_3444_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SHIFTED = ["bf16", "fp16"]
+ULP = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11}
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mclb.build()
+    mclb.load()
+
+
+@pytest.fixture(scope="module")
+def flat_oracle():
+    chi = np.array([[0.0, 2.2], [2.2, 0.0]])
+    p = inputs.flat_interface([0.5, 0.5], chi=chi, nx=64, ny=4, kappa=0.0, tau=1 / 0.9)
+    o = Oracle.from_problem(p)
+    o.run(40000)
+    m = o.moments()
+    phi = m["rho"][0] / m["rho"].sum(0)
+    return p, phi
+
+
+@pytest.mark.parametrize("precision", SHIFTED)
+@pytest.mark.parametrize("kernel", [mclb.KERNEL_FUSED, mclb.KERNEL_STAGED])
+def test_shifted_storage_bounds(precision, kernel):
+    """set_state / get_state: per-population error within one 16-bit rounding of the
+    deviation from w_i M; site mass exact to FP32 rounding."""
+    n, nx, ny = 3, 37, 11
+    rho, u = inputs.random_state(n, nx, ny, seed=5, amp=0.2, umax=0.05)
+    chi = np.full((n, n), 2.0)
+    np.fill_diagonal(chi, 0.0)
+    orc = Oracle(n, nx, ny, 1.0, chi)
+    orc.init(rho, u)
+    # equilibrium populations moved off equilibrium by 5 % Gaussian noise
+    f = orc.f * (1.0 + 0.05 * inputs.gaussian(11, orc.f.size).reshape(orc.f.shape))
+    sim = mclb.Simulation(n, nx, ny, 1.0, chi, precision=precision, kernel=kernel)
+    sim.set_state(f)
+    g = sim.get_state()
+    # set_state takes pre-collision values f(x); the stored site is x - v_i, whose mass
+    # is the sum over i of f_i(x + v_i).  Rebuild the per-site masses in that frame.
+    vx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    vy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    src = np.empty_like(f)
+    back = np.empty_like(g)
+    for i in range(9):
+        src[:, i] = np.roll(f[:, i], (-vy[i], -vx[i]), axis=(1, 2))
+        back[:, i] = np.roll(g[:, i], (-vy[i], -vx[i]), axis=(1, 2))
+    M = src.sum(axis=1, keepdims=True)
+    # d_i is rounded once; R = M - sum_j d_j carries the other roundings into w_i R
+    dev = np.abs(src - W[None, :, None, None] * M)
+    spread = W[None, :, None, None] * dev.sum(axis=1, keepdims=True)
+    bound = ULP[precision] * (dev + spread) + 4e-7 * M
+    assert np.all(np.abs(back - src) <= bound)
+    np.testing.assert_allclose(back.sum(axis=1), M[:, 0], rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("precision", SHIFTED + ["fp32"])
+def test_shifted_flat_interface_compositions(precision, flat_oracle):
+    """Bulk compositions of the binary flat interface after 40000 steps match the
+    oracle's to 1e-3, and each component's mass drifts by less than 1e-3."""
+    p, phi_ref = flat_oracle
+    sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
+    m0 = sim.conservation()["mass"]
+    sim.step(40000)
+    assert sim.status() == 0
+    m = sim.moments(mu=False, P=False)
+    phi = m["rho"][0] / m["rho"].sum(0)
+    assert abs(phi.max() - phi_ref.max()) < 1e-3
+    assert abs(phi.min() - phi_ref.min()) < 1e-3
+    assert np.max(np.abs(phi - phi_ref)) < 1e-3
+    m1 = sim.conservation()["mass"]
+    assert np.all(np.abs(m1 / m0 - 1.0) < 1e-3)
+
+
+@pytest.mark.parametrize("precision", SHIFTED)
+def test_shifted_slab_densities(precision):
+    """Polymer/solvent/non-solvent slab (Sec. 4 membrane set-up) at 512 x 128 after 3000
+    steps: every component density within 1e-3 of the oracle's."""
+    p = inputs.slab(512, 128)
+    o = Oracle.from_problem(p)
+    o.run(3000)
+    ref = o.moments()["rho"]
+    sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
+    sim.step(3000)
+    assert sim.status() == 0
+    got = sim.moments(U=False, mu=False, P=False)["rho"]
+    assert np.max(np.abs(got - ref)) < 1e-3
