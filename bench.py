@@ -37,8 +37,8 @@ if ROOT not in sys.path:
 METRIC = "MLUPS×components and % of HBM roofline; FP32 vs BF16-shifted vs batched"
 UNIT = "MLUPS×components"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["fused.cuh", "physics.cuh", "lattice.cuh"]
-PROFILE = os.path.join(ROOT, "profiles", "k_fused_fp32_n5_2048x2048.md")
+KERNEL_SOURCES = ["march.cuh", "tma.cuh", "physics.cuh", "lattice.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "k_march_fp32_n5_2048x2048.md")
 
 
 def workloads():
@@ -367,7 +367,7 @@ def main():
                          (bytes_step / 2 / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "note": f"k_fused: 72*N B per site (9 loads + 9 stores of f in FP32) per "
+                     "note": f"k_march: 72*N B per site (9 loads + 9 stores of f in FP32) per "
                              f"launch / CUDA-event time per launch; peak of {peak_src} copy bandwidth"},
         "mlups": world * S * args.steps / elapsed / 1e6,
         "gpu_launches": launches * args.steps,

@@ -62,8 +62,9 @@ typedef enum {
 /* Which kernel schedule performs a timestep. */
 typedef enum {
     MCLB_KERNEL_AUTO = 0,   /* the fused single-pass kernel                         */
-    MCLB_KERNEL_FUSED = 1,  /* one launch per step: stream, moments, potentials,
-                               force, collision in one pass over the distributions  */
+    MCLB_KERNEL_FUSED = 1,  /* stream, moments, potentials, force, collision in one
+                               pass over the distributions, then a small launch that
+                               refreshes the periodic ghost columns                 */
     MCLB_KERNEL_STAGED = 2  /* three launches per step through density and
                                potential fields in device scratch memory            */
 } mclb_kernel;
@@ -171,7 +172,8 @@ long mclb_step_count(mclb_handle h);
  * 2 * N * ny * nx * (9 * 2 + 4) in the shifted modes. */
 double mclb_bytes_per_step(mclb_handle h);
 
-/* Kernel launches one timestep issues (1 for the fused schedule, 3 for the staged). */
+/* Kernel launches one timestep issues (2 for the fused schedule: the single pass and
+ * the refresh of the periodic ghost columns; 3 for the staged). */
 int mclb_launches_per_step(mclb_handle h);
 
 /* Release everything the handle owns.  NULL is accepted.  Synchronises. */

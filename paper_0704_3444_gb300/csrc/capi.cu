@@ -149,6 +149,7 @@ struct mclb_handle_s {
     void* f[2];
     CUtensorMap tmap[2];
     CUtensorMap tmapr[2];         // density lines of the 16-bit formats
+    CUtensorMap tmapw[2];         // columns [0, nx) of the lines, for the kernel's box stores
     int cur;                      // buffer holding the current state
     long steps;
     size_t fbytes;                // bytes of one distribution buffer
@@ -196,22 +197,34 @@ int make_tmap(mclb_handle h, int b)
     if (!fn) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled unavailable");
     const Problem& P = h->P;
     const size_t sz = h->tab->storage_bytes;
-    // 4-D view (x, velocity, row, component); one box = one source row of every line
+    // 4-D view (x, velocity, row, component); one box = one velocity line of one row,
+    // all components, box_w columns
     cuuint64_t dims[4] = {(cuuint64_t)P.pitch, (cuuint64_t)Q, (cuuint64_t)P.ny, (cuuint64_t)P.N};
     cuuint64_t strides[3] = {(cuuint64_t)(P.pitch * sz), (cuuint64_t)(Q * P.pitch * sz),
                              (cuuint64_t)(P.plane * sz)};
-    cuuint32_t box[4] = {(cuuint32_t)(h->plan.W + 2 * P.hx), (cuuint32_t)Q, 1u, (cuuint32_t)P.N};
+    cuuint32_t box[4] = {(cuuint32_t)h->plan.box_w, 1u, 1u, (cuuint32_t)P.N};
     cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     CUresult r = fn(&h->tmap[b], h->tab->tma_type, 4, h->f[b], dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if (h->plan.out_w > 0) {
+        // the same 4-D view ending at column nx (boxes that reach past it are clipped):
+        // one box = out_w columns of the 9 lines of one row, all components
+        cuuint64_t wdims[4] = {(cuuint64_t)(P.nx + P.hx), (cuuint64_t)Q, (cuuint64_t)P.ny, (cuuint64_t)P.N};
+        cuuint32_t wbox[4] = {(cuuint32_t)h->plan.out_w, (cuuint32_t)Q, 1u, (cuuint32_t)P.N};
+        r = fn(&h->tmapw[b], h->tab->tma_type, 4, h->f[b], wdims, strides, wbox, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled (store view) failed (%d)", (int)r);
+    }
     if (h->tab->shifted) {
         // 3-D view (x, row, component) of the FP32 density lines; same columns per box
         cuuint64_t rdims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, (cuuint64_t)P.N};
         cuuint64_t rstrides[2] = {(cuuint64_t)(P.pitch * sizeof(float)),
                                   (cuuint64_t)(P.ny * P.pitch * sizeof(float))};
-        cuuint32_t rbox[3] = {(cuuint32_t)(h->plan.W + 2 * P.hx), 1u, (cuuint32_t)P.N};
+        cuuint32_t rbox[3] = {(cuuint32_t)h->plan.box_w, 1u, (cuuint32_t)P.N};
         r = fn(&h->tmapr[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                static_cast<char*>(h->f[b]) + P.rbytes, rdims, rstrides, rbox, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -226,8 +239,8 @@ cudaError_t launch_one_step(mclb_handle h, int from)
 {
     const Problem& P = h->P;
     if (h->fused)
-        return h->tab->step_fused(P, h->sc, h->plan, &h->tmap[from], &h->tmapr[from], h->f[from ^ 1],
-                                  h->stream);
+        return h->tab->step_fused(P, h->sc, h->plan, &h->tmap[from], &h->tmapr[from],
+                                  &h->tmapw[from ^ 1], h->f[from ^ 1], h->stream);
     return h->tab->step_staged(P, h->sc, h->f[from], h->f[from ^ 1], h->stream);
 }
 
@@ -471,7 +484,7 @@ double mclb_bytes_per_step(mclb_handle h)
 int mclb_launches_per_step(mclb_handle h)
 {
     if (check_handle(h)) return -1;
-    return h->fused ? 1 : 3;
+    return h->fused ? 2 : 3;
 }
 
 int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, double* P)

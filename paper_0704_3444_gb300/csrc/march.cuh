@@ -1,0 +1,457 @@
+// march.cuh -- one launch per timestep by column marching: every lane owns one column
+// of a strip and carries its components down a segment of rows in registers.
+//
+// The step at a site needs (Sec. 3, Eqs. ssLB, ff1-ff3, chemicalpotential, definef):
+// the pulled populations f^s_i(x - v_i) for its moments, rho^s on the 8 neighbours
+// for the kappa Laplacian in nu^s, and nu^s on the 8 neighbours for the force.  A
+// lane at column x marching down rows keeps the vertical neighbours of those fields
+// in registers and gets the horizontal ones from lanes x -+ 1 by warp shuffles.
+// Iteration k of the march handles
+//   - the moments and site terms of the lead row m = y0 - 2 + k,
+//   - nu^s of row m - 1 (rho^s of rows m - 2 .. m now known),
+//   - the collision of row m - 2 (nu^s of rows m - 3 .. m - 1 now known).
+// A warp of 32 lanes covers 32 columns: nu is valid on lanes 1..30 and the collision
+// on lanes 2..29, so a column group writes 28 columns and neighbouring groups overlap
+// by 4.  The N components of a column group are split over two warps (components
+// [0, NA) and [NA, N)); per row the pair exchanges rho^s and its share of the momentum
+// through a small shared buffer and one pair barrier, and each warp then evaluates the
+// site terms (rho, ln rho, the Flory-Huggins sums, u) for itself.  The split doubles
+// the warps that share the staged rows, which is what bounds the warps per SM.
+//
+// Shared memory holds the pulled distributions: a ring of NS stages, stage k holding
+// everything that row m = y0 - 2 + k pulls, i.e. for each velocity i the line of source
+// row m - v_i,y (all N components, columns [x0 - hx, x0 - hx + WI)).  A producer warp
+// fills each stage with nine TMA box copies (one per velocity, cp.async.bulk.tensor) on
+// one mbarrier, plus an L2 prefetch four rows ahead; the 16-bit formats add the FP32
+// reference-density lines of source rows m - 1, m, m + 1.  A stage is read by the
+// moments of row m and two iterations later by the collision of row m; each compute
+// warp then arrives on the stage's "empty" mbarrier and the producer refills it.  So
+// each stored value is loaded from HBM once per step (plus the strip and segment halos)
+// and no CTA-wide barrier is taken per row.  Every mbarrier wait is bounded; a timeout
+// sets STATUS_TIMEOUT, the copies in flight are drained and the CTA returns.
+//
+// The kernel writes columns [0, nx) only; k_ghosts then refreshes the periodic ghost
+// columns.  (Writing the few ghost copies from inside the march, with plain stores next
+// to the bulk tensor stores of the same lines, halved the speed of the CTAs that did it,
+// and the step waits for the slowest CTA.)
+#pragma once
+
+#include <type_traits>
+
+#include "tma.cuh"
+
+namespace mclb {
+
+constexpr int MARCH_HDR = 256;   // full and empty mbarriers + abort flag
+constexpr int MARCH_MAX_NS = 8;
+constexpr int MARCH_OUT = 28;    // columns written per warp
+constexpr int MARCH_PF = 4;      // L2 prefetch distance in rows
+#ifndef MARCH_GROUPS
+#define MARCH_GROUPS 1           // component groups per column group (1 or 2)
+#endif
+
+// vy of velocity i from a runtime index (bits 2i..2i+1 hold vy + 1)
+__device__ __forceinline__ int vy_rt(int i) { return (int)((0x2865u >> (2 * i)) & 3u) - 1; }
+
+template <typename T, int N, int NW, int NS, int NGP>
+struct MarchGeomT {
+    using C = typename Storage<T>::C;
+    static constexpr bool SHIFTED = Storage<T>::shifted;
+    static constexpr int NWC = NW;                                // column groups
+    static constexpr int NG = (N >= 2 && NGP == 2) ? 2 : 1;       // component groups
+    static constexpr int NA = NG == 2 ? (N + 1) / 2 : N;          // components of group 0
+    static constexpr int NB = N - NA;                             // components of group 1
+    static constexpr int NCW = NW * NG;                           // compute warps
+    static constexpr int STAGES = NS;
+    static constexpr int HX = (16 / (int)sizeof(T)) < 4 ? 4 : 16 / (int)sizeof(T);
+    static constexpr int WOUT = MARCH_OUT * NW;                   // columns written per CTA
+    static constexpr int AL = 16 / (int)sizeof(T);                // elements per 16 bytes
+    static constexpr int WI = (WOUT + 3 + HX + AL - 1) / AL * AL; // staged columns
+    static constexpr int THREADS = 32 * NCW + 32;                 // + producer warp
+    static constexpr size_t VBYTES = round_up_sz((size_t)N * WI * sizeof(T), 128);
+    static constexpr size_t RBYTES = SHIFTED ? round_up_sz((size_t)N * WI * sizeof(float), 128) : 0;
+    static constexpr size_t STAGE_BYTES = Q * VBYTES + 3 * RBYTES;
+    static constexpr uint32_t TX =
+        (uint32_t)(Q * (size_t)N * WI * sizeof(T) + (SHIFTED ? 3 * (size_t)N * WI * sizeof(float) : 0));
+    // FP32/FP64: each compute warp stages its 28 output columns of the 9 N lines in shared
+    // memory and writes them with one TMA box per row (28 columns are 16-byte multiples)
+    static constexpr bool TMA_STORE = !SHIFTED && (MARCH_OUT * sizeof(T)) % 16 == 0;
+    static constexpr size_t OBYTES = TMA_STORE ? round_up_sz((size_t)N * Q * MARCH_OUT * sizeof(T), 128) : 0;
+    static constexpr int XW = N + 4;                              // rho^s, (jx, jy) per group
+    static constexpr size_t XBYTES = NG == 2 ? (size_t)2 * NW * XW * 32 * sizeof(C) : 0;
+    static constexpr size_t SMEM = MARCH_HDR + NS * STAGE_BYTES + XBYTES + NCW * OBYTES;
+    static constexpr bool FITS = SMEM <= 227 * 1024 && WI <= 256;
+    static constexpr int MIN_CTAS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
+    // registers per thread that let MIN_CTAS CTAs share the register file: each of the 4
+    // SM sub-partitions holds 16K registers and its share of the warps (multiple of 8)
+    static constexpr int WARPS_SP = (MIN_CTAS * (THREADS / 32) + 3) / 4;
+    static constexpr int MAXREG_RAW = 16384 / (32 * WARPS_SP) / 8 * 8;
+    static constexpr int MAXREG = MAXREG_RAW > 255 ? 255 : MAXREG_RAW;
+};
+
+// Strip width and ring depth per storage type and N: the first of (4 column groups,
+// 5 stages), (4, 4), (2, 5), (2, 4) that lets two CTAs share an SM, else the first that
+// fits one CTA.
+template <typename T, int N, int NGP = MARCH_GROUPS>
+struct MarchPick {
+    using A = MarchGeomT<T, N, 4, 5, NGP>;
+    using B = MarchGeomT<T, N, 4, 4, NGP>;
+    using D = MarchGeomT<T, N, 2, 5, NGP>;
+    using E = MarchGeomT<T, N, 2, 4, NGP>;
+    static constexpr bool A2 = A::FITS && A::MIN_CTAS == 2;
+    static constexpr bool B2 = B::FITS && B::MIN_CTAS == 2;
+    static constexpr bool D2 = D::FITS && D::MIN_CTAS == 2;
+    static constexpr bool E2 = E::FITS && E::MIN_CTAS == 2;
+    static constexpr int NW = A2 ? 4 : B2 ? 4 : D2 ? 2 : E2 ? 2 : A::FITS ? 4 : B::FITS ? 4 : D::FITS ? 2 : 2;
+    static constexpr int NS = A2 ? 5 : B2 ? 4 : D2 ? 5 : E2 ? 4 : A::FITS ? 5 : B::FITS ? 4 : D::FITS ? 5 : 4;
+    using G = MarchGeomT<T, N, NW, NS, NGP>;
+};
+
+template <typename T, int N>
+using MarchGeom = typename MarchPick<T, N>::G;
+
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+__device__ __forceinline__ void pair_sync(int id)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(MarchGeom<T, N>::THREADS) __maxnreg__((MarchGeom<T, N>::MAXREG))
+k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapr,
+        const __grid_constant__ CUtensorMap tmapw, T* __restrict__ fout, const __grid_constant__ StepParams<typename Storage<T>::C> p,
+        const int H)
+{
+    using G = MarchGeom<T, N>;
+    using C = typename Storage<T>::C;
+    constexpr int NS = G::STAGES, WI = G::WI, NCW = G::NCW, XW = G::XW;
+    const int x0 = blockIdx.x * G::WOUT;
+    const int y0 = blockIdx.y * H;
+    const int Hc = min(H, p.ny - y0);
+    const int nk = Hc + 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + MARCH_MAX_NS;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 16 * MARCH_MAX_NS);
+    unsigned char* stages = smem + MARCH_HDR;
+    C* xbuf = reinterpret_cast<C*>(stages + NS * G::STAGE_BYTES);
+    unsigned char* obufs = stages + NS * G::STAGE_BYTES + G::XBYTES;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ---- producer warp: stage k (lead row y0 - 2 + k) holds, for each velocity i, the
+        // line of source row m - v_i,y; it reuses the slot of stage k - NS once all
+        // compute warps have released that one
+        auto grow = [&](int r) {
+            r %= p.ny;
+            return r + (r < 0 ? p.ny : 0);
+        };
+        int issued = 0;
+        for (int k = 0; k < nk; ++k) {
+            const int slot = k % NS;
+            if (k >= NS) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(&empty[slot], ((k / NS) - 1) & 1);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    *abort_flag = 1;
+                    break;
+                }
+            }
+            if (*abort_flag) break;
+            const int m = y0 - 2 + k;
+            unsigned char* st = stages + (size_t)slot * G::STAGE_BYTES;
+            if (lane == 0) mbar_arrive_expect_tx(&full[slot], G::TX);
+            __syncwarp();
+            if (lane < Q) {
+                tma_load_row(st + lane * G::VBYTES, &tmap, &full[slot], x0, grow(m - vy_rt(lane)), lane);
+            } else if (G::SHIFTED && lane < Q + 3) {
+                tma_load_rline(st + Q * G::VBYTES + (lane - Q) * G::RBYTES, &tmapr, &full[slot], x0,
+                               grow(m - 1 + (lane - Q)));
+            } else if (lane >= 16 && lane < 16 + Q && k + MARCH_PF < nk) {
+                tma_prefetch_row(&tmap, x0, grow(m + MARCH_PF - vy_rt(lane - 16)), lane - 16);
+            }
+            issued = k + 1;
+        }
+        __syncthreads();
+        if (*abort_flag && lane == 0) {
+            atomicOr(p.status, STATUS_TIMEOUT);
+            // the copies still in flight land before the shared memory is released
+            for (int k = max(0, issued - NS); k < issued; ++k) mbar_wait(&full[k % NS], (k / NS) & 1);
+        }
+        return;
+    }
+
+    // ---- compute warps: column group cg, component group g
+    const int cg = G::NG == 2 ? (warp >> 1) : warp;
+    const int g = G::NG == 2 ? (warp & 1) : 0;
+    const int X = x0 - 2 + MARCH_OUT * cg + lane;         // this lane's column
+    const int col = G::HX - 2 + MARCH_OUT * cg + lane;    // its staged column
+    const bool out_lane = lane >= 2 && lane < 30 && X < p.nx;
+    [[maybe_unused]] T* obuf = reinterpret_cast<T*>(obufs + warp * G::OBYTES);
+
+    // pulled value of velocity i (compile-time) for component s from a stage
+    auto pulled = [&](const unsigned char* st, int i, int s) -> C {
+        const T* line = reinterpret_cast<const T*>(st + i * G::VBYTES) + s * WI;
+        C v = to_c<T>(line[col - vx(i)]);
+        if constexpr (G::SHIFTED) {
+            const float* rl = reinterpret_cast<const float*>(st + Q * G::VBYTES + (1 - vy(i)) * G::RBYTES) + s * WI;
+            v = fma(wq<C>(i), C(rl[col - vx(i)]), v);
+        }
+        return v;
+    };
+
+    const C theta = p.theta, kappa6 = C(6) * p.kappa;
+    const C c9 = C(1.0 / 9.0), c36 = C(1.0 / 36.0), c59 = C(5.0 / 9.0);
+
+    // The march over rows for components [S0, S0 + NC).  State carried from row to row
+    // (m = lead row of the iteration about to start), per component:
+    //   Q1 = L(m-1) - 6 kappa (B(m-2) + Cc(m-1)),  Q0 = -6 kappa B(m-1)   (partial nu)
+    //   GX = D(m-2)/9 + D(m-3)/36,  Dp = D(m-2),  T2 = T(m-3),  T1 = T(m-2)
+    //   R/X/Y2, R/X/Y1 = rho^s, j^s of rows m-2, m-1;  and u of rows m-2, m-1
+    // with B = rho/9 + A/36, Cc = A/9 - 5 rho/9 (A = rho(x-1) + rho(x+1)), so that
+    // 6 sum_i w_i (rho_i - rho_0) at row r is 6 (B(r-1) + B(r+1) + Cc(r)); and with
+    // D = nu(x+1) - nu(x-1), T = nu/9 + (nu(x+1) + nu(x-1))/36, so that the force gradient
+    // 3 sum_i w_i v_i nu(x + v_i) at row r is 3 (D(r)/9 + (D(r-1) + D(r+1))/36,
+    // T(r+1) - T(r-1)).
+    auto march = [&](auto s0c, auto ncc) {
+        constexpr int S0 = decltype(s0c)::value, NC = decltype(ncc)::value;
+        C Q1[NC], Q0[NC], GX[NC], Dp[NC], T2[NC], T1[NC];
+        C R2[NC], X2[NC], Y2[NC], R1[NC], X1[NC], Y1[NC];
+        C ux2 = C(0), uy2 = C(0), ux1 = C(0), uy1 = C(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            Q1[c] = Q0[c] = GX[c] = Dp[c] = T2[c] = T1[c] = C(0);
+            R2[c] = X2[c] = Y2[c] = R1[c] = X1[c] = Y1[c] = C(0);
+        }
+
+        for (int k = 0; k < nk; ++k) {
+            const int m = y0 - 2 + k;
+            const int slot = k % NS;
+            const unsigned char* st = stages + (size_t)slot * G::STAGE_BYTES;
+            const bool ok = mbar_wait(&full[slot], (k / NS) & 1);
+            if (__any_sync(0xffffffffu, !ok)) {
+                // the partner warp may wait at the pair barrier: release it
+                *abort_flag = 1;
+                if (G::NG == 2) pair_sync(1 + cg);
+                break;
+            }
+
+            // ---- moments of row m (own components), exchanged with the partner warp
+            C R0[NC], X0[NC], Y0[NC];
+            C jxp = C(0), jyp = C(0);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                C v[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) v[i] = pulled(st, i, S0 + c);
+                const C a = v[5] - v[7], b = v[6] - v[8];
+                R0[c] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+                X0[c] = (v[1] - v[3]) + (a - b);
+                Y0[c] = (v[2] - v[4]) + (a + b);
+                jxp += X0[c];
+                jyp += Y0[c];
+            }
+            [[maybe_unused]] C* xw = xbuf + ((k & 1) * G::NWC + cg) * XW * 32 + lane;
+            C Ra[N];
+            C jx, jy;
+            if constexpr (G::NG == 2) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) xw[(S0 + c) * 32] = R0[c];
+                xw[(N + 2 * g) * 32] = jxp;
+                xw[(N + 2 * g + 1) * 32] = jyp;
+                pair_sync(1 + cg);
+                if (*abort_flag) break;
+#pragma unroll
+                for (int t = 0; t < N; ++t) Ra[t] = xw[t * 32];
+                jx = xw[N * 32] + xw[(N + 2) * 32];
+                jy = xw[(N + 1) * 32] + xw[(N + 3) * 32];
+            } else {
+#pragma unroll
+                for (int t = 0; t < N; ++t) Ra[t] = R0[t];
+                jx = jxp;
+                jy = jyp;
+            }
+
+            // ---- site terms of row m (every component's density)
+            C rho = C(0);
+#pragma unroll
+            for (int t = 0; t < N; ++t) rho += Ra[t];
+            const C inv = C(1) / rho;
+            const C ux0 = jx * inv, uy0 = jy * inv;
+            if (g == 0 && out_lane && m >= y0 && m < y0 + Hc && (!(rho > C(0)) || !isfinite(rho)))
+                atomicOr(p.status, STATUS_NONFINITE);
+            const C lnr = dev_log(rho);
+            C acc[N];
+            C sm = C(0), quad = C(0);
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                C a = C(0);
+#pragma unroll
+                for (int u = 0; u < N; ++u) a += p.chi[t * N + u] * Ra[u];
+                acc[t] = a;
+                sm += Ra[t] * p.inv_m[t];
+                quad += Ra[t] * a;
+            }
+            const C Gs = -theta * (sm * inv + C(0.5) * quad * inv * inv);
+
+            // ---- nu of row m - 1, partial nu of rows m and m + 1 (own components)
+            C Dn[NC], Tn[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const int s = S0 + c;
+                C logs = -p.th_m[s] * lnr;
+                if ((p.log_mask >> s) & 1u) {
+                    const C fl = p.log_floor * rho;
+                    logs += p.logc[s] * dev_log(R0[c] > fl ? R0[c] : fl);
+                }
+                const C L0 = logs + theta * (p.m_inv_m1[s] + acc[s] * inv) + Gs;
+                const C A = __shfl_up_sync(0xffffffffu, R0[c], 1) + __shfl_down_sync(0xffffffffu, R0[c], 1);
+                const C B0 = R0[c] * c9 + A * c36;
+                const C C0 = A * c9 - c59 * R0[c];
+                const C nu = Q1[c] - kappa6 * B0;
+                Q1[c] = Q0[c] + L0 - kappa6 * C0;
+                Q0[c] = -kappa6 * B0;
+                const C nl = __shfl_up_sync(0xffffffffu, nu, 1);
+                const C nr = __shfl_down_sync(0xffffffffu, nu, 1);
+                Dn[c] = nr - nl;
+                Tn[c] = nu * c9 + (nr + nl) * c36;
+            }
+
+            // ---- collision of row r = m - 2 (stage of iteration k - 2)
+            if (k >= 4) {
+                const unsigned char* sc = stages + (size_t)((k - 2) % NS) * G::STAGE_BYTES;
+                const int r = m - 2;
+                if constexpr (G::TMA_STORE) {
+                    // the previous row's box has been read out of the staging buffer
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
+                }
+                C e[Q];
+                eq_weights(ux2, uy2, e);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const int s = S0 + c;
+                    C f[Q];
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) f[i] = pulled(sc, i, s);
+                    const C gx = GX[c] + Dn[c] * c36;
+                    const C gy = Tn[c] - T2[c];
+                    const C ax = -p.fcoef * (C(3) * gx) + p.gx;
+                    const C ay = -p.fcoef * (C(3) * gy) + p.gy;
+                    C out[Q];
+                    collide(p, f, e, R2[c], X2[c], Y2[c], ax, ay, out);
+                    if constexpr (G::TMA_STORE) {
+                        if (lane >= 2 && lane < 30) {
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) obuf[(s * Q + i) * MARCH_OUT + lane - 2] = T(out[i]);
+                        }
+                    } else if (out_lane) {
+                        T* line = fout + line_off(p, s, r, 0) + G::HX;
+                        [[maybe_unused]] C rref = C(0);
+                        if constexpr (G::SHIFTED) {
+                            C M = C(0);
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) M += out[i];
+                            C dsum = C(0);
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) {
+                                out[i] = Storage<T>::round(out[i] - wq<C>(i) * M);
+                                dsum += out[i];
+                            }
+                            rref = M - dsum;
+                        }
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) Storage<T>::store(line + i * p.pitch + X, out[i]);
+                        if constexpr (G::SHIFTED) rho_line(fout, p, s, r)[G::HX + X] = rref;
+                    }
+                }
+            }
+            if constexpr (G::TMA_STORE) {
+                if (k >= 4) {
+                    fence_async_smem();
+                    __syncwarp();
+                    // boxes that start at or past column nx are not issued (the view
+                    // clips the others at nx)
+                    if (lane == 0 && x0 + MARCH_OUT * cg < p.nx) {
+                        tma_store_box(&tmapw, obuf, x0 + MARCH_OUT * cg + G::HX, 0, m - 2, 0);
+                        bulk_commit();
+                    }
+                }
+            }
+            if (k >= 2) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[(k - 2) % NS]);   // stage of row m - 2 done
+            }
+            // ---- advance the carried state by one row
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                GX[c] = Dn[c] * c9 + Dp[c] * c36;
+                Dp[c] = Dn[c];
+                T2[c] = T1[c];
+                T1[c] = Tn[c];
+                R2[c] = R1[c];
+                X2[c] = X1[c];
+                Y2[c] = Y1[c];
+                R1[c] = R0[c];
+                X1[c] = X0[c];
+                Y1[c] = Y0[c];
+            }
+            ux2 = ux1;
+            uy2 = uy1;
+            ux1 = ux0;
+            uy1 = uy0;
+        }
+    };
+
+    if constexpr (G::NG == 2) {
+        if (g == 0)
+            march(IC<0>{}, IC<G::NA>{});
+        else
+            march(IC<G::NA>{}, IC<G::NB>{});
+    } else {
+        march(IC<0>{}, IC<N>{});
+    }
+    if constexpr (G::TMA_STORE) {
+        if (lane == 0) bulk_wait_all();
+    }
+    __syncthreads();
+}
+
+// Periodic ghost columns of every line of f (and of the FP32 density lines in the
+// 16-bit formats): column g in [-hx, 0) and [nx, nx + hx) takes the value of column
+// g mod nx.  One thread per line.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_ghosts(T* __restrict__ f, const __grid_constant__ StepParams<typename Storage<T>::C> p, int ncomp)
+{
+    const long long nl = (long long)ncomp * p.ny * Q;
+    const long long nr = Storage<T>::shifted ? (long long)ncomp * p.ny : 0;
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl + nr) return;
+    const int hx = p.hx, nx = p.nx;
+    auto fill = [&](auto* row) {
+        for (int g = -hx; g < 0; ++g) row[hx + g] = row[hx + ((g % nx) + nx) % nx];
+        for (int g = nx; g < nx + hx; ++g) row[hx + g] = row[hx + g % nx];
+    };
+    if (l < nl) {
+        fill(f + l * p.pitch);
+    } else {
+        float* r = reinterpret_cast<float*>(reinterpret_cast<char*>(f) + p.rbytes);
+        fill(r + (l - nl) * p.pitch);
+    }
+}
+
+}  // namespace mclb

@@ -58,9 +58,12 @@ constexpr int REDUCE_BLOCKS = 256;    // fixed grid of the FP64 reductions (dete
 
 // Launch shape of the fused kernel: strips of W columns, segments of H rows,
 // NS shared-memory stages of source rows.
+// Launch plan of the single-pass kernel: strips of W written columns (TMA boxes of
+// box_w columns, one velocity line each), segments of H rows, NS stages.
 struct FusedPlan {
-    int W, NS, H;
+    int W, box_w, out_w, NS, H;
     int nstrips, nsegs;
+    int threads;
     size_t smem;
     bool ok;
 };
@@ -75,10 +78,10 @@ struct KernelTable {
     cudaError_t (*init)(const Problem&, const Scratch&, const double* rho, const double* u,
                         void* f, cudaStream_t st);
     // one fused timestep fin -> fout (tmap_in describes fin's lines, tmapr_in its density
-    // lines in the 16-bit formats)
+    // lines in the 16-bit formats, tmapw_out the columns [0, nx) of fout's lines)
     cudaError_t (*step_fused)(const Problem&, const Scratch&, const FusedPlan&,
-                              const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in, void* fout,
-                              cudaStream_t st);
+                              const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in,
+                              const CUtensorMap* tmapw_out, void* fout, cudaStream_t st);
     // one staged timestep fin -> fout (three launches through scratch)
     cudaError_t (*step_staged)(const Problem&, const Scratch&, const void* fin, void* fout,
                                cudaStream_t st);

@@ -4,7 +4,7 @@
 #include <algorithm>
 
 #include "batch.cuh"
-#include "fused.cuh"
+#include "march.cuh"
 #include "staged.cuh"
 
 namespace mclb {
@@ -61,41 +61,41 @@ struct Launch {
         });
     }
 
-    template <int N, int COLS>
-    static bool plan_cols(const Problem& P, int sm_count, FusedPlan& pl)
+    // Strips of WOUT columns, segments of H rows: one wave of CTAs, each segment as
+    // tall as the resident CTAs allow (every segment re-reads 4 halo rows and spends 4
+    // warm-up iterations), at least 8 rows.
+    template <int N>
+    static FusedPlan plan_n(const Problem& P, int sm_count)
     {
-        using G = FusedGeom<T, N, COLS>;
-        if (G::SMEM > 227 * 1024 || G::THREADS > FUSED_MAX_THREADS) return false;
-        if (cudaFuncSetAttribute(k_fused<T, N, COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        using G = MarchGeom<T, N>;
+        FusedPlan pl{};
+        pl.ok = false;
+        if (!G::FITS) return pl;
+        if (cudaFuncSetAttribute(k_march<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)G::SMEM) != cudaSuccess)
-            return false;
+            return pl;
+        // the largest shared-memory carveout, so that the resident CTAs the occupancy
+        // query counts (it assumes the largest) are the ones the launch gets
+        if (cudaFuncSetAttribute(k_march<T, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+            return pl;
         int ctas = 0;  // resident CTAs per SM as the runtime computes them (smem, registers)
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_fused<T, N, COLS>, G::THREADS,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_march<T, N>, G::THREADS,
                                                           G::SMEM) != cudaSuccess || ctas < 1)
-            return false;
-        pl.W = G::W;
-        pl.NS = G::NS;
+            return pl;
+        pl.W = G::WOUT;
+        pl.box_w = G::WI;
+        pl.out_w = G::TMA_STORE ? MARCH_OUT : 0;
+        pl.NS = G::STAGES;
         pl.smem = G::SMEM;
-        pl.ok = true;
-        pl.nstrips = (P.nx + G::W - 1) / G::W;
-        // one wave of tiles: as many row segments as resident CTAs allow, each as tall
-        // as possible (every segment re-reads 6 halo rows), at least 8 rows
+        pl.threads = G::THREADS;
+        pl.nstrips = (P.nx + G::WOUT - 1) / G::WOUT;
         const int slots = ctas * std::max(1, sm_count);
         int nsegs = std::max(1, slots / pl.nstrips);
         nsegs = std::min(nsegs, std::max(1, P.ny / 8));
         pl.H = (P.ny + nsegs - 1) / nsegs;
         pl.nsegs = (P.ny + pl.H - 1) / pl.H;
-        return true;
-    }
-
-    // two columns per component thread (64-column strips) when shared memory allows,
-    // else one (32-column strips)
-    template <int N>
-    static FusedPlan plan_n(const Problem& P, int sm_count)
-    {
-        FusedPlan pl{};
-        pl.ok = false;
-        if (!plan_cols<N, 2>(P, sm_count, pl)) plan_cols<N, 1>(P, sm_count, pl);
+        pl.ok = true;
         return pl;
     }
 
@@ -118,18 +118,16 @@ struct Launch {
 
     static cudaError_t step_fused(const Problem& P, const Scratch& sc, const FusedPlan& pl,
                                   const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in,
-                                  void* fout, cudaStream_t st)
+                                  const CUtensorMap* tmapw_out, void* fout, cudaStream_t st)
     {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
         const CUtensorMap& tr = Storage<T>::shifted ? *tmapr_in : *tmap_in;
+        const CUtensorMap& tw = pl.out_w > 0 ? *tmapw_out : *tmap_in;
         MCLB_DISPATCH_N(P.N, {
-            if (pl.W == 64)
-                k_fused<T, NN, 2><<<grid, FusedGeom<T, NN, 2>::THREADS, pl.smem, st>>>(
-                    *tmap_in, tr, (T*)fout, p, pl.H);
-            else
-                k_fused<T, NN, 1><<<grid, FusedGeom<T, NN, 1>::THREADS, pl.smem, st>>>(
-                    *tmap_in, tr, (T*)fout, p, pl.H);
+            k_march<T, NN><<<grid, pl.threads, pl.smem, st>>>(*tmap_in, tr, tw, (T*)fout, p, pl.H);
+            const long long lines = (long long)NN * P.ny * (Q + (Storage<T>::shifted ? 1 : 0));
+            k_ghosts<T><<<(unsigned)((lines + 255) / 256), 256, 0, st>>>((T*)fout, p, NN);
             return cudaGetLastError();
         });
     }

