@@ -150,6 +150,7 @@ struct mclb_handle_s {
     CUtensorMap tmap[2];
     CUtensorMap tmapr[2];         // density lines of the 16-bit formats
     CUtensorMap tmapw[2];         // columns [0, nx) of the lines, for the kernel's box stores
+    CUtensorMap tmapwr[2];        // the same for the density lines of the 16-bit formats
     int cur;                      // buffer holding the current state
     long steps;
     size_t fbytes;                // bytes of one distribution buffer
@@ -218,6 +219,18 @@ int make_tmap(mclb_handle h, int b)
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS)
             return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled (store view) failed (%d)", (int)r);
+        if (h->tab->shifted) {
+            cuuint64_t rdims[3] = {(cuuint64_t)(P.nx + P.hx), (cuuint64_t)P.ny, (cuuint64_t)P.N};
+            cuuint64_t rstrides[2] = {(cuuint64_t)(P.pitch * sizeof(float)),
+                                      (cuuint64_t)(P.ny * P.pitch * sizeof(float))};
+            cuuint32_t rbox[3] = {(cuuint32_t)h->plan.out_w, 1u, (cuuint32_t)P.N};
+            r = fn(&h->tmapwr[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                   static_cast<char*>(h->f[b]) + P.rbytes, rdims, rstrides, rbox, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled (density store view) failed (%d)", (int)r);
+        }
     }
     if (h->tab->shifted) {
         // 3-D view (x, row, component) of the FP32 density lines; same columns per box
@@ -240,7 +253,8 @@ cudaError_t launch_one_step(mclb_handle h, int from)
     const Problem& P = h->P;
     if (h->fused)
         return h->tab->step_fused(P, h->sc, h->plan, &h->tmap[from], &h->tmapr[from],
-                                  &h->tmapw[from ^ 1], h->f[from ^ 1], h->stream);
+                                  &h->tmapw[from ^ 1], &h->tmapwr[from ^ 1], h->f[from ^ 1],
+                                  h->stream);
     return h->tab->step_staged(P, h->sc, h->f[from], h->f[from ^ 1], h->stream);
 }
 

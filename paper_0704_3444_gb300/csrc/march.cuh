@@ -30,8 +30,8 @@
 // and no CTA-wide barrier is taken per row.  Every mbarrier wait is bounded; a timeout
 // sets STATUS_TIMEOUT, the copies in flight are drained and the CTA returns.
 //
-// The kernel writes columns [0, nx) only; k_ghosts then refreshes the periodic ghost
-// columns.  (Writing the few ghost copies from inside the march, with plain stores next
+// The kernel writes columns [0, nx) only; k_ghosts (ghosts.cuh) then refreshes the
+// periodic ghost columns.  (Writing the few ghost copies from inside the march, with plain stores next
 // to the bulk tensor stores of the same lines, halved the speed of the CTAs that did it,
 // and the step waits for the slowest CTA.)
 #pragma once
@@ -42,7 +42,7 @@
 
 namespace mclb {
 
-constexpr int MARCH_HDR = 256;   // full and empty mbarriers + abort flag
+constexpr int MARCH_HDR = 256;   // full, empty and row mbarriers + abort flag
 constexpr int MARCH_MAX_NS = 8;
 constexpr int MARCH_OUT = 28;    // columns written per warp
 constexpr int MARCH_PF = 4;      // L2 prefetch distance in rows
@@ -77,9 +77,15 @@ struct MarchGeomT {
     // memory and writes them with one TMA box per row (28 columns are 16-byte multiples)
     static constexpr bool TMA_STORE = !SHIFTED && (MARCH_OUT * sizeof(T)) % 16 == 0;
     static constexpr size_t OBYTES = TMA_STORE ? round_up_sz((size_t)N * Q * MARCH_OUT * sizeof(T), 128) : 0;
+    // 16-bit formats (28 columns are not a 16-byte multiple): the compute warps fill one
+    // double-buffered CTA staging area (deviations and FP32 reference densities of the
+    // WOUT columns) and one thread writes it with two TMA boxes per row
+    static constexpr bool CTA_STORE = SHIFTED && (WOUT * sizeof(T)) % 16 == 0;
+    static constexpr size_t CDEV = CTA_STORE ? round_up_sz((size_t)N * Q * WOUT * sizeof(T), 128) : 0;
+    static constexpr size_t CBUF = CTA_STORE ? CDEV + round_up_sz((size_t)N * WOUT * sizeof(float), 128) : 0;
     static constexpr int XW = N + 4;                              // rho^s, (jx, jy) per group
     static constexpr size_t XBYTES = NG == 2 ? (size_t)2 * NW * XW * 32 * sizeof(C) : 0;
-    static constexpr size_t SMEM = MARCH_HDR + NS * STAGE_BYTES + XBYTES + NCW * OBYTES;
+    static constexpr size_t SMEM = MARCH_HDR + NS * STAGE_BYTES + XBYTES + NCW * OBYTES + 2 * CBUF;
     static constexpr bool FITS = SMEM <= 227 * 1024 && WI <= 256;
     static constexpr int MIN_CTAS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
     // registers per thread that let MIN_CTAS CTAs share the register file: each of the 4
@@ -121,7 +127,8 @@ __device__ __forceinline__ void pair_sync(int id)
 template <typename T, int N>
 __global__ void __launch_bounds__(MarchGeom<T, N>::THREADS) __maxnreg__((MarchGeom<T, N>::MAXREG))
 k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapr,
-        const __grid_constant__ CUtensorMap tmapw, T* __restrict__ fout, const __grid_constant__ StepParams<typename Storage<T>::C> p,
+        const __grid_constant__ CUtensorMap tmapw, const __grid_constant__ CUtensorMap tmapwr,
+        T* __restrict__ fout, const __grid_constant__ StepParams<typename Storage<T>::C> p,
         const int H)
 {
     using G = MarchGeom<T, N>;
@@ -136,7 +143,8 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + MARCH_MAX_NS;
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 16 * MARCH_MAX_NS);
+    uint64_t* rowbar = empty + MARCH_MAX_NS;   // compute warps, once per collided row
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 24 * MARCH_MAX_NS);
     unsigned char* stages = smem + MARCH_HDR;
     C* xbuf = reinterpret_cast<C*>(stages + NS * G::STAGE_BYTES);
     unsigned char* obufs = stages + NS * G::STAGE_BYTES + G::XBYTES;
@@ -146,6 +154,7 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], NCW);
         }
+        mbar_init(rowbar, NCW);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -201,6 +210,9 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
     const int col = G::HX - 2 + MARCH_OUT * cg + lane;    // its staged column
     const bool out_lane = lane >= 2 && lane < 30 && X < p.nx;
     [[maybe_unused]] T* obuf = reinterpret_cast<T*>(obufs + warp * G::OBYTES);
+    [[maybe_unused]] unsigned char* cbufs = obufs + G::NCW * G::OBYTES;
+    [[maybe_unused]] const int ocol = MARCH_OUT * cg + lane - 2;   // column within the CTA's WOUT
+
 
     // pulled value of velocity i (compile-time) for component s from a stage
     auto pulled = [&](const unsigned char* st, int i, int s) -> C {
@@ -358,6 +370,25 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
 #pragma unroll
                             for (int i = 0; i < Q; ++i) obuf[(s * Q + i) * MARCH_OUT + lane - 2] = T(out[i]);
                         }
+                    } else if constexpr (G::CTA_STORE) {
+                        if (lane >= 2 && lane < 30) {
+                            // deviations from w_i M, rounded to storage, and the compensated
+                            // reference density R = M - sum_i d_i (the rule of store_site)
+                            unsigned char* cb = cbufs + ((k - 4) & 1) * G::CBUF;
+                            T* dv = reinterpret_cast<T*>(cb);
+                            float* rv = reinterpret_cast<float*>(cb + G::CDEV);
+                            C M = C(0);
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) M += out[i];
+                            C dsum = C(0);
+#pragma unroll
+                            for (int i = 0; i < Q; ++i) {
+                                const C d = Storage<T>::round(out[i] - wq<C>(i) * M);
+                                dsum += d;
+                                Storage<T>::store(dv + (s * Q + i) * G::WOUT + ocol, d);
+                            }
+                            rv[s * G::WOUT + ocol] = float(M - dsum);
+                        }
                     } else if (out_lane) {
                         T* line = fout + line_off(p, s, r, 0) + G::HX;
                         [[maybe_unused]] C rref = C(0);
@@ -387,6 +418,26 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
                     // clips the others at nx)
                     if (lane == 0 && x0 + MARCH_OUT * cg < p.nx) {
                         tma_store_box(&tmapw, obuf, x0 + MARCH_OUT * cg + G::HX, 0, m - 2, 0);
+                        bulk_commit();
+                    }
+                }
+            }
+            if constexpr (G::CTA_STORE) {
+                if (k >= 4) {
+                    fence_async_smem();
+                    // the box issued one row earlier has been read out of the other buffer
+                    // before any warp passes this barrier and refills that buffer
+                    if (threadIdx.x == 0) bulk_wait_read();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(rowbar);
+                    if (__any_sync(0xffffffffu, !mbar_wait(rowbar, (k - 4) & 1))) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    if (threadIdx.x == 0) {
+                        const unsigned char* cb = cbufs + ((k - 4) & 1) * G::CBUF;
+                        tma_store_box(&tmapw, cb, x0 + G::HX, 0, m - 2, 0);
+                        tma_store_box3(&tmapwr, cb + G::CDEV, x0 + G::HX, m - 2, 0);
                         bulk_commit();
                     }
                 }
@@ -427,31 +478,10 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
     if constexpr (G::TMA_STORE) {
         if (lane == 0) bulk_wait_all();
     }
-    __syncthreads();
-}
-
-// Periodic ghost columns of every line of f (and of the FP32 density lines in the
-// 16-bit formats): column g in [-hx, 0) and [nx, nx + hx) takes the value of column
-// g mod nx.  One thread per line.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_ghosts(T* __restrict__ f, const __grid_constant__ StepParams<typename Storage<T>::C> p, int ncomp)
-{
-    const long long nl = (long long)ncomp * p.ny * Q;
-    const long long nr = Storage<T>::shifted ? (long long)ncomp * p.ny : 0;
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nl + nr) return;
-    const int hx = p.hx, nx = p.nx;
-    auto fill = [&](auto* row) {
-        for (int g = -hx; g < 0; ++g) row[hx + g] = row[hx + ((g % nx) + nx) % nx];
-        for (int g = nx; g < nx + hx; ++g) row[hx + g] = row[hx + g % nx];
-    };
-    if (l < nl) {
-        fill(f + l * p.pitch);
-    } else {
-        float* r = reinterpret_cast<float*>(reinterpret_cast<char*>(f) + p.rbytes);
-        fill(r + (l - nl) * p.pitch);
+    if constexpr (G::CTA_STORE) {
+        if (threadIdx.x == 0) bulk_wait_all();
     }
+    __syncthreads();
 }
 
 }  // namespace mclb

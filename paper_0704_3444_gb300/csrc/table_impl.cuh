@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "batch.cuh"
+#include "ghosts.cuh"
 #include "march.cuh"
 #include "staged.cuh"
 
@@ -85,7 +86,7 @@ struct Launch {
             return pl;
         pl.W = G::WOUT;
         pl.box_w = G::WI;
-        pl.out_w = G::TMA_STORE ? MARCH_OUT : 0;
+        pl.out_w = G::TMA_STORE ? MARCH_OUT : (G::CTA_STORE ? G::WOUT : 0);
         pl.NS = G::STAGES;
         pl.smem = G::SMEM;
         pl.threads = G::THREADS;
@@ -118,16 +119,18 @@ struct Launch {
 
     static cudaError_t step_fused(const Problem& P, const Scratch& sc, const FusedPlan& pl,
                                   const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in,
-                                  const CUtensorMap* tmapw_out, void* fout, cudaStream_t st)
+                                  const CUtensorMap* tmapw_out, const CUtensorMap* tmapwr_out,
+                                  void* fout, cudaStream_t st)
     {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
         const CUtensorMap& tr = Storage<T>::shifted ? *tmapr_in : *tmap_in;
         const CUtensorMap& tw = pl.out_w > 0 ? *tmapw_out : *tmap_in;
+        const CUtensorMap& twr = (pl.out_w > 0 && Storage<T>::shifted) ? *tmapwr_out : *tmap_in;
         MCLB_DISPATCH_N(P.N, {
-            k_march<T, NN><<<grid, pl.threads, pl.smem, st>>>(*tmap_in, tr, tw, (T*)fout, p, pl.H);
-            const long long lines = (long long)NN * P.ny * (Q + (Storage<T>::shifted ? 1 : 0));
-            k_ghosts<T><<<(unsigned)((lines + 255) / 256), 256, 0, st>>>((T*)fout, p, NN);
+            k_march<T, NN><<<grid, pl.threads, pl.smem, st>>>(*tmap_in, tr, tw, twr, (T*)fout, p, pl.H);
+            const long long ghosts = (long long)NN * P.ny * (Q + (Storage<T>::shifted ? 1 : 0)) * 2 * P.hx;
+            k_ghosts<T><<<(unsigned)((ghosts + 255) / 256), 256, 0, st>>>((T*)fout, p, NN);
             return cudaGetLastError();
         });
     }

@@ -110,6 +110,15 @@ __device__ __forceinline__ void tma_store_box(const CUtensorMap* map, const void
                  "r"(smem_u32(src)), "r"(col), "r"(line), "r"(row), "r"(comp)
                  : "memory");
 }
+// One 3-D TMA box (columns, 1 row, all components) from shared memory to global.
+__device__ __forceinline__ void tma_store_box3(const CUtensorMap* map, const void* src, int col,
+                                               int row, int comp)
+{
+    const uint64_t desc = reinterpret_cast<uint64_t>(map);
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(desc),
+                 "r"(smem_u32(src)), "r"(col), "r"(row), "r"(comp)
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // wait until the bulk stores of this thread have finished reading shared memory
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
