@@ -26,7 +26,7 @@
  *                     are the ones listed in Sec. 3
  *   5. streaming      f(r + v_i, t + 1) = f*(r, t)                     (Eq. ssLB)
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - mu is used per unit mass, mu^s / m^s = d psi / d rho^s, so that
  *     rho^s grad(mu^s/m^s) = n^s grad mu^s (identical for m = 1);
  *   - theta, the Flory-Huggins temperature, is a free parameter;
