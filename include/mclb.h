@@ -211,10 +211,12 @@ int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_o
 
 /* ----------------------------------------------------------------------------
  * Batched simulations: count independent problems (each its own N, grid, chi, tau,
- * ...) advanced together by the staged schedule: per timestep, three launches for
- * each distinct N in the batch cover every instance (each block works on one
- * instance, found through a block-to-instance table), replayed from a CUDA graph in
- * chunks of 32 steps.  precision and stream are taken from params[0]; kernel is
+ * ...) advanced together.  Per timestep, for each distinct N in the batch, one launch
+ * of the single-pass kernel covers every instance with that N (each CTA finds its
+ * instance, column strip and row segment in a table built at the first step) and one
+ * launch refreshes their ghost columns; where that kernel cannot be set up the group
+ * falls back to the staged schedule (three launches).  Steps are replayed from a CUDA
+ * graph in chunks of 32.  precision and stream are taken from params[0]; kernel is
  * ignored.  Instances share no data.  Every instance must be initialised
  * (mclb_batch_init_fields) before the first mclb_batch_step.  Errors as for the
  * single-simulation calls, and EINVAL for an index outside 0..count-1.
@@ -225,7 +227,8 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out);
 int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const double* u);
 /* Enqueue nsteps timesteps of every instance; returns without waiting. */
 int mclb_batch_step(mclb_batch b, long nsteps);
-/* Kernel launches one batched timestep issues (3 per distinct N). */
+/* Kernel launches one batched timestep issues (2 per distinct N, 3 for a group on the
+ * staged schedule). */
 int mclb_batch_launches_per_step(mclb_batch b);
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P);
 int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count);

@@ -1,10 +1,16 @@
-// batch.cuh -- many independent simulations advanced by the staged schedule in one set
-// of launches: each block works on one instance, found through a block-to-instance
-// table, and runs the same per-site code as the single-simulation kernels.
+// batch.cuh -- many independent simulations advanced together.  All instances that share
+// N are advanced by one launch of the single-pass march (kb_march: each CTA looks up its
+// instance, strip and segment in a table and runs march_cta with that instance's
+// parameters and tensor maps) followed by one ghost-column refresh (kb_ghosts).  When an
+// instance cannot use the march (its tensor maps could not be built), the group falls
+// back to the staged schedule over a block-to-instance table (kb_density, kb_potential,
+// kb_collide), which runs the same per-site code as the single-simulation kernels.
 #pragma once
 
+#include <algorithm>
 #include <vector>
 
+#include "march.cuh"
 #include "staged.cuh"
 
 namespace mclb {
@@ -49,20 +55,198 @@ kb_collide(const BatchItem<T>* __restrict__ items, const int* __restrict__ blk2i
     collide_site<T, N>(it.f[parity], it.f[parity ^ 1], it.nu, it.p, site);
 }
 
+// Device-side description of one instance for the batched march: its tensor maps
+// ([buffer][load view, density-line load view, store view, density-line store view]),
+// parameters and buffers.  Tensor maps in global memory must be 64-byte aligned.
+template <typename T>
+struct alignas(64) MarchItem {
+    CUtensorMap maps[2][4];
+    StepParams<typename Storage<T>::C> p;
+    T* f[2];
+};
+
+// One CTA of the batched march: instance, first written column, first row, rows.
+struct MarchCta {
+    int inst, x0, y0, H;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(MarchGeom<T, N>::THREADS) __maxnreg__((MarchGeom<T, N>::MAXREG))
+kb_march(const MarchItem<T>* __restrict__ items, const MarchCta* __restrict__ ctas, int parity)
+{
+    using C = typename Storage<T>::C;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ StepParams<C> ps;
+    const MarchCta c = ctas[blockIdx.x];
+    const MarchItem<T>& it = items[c.inst];
+    static_assert(sizeof(StepParams<C>) % sizeof(int) == 0, "parameter copy by words");
+    const int* src = reinterpret_cast<const int*>(&it.p);
+    int* dst = reinterpret_cast<int*>(&ps);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepParams<C>) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    if (threadIdx.x == 0) {
+        // the tensor maps were written to global memory before the launch; make them
+        // visible to the tensor-map proxy before the first copy uses them
+        for (int b = 0; b < 2; ++b)
+            for (int j = 0; j < 4; ++j)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it.maps[b][j])
+                             : "memory");
+    }
+    __syncthreads();
+    march_cta<T, N>(&it.maps[parity][0], &it.maps[parity][1], &it.maps[parity ^ 1][2],
+                    &it.maps[parity ^ 1][3], it.f[parity ^ 1], ps, c.x0, c.y0, c.H, smem);
+}
+
+// Ghost columns of every instance's new buffer (parity ^ 1); instance k owns threads
+// [start[k], start[k + 1]), laid out as in k_ghosts.
+template <typename T>
+__global__ void __launch_bounds__(256)
+kb_ghosts(const MarchItem<T>* __restrict__ items, const long long* __restrict__ start, int count,
+          int parity, int ncomp)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= start[count]) return;
+    int lo = 0, hi = count - 1;   // last k with start[k] <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const MarchItem<T>& it = items[lo];
+    const auto& p = it.p;
+    const int hx = p.hx, nx = p.nx, per = 2 * hx;
+    const long long nl = (long long)ncomp * p.ny * Q;
+    const long long u = t - start[lo];
+    const long long l = u / per;
+    const int j = (int)(u - l * per);
+    const int gcol = j < hx ? j - hx : nx + (j - hx);
+    const int srcc = ((gcol % nx) + nx) % nx;
+    T* f = it.f[parity ^ 1];
+    if (l < nl) {
+        T* row = f + l * p.pitch + hx;
+        row[gcol] = row[srcc];
+    } else {
+        float* row = reinterpret_cast<float*>(reinterpret_cast<char*>(f) + p.rbytes) + (l - nl) * p.pitch + hx;
+        row[gcol] = row[srcc];
+    }
+}
+
 // One group of instances sharing N.
 template <typename T>
 struct BatchGroup {
     int N = 0;
+    // staged schedule
     int nblocks = 0;
     BatchItem<T>* items = nullptr;
     int* blk2inst = nullptr;
+    // batched march
+    bool march = false;
+    int count = 0;
+    MarchItem<T>* mitems = nullptr;
+    MarchCta* ctas = nullptr;
+    int nctas = 0;
+    long long* gstart = nullptr;
+    long long gthreads = 0;
 };
+
+// Table of the batched march's CTAs: strips of WOUT columns, segments of about the same
+// height everywhere (chosen so that the launch is about six waves deep), tallest first.
+template <typename T, int N>
+std::vector<MarchCta> march_ctas(int count, const Problem* probs, int slots)
+{
+    using G = MarchGeom<T, N>;
+    long long rows = 0;
+    for (int k = 0; k < count; ++k) rows += (long long)((probs[k].nx + G::WOUT - 1) / G::WOUT) * probs[k].ny;
+    const int target = (int)std::max<long long>(16, rows / std::max(1, 6 * slots));
+    std::vector<MarchCta> v;
+    for (int k = 0; k < count; ++k) {
+        const int nx = probs[k].nx, ny = probs[k].ny;
+        const int nsegs = std::max(1, (ny + target / 2) / target);
+        const int H = (ny + nsegs - 1) / nsegs;
+        for (int x0 = 0; x0 < nx; x0 += G::WOUT)
+            for (int y0 = 0; y0 < ny; y0 += H) v.push_back(MarchCta{k, x0, y0, std::min(H, ny - y0)});
+    }
+    std::stable_sort(v.begin(), v.end(), [](const MarchCta& a, const MarchCta& b) { return a.H > b.H; });
+    return v;
+}
+
+template <typename T, int N>
+bool march_group_create(BatchGroup<T>* g, int count, const Problem* probs, const Scratch* scs,
+                        void* const* fa, void* const* fb, const CUtensorMap* maps, int sm_count,
+                        cudaStream_t st)
+{
+    using G = MarchGeom<T, N>;
+    using C = typename Storage<T>::C;
+    if (!G::FITS) return false;
+    const size_t smem = G::SMEM;
+    if (cudaFuncSetAttribute(kb_march<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(kb_march<T, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_march<T, N>, G::THREADS, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    std::vector<MarchItem<T>> items(count);
+    std::vector<long long> gstart(count + 1, 0);
+    for (int k = 0; k < count; ++k) {
+        for (int b = 0; b < 2; ++b)
+            for (int j = 0; j < 4; ++j) items[k].maps[b][j] = maps[(size_t)k * 8 + b * 4 + j];
+        items[k].p = make_params<C>(probs[k], scs[k].status);
+        items[k].f[0] = static_cast<T*>(fa[k]);
+        items[k].f[1] = static_cast<T*>(fb[k]);
+        const long long lines = (long long)N * probs[k].ny * (Q + (Storage<T>::shifted ? 1 : 0));
+        gstart[k + 1] = gstart[k] + lines * 2 * probs[k].hx;
+    }
+    const std::vector<MarchCta> ctas = march_ctas<T, N>(count, probs, per_sm * std::max(1, sm_count));
+    if (ctas.size() > (size_t)INT32_MAX) return false;
+    if (cudaMalloc(&g->mitems, sizeof(MarchItem<T>) * count) != cudaSuccess ||
+        cudaMalloc(&g->ctas, sizeof(MarchCta) * ctas.size()) != cudaSuccess ||
+        cudaMalloc(&g->gstart, sizeof(long long) * (count + 1)) != cudaSuccess ||
+        cudaMemcpyAsync(g->mitems, items.data(), sizeof(MarchItem<T>) * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(g->ctas, ctas.data(), sizeof(MarchCta) * ctas.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(g->gstart, gstart.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    g->march = true;
+    g->count = count;
+    g->nctas = (int)ctas.size();
+    g->gthreads = gstart[count];
+    return true;
+}
+
+template <typename T>
+void batch_group_destroy(void* group);
 
 template <typename T>
 void* batch_group_create(int N, int count, const Problem* probs, const Scratch* scs,
-                         void* const* fa, void* const* fb, cudaStream_t st)
+                         void* const* fa, void* const* fb, const CUtensorMap* maps, int sm_count,
+                         cudaStream_t st)
 {
     using C = typename Storage<T>::C;
+    if (maps) {
+        auto* g = new BatchGroup<T>();
+        g->N = N;
+        bool ok = false;
+        switch (N) {
+            case 1: ok = march_group_create<T, 1>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 2: ok = march_group_create<T, 2>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 3: ok = march_group_create<T, 3>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 4: ok = march_group_create<T, 4>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 5: ok = march_group_create<T, 5>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 6: ok = march_group_create<T, 6>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 7: ok = march_group_create<T, 7>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 8: ok = march_group_create<T, 8>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            default: break;
+        }
+        if (ok) return g;
+        batch_group_destroy<T>(g);
+    }
     std::vector<BatchItem<T>> items(count);
     std::vector<int> map;
     long long blocks = 0;
@@ -99,6 +283,13 @@ void* batch_group_create(int N, int count, const Problem* probs, const Scratch* 
 template <typename T, int N>
 cudaError_t batch_group_step_n(const BatchGroup<T>* g, int parity, cudaStream_t st)
 {
+    if (g->march) {
+        using G = MarchGeom<T, N>;
+        kb_march<T, N><<<g->nctas, G::THREADS, G::SMEM, st>>>(g->mitems, g->ctas, parity);
+        kb_ghosts<T><<<(unsigned)((g->gthreads + 255) / 256), 256, 0, st>>>(g->mitems, g->gstart, g->count,
+                                                                            parity, N);
+        return cudaGetLastError();
+    }
     kb_density<T, N><<<g->nblocks, SITE_THREADS, 0, st>>>(g->items, g->blk2inst, parity);
     kb_potential<T, N><<<g->nblocks, SITE_THREADS, 0, st>>>(g->items, g->blk2inst);
     kb_collide<T, N><<<g->nblocks, SITE_THREADS, 0, st>>>(g->items, g->blk2inst, parity);
@@ -123,12 +314,21 @@ cudaError_t batch_group_step(void* group, int parity, cudaStream_t st)
 }
 
 template <typename T>
+int batch_group_launches(const void* group)
+{
+    return static_cast<const BatchGroup<T>*>(group)->march ? 2 : 3;
+}
+
+template <typename T>
 void batch_group_destroy(void* group)
 {
     auto* g = static_cast<BatchGroup<T>*>(group);
     if (!g) return;
     if (g->items) cudaFree(g->items);
     if (g->blk2inst) cudaFree(g->blk2inst);
+    if (g->mitems) cudaFree(g->mitems);
+    if (g->ctas) cudaFree(g->ctas);
+    if (g->gstart) cudaFree(g->gstart);
     delete g;
 }
 

@@ -685,16 +685,29 @@ int batch_build(mclb_batch b)
         std::vector<Problem> probs;
         std::vector<Scratch> scs;
         std::vector<void*> fa, fb;
+        std::vector<CUtensorMap> maps;
+        bool fused = true;
         for (auto h : b->items)
             if (h->P.N == n) {
                 probs.push_back(h->P);
                 scs.push_back(h->sc);
                 fa.push_back(h->f[0]);
                 fb.push_back(h->f[1]);
+                fused = fused && h->fused;
+                for (int k = 0; k < 2; ++k) {
+                    maps.push_back(h->tmap[k]);
+                    maps.push_back(h->tmapr[k]);
+                    maps.push_back(h->tmapw[k]);
+                    maps.push_back(h->tmapwr[k]);
+                }
             }
         if (probs.empty()) continue;
+        int dev = 0, sms = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            cudaGetLastError();
         void* g = b->tab->batch_create(n, (int)probs.size(), probs.data(), scs.data(), fa.data(),
-                                       fb.data(), b->stream);
+                                       fb.data(), fused ? maps.data() : nullptr, sms, b->stream);
         if (!g) {
             batch_drop(b);
             return fail(MCLB_ENOMEM, "batched launch tables for N=%d could not be built", n);
@@ -765,7 +778,7 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
     for (int k = 0; k < count; ++k) {
         mclb_params p = params[k];
         p.precision = params[0].precision;
-        p.kernel = MCLB_KERNEL_STAGED;
+        p.kernel = MCLB_KERNEL_AUTO;   // builds the tensor maps the batched march uses
         p.stream = b->stream;
         mclb_handle h = nullptr;
         int rc = mclb_create(&p, &h);
@@ -836,7 +849,9 @@ int mclb_batch_launches_per_step(mclb_batch b)
 {
     if (!b || b->magic != MAGIC) return -1;
     if (b->dirty && batch_build(b)) return -1;
-    return 3 * (int)b->groups.size();
+    int n = 0;
+    for (const void* g : b->groups) n += b->tab->batch_launches(g);
+    return n;
 }
 
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P)

@@ -124,23 +124,24 @@ __device__ __forceinline__ void pair_sync(int id)
     asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
 }
 
+// The march of one CTA over the strip starting at column x0 and the segment of H rows
+// starting at row y0 (tmap/tmapr: load views of the input buffer; tmapw/tmapwr: store
+// views of fout; p may live in parameter or shared memory).
 template <typename T, int N>
-__global__ void __launch_bounds__(MarchGeom<T, N>::THREADS) __maxnreg__((MarchGeom<T, N>::MAXREG))
-k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapr,
-        const __grid_constant__ CUtensorMap tmapw, const __grid_constant__ CUtensorMap tmapwr,
-        T* __restrict__ fout, const __grid_constant__ StepParams<typename Storage<T>::C> p,
-        const int H)
+__device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtensorMap* tmapr,
+                                          const CUtensorMap* tmapw, const CUtensorMap* tmapwr,
+                                          T* __restrict__ fout,
+                                          const StepParams<typename Storage<T>::C>& p,
+                                          const int x0, const int y0, const int H,
+                                          unsigned char* smem)
 {
     using G = MarchGeom<T, N>;
     using C = typename Storage<T>::C;
     constexpr int NS = G::STAGES, WI = G::WI, NCW = G::NCW, XW = G::XW;
-    const int x0 = blockIdx.x * G::WOUT;
-    const int y0 = blockIdx.y * H;
     const int Hc = min(H, p.ny - y0);
     const int nk = Hc + 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + MARCH_MAX_NS;
     uint64_t* rowbar = empty + MARCH_MAX_NS;   // compute warps, once per collided row
@@ -185,12 +186,12 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
             if (lane == 0) mbar_arrive_expect_tx(&full[slot], G::TX);
             __syncwarp();
             if (lane < Q) {
-                tma_load_row(st + lane * G::VBYTES, &tmap, &full[slot], x0, grow(m - vy_rt(lane)), lane);
+                tma_load_row(st + lane * G::VBYTES, tmap, &full[slot], x0, grow(m - vy_rt(lane)), lane);
             } else if (G::SHIFTED && lane < Q + 3) {
-                tma_load_rline(st + Q * G::VBYTES + (lane - Q) * G::RBYTES, &tmapr, &full[slot], x0,
+                tma_load_rline(st + Q * G::VBYTES + (lane - Q) * G::RBYTES, tmapr, &full[slot], x0,
                                grow(m - 1 + (lane - Q)));
             } else if (lane >= 16 && lane < 16 + Q && k + MARCH_PF < nk) {
-                tma_prefetch_row(&tmap, x0, grow(m + MARCH_PF - vy_rt(lane - 16)), lane - 16);
+                tma_prefetch_row(tmap, x0, grow(m + MARCH_PF - vy_rt(lane - 16)), lane - 16);
             }
             issued = k + 1;
         }
@@ -417,7 +418,7 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
                     // boxes that start at or past column nx are not issued (the view
                     // clips the others at nx)
                     if (lane == 0 && x0 + MARCH_OUT * cg < p.nx) {
-                        tma_store_box(&tmapw, obuf, x0 + MARCH_OUT * cg + G::HX, 0, m - 2, 0);
+                        tma_store_box(tmapw, obuf, x0 + MARCH_OUT * cg + G::HX, 0, m - 2, 0);
                         bulk_commit();
                     }
                 }
@@ -436,8 +437,8 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
                     }
                     if (threadIdx.x == 0) {
                         const unsigned char* cb = cbufs + ((k - 4) & 1) * G::CBUF;
-                        tma_store_box(&tmapw, cb, x0 + G::HX, 0, m - 2, 0);
-                        tma_store_box3(&tmapwr, cb + G::CDEV, x0 + G::HX, m - 2, 0);
+                        tma_store_box(tmapw, cb, x0 + G::HX, 0, m - 2, 0);
+                        tma_store_box3(tmapwr, cb + G::CDEV, x0 + G::HX, m - 2, 0);
                         bulk_commit();
                     }
                 }
@@ -482,6 +483,18 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
         if (threadIdx.x == 0) bulk_wait_all();
     }
     __syncthreads();
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(MarchGeom<T, N>::THREADS) __maxnreg__((MarchGeom<T, N>::MAXREG))
+k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapr,
+        const __grid_constant__ CUtensorMap tmapw, const __grid_constant__ CUtensorMap tmapwr,
+        T* __restrict__ fout, const __grid_constant__ StepParams<typename Storage<T>::C> p,
+        const int H)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    march_cta<T, N>(&tmap, &tmapr, &tmapw, &tmapwr, fout, p, blockIdx.x * MarchGeom<T, N>::WOUT,
+                    blockIdx.y * H, H, smem);
 }
 
 }  // namespace mclb

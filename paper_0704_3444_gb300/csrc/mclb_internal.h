@@ -101,11 +101,15 @@ struct KernelTable {
                              cudaStream_t st);
     cudaError_t (*set_state)(const Problem&, const Scratch&, const double* in, void* f,
                              cudaStream_t st);
-    // batches: a group of `count` instances with the same N (buffers fa/fb, scratch scs);
-    // one staged step of the whole group reads buffer `parity` and writes the other
+    // batches: a group of `count` instances with the same N (buffers fa/fb, scratch scs,
+    // 8 tensor maps per instance [buffer][load, density load, store, density store] or
+    // NULL); one step of the whole group reads buffer `parity` and writes the other, by
+    // the batched march when the maps are given and it fits, else by the staged schedule
     void* (*batch_create)(int N, int count, const Problem* probs, const Scratch* scs,
-                          void* const* fa, void* const* fb, cudaStream_t st);
+                          void* const* fa, void* const* fb, const CUtensorMap* maps, int sm_count,
+                          cudaStream_t st);
     cudaError_t (*batch_step)(void* group, int parity, cudaStream_t st);
+    int (*batch_launches)(const void* group);   // kernel launches of one group step
     void (*batch_destroy)(void* group);
 };
 

@@ -216,6 +216,7 @@ inline KernelTable make_table(CUtensorMapDataType tt)
     t.set_state = &Launch<T>::set_state;
     t.batch_create = &batch_group_create<T>;
     t.batch_step = &batch_group_step<T>;
+    t.batch_launches = &batch_group_launches<T>;
     t.batch_destroy = &batch_group_destroy<T>;
     return t;
 }

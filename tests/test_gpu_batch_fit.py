@@ -33,7 +33,7 @@ def test_batch_matches_oracle(precision, tol):
     probs = _instances()
     b = mclb.Batch(probs, precision=precision)
     b.init_all()
-    assert b.launches_per_step == 6  # three per distinct N (2 and 3)
+    assert b.launches_per_step == 4  # march + ghost refresh per distinct N (2 and 3)
     b.step(45)
     rc, per = b.status()
     assert rc == 0 and all(v == 0 for v in per)
