@@ -22,7 +22,7 @@
 // everything that row m = y0 - 2 + k pulls, i.e. for each velocity i the line of source
 // row m - v_i,y (all N components, columns [x0 - hx, x0 - hx + WI)).  A producer warp
 // fills each stage with nine TMA box copies (one per velocity, cp.async.bulk.tensor) on
-// one mbarrier, plus an L2 prefetch four rows ahead; the 16-bit formats add the FP32
+// one mbarrier, plus an L2 prefetch one row ahead; the 16-bit formats add the FP32
 // reference-density lines of source rows m - 1, m, m + 1.  A stage is read by the
 // moments of row m and two iterations later by the collision of row m; each compute
 // warp then arrives on the stage's "empty" mbarrier and the producer refills it.  So
@@ -45,7 +45,7 @@ namespace mclb {
 constexpr int MARCH_HDR = 256;   // full, empty and row mbarriers + abort flag
 constexpr int MARCH_MAX_NS = 8;
 constexpr int MARCH_OUT = 28;    // columns written per warp
-constexpr int MARCH_PF = 4;      // L2 prefetch distance in rows
+constexpr int MARCH_PF = 1;      // L2 prefetch distance in rows (2 and more thrash L2)
 #ifndef MARCH_GROUPS
 #define MARCH_GROUPS 1           // component groups per column group (1 or 2)
 #endif
