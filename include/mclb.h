@@ -215,8 +215,10 @@ int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_o
  * of the single-pass kernel covers every instance with that N (each CTA finds its
  * instance, column strip and row segment in a table built at the first step) and one
  * launch refreshes their ghost columns; where that kernel cannot be set up the group
- * falls back to the staged schedule (three launches).  Steps are replayed from a CUDA
- * graph in chunks of 32.  precision and stream are taken from params[0]; kernel is
+ * falls back to the staged schedule (three launches).  The first step after the batch
+ * is (re)built picks each group's partition into row segments by timing a few
+ * candidates on the current state (the state is not changed; the call synchronises).
+ * Steps are replayed from a CUDA graph in chunks of 32.  precision and stream are taken from params[0]; kernel is
  * ignored.  Instances share no data.  Every instance must be initialised
  * (mclb_batch_init_fields) before the first mclb_batch_step.  Errors as for the
  * single-simulation calls, and EINVAL for an index outside 0..count-1.

@@ -138,25 +138,31 @@ struct BatchGroup {
     int nblocks = 0;
     BatchItem<T>* items = nullptr;
     int* blk2inst = nullptr;
-    // batched march
+    // batched march: candidate CTA tables (segment heights for different wave counts),
+    // the one in use picked by timing them at the first step
     bool march = false;
+    bool tuned = false;
     int count = 0;
     MarchItem<T>* mitems = nullptr;
-    MarchCta* ctas = nullptr;
-    int nctas = 0;
+    std::vector<MarchCta*> cand;
+    std::vector<int> cand_n;
+    std::vector<int> cand_waves;
+    int pick = 0;
     long long* gstart = nullptr;
     long long gthreads = 0;
 };
 
+constexpr int MARCH_WAVES[] = {2, 4, 8, 16};
+
 // Table of the batched march's CTAs: strips of WOUT columns, segments of about the same
-// height everywhere (chosen so that the launch is about six waves deep), tallest first.
+// height everywhere (chosen so that the launch is about `waves` waves deep), tallest first.
 template <typename T, int N>
-std::vector<MarchCta> march_ctas(int count, const Problem* probs, int slots)
+std::vector<MarchCta> march_ctas(int count, const Problem* probs, int slots, int waves)
 {
     using G = MarchGeom<T, N>;
     long long rows = 0;
     for (int k = 0; k < count; ++k) rows += (long long)((probs[k].nx + G::WOUT - 1) / G::WOUT) * probs[k].ny;
-    const int target = (int)std::max<long long>(16, rows / std::max(1, 6 * slots));
+    const int target = (int)std::max<long long>(8, rows / std::max(1, waves * slots));
     std::vector<MarchCta> v;
     for (int k = 0; k < count; ++k) {
         const int nx = probs[k].nx, ny = probs[k].ny;
@@ -201,23 +207,71 @@ bool march_group_create(BatchGroup<T>* g, int count, const Problem* probs, const
         const long long lines = (long long)N * probs[k].ny * (Q + (Storage<T>::shifted ? 1 : 0));
         gstart[k + 1] = gstart[k] + lines * 2 * probs[k].hx;
     }
-    const std::vector<MarchCta> ctas = march_ctas<T, N>(count, probs, per_sm * std::max(1, sm_count));
-    if (ctas.size() > (size_t)INT32_MAX) return false;
     if (cudaMalloc(&g->mitems, sizeof(MarchItem<T>) * count) != cudaSuccess ||
-        cudaMalloc(&g->ctas, sizeof(MarchCta) * ctas.size()) != cudaSuccess ||
         cudaMalloc(&g->gstart, sizeof(long long) * (count + 1)) != cudaSuccess ||
         cudaMemcpyAsync(g->mitems, items.data(), sizeof(MarchItem<T>) * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(g->ctas, ctas.data(), sizeof(MarchCta) * ctas.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(g->gstart, gstart.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaMemcpyAsync(g->gstart, gstart.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    for (int waves : MARCH_WAVES) {
+        const std::vector<MarchCta> ctas = march_ctas<T, N>(count, probs, per_sm * std::max(1, sm_count), waves);
+        if (ctas.empty() || ctas.size() > (size_t)INT32_MAX) return false;
+        MarchCta* d = nullptr;
+        if (cudaMalloc(&d, sizeof(MarchCta) * ctas.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        g->cand.push_back(d);
+        g->cand_n.push_back((int)ctas.size());
+        g->cand_waves.push_back(waves);
+        if (cudaMemcpyAsync(d, ctas.data(), sizeof(MarchCta) * ctas.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     g->march = true;
     g->count = count;
-    g->nctas = (int)ctas.size();
+    g->pick = 1;   // six waves' worth until tuned
     g->gthreads = gstart[count];
     return true;
+}
+
+// Time every candidate CTA table on the current state (each run reads buffer `parity`
+// and rewrites the other buffer with the same values, so the state is unchanged) and
+// keep the fastest.  Synchronises the stream.
+template <typename T, int N>
+cudaError_t march_group_tune(BatchGroup<T>* g, int parity, cudaStream_t st)
+{
+    using G = MarchGeom<T, N>;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (size_t c = 0; c < g->cand.size() && err == cudaSuccess; ++c) {
+        kb_march<T, N><<<g->cand_n[c], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[c], parity);
+        err = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) {
+            kb_march<T, N><<<g->cand_n[c], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[c], parity);
+            err = cudaGetLastError();
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && ms < best) {
+            best = ms;
+            g->pick = (int)c;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    g->tuned = true;
+    return err;
 }
 
 template <typename T>
@@ -285,7 +339,7 @@ cudaError_t batch_group_step_n(const BatchGroup<T>* g, int parity, cudaStream_t 
 {
     if (g->march) {
         using G = MarchGeom<T, N>;
-        kb_march<T, N><<<g->nctas, G::THREADS, G::SMEM, st>>>(g->mitems, g->ctas, parity);
+        kb_march<T, N><<<g->cand_n[g->pick], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[g->pick], parity);
         kb_ghosts<T><<<(unsigned)((g->gthreads + 255) / 256), 256, 0, st>>>(g->mitems, g->gstart, g->count,
                                                                             parity, N);
         return cudaGetLastError();
@@ -314,6 +368,32 @@ cudaError_t batch_group_step(void* group, int parity, cudaStream_t st)
 }
 
 template <typename T>
+cudaError_t batch_group_tune(void* group, int parity, cudaStream_t st)
+{
+    auto* g = static_cast<BatchGroup<T>*>(group);
+    if (!g->march || g->tuned) return cudaSuccess;
+    switch (g->N) {
+        case 1: return march_group_tune<T, 1>(g, parity, st);
+        case 2: return march_group_tune<T, 2>(g, parity, st);
+        case 3: return march_group_tune<T, 3>(g, parity, st);
+        case 4: return march_group_tune<T, 4>(g, parity, st);
+        case 5: return march_group_tune<T, 5>(g, parity, st);
+        case 6: return march_group_tune<T, 6>(g, parity, st);
+        case 7: return march_group_tune<T, 7>(g, parity, st);
+        case 8: return march_group_tune<T, 8>(g, parity, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// waves of the CTA table in use (0 for the staged schedule)
+template <typename T>
+int batch_group_waves(const void* group)
+{
+    const auto* g = static_cast<const BatchGroup<T>*>(group);
+    return g->march ? g->cand_waves[g->pick] : 0;
+}
+
+template <typename T>
 int batch_group_launches(const void* group)
 {
     return static_cast<const BatchGroup<T>*>(group)->march ? 2 : 3;
@@ -327,7 +407,7 @@ void batch_group_destroy(void* group)
     if (g->items) cudaFree(g->items);
     if (g->blk2inst) cudaFree(g->blk2inst);
     if (g->mitems) cudaFree(g->mitems);
-    if (g->ctas) cudaFree(g->ctas);
+    for (MarchCta* d : g->cand) cudaFree(d);
     if (g->gstart) cudaFree(g->gstart);
     delete g;
 }

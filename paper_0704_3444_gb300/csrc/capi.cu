@@ -827,6 +827,8 @@ int mclb_batch_step(mclb_batch b, long nsteps)
         if (rc) return rc;
     }
     cudaGetLastError();
+    if (nsteps > 0)
+        for (void* g : b->groups) CK(b->tab->batch_tune(g, b->parity, b->stream));
     long left = nsteps;
     while (left >= GRAPH_STEPS) {
         if (!b->graph_tried[b->parity]) batch_capture(b, b->parity);

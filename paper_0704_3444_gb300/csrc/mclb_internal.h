@@ -110,6 +110,10 @@ struct KernelTable {
                           cudaStream_t st);
     cudaError_t (*batch_step)(void* group, int parity, cudaStream_t st);
     int (*batch_launches)(const void* group);   // kernel launches of one group step
+    // pick the group's work partition by timing the candidates on the current state
+    // (reads buffer `parity`, rewrites the other with the same values; synchronises)
+    cudaError_t (*batch_tune)(void* group, int parity, cudaStream_t st);
+    int (*batch_waves)(const void* group);      // waves of the partition in use, 0 if staged
     void (*batch_destroy)(void* group);
 };
 

@@ -217,6 +217,8 @@ inline KernelTable make_table(CUtensorMapDataType tt)
     t.batch_create = &batch_group_create<T>;
     t.batch_step = &batch_group_step<T>;
     t.batch_launches = &batch_group_launches<T>;
+    t.batch_tune = &batch_group_tune<T>;
+    t.batch_waves = &batch_group_waves<T>;
     t.batch_destroy = &batch_group_destroy<T>;
     return t;
 }

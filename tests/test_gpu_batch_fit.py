@@ -80,3 +80,26 @@ def test_fit_equilibrium_flat_interface():
     lo, hi = thermo.binodal_binary(2.2)
     assert abs(fit[0, 0] - hi) < 0.015 and abs(fit[1, 0] - lo) < 0.015
     np.testing.assert_allclose(fit.sum(1), 1.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("bf16", 2e-4)])
+def test_batch_matches_single_handles(precision, tol):
+    """The batched march runs the single-lattice kernel's per-site arithmetic on another
+    tiling (one common segment height, instances packed into one launch, parameters read
+    from shared memory); after the same steps every instance's densities agree with those
+    of its own handle to the rounding of the storage format (the two kernels are compiled
+    separately, so their FMA contractions may differ in the last bit)."""
+    probs = _instances()
+    b = mclb.Batch(probs, precision=precision)
+    b.init_all()
+    b.step(37)
+    rc, per = b.status()
+    assert rc == 0 and all(v == 0 for v in per)
+    for k, p in enumerate(probs):
+        sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
+        sim.step(37)
+        assert sim.status() == 0
+        a, c = sim.moments(mu=False, P=False)["rho"], b.moments(k)["rho"]
+        assert np.max(np.abs(a - c)) <= tol * np.abs(a).max(), k
+        sim.close()
+    b.close()
