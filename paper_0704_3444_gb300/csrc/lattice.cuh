@@ -66,6 +66,7 @@ struct Storage<__nv_bfloat16> {
         *p = __float2bfloat16_rn(v);
     }
     __device__ __forceinline__ static C round(C v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+    __device__ __forceinline__ static __nv_bfloat16 pack(C v) { return __float2bfloat16_rn(v); }
 };
 
 template <>
@@ -75,6 +76,7 @@ struct Storage<__half> {
     __device__ __forceinline__ static C load(const __half* p) { return __half2float(__ldg(p)); }
     __device__ __forceinline__ static void store(__half* p, C v) { *p = __float2half_rn(v); }
     __device__ __forceinline__ static C round(C v) { return __half2float(__float2half_rn(v)); }
+    __device__ __forceinline__ static __half pack(C v) { return __float2half_rn(v); }
 };
 
 // Kernel parameters in the arithmetic type.  Built on the host from a Problem.

@@ -384,9 +384,9 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                             C dsum = C(0);
 #pragma unroll
                             for (int i = 0; i < Q; ++i) {
-                                const C d = Storage<T>::round(out[i] - wq<C>(i) * M);
-                                dsum += d;
-                                Storage<T>::store(dv + (s * Q + i) * G::WOUT + ocol, d);
+                                const T d = Storage<T>::pack(out[i] - wq<C>(i) * M);
+                                dsum += to_c<T>(d);
+                                dv[(s * Q + i) * G::WOUT + ocol] = d;
                             }
                             rv[s * G::WOUT + ocol] = float(M - dsum);
                         }
