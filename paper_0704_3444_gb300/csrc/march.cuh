@@ -11,12 +11,7 @@
 //   - nu^s of row m - 1 (rho^s of rows m - 2 .. m now known),
 //   - the collision of row m - 2 (nu^s of rows m - 3 .. m - 1 now known).
 // A warp of 32 lanes covers 32 columns: nu is valid on lanes 1..30 and the collision
-// on lanes 2..29, so a column group writes 28 columns and neighbouring groups overlap
-// by 4.  The N components of a column group are split over two warps (components
-// [0, NA) and [NA, N)); per row the pair exchanges rho^s and its share of the momentum
-// through a small shared buffer and one pair barrier, and each warp then evaluates the
-// site terms (rho, ln rho, the Flory-Huggins sums, u) for itself.  The split doubles
-// the warps that share the staged rows, which is what bounds the warps per SM.
+// on lanes 2..29, so a warp writes 28 columns and neighbouring warps overlap by 4.
 //
 // Shared memory holds the pulled distributions: a ring of NS stages, stage k holding
 // everything that row m = y0 - 2 + k pulls, i.e. for each velocity i the line of source
@@ -36,8 +31,6 @@
 // and the step waits for the slowest CTA.)
 #pragma once
 
-#include <type_traits>
-
 #include "tma.cuh"
 
 namespace mclb {
@@ -46,22 +39,16 @@ constexpr int MARCH_HDR = 256;   // full, empty and row mbarriers + abort flag
 constexpr int MARCH_MAX_NS = 8;
 constexpr int MARCH_OUT = 28;    // columns written per warp
 constexpr int MARCH_PF = 1;      // L2 prefetch distance in rows (2 and more thrash L2)
-#ifndef MARCH_GROUPS
-#define MARCH_GROUPS 1           // component groups per column group (1 or 2)
-#endif
 
 // vy of velocity i from a runtime index (bits 2i..2i+1 hold vy + 1)
 __device__ __forceinline__ int vy_rt(int i) { return (int)((0x2865u >> (2 * i)) & 3u) - 1; }
 
-template <typename T, int N, int NW, int NS, int NGP>
+template <typename T, int N, int NW, int NS>
 struct MarchGeomT {
     using C = typename Storage<T>::C;
     static constexpr bool SHIFTED = Storage<T>::shifted;
     static constexpr int NWC = NW;                                // column groups
-    static constexpr int NG = (N >= 2 && NGP == 2) ? 2 : 1;       // component groups
-    static constexpr int NA = NG == 2 ? (N + 1) / 2 : N;          // components of group 0
-    static constexpr int NB = N - NA;                             // components of group 1
-    static constexpr int NCW = NW * NG;                           // compute warps
+    static constexpr int NCW = NW;                                // compute warps
     static constexpr int STAGES = NS;
     static constexpr int HX = (16 / (int)sizeof(T)) < 4 ? 4 : 16 / (int)sizeof(T);
     static constexpr int WOUT = MARCH_OUT * NW;                   // columns written per CTA
@@ -83,9 +70,7 @@ struct MarchGeomT {
     static constexpr bool CTA_STORE = SHIFTED && (WOUT * sizeof(T)) % 16 == 0;
     static constexpr size_t CDEV = CTA_STORE ? round_up_sz((size_t)N * Q * WOUT * sizeof(T), 128) : 0;
     static constexpr size_t CBUF = CTA_STORE ? CDEV + round_up_sz((size_t)N * WOUT * sizeof(float), 128) : 0;
-    static constexpr int XW = N + 4;                              // rho^s, (jx, jy) per group
-    static constexpr size_t XBYTES = NG == 2 ? (size_t)2 * NW * XW * 32 * sizeof(C) : 0;
-    static constexpr size_t SMEM = MARCH_HDR + NS * STAGE_BYTES + XBYTES + NCW * OBYTES + 2 * CBUF;
+    static constexpr size_t SMEM = MARCH_HDR + NS * STAGE_BYTES + NCW * OBYTES + 2 * CBUF;
     static constexpr bool FITS = SMEM <= 227 * 1024 && WI <= 256;
     static constexpr int MIN_CTAS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
     // registers per thread that let MIN_CTAS CTAs share the register file: each of the 4
@@ -98,31 +83,24 @@ struct MarchGeomT {
 // Strip width and ring depth per storage type and N: the first of (4 column groups,
 // 5 stages), (4, 4), (2, 5), (2, 4) that lets two CTAs share an SM, else the first that
 // fits one CTA.
-template <typename T, int N, int NGP = MARCH_GROUPS>
+template <typename T, int N>
 struct MarchPick {
-    using A = MarchGeomT<T, N, 4, 5, NGP>;
-    using B = MarchGeomT<T, N, 4, 4, NGP>;
-    using D = MarchGeomT<T, N, 2, 5, NGP>;
-    using E = MarchGeomT<T, N, 2, 4, NGP>;
+    using A = MarchGeomT<T, N, 4, 5>;
+    using B = MarchGeomT<T, N, 4, 4>;
+    using D = MarchGeomT<T, N, 2, 5>;
+    using E = MarchGeomT<T, N, 2, 4>;
     static constexpr bool A2 = A::FITS && A::MIN_CTAS == 2;
     static constexpr bool B2 = B::FITS && B::MIN_CTAS == 2;
     static constexpr bool D2 = D::FITS && D::MIN_CTAS == 2;
     static constexpr bool E2 = E::FITS && E::MIN_CTAS == 2;
     static constexpr int NW = A2 ? 4 : B2 ? 4 : D2 ? 2 : E2 ? 2 : A::FITS ? 4 : B::FITS ? 4 : D::FITS ? 2 : 2;
     static constexpr int NS = A2 ? 5 : B2 ? 4 : D2 ? 5 : E2 ? 4 : A::FITS ? 5 : B::FITS ? 4 : D::FITS ? 5 : 4;
-    using G = MarchGeomT<T, N, NW, NS, NGP>;
+    using G = MarchGeomT<T, N, NW, NS>;
 };
 
 template <typename T, int N>
 using MarchGeom = typename MarchPick<T, N>::G;
 
-template <int V>
-using IC = std::integral_constant<int, V>;
-
-__device__ __forceinline__ void pair_sync(int id)
-{
-    asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
-}
 
 // The march of one CTA over the strip starting at column x0 and the segment of H rows
 // starting at row y0 (tmap/tmapr: load views of the input buffer; tmapw/tmapwr: store
@@ -137,7 +115,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
 {
     using G = MarchGeom<T, N>;
     using C = typename Storage<T>::C;
-    constexpr int NS = G::STAGES, WI = G::WI, NCW = G::NCW, XW = G::XW;
+    constexpr int NS = G::STAGES, WI = G::WI, NCW = G::NCW;
     const int Hc = min(H, p.ny - y0);
     const int nk = Hc + 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -147,8 +125,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     uint64_t* rowbar = empty + MARCH_MAX_NS;   // compute warps, once per collided row
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 24 * MARCH_MAX_NS);
     unsigned char* stages = smem + MARCH_HDR;
-    C* xbuf = reinterpret_cast<C*>(stages + NS * G::STAGE_BYTES);
-    unsigned char* obufs = stages + NS * G::STAGE_BYTES + G::XBYTES;
+    unsigned char* obufs = stages + NS * G::STAGE_BYTES;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -205,8 +182,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     }
 
     // ---- compute warps: column group cg, component group g
-    const int cg = G::NG == 2 ? (warp >> 1) : warp;
-    const int g = G::NG == 2 ? (warp & 1) : 0;
+    const int cg = warp;   // column group
     const int X = x0 - 2 + MARCH_OUT * cg + lane;         // this lane's column
     const int col = G::HX - 2 + MARCH_OUT * cg + lane;    // its staged column
     const bool out_lane = lane >= 2 && lane < 30 && X < p.nx;
@@ -229,7 +205,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     const C theta = p.theta, kappa6 = C(6) * p.kappa;
     const C c9 = C(1.0 / 9.0), c36 = C(1.0 / 36.0), c59 = C(5.0 / 9.0);
 
-    // The march over rows for components [S0, S0 + NC).  State carried from row to row
+    // The march over rows.  State carried from row to row
     // (m = lead row of the iteration about to start), per component:
     //   Q1 = L(m-1) - 6 kappa (B(m-2) + Cc(m-1)),  Q0 = -6 kappa B(m-1)   (partial nu)
     //   GX = D(m-2)/9 + D(m-3)/36,  Dp = D(m-2),  T2 = T(m-3),  T1 = T(m-2)
@@ -239,8 +215,8 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     // D = nu(x+1) - nu(x-1), T = nu/9 + (nu(x+1) + nu(x-1))/36, so that the force gradient
     // 3 sum_i w_i v_i nu(x + v_i) at row r is 3 (D(r)/9 + (D(r-1) + D(r+1))/36,
     // T(r+1) - T(r-1)).
-    auto march = [&](auto s0c, auto ncc) {
-        constexpr int S0 = decltype(s0c)::value, NC = decltype(ncc)::value;
+    auto march = [&]() {
+        constexpr int S0 = 0, NC = N;   // the components this warp carries
         C Q1[NC], Q0[NC], GX[NC], Dp[NC], T2[NC], T1[NC];
         C R2[NC], X2[NC], Y2[NC], R1[NC], X1[NC], Y1[NC];
         C ux2 = C(0), uy2 = C(0), ux1 = C(0), uy1 = C(0);
@@ -256,13 +232,11 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             const unsigned char* st = stages + (size_t)slot * G::STAGE_BYTES;
             const bool ok = mbar_wait(&full[slot], (k / NS) & 1);
             if (__any_sync(0xffffffffu, !ok)) {
-                // the partner warp may wait at the pair barrier: release it
                 *abort_flag = 1;
-                if (G::NG == 2) pair_sync(1 + cg);
                 break;
             }
 
-            // ---- moments of row m (own components), exchanged with the partner warp
+            // ---- moments of row m
             C R0[NC], X0[NC], Y0[NC];
             C jxp = C(0), jyp = C(0);
 #pragma unroll
@@ -277,26 +251,8 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                 jxp += X0[c];
                 jyp += Y0[c];
             }
-            [[maybe_unused]] C* xw = xbuf + ((k & 1) * G::NWC + cg) * XW * 32 + lane;
-            C Ra[N];
-            C jx, jy;
-            if constexpr (G::NG == 2) {
-#pragma unroll
-                for (int c = 0; c < NC; ++c) xw[(S0 + c) * 32] = R0[c];
-                xw[(N + 2 * g) * 32] = jxp;
-                xw[(N + 2 * g + 1) * 32] = jyp;
-                pair_sync(1 + cg);
-                if (*abort_flag) break;
-#pragma unroll
-                for (int t = 0; t < N; ++t) Ra[t] = xw[t * 32];
-                jx = xw[N * 32] + xw[(N + 2) * 32];
-                jy = xw[(N + 1) * 32] + xw[(N + 3) * 32];
-            } else {
-#pragma unroll
-                for (int t = 0; t < N; ++t) Ra[t] = R0[t];
-                jx = jxp;
-                jy = jyp;
-            }
+            const C (&Ra)[N] = R0;
+            const C jx = jxp, jy = jyp;
 
             // ---- site terms of row m (every component's density)
             C rho = C(0);
@@ -304,7 +260,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             for (int t = 0; t < N; ++t) rho += Ra[t];
             const C inv = C(1) / rho;
             const C ux0 = jx * inv, uy0 = jy * inv;
-            if (g == 0 && out_lane && m >= y0 && m < y0 + Hc && (!(rho > C(0)) || !isfinite(rho)))
+            if (out_lane && m >= y0 && m < y0 + Hc && (!(rho > C(0)) || !isfinite(rho)))
                 atomicOr(p.status, STATUS_NONFINITE);
             const C lnr = dev_log(rho);
             C acc[N];
@@ -468,14 +424,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
         }
     };
 
-    if constexpr (G::NG == 2) {
-        if (g == 0)
-            march(IC<0>{}, IC<G::NA>{});
-        else
-            march(IC<G::NA>{}, IC<G::NB>{});
-    } else {
-        march(IC<0>{}, IC<N>{});
-    }
+    march();
     if constexpr (G::TMA_STORE) {
         if (lane == 0) bulk_wait_all();
     }

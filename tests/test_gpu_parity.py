@@ -206,3 +206,36 @@ def test_full_size_single_step_fp32(name, make):
     g = sim.get_state()
     err = np.max(np.abs(g - orc.f)) / np.abs(orc.f).max()
     assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("name,make", [
+    ("n5_2048x2048", lambda: inputs.multi_uniform(steps=1)),
+    ("slab_8192x2048", lambda: inputs.slab(steps=1)),
+])
+def test_full_size_single_step_bf16(name, make):
+    """BF16-shifted storage at the full sizes, in the launch configuration the benchmark
+    times: 10 steps on the GPU, then one more on both sides from the GPU's own state.
+    The post-collision mass of every site and component (the stored populations taken
+    back to the site that wrote them) is the oracle's to FP32 rounding, because the
+    reference density makes each site's stored mass exact; every population is within
+    two BF16 roundings of the largest deviation from w_i rho^s."""
+    p = make()
+    sim = mclb.Simulation.from_problem(p, precision="bf16", kernel=mclb.KERNEL_FUSED)
+    sim.step(10)
+    f0 = sim.get_state()
+    orc = Oracle(p.ncomp, p.nx, p.ny, p.tau, p.chi, p.m, p.theta, p.kappa, p.force)
+    orc.set_state(f0)
+    del f0
+    orc.run(1)
+    sim.step(1)
+    assert sim.status() == 0
+    g = sim.get_state()
+    o = orc.f
+    vx = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    vy = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    mass_g = sum(np.roll(g[:, i], (-vy[i], -vx[i]), axis=(1, 2)) for i in range(9))
+    mass_o = sum(np.roll(o[:, i], (-vy[i], -vx[i]), axis=(1, 2)) for i in range(9))
+    assert np.max(np.abs(mass_g - mass_o)) < 2e-6 * np.abs(mass_o).max()
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[None, :, None, None]
+    dev = np.abs(o - w * o.sum(axis=1, keepdims=True)).max()
+    assert np.max(np.abs(g - o)) < 2.0 ** -7 * dev + 2e-6 * np.abs(o).max()
