@@ -171,6 +171,18 @@ def time_steps(torch, sim, steps, warmup, stream):
     return start.elapsed_time(stop) / 1e3
 
 
+def job_rate(torch, dist, work, elapsed, world, device):
+    """Whole-job rate over all ranks: every rank has done `work` site-component updates in
+    `elapsed` seconds of its own; the job took as long as the slowest rank (barrier, then
+    the maximum over ranks).  Returns (MLUPS x N of the whole job, that maximum)."""
+    if dist is not None:
+        dist.barrier()
+        t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return world * work / elapsed / 1e6, elapsed
+
+
 def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=50):
     """512 independent binary/ternary FP32 simulations of uneven size advanced together
     (one batch handle, graph-replayed launches) against the same instances advanced one
@@ -334,16 +346,11 @@ def main():
         stop.record(stream)
         torch.cuda.synchronize()
     elapsed = start.elapsed_time(stop) / 1e3
-    if dist:
-        dist.barrier()
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    value, elapsed = job_rate(torch, dist, S * N * args.steps, elapsed, world, "cuda")
     status = sim.status()
     if status != 0:
         raise SystemExit(f"device status {status} after the timed steps")
     clocks = clk.summary()
-    value = world * S * N * args.steps / elapsed / 1e6
     per_launch = elapsed / args.steps
     peak, peak_src = hbm_peak()
     achieved = bytes_step / per_launch / 1e9
