@@ -103,3 +103,47 @@ def test_batch_matches_single_handles(precision, tol):
         assert np.max(np.abs(a - c)) <= tol * np.abs(a).max(), k
         sim.close()
     b.close()
+
+
+@pytest.fixture(scope="module")
+def ternary_flat():
+    """The paper's ternary chi set (chi_AB = 3, chi_AC = 0.5, chi_BC = 0.2, 1/tau = 0.9,
+    Sec. 4) started as two slabs at the ends of the Flory-Huggins tie line through
+    (0.4, 0.4, 0.2), run by the oracle to stationarity; returns the problem and the
+    oracle's plateau compositions (means over 16 columns in the middle of each slab)."""
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    q1, q2 = thermo.tie_line(chi, np.ones(3), [0.4, 0.4, 0.2])
+    hi, lo = (q1, q2) if q1[0] > q2[0] else (q2, q1)
+    nx, ny = 128, 4
+    x = np.arange(nx)
+    inside = (x >= nx // 4) & (x < 3 * nx // 4)
+    phi = np.where(inside[None, :], np.asarray(hi)[:, None], np.asarray(lo)[:, None])
+    rho = np.repeat(phi[:, None, :], ny, axis=1)
+    p = inputs.Problem(name="ternary_slabs", ncomp=3, nx=nx, ny=ny, tau=1 / 0.9, chi=chi,
+                       m=np.ones(3), theta=1 / 3, kappa=0.0, force=(0.0, 0.0), rho=rho,
+                       u=np.zeros((2, ny, nx)))
+    o = Oracle.from_problem(p)
+    o.run(20000)
+    m = o.moments()
+    ph = m["rho"] / m["rho"].sum(0)
+    a = ph[:, :, nx // 2 - 8:nx // 2 + 8].mean(axis=(1, 2))
+    b = np.concatenate([ph[:, :, :8], ph[:, :, -8:]], axis=2).mean(axis=(1, 2))
+    return p, a, b, hi, lo
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp16"])
+def test_fit_equilibrium_ternary_slabs(precision, ternary_flat):
+    """Two coexisting ternary phases (Sec. 4): after 20000 steps the fitted bulk
+    compositions equal the oracle's plateaus to 1e-3 in every storage format, and lie
+    within 0.05 of the Flory-Huggins tie line they started from."""
+    p, a, b, hi, lo = ternary_flat
+    sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
+    sim.step(20000)
+    assert sim.status() == 0
+    fit = sim.fit_equilibrium(2)        # phase 0 seeded at the site richest in component 0
+    assert np.max(np.abs(fit[0] - a)) < 1e-3, (fit, a)
+    assert np.max(np.abs(fit[1] - b)) < 1e-3, (fit, b)
+    assert np.max(np.abs(fit[0] - hi)) < 0.05 and np.max(np.abs(fit[1] - lo)) < 0.05
