@@ -330,13 +330,13 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                     } else if constexpr (G::CTA_STORE) {
                         if (lane >= 2 && lane < 30) {
                             // deviations from w_i M, rounded to storage, and the compensated
-                            // reference density R = M - sum_i d_i (the rule of store_site)
+                            // reference density R = M - sum_i d_i.  M is the site's
+                            // pre-collision mass rho^s, which the collision conserves: the
+                            // stored site mass is then rho^s to FP32 rounding.
                             unsigned char* cb = cbufs + ((k - 4) & 1) * G::CBUF;
                             T* dv = reinterpret_cast<T*>(cb);
                             float* rv = reinterpret_cast<float*>(cb + G::CDEV);
-                            C M = C(0);
-#pragma unroll
-                            for (int i = 0; i < Q; ++i) M += out[i];
+                            const C M = R2[c];
                             C dsum = C(0);
 #pragma unroll
                             for (int i = 0; i < Q; ++i) {
@@ -350,9 +350,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                         T* line = fout + line_off(p, s, r, 0) + G::HX;
                         [[maybe_unused]] C rref = C(0);
                         if constexpr (G::SHIFTED) {
-                            C M = C(0);
-#pragma unroll
-                            for (int i = 0; i < Q; ++i) M += out[i];
+                            const C M = R2[c];   // pre-collision mass, conserved by the collision
                             C dsum = C(0);
 #pragma unroll
                             for (int i = 0; i < Q; ++i) {
