@@ -167,6 +167,14 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count);
 /* Timesteps taken since the last init / set_state. */
 long mclb_step_count(mclb_handle h);
 
+/* Test hook for the failure path of the single-pass kernel (no counterpart in the
+ * paper): while on != 0, its steps issue no copies, so every CTA's first bounded wait
+ * runs out (after about 2 s), the CTA returns, and mclb_status then reports
+ * MCLB_ETIMEOUT.  The distributions are left unspecified: initialise again after
+ * switching it off.  Steps are not replayed from CUDA graphs while it is on.  No effect
+ * on the staged schedule.  Errors: EHANDLE. */
+int mclb_test_withhold_copies(mclb_handle h, int on);
+
 /* HBM bytes one timestep must move at least: every stored value read once and
  * written once, 2 * N * ny * nx * (9 * storage size) in FP64 and FP32 and
  * 2 * N * ny * nx * (9 * 2 + 4) in the shifted modes. */

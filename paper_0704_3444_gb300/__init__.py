@@ -72,6 +72,7 @@ def load():
             "mclb_init_fields": ([H, dp, dp], ctypes.c_int),
             "mclb_init_fields_device": ([H, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
             "mclb_step": ([H, ctypes.c_long], ctypes.c_int),
+            "mclb_test_withhold_copies": ([H, ctypes.c_int], ctypes.c_int),
             "mclb_status": ([H], ctypes.c_int),
             "mclb_moments": ([H, dp, dp, dp, dp], ctypes.c_int),
             "mclb_moments_device": ([H] + [ctypes.c_void_p] * 4, ctypes.c_int),
@@ -236,6 +237,10 @@ class Simulation:
     @property
     def step_count(self) -> int:
         return self.lib.mclb_step_count(self.h)
+
+    def test_withhold_copies(self, on: bool):
+        """Test hook (mclb_test_withhold_copies): single-pass steps issue no copies."""
+        _check(self.lib.mclb_test_withhold_copies(self.h, int(bool(on))), "mclb_test_withhold_copies")
 
     @property
     def bytes_per_step(self) -> float:

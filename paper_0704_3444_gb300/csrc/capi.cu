@@ -461,7 +461,7 @@ int mclb_step(mclb_handle h, long nsteps)
     }
     cudaGetLastError();
     long left = nsteps;
-    while (left >= GRAPH_STEPS) {
+    while (left >= GRAPH_STEPS && !h->P.withhold) {
         if (!h->graph_tried[h->cur]) try_capture(h, h->cur);
         if (!h->graph[h->cur]) break;
         CK(cudaGraphLaunch(h->graph[h->cur], h->stream));
@@ -487,6 +487,14 @@ int mclb_status(mclb_handle h)
 }
 
 long mclb_step_count(mclb_handle h) { return check_handle(h) ? -1 : h->steps; }
+
+int mclb_test_withhold_copies(mclb_handle h, int on)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    h->P.withhold = on ? 1 : 0;
+    return MCLB_OK;
+}
 
 double mclb_bytes_per_step(mclb_handle h)
 {

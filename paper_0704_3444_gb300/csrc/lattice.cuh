@@ -100,6 +100,7 @@ struct StepParams {
     C inv_m[NMAX];        // 1/m^s
     C m[NMAX];
     unsigned int log_mask; // bit s set when logc[s] != 0
+    int withhold;          // test hook: the single-pass kernel issues no copies
     unsigned int* status;
 };
 
@@ -132,6 +133,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
         p.inv_m[a] = C(1.0 / P.m[a]);
         p.m[a] = C(P.m[a]);
     }
+    p.withhold = P.withhold;
     p.status = status;
     return p;
 }

@@ -147,7 +147,9 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             return r + (r < 0 ? p.ny : 0);
         };
         int issued = 0;
-        for (int k = 0; k < nk; ++k) {
+        // (test hook: with p.withhold no copy is issued, so that every compute warp's first
+        // bounded wait runs out and the CTA takes the timeout path)
+        for (int k = 0; k < (p.withhold ? 0 : nk); ++k) {
             const int slot = k % NS;
             if (k >= NS) {
                 bool ok = true;

@@ -34,6 +34,7 @@ struct Problem {
     double tau, theta, kappa, gx, gy;
     double chi[NMAX * NMAX];
     double m[NMAX];
+    int withhold;           // test hook: the single-pass kernel issues no copies
     long long rbytes;       // 16-bit formats: byte offset of the FP32 density lines
                             // ([s][y][pitch], same ghosts) after the deviations; else 0
 };
