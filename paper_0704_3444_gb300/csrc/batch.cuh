@@ -96,26 +96,21 @@ kb_march(const MarchItem<T>* __restrict__ items, const MarchCta* __restrict__ ct
                     &it.maps[parity ^ 1][3], it.f[parity ^ 1], ps, c.x0, c.y0, c.H, smem);
 }
 
-// Ghost columns of every instance's new buffer (parity ^ 1); instance k owns threads
-// [start[k], start[k + 1]), laid out as in k_ghosts.
+// Ghost columns of every instance's new buffer (parity ^ 1), laid out per instance as in
+// k_ghosts: instance k owns ghost values [0, start[k + 1] - start[k]), handled by the
+// blocks [first[k], first[k + 1]) of 256 threads; blk2inst gives each block's instance.
 template <typename T>
 __global__ void __launch_bounds__(256)
-kb_ghosts(const MarchItem<T>* __restrict__ items, const long long* __restrict__ start, int count,
-          int parity, int ncomp)
+kb_ghosts(const MarchItem<T>* __restrict__ items, const long long* __restrict__ start,
+          const int* __restrict__ first, const int* __restrict__ blk2inst, int parity, int ncomp)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= start[count]) return;
-    int lo = 0, hi = count - 1;   // last k with start[k] <= t
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (start[mid] <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    const MarchItem<T>& it = items[lo];
+    const int k = blk2inst[blockIdx.x];
+    const long long u = (long long)(blockIdx.x - first[k]) * blockDim.x + threadIdx.x;
+    if (u >= start[k + 1] - start[k]) return;
+    const MarchItem<T>& it = items[k];
     const auto& p = it.p;
     const int hx = p.hx, nx = p.nx, per = 2 * hx;
     const long long nl = (long long)ncomp * p.ny * Q;
-    const long long u = t - start[lo];
     const long long l = u / per;
     const int j = (int)(u - l * per);
     const int gcol = j < hx ? j - hx : nx + (j - hx);
@@ -149,7 +144,9 @@ struct BatchGroup {
     std::vector<int> cand_waves;
     int pick = 0;
     long long* gstart = nullptr;
-    long long gthreads = 0;
+    int* gfirst = nullptr;      // first ghost block of each instance
+    int* gblk2inst = nullptr;   // instance of each ghost block
+    int gblocks = 0;
 };
 
 constexpr int MARCH_WAVES[] = {2, 4, 8, 16};
@@ -198,6 +195,7 @@ bool march_group_create(BatchGroup<T>* g, int count, const Problem* probs, const
     }
     std::vector<MarchItem<T>> items(count);
     std::vector<long long> gstart(count + 1, 0);
+    std::vector<int> gfirst(count + 1, 0), gmap;
     for (int k = 0; k < count; ++k) {
         for (int b = 0; b < 2; ++b)
             for (int j = 0; j < 4; ++j) items[k].maps[b][j] = maps[(size_t)k * 8 + b * 4 + j];
@@ -206,9 +204,18 @@ bool march_group_create(BatchGroup<T>* g, int count, const Problem* probs, const
         items[k].f[1] = static_cast<T*>(fb[k]);
         const long long lines = (long long)N * probs[k].ny * (Q + (Storage<T>::shifted ? 1 : 0));
         gstart[k + 1] = gstart[k] + lines * 2 * probs[k].hx;
+        const long long nb = (gstart[k + 1] - gstart[k] + 255) / 256;
+        if ((long long)gmap.size() + nb > INT32_MAX) return false;
+        gfirst[k] = (int)gmap.size();
+        gmap.insert(gmap.end(), (size_t)nb, k);
     }
+    gfirst[count] = (int)gmap.size();
     if (cudaMalloc(&g->mitems, sizeof(MarchItem<T>) * count) != cudaSuccess ||
         cudaMalloc(&g->gstart, sizeof(long long) * (count + 1)) != cudaSuccess ||
+        cudaMalloc(&g->gfirst, sizeof(int) * (count + 1)) != cudaSuccess ||
+        cudaMalloc(&g->gblk2inst, sizeof(int) * gmap.size()) != cudaSuccess ||
+        cudaMemcpyAsync(g->gfirst, gfirst.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(g->gblk2inst, gmap.data(), sizeof(int) * gmap.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(g->mitems, items.data(), sizeof(MarchItem<T>) * count, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(g->gstart, gstart.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, st) != cudaSuccess) {
         cudaGetLastError();
@@ -237,7 +244,7 @@ bool march_group_create(BatchGroup<T>* g, int count, const Problem* probs, const
     g->march = true;
     g->count = count;
     g->pick = 1;   // six waves' worth until tuned
-    g->gthreads = gstart[count];
+    g->gblocks = (int)gmap.size();
     return true;
 }
 
@@ -340,8 +347,7 @@ cudaError_t batch_group_step_n(const BatchGroup<T>* g, int parity, cudaStream_t 
     if (g->march) {
         using G = MarchGeom<T, N>;
         kb_march<T, N><<<g->cand_n[g->pick], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[g->pick], parity);
-        kb_ghosts<T><<<(unsigned)((g->gthreads + 255) / 256), 256, 0, st>>>(g->mitems, g->gstart, g->count,
-                                                                            parity, N);
+        kb_ghosts<T><<<g->gblocks, 256, 0, st>>>(g->mitems, g->gstart, g->gfirst, g->gblk2inst, parity, N);
         return cudaGetLastError();
     }
     kb_density<T, N><<<g->nblocks, SITE_THREADS, 0, st>>>(g->items, g->blk2inst, parity);
@@ -409,6 +415,8 @@ void batch_group_destroy(void* group)
     if (g->mitems) cudaFree(g->mitems);
     for (MarchCta* d : g->cand) cudaFree(d);
     if (g->gstart) cudaFree(g->gstart);
+    if (g->gfirst) cudaFree(g->gfirst);
+    if (g->gblk2inst) cudaFree(g->gblk2inst);
     delete g;
 }
 

@@ -199,8 +199,9 @@ int make_tmap(mclb_handle h, int b)
     const Problem& P = h->P;
     const size_t sz = h->tab->storage_bytes;
     // 4-D view (x, velocity, row, component); one box = one velocity line of one row,
-    // all components, box_w columns
-    cuuint64_t dims[4] = {(cuuint64_t)P.pitch, (cuuint64_t)Q, (cuuint64_t)P.ny, (cuuint64_t)P.N};
+    // all components, box_w columns.  The view ends after the right ghost columns, so the
+    // part of a box beyond them (line padding) is filled with zeros, not read from memory.
+    cuuint64_t dims[4] = {(cuuint64_t)(P.nx + 2 * P.hx), (cuuint64_t)Q, (cuuint64_t)P.ny, (cuuint64_t)P.N};
     cuuint64_t strides[3] = {(cuuint64_t)(P.pitch * sz), (cuuint64_t)(Q * P.pitch * sz),
                              (cuuint64_t)(P.plane * sz)};
     cuuint32_t box[4] = {(cuuint32_t)h->plan.box_w, 1u, 1u, (cuuint32_t)P.N};
@@ -234,7 +235,7 @@ int make_tmap(mclb_handle h, int b)
     }
     if (h->tab->shifted) {
         // 3-D view (x, row, component) of the FP32 density lines; same columns per box
-        cuuint64_t rdims[3] = {(cuuint64_t)P.pitch, (cuuint64_t)P.ny, (cuuint64_t)P.N};
+        cuuint64_t rdims[3] = {(cuuint64_t)(P.nx + 2 * P.hx), (cuuint64_t)P.ny, (cuuint64_t)P.N};
         cuuint64_t rstrides[2] = {(cuuint64_t)(P.pitch * sizeof(float)),
                                   (cuuint64_t)(P.ny * P.pitch * sizeof(float))};
         cuuint32_t rbox[3] = {(cuuint32_t)h->plan.box_w, 1u, (cuuint32_t)P.N};
