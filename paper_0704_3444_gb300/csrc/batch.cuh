@@ -341,15 +341,20 @@ void* batch_group_create(int N, int count, const Problem* probs, const Scratch* 
     return g;
 }
 
+// Part 0 of a group step: the batched march (or the whole staged step); part 1: the
+// ghost-column refresh of the buffer part 0 wrote (nothing for the staged schedule).
 template <typename T, int N>
-cudaError_t batch_group_step_n(const BatchGroup<T>* g, int parity, cudaStream_t st)
+cudaError_t batch_group_step_n(const BatchGroup<T>* g, int parity, cudaStream_t st, int part)
 {
     if (g->march) {
         using G = MarchGeom<T, N>;
-        kb_march<T, N><<<g->cand_n[g->pick], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[g->pick], parity);
-        kb_ghosts<T><<<g->gblocks, 256, 0, st>>>(g->mitems, g->gstart, g->gfirst, g->gblk2inst, parity, N);
+        if (part == 0)
+            kb_march<T, N><<<g->cand_n[g->pick], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[g->pick], parity);
+        else
+            kb_ghosts<T><<<g->gblocks, 256, 0, st>>>(g->mitems, g->gstart, g->gfirst, g->gblk2inst, parity, N);
         return cudaGetLastError();
     }
+    if (part != 0) return cudaSuccess;
     kb_density<T, N><<<g->nblocks, SITE_THREADS, 0, st>>>(g->items, g->blk2inst, parity);
     kb_potential<T, N><<<g->nblocks, SITE_THREADS, 0, st>>>(g->items, g->blk2inst);
     kb_collide<T, N><<<g->nblocks, SITE_THREADS, 0, st>>>(g->items, g->blk2inst, parity);
@@ -357,18 +362,18 @@ cudaError_t batch_group_step_n(const BatchGroup<T>* g, int parity, cudaStream_t 
 }
 
 template <typename T>
-cudaError_t batch_group_step(void* group, int parity, cudaStream_t st)
+cudaError_t batch_group_step(void* group, int parity, cudaStream_t st, int part)
 {
     const auto* g = static_cast<const BatchGroup<T>*>(group);
     switch (g->N) {
-        case 1: return batch_group_step_n<T, 1>(g, parity, st);
-        case 2: return batch_group_step_n<T, 2>(g, parity, st);
-        case 3: return batch_group_step_n<T, 3>(g, parity, st);
-        case 4: return batch_group_step_n<T, 4>(g, parity, st);
-        case 5: return batch_group_step_n<T, 5>(g, parity, st);
-        case 6: return batch_group_step_n<T, 6>(g, parity, st);
-        case 7: return batch_group_step_n<T, 7>(g, parity, st);
-        case 8: return batch_group_step_n<T, 8>(g, parity, st);
+        case 1: return batch_group_step_n<T, 1>(g, parity, st, part);
+        case 2: return batch_group_step_n<T, 2>(g, parity, st, part);
+        case 3: return batch_group_step_n<T, 3>(g, parity, st, part);
+        case 4: return batch_group_step_n<T, 4>(g, parity, st, part);
+        case 5: return batch_group_step_n<T, 5>(g, parity, st, part);
+        case 6: return batch_group_step_n<T, 6>(g, parity, st, part);
+        case 7: return batch_group_step_n<T, 7>(g, parity, st, part);
+        case 8: return batch_group_step_n<T, 8>(g, parity, st, part);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -672,6 +672,10 @@ struct mclb_batch_s {
     int parity;                       // buffer holding every instance's current state
     cudaGraphExec_t graph[2];
     bool graph_tried[2];
+    // a group's ghost refresh runs on the side stream, overlapping the next group's march;
+    // ev_main[g] = group g's march done, ev_side[g] = its ghost refresh done
+    cudaStream_t side;
+    std::vector<cudaEvent_t> ev_main, ev_side;
 };
 
 namespace {
@@ -680,6 +684,10 @@ void batch_drop(mclb_batch b)
 {
     for (void* g : b->groups) b->tab->batch_destroy(g);
     b->groups.clear();
+    for (cudaEvent_t e : b->ev_main) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_side) cudaEventDestroy(e);
+    b->ev_main.clear();
+    b->ev_side.clear();
     for (int k = 0; k < 2; ++k) {
         if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
         b->graph[k] = nullptr;
@@ -722,16 +730,45 @@ int batch_build(mclb_batch b)
             return fail(MCLB_ENOMEM, "batched launch tables for N=%d could not be built", n);
         }
         b->groups.push_back(g);
+        cudaEvent_t e1 = nullptr, e2 = nullptr;
+        if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) {
+            if (e1) cudaEventDestroy(e1);
+            batch_drop(b);
+            return fail(MCLB_ECUDA, "cudaEventCreate failed");
+        }
+        b->ev_main.push_back(e1);
+        b->ev_side.push_back(e2);
     }
     b->dirty = false;
     return MCLB_OK;
 }
 
-cudaError_t batch_launch(mclb_batch b, int parity)
+// One batched timestep.  Group g's march waits for g's previous ghost refresh (side
+// stream); its own refresh then runs on the side stream while the next group marches.
+// wait_side = false skips the first wait (the first step of a stream capture, whose
+// stream has already joined the side stream: a captured stream may not wait on an event
+// recorded outside the capture).
+cudaError_t batch_launch(mclb_batch b, int parity, bool wait_side = true)
 {
-    for (void* g : b->groups) {
-        const cudaError_t e = b->tab->batch_step(g, parity, b->stream);
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        cudaError_t e = wait_side ? cudaStreamWaitEvent(b->stream, b->ev_side[g], 0) : cudaSuccess;
+        if (e == cudaSuccess) e = b->tab->batch_step(b->groups[g], parity, b->stream, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_main[g], b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->ev_main[g], 0);
+        if (e == cudaSuccess) e = b->tab->batch_step(b->groups[g], parity, b->side, 1);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_side[g], b->side);
         if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The main stream waits for every ghost refresh issued so far.
+cudaError_t batch_join(mclb_batch b)
+{
+    for (cudaEvent_t e : b->ev_side) {
+        const cudaError_t r = cudaStreamWaitEvent(b->stream, e, 0);
+        if (r != cudaSuccess) return r;
     }
     return cudaSuccess;
 }
@@ -740,6 +777,10 @@ void batch_capture(mclb_batch b, int from)
 {
     b->graph_tried[from] = true;
     b->graph[from] = nullptr;
+    if (batch_join(b) != cudaSuccess) {   // outside the capture
+        cudaGetLastError();
+        return;
+    }
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return;
@@ -747,11 +788,16 @@ void batch_capture(mclb_batch b, int from)
     int par = from;
     bool ok = true;
     for (int k = 0; k < GRAPH_STEPS && ok; ++k) {
-        ok = batch_launch(b, par) == cudaSuccess;
+        ok = batch_launch(b, par, k > 0) == cudaSuccess;
         par ^= 1;
     }
+    ok = ok && batch_join(b) == cudaSuccess;   // the side stream rejoins before the capture ends
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    // the events were last recorded inside the capture; record them again outside it so
+    // that later waits outside a capture refer to an ordinary record
+    for (cudaEvent_t ev : b->ev_main) cudaEventRecord(ev, b->stream);
+    for (cudaEvent_t ev : b->ev_side) cudaEventRecord(ev, b->stream);
     if (ok && e == cudaSuccess && g) {
         cudaGraphExec_t ex = nullptr;
         if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) b->graph[from] = ex;
@@ -783,6 +829,11 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
             return fail(MCLB_ECUDA, "cudaStreamCreate failed");
         }
         b->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
+        b->side = nullptr;
+        mclb_batch_destroy(b);
+        return fail(MCLB_ECUDA, "cudaStreamCreate failed");
     }
     for (int k = 0; k < count; ++k) {
         mclb_params p = params[k];
@@ -849,6 +900,7 @@ int mclb_batch_step(mclb_batch b, long nsteps)
         CK(batch_launch(b, b->parity));
         b->parity ^= 1;
     }
+    CK(batch_join(b));   // later work on the batch's stream sees every ghost refresh
     for (auto h : b->items) {
         h->cur = b->parity;
         h->steps += nsteps;
@@ -904,8 +956,10 @@ int mclb_batch_destroy(mclb_batch b)
     if (!b) return MCLB_OK;
     if (b->magic != MAGIC) return fail(MCLB_EHANDLE, "batch destroyed or not a batch");
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->side) cudaStreamSynchronize(b->side);
     batch_drop(b);
     for (auto h : b->items) mclb_destroy(h);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     b->magic = DEAD;
     delete b;

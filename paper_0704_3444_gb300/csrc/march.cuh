@@ -183,15 +183,14 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
         return;
     }
 
-    // ---- compute warps: column group cg, component group g
-    const int cg = warp;   // column group
+    // ---- compute warps: warp cg covers columns x0 - 2 + 28 cg .. x0 + 29 + 28 cg
+    const int cg = warp;
     const int X = x0 - 2 + MARCH_OUT * cg + lane;         // this lane's column
     const int col = G::HX - 2 + MARCH_OUT * cg + lane;    // its staged column
     const bool out_lane = lane >= 2 && lane < 30 && X < p.nx;
     [[maybe_unused]] T* obuf = reinterpret_cast<T*>(obufs + warp * G::OBYTES);
     [[maybe_unused]] unsigned char* cbufs = obufs + G::NCW * G::OBYTES;
     [[maybe_unused]] const int ocol = MARCH_OUT * cg + lane - 2;   // column within the CTA's WOUT
-
 
     // pulled value of velocity i (compile-time) for component s from a stage
     auto pulled = [&](const unsigned char* st, int i, int s) -> C {
@@ -218,12 +217,11 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     // 3 sum_i w_i v_i nu(x + v_i) at row r is 3 (D(r)/9 + (D(r-1) + D(r+1))/36,
     // T(r+1) - T(r-1)).
     auto march = [&]() {
-        constexpr int S0 = 0, NC = N;   // the components this warp carries
-        C Q1[NC], Q0[NC], GX[NC], Dp[NC], T2[NC], T1[NC];
-        C R2[NC], X2[NC], Y2[NC], R1[NC], X1[NC], Y1[NC];
+        C Q1[N], Q0[N], GX[N], Dp[N], T2[N], T1[N];
+        C R2[N], X2[N], Y2[N], R1[N], X1[N], Y1[N];
         C ux2 = C(0), uy2 = C(0), ux1 = C(0), uy1 = C(0);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
+        for (int c = 0; c < N; ++c) {
             Q1[c] = Q0[c] = GX[c] = Dp[c] = T2[c] = T1[c] = C(0);
             R2[c] = X2[c] = Y2[c] = R1[c] = X1[c] = Y1[c] = C(0);
         }
@@ -239,13 +237,13 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             }
 
             // ---- moments of row m
-            C R0[NC], X0[NC], Y0[NC];
+            C R0[N], X0[N], Y0[N];
             C jxp = C(0), jyp = C(0);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
+            for (int c = 0; c < N; ++c) {
                 C v[Q];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) v[i] = pulled(st, i, S0 + c);
+                for (int i = 0; i < Q; ++i) v[i] = pulled(st, i, c);
                 const C a = v[5] - v[7], b = v[6] - v[8];
                 R0[c] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
                 X0[c] = (v[1] - v[3]) + (a - b);
@@ -253,15 +251,13 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                 jxp += X0[c];
                 jyp += Y0[c];
             }
-            const C (&Ra)[N] = R0;
-            const C jx = jxp, jy = jyp;
 
-            // ---- site terms of row m (every component's density)
+            // ---- site terms of row m
             C rho = C(0);
 #pragma unroll
-            for (int t = 0; t < N; ++t) rho += Ra[t];
+            for (int t = 0; t < N; ++t) rho += R0[t];
             const C inv = C(1) / rho;
-            const C ux0 = jx * inv, uy0 = jy * inv;
+            const C ux0 = jxp * inv, uy0 = jyp * inv;
             if (out_lane && m >= y0 && m < y0 + Hc && (!(rho > C(0)) || !isfinite(rho)))
                 atomicOr(p.status, STATUS_NONFINITE);
             const C lnr = dev_log(rho);
@@ -271,18 +267,18 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             for (int t = 0; t < N; ++t) {
                 C a = C(0);
 #pragma unroll
-                for (int u = 0; u < N; ++u) a += p.chi[t * N + u] * Ra[u];
+                for (int u = 0; u < N; ++u) a += p.chi[t * N + u] * R0[u];
                 acc[t] = a;
-                sm += Ra[t] * p.inv_m[t];
-                quad += Ra[t] * a;
+                sm += R0[t] * p.inv_m[t];
+                quad += R0[t] * a;
             }
             const C Gs = -theta * (sm * inv + C(0.5) * quad * inv * inv);
 
-            // ---- nu of row m - 1, partial nu of rows m and m + 1 (own components)
-            C Dn[NC], Tn[NC];
+            // ---- nu of row m - 1, partial nu of rows m and m + 1
+            C Dn[N], Tn[N];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int s = S0 + c;
+            for (int s = 0; s < N; ++s) {
+                const int c = s;
                 C logs = -p.th_m[s] * lnr;
                 if ((p.log_mask >> s) & 1u) {
                     const C fl = p.log_floor * rho;
@@ -313,8 +309,8 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                 C e[Q];
                 eq_weights(ux2, uy2, e);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const int s = S0 + c;
+                for (int c = 0; c < N; ++c) {
+                    const int s = c;
                     C f[Q];
 #pragma unroll
                     for (int i = 0; i < Q; ++i) f[i] = pulled(sc, i, s);
@@ -405,7 +401,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             }
             // ---- advance the carried state by one row
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
+            for (int c = 0; c < N; ++c) {
                 GX[c] = Dn[c] * c9 + Dp[c] * c36;
                 Dp[c] = Dn[c];
                 T2[c] = T1[c];

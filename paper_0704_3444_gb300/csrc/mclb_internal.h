@@ -109,7 +109,9 @@ struct KernelTable {
     void* (*batch_create)(int N, int count, const Problem* probs, const Scratch* scs,
                           void* const* fa, void* const* fb, const CUtensorMap* maps, int sm_count,
                           cudaStream_t st);
-    cudaError_t (*batch_step)(void* group, int parity, cudaStream_t st);
+    // part 0: the batched march (or the whole staged step); part 1: the ghost refresh of
+    // the buffer part 0 wrote (nothing for the staged schedule)
+    cudaError_t (*batch_step)(void* group, int parity, cudaStream_t st, int part);
     int (*batch_launches)(const void* group);   // kernel launches of one group step
     // pick the group's work partition by timing the candidates on the current state
     // (reads buffer `parity`, rewrites the other with the same values; synchronises)
