@@ -155,8 +155,12 @@ struct mclb_handle_s {
     long steps;
     size_t fbytes;                // bytes of one distribution buffer
     unsigned int* status_host;    // pinned mirror of the device status word
-    cudaEvent_t status_event;
+    cudaEvent_t status_event;     // the mirror's copy has landed
     bool status_pending;
+    // the status word is copied on its own stream, after an event that marks the work
+    // queued so far, so that the next step's kernels do not wait behind the copy
+    cudaStream_t status_stream;
+    cudaEvent_t queued;
     cudaGraphExec_t graph[2];     // GRAPH_STEPS steps starting from buffer 0 / 1
     bool graph_tried[2];
     double* dtmp;                 // device FP64 staging for host copies
@@ -286,10 +290,22 @@ void try_capture(mclb_handle h, int from)
 
 int enqueue_status_copy(mclb_handle h)
 {
+    CK(cudaEventRecord(h->queued, h->stream));
+    CK(cudaStreamWaitEvent(h->status_stream, h->queued, 0));
     CK(cudaMemcpyAsync(h->status_host, h->sc.status, sizeof(unsigned int),
-                       cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaEventRecord(h->status_event, h->stream));
+                       cudaMemcpyDeviceToHost, h->status_stream));
+    CK(cudaEventRecord(h->status_event, h->status_stream));
     h->status_pending = true;
+    return MCLB_OK;
+}
+
+// A status copy still in flight lands before the status word is cleared.
+int settle_status(mclb_handle h)
+{
+    if (h->status_pending) {
+        CK(cudaEventSynchronize(h->status_event));
+        h->status_pending = false;
+    }
     return MCLB_OK;
 }
 
@@ -361,8 +377,11 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess)
         return bail(fail(MCLB_ENOMEM, "pinned status word"));
     *h->status_host = 0;
-    if (cudaEventCreateWithFlags(&h->status_event, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&h->status_event, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->queued, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaEventCreate failed"));
+    if (cudaStreamCreateWithFlags(&h->status_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
     h->fused = false;
     if (h->kernel != MCLB_KERNEL_STAGED) {
         h->plan = h->tab->plan_fused(P, sms);
@@ -394,8 +413,11 @@ int mclb_destroy(mclb_handle h)
     if (h->sc.partial) cudaFree(h->sc.partial);
     if (h->sc.status) cudaFree(h->sc.status);
     if (h->dtmp) cudaFree(h->dtmp);
+    if (h->status_stream) cudaStreamSynchronize(h->status_stream);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->status_event) cudaEventDestroy(h->status_event);
+    if (h->queued) cudaEventDestroy(h->queued);
+    if (h->status_stream) cudaStreamDestroy(h->status_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     h->magic = DEAD;
     delete h;
@@ -404,6 +426,8 @@ int mclb_destroy(mclb_handle h)
 
 static int init_common(mclb_handle h, const double* rho_d, const double* u_d)
 {
+    int rc = settle_status(h);
+    if (rc) return rc;
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
     CK(h->tab->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
     h->cur = 0;
@@ -584,6 +608,8 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
     rc = ensure_dtmp(h, want);
     if (rc) return rc;
     CK(cudaMemcpyAsync(h->dtmp, f, sizeof(double) * want, cudaMemcpyHostToDevice, h->stream));
+    rc = settle_status(h);
+    if (rc) return rc;
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
     CK(h->tab->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
     CK(cudaStreamSynchronize(h->stream));
