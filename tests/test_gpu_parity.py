@@ -59,6 +59,12 @@ CASES = [
     (40, 33, 6, 10, 0.9, 0.4, 0.01, None, (0.0, 0.0)),
     (33, 40, 7, 10, 1.0, 1 / 3, 0.02, None, (0.0, 0.0)),
     (64, 20, 8, 10, 1.1, 1 / 3, 0.01, [1, 1, 2, 1, 1, 3, 1, 1], (0.0, 0.0)),
+    # degenerate and ragged shapes: one and two rows (every row its own vertical
+    # neighbour), fewer columns than ghost columns, one column past a 112-column strip
+    (9, 1, 2, 20, 0.9, 1 / 3, 0.01, None, (1e-4, 0.0)),
+    (6, 2, 3, 20, 1.0, 0.4, 0.02, None, (0.0, 1e-4)),
+    (2, 7, 2, 20, 0.8, 1 / 3, 0.01, None, (0.0, 0.0)),
+    (113, 5, 2, 15, 1.0, 1 / 3, 0.01, None, (0.0, 0.0)),
 ]
 
 
