@@ -245,3 +245,29 @@ def test_full_size_single_step_bf16(name, make):
     w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[None, :, None, None]
     dev = np.abs(o - w * o.sum(axis=1, keepdims=True)).max()
     assert np.max(np.abs(g - o)) < 2.0 ** -7 * dev + 2e-6 * np.abs(o).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 2e-3)])
+def test_maximum_size_by_periodic_tiling(precision, tol):
+    """A lattice whose buffers exceed 2^32 elements (12288 x 8192, N = 5: 4.5e9 values and
+    line-plane strides above 4 GB per buffer) holding a field that repeats a 96 x 64 tile:
+    the periodic lattice then evolves as the tile does, so after 5 steps every one of the
+    16384 tiles equals the oracle's run on the tile alone (to the format's tolerance)."""
+    n, tw, th, reps_x, reps_y = 5, 96, 64, 128, 128
+    rho_t, u_t = inputs.random_state(n, tw, th, seed=4242, amp=0.3, umax=0.02)
+    chi = _chi(n, 77)
+    orc = Oracle(n, tw, th, 0.9, chi, None, 1 / 3, 0.01, (0.0, 0.0))
+    orc.init(rho_t, u_t)
+    orc.run(5)
+    want = orc.moments()["rho"]
+    nx, ny = tw * reps_x, th * reps_y
+    sim = mclb.Simulation(n, nx, ny, 0.9, chi, None, 1 / 3, 0.01, (0.0, 0.0), precision,
+                          mclb.KERNEL_FUSED)
+    sim.init_fields(np.tile(rho_t, (1, reps_y, reps_x)), np.tile(u_t, (1, reps_y, reps_x)))
+    sim.step(5)
+    assert sim.status() == 0
+    got = sim.moments(U=False, mu=False, P=False)["rho"]
+    sim.close()
+    tiles = got.reshape(n, reps_y, th, reps_x, tw)
+    err = np.max(np.abs(tiles - want[:, None, :, None, :]))
+    assert err < tol * np.abs(want).max(), err
