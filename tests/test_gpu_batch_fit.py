@@ -147,3 +147,35 @@ def test_fit_equilibrium_ternary_slabs(precision, ternary_flat):
     assert np.max(np.abs(fit[0] - a)) < 1e-3, (fit, a)
     assert np.max(np.abs(fit[1] - b)) < 1e-3, (fit, b)
     assert np.max(np.abs(fit[0] - hi)) < 0.05 and np.max(np.abs(fit[1] - lo)) < 0.05
+
+
+def test_polymer_binary_matches_oracle():
+    """The paper's polymer binary (m = (10, 1), chi = 0.94, kappa = 0, 1/tau = 0.9,
+    Sec. 4), started as two slabs at the Flory-Huggins binodal: the polymer's logarithmic
+    terms (theta/m - 1/3 != 0) run through the floored-log path.  After 20000 steps the
+    FP32 volume-fraction profile equals the oracle's to 1e-3 at every site, and the BF16
+    fit of both phases equals the FP32 one to 1e-3."""
+    chi = np.array([[0.0, 0.94], [0.94, 0.0]])
+    m = np.array([10.0, 1.0])
+    lo, hi = thermo.binodal_binary(0.94, 10.0, 1.0)
+    nx, ny = 128, 4
+    x = np.arange(nx)
+    phi_a = np.where((x >= nx // 4) & (x < 3 * nx // 4), hi, lo)
+    rho = np.stack([np.tile(phi_a, (ny, 1)), np.tile(1 - phi_a, (ny, 1))])
+    p = inputs.Problem(name="polymer_slabs", ncomp=2, nx=nx, ny=ny, tau=1 / 0.9, chi=chi, m=m,
+                       theta=1 / 3, kappa=0.0, force=(0.0, 0.0), rho=rho, u=np.zeros((2, ny, nx)))
+    o = Oracle.from_problem(p)
+    o.run(20000)
+    mo = o.moments()
+    phi_o = mo["rho"][0] / mo["rho"].sum(0)
+    fits = {}
+    for precision in ("fp32", "bf16"):
+        sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
+        sim.step(20000)
+        assert sim.status() == 0
+        if precision == "fp32":
+            g = sim.moments(mu=False, P=False)
+            assert np.max(np.abs(g["rho"][0] / g["rho"].sum(0) - phi_o)) < 1e-3
+        fits[precision] = sim.fit_equilibrium(2)
+        sim.close()
+    assert np.max(np.abs(fits["bf16"] - fits["fp32"])) < 1e-3
