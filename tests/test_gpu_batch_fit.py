@@ -179,3 +179,46 @@ def test_polymer_binary_matches_oracle():
         fits[precision] = sim.fit_equilibrium(2)
         sim.close()
     assert np.max(np.abs(fits["bf16"] - fits["fp32"])) < 1e-3
+
+
+def test_batch_binodal_sweep_matches_oracle():
+    """The paper's monomer binodal experiment (Sec. 4: m = (1, 1), kappa = 0, 1/tau = 0.7
+    and 0.9) as one batch of ten flat interfaces, chi = 2.1 ... 2.5, each started as two
+    slabs at its Flory-Huggins binodal.  After 40000 FP32 steps both plateaus of every
+    instance equal the oracle's to 1e-3; their distance from the binodal grows with chi
+    (the sharp-interface lattice gap, which the oracle shows vanishing as kappa widens the
+    interface)."""
+    nx, ny = 64, 2
+    x = np.arange(nx)
+    inside = (x >= nx // 4) & (x < 3 * nx // 4)
+    probs, binodals = [], []
+    for itau in (0.7, 0.9):
+        for chi_v in (2.1, 2.2, 2.3, 2.4, 2.5):
+            lo, hi = thermo.binodal_binary(chi_v)
+            phi_a = np.where(inside, hi, lo)
+            rho = np.stack([np.tile(phi_a, (ny, 1)), np.tile(1 - phi_a, (ny, 1))])
+            chi = np.array([[0.0, chi_v], [chi_v, 0.0]])
+            probs.append(inputs.Problem(name=f"binodal_{itau}_{chi_v}", ncomp=2, nx=nx, ny=ny,
+                                        tau=1 / itau, chi=chi, m=np.ones(2), theta=1 / 3,
+                                        kappa=0.0, force=(0.0, 0.0), rho=rho,
+                                        u=np.zeros((2, ny, nx))))
+            binodals.append(hi)
+    b = mclb.Batch(probs, precision="fp32")
+    b.init_all()
+    b.step(40000)
+    rc, per = b.status()
+    assert rc == 0 and all(v == 0 for v in per)
+    gaps = []
+    for k, p in enumerate(probs):
+        o = Oracle.from_problem(p)
+        o.run(40000)
+        mo = o.moments()["rho"]
+        want = mo[0] / mo.sum(0)
+        mg = b.moments(k)["rho"]
+        got = mg[0] / mg.sum(0)
+        for c in (nx // 2, 0):
+            assert abs(got[0, c] - want[0, c]) < 1e-3, (p.name, c, got[0, c], want[0, c])
+        gaps.append(got[0, nx // 2] - binodals[k])
+    gaps = np.array(gaps).reshape(2, 5)
+    assert np.all(np.diff(gaps, axis=1) > 0), gaps
+    b.close()
