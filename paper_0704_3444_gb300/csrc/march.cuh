@@ -17,13 +17,14 @@
 // everything that row m = y0 - 2 + k pulls, i.e. for each velocity i the line of source
 // row m - v_i,y (all N components, columns [x0 - hx, x0 - hx + WI)).  A producer warp
 // fills each stage with nine TMA box copies (one per velocity, cp.async.bulk.tensor) on
-// one mbarrier, plus an L2 prefetch one row ahead; the 16-bit formats add the FP32
-// reference-density lines of source rows m - 1, m, m + 1.  A stage is read by the
-// moments of row m and two iterations later by the collision of row m; each compute
-// warp then arrives on the stage's "empty" mbarrier and the producer refills it.  So
-// each stored value is loaded from HBM once per step (plus the strip and segment halos)
-// and no CTA-wide barrier is taken per row.  Every mbarrier wait is bounded; a timeout
-// sets STATUS_TIMEOUT, the copies in flight are drained and the CTA returns.
+// one mbarrier, plus an L2 prefetch one row ahead; in the 16-bit formats it also brings
+// the FP32 reference-density line of row m + 1 into a ring that holds those of the rows
+// the live stages pull from.  A stage is read by the moments of row m and two iterations
+// later by the collision of row m; each compute warp then arrives on the stage's "empty"
+// mbarrier and the producer refills it.  So each stored value is loaded from HBM once per
+// step (plus the strip and segment halos), and only the 16-bit box stores synchronise the
+// compute warps once per row.  Every mbarrier wait is bounded; a timeout sets
+// STATUS_TIMEOUT, the copies in flight are drained and the CTA returns.
 //
 // The kernel writes columns [0, nx) only; k_ghosts (ghosts.cuh) then refreshes the
 // periodic ghost columns.  (Writing the few ghost copies from inside the march, with plain stores next
@@ -56,23 +57,34 @@ struct MarchGeomT {
     static constexpr int WI = (WOUT + 3 + HX + AL - 1) / AL * AL; // staged columns
     static constexpr int THREADS = 32 * NCW + 32;                 // + producer warp
     static constexpr size_t VBYTES = round_up_sz((size_t)N * WI * sizeof(T), 128);
+    static constexpr size_t STAGE_BYTES = Q * VBYTES;
+    static constexpr uint32_t TXV = (uint32_t)(Q * (size_t)N * WI * sizeof(T));
+    // 16-bit formats: the FP32 reference-density line of every source row is loaded once
+    // into a ring of NS + 2 lines (a stage of row m reads rows m - 1 .. m + 1, and the
+    // collision reads them again two iterations later)
+    static constexpr int NR = SHIFTED ? NS + 2 : 0;
     static constexpr size_t RBYTES = SHIFTED ? round_up_sz((size_t)N * WI * sizeof(float), 128) : 0;
-    static constexpr size_t STAGE_BYTES = Q * VBYTES + 3 * RBYTES;
-    static constexpr uint32_t TX =
-        (uint32_t)(Q * (size_t)N * WI * sizeof(T) + (SHIFTED ? 3 * (size_t)N * WI * sizeof(float) : 0));
+    static constexpr uint32_t TXR = SHIFTED ? (uint32_t)((size_t)N * WI * sizeof(float)) : 0u;
     // FP32/FP64: each compute warp stages its 28 output columns of the 9 N lines in shared
     // memory and writes them with one TMA box per row (28 columns are 16-byte multiples)
     static constexpr bool TMA_STORE = !SHIFTED && (MARCH_OUT * sizeof(T)) % 16 == 0;
     static constexpr size_t OBYTES = TMA_STORE ? round_up_sz((size_t)N * Q * MARCH_OUT * sizeof(T), 128) : 0;
-    // 16-bit formats (28 columns are not a 16-byte multiple): the compute warps fill one
-    // double-buffered CTA staging area (deviations and FP32 reference densities of the
-    // WOUT columns) and one thread writes it with two TMA boxes per row
+    // 16-bit formats (28 columns are not a 16-byte multiple): the compute warps fill a CTA
+    // staging area (deviations and FP32 reference densities of the WOUT columns, NB
+    // buffers) and one thread writes it with two TMA boxes per row
     static constexpr bool CTA_STORE = SHIFTED && (WOUT * sizeof(T)) % 16 == 0;
     static constexpr size_t CDEV = CTA_STORE ? round_up_sz((size_t)N * Q * WOUT * sizeof(T), 128) : 0;
     static constexpr size_t CBUF = CTA_STORE ? CDEV + round_up_sz((size_t)N * WOUT * sizeof(float), 128) : 0;
-    static constexpr size_t SMEM = MARCH_HDR + NS * STAGE_BYTES + NCW * OBYTES + 2 * CBUF;
+    static constexpr size_t BASE = MARCH_HDR + NS * STAGE_BYTES + NR * RBYTES + NCW * OBYTES;
+    // one staging buffer instead of two where that alone lets a third CTA share the SM
+    // (the warps then wait, before refilling it, until the previous row's box has been
+    // read out of it)
+    static constexpr int NB = (CTA_STORE && 3 * (BASE + 2 * CBUF + 1024) > 228 * 1024 &&
+                               3 * (BASE + CBUF + 1024) <= 228 * 1024) ? 1 : 2;
+    static constexpr size_t SMEM = BASE + NB * CBUF;
     static constexpr bool FITS = SMEM <= 227 * 1024 && WI <= 256;
-    static constexpr int MIN_CTAS = (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
+    static constexpr int MIN_CTAS = (3 * (SMEM + 1024) <= 228 * 1024) ? 3
+                                    : (2 * (SMEM + 1024) <= 228 * 1024) ? 2 : 1;
     // registers per thread that let MIN_CTAS CTAs share the register file: each of the 4
     // SM sub-partitions holds 16K registers and its share of the warps (multiple of 8)
     static constexpr int WARPS_SP = (MIN_CTAS * (THREADS / 32) + 3) / 4;
@@ -81,20 +93,27 @@ struct MarchGeomT {
 };
 
 // Strip width and ring depth per storage type and N: the first of (4 column groups,
-// 5 stages), (4, 4), (2, 5), (2, 4) that lets two CTAs share an SM, else the first that
-// fits one CTA.
+// 5 stages), (4, 4) that lets three CTAs share an SM (three stages per CTA leave too few
+// bytes in flight), else the first of (4, 5), (4, 4), (2, 5), (2, 4) that lets two CTAs
+// share an SM, else the first that fits one CTA.  A third CTA hides more of the
+// per-row latency: 2048^2 x 5 BF16 64.7k -> 72.1k and 8192 x 2048 x 3 FP32 73.6k ->
+// 81.6k MLUPS x N.
 template <typename T, int N>
 struct MarchPick {
     using A = MarchGeomT<T, N, 4, 5>;
     using B = MarchGeomT<T, N, 4, 4>;
     using D = MarchGeomT<T, N, 2, 5>;
     using E = MarchGeomT<T, N, 2, 4>;
-    static constexpr bool A2 = A::FITS && A::MIN_CTAS == 2;
-    static constexpr bool B2 = B::FITS && B::MIN_CTAS == 2;
-    static constexpr bool D2 = D::FITS && D::MIN_CTAS == 2;
-    static constexpr bool E2 = E::FITS && E::MIN_CTAS == 2;
-    static constexpr int NW = A2 ? 4 : B2 ? 4 : D2 ? 2 : E2 ? 2 : A::FITS ? 4 : B::FITS ? 4 : D::FITS ? 2 : 2;
-    static constexpr int NS = A2 ? 5 : B2 ? 4 : D2 ? 5 : E2 ? 4 : A::FITS ? 5 : B::FITS ? 4 : D::FITS ? 5 : 4;
+    static constexpr bool A3 = A::FITS && A::MIN_CTAS >= 3;
+    static constexpr bool B3 = B::FITS && B::MIN_CTAS >= 3;
+    static constexpr bool A2 = A::FITS && A::MIN_CTAS >= 2;
+    static constexpr bool B2 = B::FITS && B::MIN_CTAS >= 2;
+    static constexpr bool D2 = D::FITS && D::MIN_CTAS >= 2;
+    static constexpr bool E2 = E::FITS && E::MIN_CTAS >= 2;
+    static constexpr int NW = A3 ? 4 : B3 ? 4 : A2 ? 4 : B2 ? 4 : D2 ? 2 : E2 ? 2
+                              : A::FITS ? 4 : B::FITS ? 4 : D::FITS ? 2 : 2;
+    static constexpr int NS = A3 ? 5 : B3 ? 4 : A2 ? 5 : B2 ? 4 : D2 ? 5 : E2 ? 4
+                              : A::FITS ? 5 : B::FITS ? 4 : D::FITS ? 5 : 4;
     using G = MarchGeomT<T, N, NW, NS>;
 };
 
@@ -123,9 +142,12 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + MARCH_MAX_NS;
     uint64_t* rowbar = empty + MARCH_MAX_NS;   // compute warps, once per collided row
+    uint64_t* sfree = rowbar + 1;              // single staging buffer read out (NB = 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + 24 * MARCH_MAX_NS);
     unsigned char* stages = smem + MARCH_HDR;
-    unsigned char* obufs = stages + NS * G::STAGE_BYTES;
+    unsigned char* rring = stages + NS * G::STAGE_BYTES;   // 16-bit formats: R lines
+    unsigned char* obufs = rring + G::NR * G::RBYTES;
+    constexpr int NR1 = G::NR > 0 ? G::NR : 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -133,6 +155,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             mbar_init(&empty[s], NCW);
         }
         mbar_init(rowbar, NCW);
+        mbar_init(sfree, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -162,13 +185,18 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             if (*abort_flag) break;
             const int m = y0 - 2 + k;
             unsigned char* st = stages + (size_t)slot * G::STAGE_BYTES;
-            if (lane == 0) mbar_arrive_expect_tx(&full[slot], G::TX);
+            // the first stage also brings the R lines of rows m - 1 and m; every stage brings
+            // that of row m + 1, into ring slot (k + 2) mod NR (ring index k + j holds row
+            // m - 1 + j)
+            if (lane == 0)
+                mbar_arrive_expect_tx(&full[slot], G::TXV + (k == 0 ? 3u : 1u) * G::TXR);
             __syncwarp();
             if (lane < Q) {
                 tma_load_row(st + lane * G::VBYTES, tmap, &full[slot], x0, grow(m - vy_rt(lane)), lane);
-            } else if (G::SHIFTED && lane < Q + 3) {
-                tma_load_rline(st + Q * G::VBYTES + (lane - Q) * G::RBYTES, tmapr, &full[slot], x0,
-                               grow(m - 1 + (lane - Q)));
+            } else if (G::SHIFTED && lane < Q + 3 && (k == 0 || lane == Q + 2)) {
+                const int j = lane - Q;
+                tma_load_rline(rring + (size_t)((k + j) % NR1) * G::RBYTES, tmapr, &full[slot], x0,
+                               grow(m - 1 + j));
             } else if (lane >= 16 && lane < 16 + Q && k + MARCH_PF < nk) {
                 tma_prefetch_row(tmap, x0, grow(m + MARCH_PF - vy_rt(lane - 16)), lane - 16);
             }
@@ -192,14 +220,21 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     [[maybe_unused]] unsigned char* cbufs = obufs + G::NCW * G::OBYTES;
     [[maybe_unused]] const int ocol = MARCH_OUT * cg + lane - 2;   // column within the CTA's WOUT
 
+    // R lines of rows m - 1, m, m + 1 for the stage of iteration kk (16-bit formats), as
+    // offsets in floats from the ring
+    const float* rbase = reinterpret_cast<const float*>(rring) + col;
+    struct RLines { int o[3]; };
+    auto rlines = [&](int kk) {
+        RLines L;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) L.o[j] = ((kk + j) % NR1) * (int)(G::RBYTES / sizeof(float));
+        return L;
+    };
     // pulled value of velocity i (compile-time) for component s from a stage
-    auto pulled = [&](const unsigned char* st, int i, int s) -> C {
+    auto pulled = [&](const unsigned char* st, const RLines& L, int i, int s) -> C {
         const T* line = reinterpret_cast<const T*>(st + i * G::VBYTES) + s * WI;
         C v = to_c<T>(line[col - vx(i)]);
-        if constexpr (G::SHIFTED) {
-            const float* rl = reinterpret_cast<const float*>(st + Q * G::VBYTES + (1 - vy(i)) * G::RBYTES) + s * WI;
-            v = fma(wq<C>(i), C(rl[col - vx(i)]), v);
-        }
+        if constexpr (G::SHIFTED) v = fma(wq<C>(i), C(rbase[L.o[1 - vy(i)] + s * WI - vx(i)]), v);
         return v;
     };
 
@@ -239,11 +274,12 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             // ---- moments of row m
             C R0[N], X0[N], Y0[N];
             C jxp = C(0), jyp = C(0);
+            [[maybe_unused]] const RLines Lm = rlines(k);
 #pragma unroll
             for (int c = 0; c < N; ++c) {
                 C v[Q];
 #pragma unroll
-                for (int i = 0; i < Q; ++i) v[i] = pulled(st, i, c);
+                for (int i = 0; i < Q; ++i) v[i] = pulled(st, Lm, i, c);
                 const C a = v[5] - v[7], b = v[6] - v[8];
                 R0[c] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
                 X0[c] = (v[1] - v[3]) + (a - b);
@@ -308,18 +344,35 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                 }
                 C e[Q];
                 eq_weights(ux2, uy2, e);
+                [[maybe_unused]] const RLines Lc = rlines(k - 2);
+                if constexpr (G::CTA_STORE && G::NB == 1) {
+                    // the box stored one row earlier has left the staging buffer
+                    if (k >= 5) {
+                        if (threadIdx.x == 0) {
+                            bulk_wait_read();
+                            mbar_arrive(sfree);
+                        }
+                        if (__any_sync(0xffffffffu, !mbar_wait(sfree, (k - 5) & 1))) {
+                            *abort_flag = 1;
+                            break;
+                        }
+                    }
+                }
 #pragma unroll
                 for (int c = 0; c < N; ++c) {
                     const int s = c;
                     C f[Q];
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) f[i] = pulled(sc, i, s);
+                    for (int i = 0; i < Q; ++i) f[i] = pulled(sc, Lc, i, s);
                     const C gx = GX[c] + Dn[c] * c36;
                     const C gy = Tn[c] - T2[c];
                     const C ax = -p.fcoef * (C(3) * gx) + p.gx;
                     const C ay = -p.fcoef * (C(3) * gy) + p.gy;
                     C out[Q];
-                    collide(p, f, e, R2[c], X2[c], Y2[c], ax, ay, out);
+                    // 16-bit box stores: out_i is already the deviation f*_i - w_i M, with M
+                    // the site's pre-collision mass rho^s, which the collision conserves
+                    collide(p, f, e, R2[c], X2[c], Y2[c], ax, ay, out,
+                            G::CTA_STORE ? R2[c] : C(0));
                     if constexpr (G::TMA_STORE) {
                         if (lane >= 2 && lane < 30) {
 #pragma unroll
@@ -327,18 +380,17 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                         }
                     } else if constexpr (G::CTA_STORE) {
                         if (lane >= 2 && lane < 30) {
-                            // deviations from w_i M, rounded to storage, and the compensated
-                            // reference density R = M - sum_i d_i.  M is the site's
-                            // pre-collision mass rho^s, which the collision conserves: the
-                            // stored site mass is then rho^s to FP32 rounding.
-                            unsigned char* cb = cbufs + ((k - 4) & 1) * G::CBUF;
+                            // deviations from w_i M rounded to storage, and the compensated
+                            // reference density R = M - sum_i d_i: the stored site mass is
+                            // then rho^s to FP32 rounding
+                            unsigned char* cb = cbufs + (G::NB == 2 ? ((k - 4) & 1) : 0) * G::CBUF;
                             T* dv = reinterpret_cast<T*>(cb);
                             float* rv = reinterpret_cast<float*>(cb + G::CDEV);
                             const C M = R2[c];
                             C dsum = C(0);
 #pragma unroll
                             for (int i = 0; i < Q; ++i) {
-                                const T d = Storage<T>::pack(out[i] - wq<C>(i) * M);
+                                const T d = Storage<T>::pack(out[i]);
                                 dsum += to_c<T>(d);
                                 dv[(s * Q + i) * G::WOUT + ocol] = d;
                             }
@@ -378,9 +430,9 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             if constexpr (G::CTA_STORE) {
                 if (k >= 4) {
                     fence_async_smem();
-                    // the box issued one row earlier has been read out of the other buffer
-                    // before any warp passes this barrier and refills that buffer
-                    if (threadIdx.x == 0) bulk_wait_read();
+                    // two buffers: the box issued one row earlier has been read out of the
+                    // other buffer before any warp passes this barrier and refills that one
+                    if (G::NB == 2 && threadIdx.x == 0) bulk_wait_read();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(rowbar);
                     if (__any_sync(0xffffffffu, !mbar_wait(rowbar, (k - 4) & 1))) {
@@ -388,7 +440,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                         break;
                     }
                     if (threadIdx.x == 0) {
-                        const unsigned char* cb = cbufs + ((k - 4) & 1) * G::CBUF;
+                        const unsigned char* cb = cbufs + (G::NB == 2 ? ((k - 4) & 1) : 0) * G::CBUF;
                         tma_store_box(tmapw, cb, x0 + G::HX, 0, m - 2, 0);
                         tma_store_box3(tmapwr, cb + G::CDEV, x0 + G::HX, m - 2, 0);
                         bulk_commit();

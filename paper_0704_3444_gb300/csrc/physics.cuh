@@ -162,12 +162,14 @@ __device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
 //   f* = f + (f^e - f)/tau + F,  f^e_i = rho^s e_i,
 //   F_i = w_i [3 rho^s (v_i.a) + 9 (v_i.a)(v_i.j) - 3 a.j]   (Eqs. ff1-ff3, j = rho^s u^s),
 // evaluated as f (1 - 1/tau) + (rho^s/tau) e_i + w_i [(v_i.a)(9 v_i.j + 3 rho^s) - 3 a.j].
+// With a nonzero `shift` M it returns f*_i - w_i M instead (the deviations the 16-bit
+// formats store), the subtraction folded into the forcing bracket.
 template <typename C>
 __device__ __forceinline__ void collide(const StepParams<C>& p, const C (&f)[Q], const C (&e)[Q],
-                                        C r, C jx, C jy, C ax, C ay, C (&out)[Q])
+                                        C r, C jx, C jy, C ax, C ay, C (&out)[Q], C shift = C(0))
 {
     const VDots<C> da(ax, ay), dj(jx, jy);
-    const C m3aj = C(-3) * (ax * jx + ay * jy);
+    const C m3aj = C(-3) * (ax * jx + ay * jy) - shift;
     const C r3 = C(3) * r;
     const C omr = p.omega * r;
     const C keep = C(1) - p.omega;
