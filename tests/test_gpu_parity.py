@@ -88,6 +88,31 @@ def test_fp64_state_parity(case, kernel):
     sim.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("bf16", 2e-3), ("fp16", 2e-3)])
+@pytest.mark.parametrize("n", range(1, 9))
+def test_fused_every_n(n, precision, tol):
+    """The single-pass kernel for every component count in FP32 and the 16-bit formats:
+    each N compiles its own geometry (4- or 2-warp strips, two or three CTAs per SM, one
+    or two box-store staging buffers), so each runs 12 steps on a 130 x 37 grid (two
+    112-column or three 56-column strips, ragged in both directions) with kappa, m != 1,
+    theta != 1/3 and a body force on; densities within tol (relative to their max: FP32
+    rounding, or one 16-bit rounding of the deviations) of the oracle's, and component
+    masses kept to 1e-6."""
+    nx, ny = 130, 37
+    rho, u = inputs.random_state(n, nx, ny, seed=4000 + n, amp=0.3, umax=0.03)
+    m = [1.0 + (k % 3) for k in range(n)]
+    sim, orc = _pair(n, nx, ny, 0.9, _chi(n, 77 + n), m, 0.4, 0.02, (1e-5, -2e-5), precision,
+                     mclb.KERNEL_FUSED, rho, u)
+    m0 = sim.conservation()["mass"]
+    sim.step(12)
+    orc.run(12)
+    assert sim.status() == 0
+    got, want = sim.moments(mu=False, P=False)["rho"], orc.moments()["rho"]
+    assert _rel(got, want) < tol
+    np.testing.assert_allclose(sim.conservation()["mass"], m0, rtol=1e-6)
+    sim.close()
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_binary_64_full_horizon_fp64(kernel):
     """The 64 x 64 binary workload (chi = 2.2, kappa = 0.01, tau = 1), all 1000 steps in FP64."""
