@@ -391,7 +391,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
 #pragma unroll
                             for (int i = 0; i < Q; ++i) {
                                 const T d = Storage<T>::pack(out[i]);
-                                dsum += to_c<T>(d);
+                                dsum = add_wide<T>(dsum, d);
                                 dv[(s * Q + i) * G::WOUT + ocol] = d;
                             }
                             rv[s * G::WOUT + ocol] = float(M - dsum);

@@ -138,6 +138,26 @@ __device__ __forceinline__ float to_c<__nv_bfloat16>(__nv_bfloat16 v) { return _
 template <>
 __device__ __forceinline__ float to_c<__half>(__half v) { return __half2float(v); }
 
+// acc + v for a value in storage precision, the widening folded into the add (PTX mixed
+// precision add, .f32 result from a .bf16/.f16 operand; exact widening, one rounding as
+// to_c(v) + acc)
+template <typename T>
+__device__ __forceinline__ float add_wide(float acc, T v);
+template <>
+__device__ __forceinline__ float add_wide<__nv_bfloat16>(float acc, __nv_bfloat16 v)
+{
+    float r;
+    asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(r) : "h"(__bfloat16_as_ushort(v)), "f"(acc));
+    return r;
+}
+template <>
+__device__ __forceinline__ float add_wide<__half>(float acc, __half v)
+{
+    float r;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(__half_as_ushort(v)), "f"(acc));
+    return r;
+}
+
 __host__ __device__ constexpr size_t round_up_sz(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
 }  // namespace mclb
