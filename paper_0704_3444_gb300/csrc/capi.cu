@@ -385,11 +385,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     h->fused = false;
     if (h->kernel != MCLB_KERNEL_STAGED) {
         h->plan = h->tab->plan_fused(P, sms);
-        if (h->plan.ok) {
-            h->magic = MAGIC;
-            if (make_tmap(h, 0) == MCLB_OK && make_tmap(h, 1) == MCLB_OK) h->fused = true;
-            h->magic = 0;
-        }
+        if (h->plan.ok && make_tmap(h, 0) == MCLB_OK && make_tmap(h, 1) == MCLB_OK) h->fused = true;
         if (!h->fused && h->kernel == MCLB_KERNEL_FUSED)
             return bail(fail(MCLB_EINVAL, "fused kernel unavailable for this problem"));
     }
@@ -403,7 +399,9 @@ int mclb_destroy(mclb_handle h)
 {
     if (!h) return MCLB_OK;
     if (h->magic != MAGIC) return fail(MCLB_EHANDLE, "handle destroyed or not a handle");
+    // queued steps and a status copy still in flight finish before anything is freed
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->status_stream) cudaStreamSynchronize(h->status_stream);
     for (int b = 0; b < 2; ++b) {
         if (h->graph[b]) cudaGraphExecDestroy(h->graph[b]);
         if (h->f[b]) cudaFree(h->f[b]);
@@ -413,7 +411,6 @@ int mclb_destroy(mclb_handle h)
     if (h->sc.partial) cudaFree(h->sc.partial);
     if (h->sc.status) cudaFree(h->sc.status);
     if (h->dtmp) cudaFree(h->dtmp);
-    if (h->status_stream) cudaStreamSynchronize(h->status_stream);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->status_event) cudaEventDestroy(h->status_event);
     if (h->queued) cudaEventDestroy(h->queued);
