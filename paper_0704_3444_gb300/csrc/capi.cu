@@ -4,6 +4,7 @@
 // prec_*.cu units; this file only orchestrates.
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -438,7 +439,21 @@ int mclb_init_fields(mclb_handle h, const double* rho, const double* u)
     if (rc) return rc;
     if (!rho) return fail(MCLB_EINVAL, "rho is NULL");
     const Problem& P = h->P;
-    for (long long c = 0; c < P.S; ++c) {
+    // upload, then check on the device; the state is touched only if every site passes
+    rc = ensure_dtmp(h, (size_t)(P.N + 2) * P.S + 1);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->dtmp, rho, sizeof(double) * P.N * P.S, cudaMemcpyHostToDevice,
+                       h->stream));
+    if (u)
+        CK(cudaMemcpyAsync(h->dtmp + P.N * P.S, u, sizeof(double) * 2 * P.S,
+                           cudaMemcpyHostToDevice, h->stream));
+    unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(h->dtmp + (P.N + 2) * P.S);
+    CK(check_fields(h->dtmp, u ? h->dtmp + P.N * P.S : nullptr, P.N, P.S, d_bad, h->stream));
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (bad != ULLONG_MAX) {   // name the first failing site and what failed there
+        const long long c = (long long)bad;
         double tot = 0.0;
         for (int s = 0; s < P.N; ++s) {
             const double v = rho[s * P.S + c];
@@ -446,16 +461,8 @@ int mclb_init_fields(mclb_handle h, const double* rho, const double* u)
             tot += v;
         }
         if (!(tot > 0.0)) return fail(MCLB_EINVAL, "total density <= 0 at site %lld", c);
-        if (u && (!std::isfinite(u[c]) || !std::isfinite(u[P.S + c])))
-            return fail(MCLB_EINVAL, "u not finite at site %lld", c);
+        return fail(MCLB_EINVAL, "u not finite at site %lld", c);
     }
-    rc = ensure_dtmp(h, (size_t)(P.N + 2) * P.S);
-    if (rc) return rc;
-    CK(cudaMemcpyAsync(h->dtmp, rho, sizeof(double) * P.N * P.S, cudaMemcpyHostToDevice,
-                       h->stream));
-    if (u)
-        CK(cudaMemcpyAsync(h->dtmp + P.N * P.S, u, sizeof(double) * 2 * P.S,
-                           cudaMemcpyHostToDevice, h->stream));
     rc = init_common(h, h->dtmp, u ? h->dtmp + P.N * P.S : nullptr);
     if (rc) return rc;
     CK(cudaStreamSynchronize(h->stream));
@@ -600,11 +607,15 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
     const Problem& P = h->P;
     const size_t want = (size_t)P.N * Q * P.S;
     if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
-    for (size_t k = 0; k < want; ++k)
-        if (!std::isfinite(f[k])) return fail(MCLB_EINVAL, "state not finite");
-    rc = ensure_dtmp(h, want);
+    rc = ensure_dtmp(h, want + 1);
     if (rc) return rc;
     CK(cudaMemcpyAsync(h->dtmp, f, sizeof(double) * want, cudaMemcpyHostToDevice, h->stream));
+    unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(h->dtmp + want);
+    CK(check_finite(h->dtmp, (long long)want, d_bad, h->stream));
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (bad != ULLONG_MAX) return fail(MCLB_EINVAL, "state not finite at value %llu", bad);
     rc = settle_status(h);
     if (rc) return rc;
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));

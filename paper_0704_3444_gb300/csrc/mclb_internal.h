@@ -23,8 +23,9 @@ constexpr int ROW_ALIGN = 128;  // data columns per row are padded to a multiple
 // component is a single 4-D TMA box.  hx ghost columns on each side of a line
 // repeat the periodic neighbours (ghost column g in [-hx, 0) u [nx, nx + hx)
 // holds column g mod nx) and a line is padded to pitch = 2 hx + roundup(nx,
-// ROW_ALIGN) elements.  Every kernel that writes distributions also writes the
-// ghosts, so that the fused kernel moves whole aligned row segments with TMA.
+// ROW_ALIGN) elements.  The ghosts are rewritten after every write of the
+// distributions (by the staged kernels themselves, by k_ghosts after the single-pass
+// kernel), so that the single-pass kernel moves whole aligned row segments with TMA.
 struct Problem {
     int N, nx, ny;
     long long S;            // nx * ny sites
@@ -57,8 +58,6 @@ enum : unsigned int {
 
 constexpr int REDUCE_BLOCKS = 256;    // fixed grid of the FP64 reductions (deterministic)
 
-// Launch shape of the fused kernel: strips of W columns, segments of H rows,
-// NS shared-memory stages of source rows.
 // Launch plan of the single-pass kernel: strips of W written columns (TMA boxes of
 // box_w columns, one velocity line each), segments of H rows, NS stages.
 struct FusedPlan {
@@ -119,6 +118,15 @@ struct KernelTable {
     int (*batch_waves)(const void* group);      // waves of the partition in use, 0 if staged
     void (*batch_destroy)(void* group);
 };
+
+// Device checks of FP64 boundary data (checks.cu).  *first_bad receives the smallest
+// failing site (check_fields: a density not finite, total density not positive, or u,
+// which may be null, not finite) or index (check_finite), and stays ULLONG_MAX when
+// everything passes.  Stream ordered; the caller reads first_bad back.
+cudaError_t check_fields(const double* rho, const double* u, int N, long long S,
+                         unsigned long long* first_bad, cudaStream_t st);
+cudaError_t check_finite(const double* a, long long n, unsigned long long* first_bad,
+                         cudaStream_t st);
 
 const KernelTable& table_fp64();
 const KernelTable& table_fp32();

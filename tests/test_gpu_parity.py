@@ -201,6 +201,41 @@ def test_state_roundtrip(precision):
         assert np.max(np.abs(g - orc.f)) < tol * np.abs(orc.f).max()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_invalid_host_input_rejected(precision):
+    """init_fields and set_state check their host data on the device after the upload:
+    a non-finite density, a non-positive total density, a non-finite velocity or a
+    non-finite population is rejected with EINVAL naming the first failing site or value,
+    and the handle's state is left as it was."""
+    n, nx, ny = 3, 40, 30
+    rho, u = inputs.random_state(n, nx, ny, seed=91, amp=0.2, umax=0.02)
+    sim = mclb.Simulation(n, nx, ny, 0.9, inputs.uniform_chi(n, 1.5), precision=precision)
+    sim.init_fields(rho, u)
+    sim.step(3)
+    before = sim.get_state()
+    cases = []
+    r = rho.copy(); r[1, 7, 11] = np.nan; r[0, 20, 5] = np.inf
+    cases.append((r, u, "rho not finite at site %d" % (7 * nx + 11)))
+    r = rho.copy(); r[:, 12, 30] = -0.1
+    cases.append((r, u, "total density <= 0 at site %d" % (12 * nx + 30)))
+    v = u.copy(); v[1, 25, 2] = np.nan
+    cases.append((rho, v, "u not finite at site %d" % (25 * nx + 2)))
+    for r, v, msg in cases:
+        with pytest.raises(mclb.MclbError) as ei:
+            sim.init_fields(r, v)
+        assert mclb.STATUS[ei.value.code] == "EINVAL" and msg in str(ei.value)
+        assert np.array_equal(sim.get_state(), before)
+    f = before.copy()
+    f[2, 4, 9, 13] = np.nan
+    with pytest.raises(mclb.MclbError) as ei:
+        sim.set_state(f)
+    assert mclb.STATUS[ei.value.code] == "EINVAL"
+    assert "value %d" % np.ravel_multi_index((2, 4, 9, 13), f.shape) in str(ei.value)
+    assert np.array_equal(sim.get_state(), before)
+    assert sim.status() == 0
+    sim.close()
+
+
 def test_nonpositive_density_sets_status():
     """A host-made bad input (negative total density at one site, passed through the
     unvalidated device entry point) is reported as ENONFINITE after the step."""
