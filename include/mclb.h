@@ -108,8 +108,10 @@ int mclb_create(const mclb_params* params, mclb_handle* out);
 /* Set f^s_i(r, 0) to the equilibrium of the given fields (Sec. 3 equilibrium
  * moments with the barycentric u).  rho: N*ny*nx component densities rho^s, each
  * > 0 in total per site; u: 2*ny*nx barycentric velocity or NULL for rest.
- * Host pointers; the copy is synchronous.  Resets the step counter.  Errors:
- * EHANDLE, EINVAL (NULL rho, non-finite value, non-positive total density), ECUDA. */
+ * Host pointers; the copy is synchronous.  The values are checked on the device after
+ * the upload; on EINVAL the message names the first failing site and the state is
+ * left as it was.  Resets the step counter.  Errors: EHANDLE, EINVAL (NULL rho,
+ * non-finite value, non-positive total density), ECUDA. */
 int mclb_init_fields(mclb_handle h, const double* rho, const double* u);
 
 /* As mclb_init_fields, but rho and u are device pointers (same layouts) read in
@@ -159,8 +161,9 @@ int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi);
  * [s][i][y][x] (count must equal N*9*ny*nx).  Host pointers, synchronous.  Getting
  * and setting a state is exact in FP64 and FP32; in the shifted modes setting
  * stores the state as R and 16-bit deviations (see mclb_precision), so a state
- * read back differs by the rounding of the deviations.  Errors: EHANDLE, EINVAL,
- * ECUDA. */
+ * read back differs by the rounding of the deviations.  set_state checks the values
+ * on the device after the upload and leaves the state as it was if one is not finite.
+ * Errors: EHANDLE, EINVAL (count, NULL, a non-finite value), ECUDA. */
 int mclb_get_state(mclb_handle h, double* f, size_t count);
 int mclb_set_state(mclb_handle h, const double* f, size_t count);
 
