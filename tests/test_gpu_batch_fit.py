@@ -222,3 +222,48 @@ def test_batch_binodal_sweep_matches_oracle():
     gaps = np.array(gaps).reshape(2, 5)
     assert np.all(np.diff(gaps, axis=1) > 0), gaps
     b.close()
+
+
+def test_batch_ternary_sweep_matches_oracle():
+    """The paper's ternary monomer sweep (Sec. 4: chi_AB = 3, chi_AC = 0.5, chi_BC = 0.2,
+    1/tau = 0.9): mean compositions on the line from the printed critical point
+    (0.32, 0.32, 0.36) toward (0.5, 0.5, 0), at 0.1, 0.4 and 0.7 of the way, each started
+    as two slabs at the ends of its Flory-Huggins tie line and run as one batch.  After
+    20000 FP32 steps both plateaus of every instance equal the oracle's to 1e-3, and their
+    distance from the tie line grows along the line (the sharp-interface gap)."""
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    nx, ny = 128, 2
+    x = np.arange(nx)
+    inside = (x >= nx // 4) & (x < 3 * nx // 4)
+    pc, end = np.array([0.32, 0.32, 0.36]), np.array([0.5, 0.5, 0.0])
+    probs, ties = [], []
+    for s in (0.1, 0.4, 0.7):
+        q1, q2 = thermo.tie_line(chi, np.ones(3), pc + s * (end - pc))
+        hi, lo = (q1, q2) if q1[0] > q2[0] else (q2, q1)
+        phi = np.where(inside[None, :], np.asarray(hi)[:, None], np.asarray(lo)[:, None])
+        probs.append(inputs.Problem(name=f"ternary_sweep_{s}", ncomp=3, nx=nx, ny=ny, tau=1 / 0.9,
+                                    chi=chi, m=np.ones(3), theta=1 / 3, kappa=0.0,
+                                    force=(0.0, 0.0), rho=np.repeat(phi[:, None, :], ny, axis=1),
+                                    u=np.zeros((2, ny, nx))))
+        ties.append((np.asarray(hi), np.asarray(lo)))
+    b = mclb.Batch(probs, precision="fp32")
+    b.init_all()
+    b.step(20000)
+    rc, per = b.status()
+    assert rc == 0 and all(v == 0 for v in per)
+    gaps = []
+    for k, p in enumerate(probs):
+        o = Oracle.from_problem(p)
+        o.run(20000)
+        mo = o.moments()["rho"]
+        want = mo / mo.sum(0)
+        mg = b.moments(k)["rho"]
+        got = mg / mg.sum(0)
+        for c in (nx // 2, 0):
+            assert np.max(np.abs(got[:, 0, c] - want[:, 0, c])) < 1e-3, (p.name, c)
+        gaps.append(np.max(np.abs(got[:, 0, nx // 2] - ties[k][0])))
+    assert gaps[0] < gaps[1] < gaps[2], gaps
+    b.close()
