@@ -126,6 +126,22 @@ def _tensor_ptr(t) -> Optional[int]:
     return int(t.data_ptr())
 
 
+def _fields(rho, u, ncomp, ny, nx, device=False):
+    """Check the sizes of initial fields (the C call reads N*ny*nx and 2*ny*nx doubles)."""
+    if not device:
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+    for name, a, want in (("rho", rho, ncomp * ny * nx), ("u", u, 2 * ny * nx)):
+        if a is None:
+            continue
+        n = a.numel() if device else a.size
+        if n != want:
+            raise ValueError(f"{name} has {n} values, expected {want} ({name} layout [k][y][x])")
+        if device and (str(a.dtype) != "torch.float64" or not a.is_contiguous() or not a.is_cuda):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    return rho, u
+
+
 def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, force=(0.0, 0.0),
                 precision="fp32", kernel=KERNEL_AUTO, stream=None):
     """Build an mclb_params struct; returns (struct, keep-alive arrays)."""
@@ -185,11 +201,11 @@ class Simulation:
         return (self.ny, self.nx)
 
     def init_fields(self, rho, u=None):
-        rho = np.ascontiguousarray(rho, dtype=np.float64)
-        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        rho, uu = _fields(rho, u, self.ncomp, self.ny, self.nx)
         _check(self.lib.mclb_init_fields(self.h, _dp(rho), _dp(uu)), "mclb_init_fields")
 
     def init_fields_device(self, rho_t, u_t=None):
+        _fields(rho_t, u_t, self.ncomp, self.ny, self.nx, device=True)
         _check(self.lib.mclb_init_fields_device(self.h, _tensor_ptr(rho_t), _tensor_ptr(u_t)),
                "mclb_init_fields_device")
 
@@ -281,8 +297,8 @@ class Batch:
             pass
 
     def init_fields(self, index, rho, u=None):
-        rho = np.ascontiguousarray(rho, dtype=np.float64)
-        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        pr = self.problems[int(index)]
+        rho, uu = _fields(rho, u, pr.ncomp, pr.ny, pr.nx)
         _check(self.lib.mclb_batch_init_fields(self.h, int(index), _dp(rho), _dp(uu)),
                "mclb_batch_init_fields")
 

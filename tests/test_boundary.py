@@ -74,3 +74,16 @@ def test_null_and_foreign_handles(lib):
     h = ctypes.c_void_p()
     assert lib.mclb_create(None, ctypes.byref(h)) == -1
     assert lib.mclb_create(ctypes.byref(_params()[0]), None) == -1
+
+
+def test_binding_checks_field_sizes():
+    """The binding refuses initial fields whose sizes do not match the handle (the C call
+    would read N*ny*nx and 2*ny*nx doubles from the host pointers)."""
+    rho, u = np.full((3, 4, 5), 1 / 3), np.zeros((2, 4, 5))
+    r, v = mclb._fields(rho, u, 3, 4, 5)
+    assert r.flags["C_CONTIGUOUS"] and r.dtype == np.float64 and v.shape == (2, 4, 5)
+    assert mclb._fields(rho, None, 3, 4, 5)[1] is None
+    with pytest.raises(ValueError, match="rho has 60 values, expected 80"):
+        mclb._fields(rho, u, 4, 4, 5)
+    with pytest.raises(ValueError, match="u has 20 values, expected 40"):
+        mclb._fields(rho, np.zeros((1, 4, 5)), 3, 4, 5)
