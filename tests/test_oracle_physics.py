@@ -99,6 +99,49 @@ def test_spinodal_growth_rate():
     assert 3.0 < errs[0] / errs[1] < 5.0
 
 
+@pytest.mark.parametrize("m,phibar", [((1.0, 1.0, 1.0), (0.25, 0.25, 0.5)),
+                                       ((10.0, 1.0, 1.0), (0.1, 0.3, 0.6))])
+def test_ternary_linear_modes(m, phibar):
+    """Eq. woche linearised about a uniform ternary composition (the paper's chi set
+    chi_AB = 3, chi_AC = 0.5, chi_BC = 0.2, 1/tau = 0.9, kappa = 0): a composition mode of
+    wavenumber k along an eigenvector of L H, with the mobility L = diag(phi) - phi phi^T and
+    the Hessian H = theta (diag(1 / (m phi)) + chi) of the mass-specific potentials, changes
+    at the rate -(tau - 1/2) k^2 lambda.  Both modes of each case (for m = (10, 1, 1) at
+    (0.1, 0.3, 0.6) one of them grows), O(k^2) convergence from 32 to 64 sites and a
+    Richardson limit below 1e-3.  A transposed or mis-indexed chi, or a wrong 1/m, moves the
+    eigenvalues."""
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    m, pb = np.asarray(m), np.asarray(phibar)
+    theta, tau = 1 / 3, 1 / 0.9
+    lam, V = np.linalg.eig((np.diag(pb) - np.outer(pb, pb)) @ (theta * (np.diag(1 / (m * pb)) + chi)))
+    lam, V = lam.real, V.real
+    U = np.linalg.inv(V)          # rows: the dual (left) eigenvectors
+    for i in np.argsort(-np.abs(lam))[:2]:
+        errs = []
+        for nx in (32, 64):
+            k = 2 * math.pi / nx
+            x = np.arange(nx)
+            rho = (pb[:, None] + 1e-6 * V[:, i, None] * np.sin(k * x)[None, :])[:, None, :]
+            o = Oracle(3, nx, 1, tau, chi, m=m, theta=theta)
+            o.init(rho, np.zeros((2, 1, nx)))
+
+            def amplitude():
+                r = o.moments()["rho"][:, 0, :]
+                return 2 * np.mean((U[i] @ (r / r.sum(0) - pb[:, None])) * np.sin(k * x))
+
+            o.run(200)
+            a0 = amplitude()
+            pred = -(tau - 0.5) * k * k * lam[i]
+            span = int(2 / abs(pred))
+            o.run(span)
+            errs.append(math.log(abs(amplitude() / a0)) / span / pred - 1.0)
+        assert abs(errs[1]) < 0.03 and 3.5 < errs[0] / errs[1] < 4.5, (lam[i], errs)
+        assert abs((4 * errs[1] - errs[0]) / 3) < 1e-3, (lam[i], errs)
+
+
 def test_flat_interface_binary_coexistence():
     """Binary monomer, chi = 2.2, kappa = 0, 1/tau = 0.9, sinusoid of amplitude 0.1 over
     the lattice (Sec. 4), 64 sites so that one domain forms.  Bulk compositions within
