@@ -142,6 +142,71 @@ def test_ternary_linear_modes(m, phibar):
         assert abs((4 * errs[1] - errs[0]) / 3) < 1e-3, (lam[i], errs)
 
 
+def _uniform_mixture(nx, tau, rho_line=None, uy_line=None):
+    chi = np.array([[0.0, 1.0, 0.5], [1.0, 0.0, 0.3], [0.5, 0.3, 0.0]])
+    phi0 = np.array([0.3, 0.3, 0.4])
+    rho = phi0[:, None, None] * (np.ones(nx) if rho_line is None else rho_line)[None, None, :]
+    u = np.zeros((2, 1, nx))
+    if uy_line is not None:
+        u[1, 0] = uy_line
+    o = Oracle(3, nx, 1, tau, chi)
+    o.init(rho, u)
+    return o
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.2])
+def test_shear_wave_viscosity(tau):
+    """A transverse velocity mode on a uniform ternary mixture (no composition gradient,
+    so no force) decays at nu k^2 with the BGK viscosity nu = (tau - 1/2)/3 of the overall
+    fluid (Sec. 3, the Navier-Stokes equation the summed LB equation recovers).  O(k^2)
+    convergence, Richardson limit below 1e-4."""
+    nu = (tau - 0.5) / 3
+    errs = []
+    for nx in (32, 64):
+        k = 2 * math.pi / nx
+        x = np.arange(nx)
+        o = _uniform_mixture(nx, tau, uy_line=1e-5 * np.sin(k * x))
+
+        def amplitude():
+            return 2 * np.mean(o.moments()["U"][1, 0] * np.sin(k * x))
+
+        o.run(50)
+        a0 = amplitude()
+        span = int(1 / (nu * k * k))
+        o.run(span)
+        errs.append(math.log(amplitude() / a0) / span / (-nu * k * k) - 1.0)
+    assert abs(errs[1]) < 2e-3 and 3.5 < errs[0] / errs[1] < 4.5, errs
+    assert abs((4 * errs[1] - errs[0]) / 3) < 1e-4, errs
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.2])
+def test_sound_speed_of_the_mixture(tau):
+    """A density wave of uniform composition leaves the Flory-Huggins potentials unchanged
+    (they depend on phi only; the bulk pressure sum rho mu - psi is identically zero), but
+    nu^s = mu^s/m^s - (1/3) ln rho^s of Eq. definef then gives the force
+    (1 - 1/(2 tau)) (1/3) grad rho, which cancels that part of the lattice pressure rho/3.
+    The wave therefore travels at c^2 = 1/(6 tau), not 1/3: O(k^2) convergence, Richardson
+    limit below 1e-4.  A dropped or mis-signed (1/3) ln rho^s term gives 1/3 or more."""
+    c2 = 1 / (6 * tau)
+    errs = []
+    for nx in (32, 64):
+        k = 2 * math.pi / nx
+        x = np.arange(nx)
+        o = _uniform_mixture(nx, tau, rho_line=1 + 1e-5 * np.cos(k * x))
+        sig = []
+        for _ in range(int(6 * 2 * math.pi / (k * math.sqrt(c2)))):
+            r = o.moments()["rho"].sum(0)[0]
+            sig.append(2 * np.mean((r - r.mean()) * np.cos(k * x)))
+            o.run(1)
+        sig = np.array(sig)
+        zc = np.where(np.diff(np.sign(sig)) != 0)[0]
+        crossings = zc + sig[zc] / (sig[zc] - sig[zc + 1])   # linear interpolation
+        omega = math.pi / np.mean(np.diff(crossings))
+        errs.append((omega / k) ** 2 / c2 - 1.0)
+    assert abs(errs[1]) < 3e-3 and 3.5 < errs[0] / errs[1] < 4.5, errs
+    assert abs((4 * errs[1] - errs[0]) / 3) < 1e-4, errs
+
+
 def test_flat_interface_binary_coexistence():
     """Binary monomer, chi = 2.2, kappa = 0, 1/tau = 0.9, sinusoid of amplitude 0.1 over
     the lattice (Sec. 4), 64 sites so that one domain forms.  Bulk compositions within
