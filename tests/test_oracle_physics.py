@@ -154,6 +154,30 @@ def _uniform_mixture(nx, tau, rho_line=None, uy_line=None):
     return o
 
 
+def test_body_force_on_a_uniform_mixture():
+    """A uniform ternary mixture at rest under a body acceleration g: the forcing adds
+    rho g of momentum per step (Eqs. ff1-ff3) and nothing else changes, so after t steps
+    the output velocity U = u + a/2 (Eq. scon) is exactly (t + 1/2) g, and the densities
+    stay uniform.  Reporting the bare u instead, or a forcing first moment off by any
+    factor, fails at once."""
+    chi = np.array([[0.0, 1.0, 0.5], [1.0, 0.0, 0.3], [0.5, 0.3, 0.0]])
+    g = np.array([3e-6, -2e-6])
+    nx, ny = 6, 5
+    rho = np.array([0.3, 0.3, 0.4])[:, None, None] * np.ones((3, ny, nx))
+    o = Oracle(3, nx, ny, 0.9, chi, force=tuple(g))
+    o.init(rho, np.zeros((2, ny, nx)))
+    done = 0
+    for t in (1, 7, 40):
+        o.run(t - done)
+        done = t
+        m = o.moments()
+        # rounding of a momentum that is a small difference of O(0.1) populations: about
+        # 1e-17 per step, against the g/2 = 1e-6 that separates U from the bare u
+        for a in range(2):
+            np.testing.assert_allclose(m["U"][a], (t + 0.5) * g[a], rtol=0, atol=1e-15 * (t + 1))
+        np.testing.assert_allclose(m["rho"], rho, rtol=1e-13, atol=0)
+
+
 @pytest.mark.parametrize("tau", [0.8, 1.2])
 def test_shear_wave_viscosity(tau):
     """A transverse velocity mode on a uniform ternary mixture (no composition gradient,
