@@ -154,6 +154,32 @@ def _uniform_mixture(nx, tau, rho_line=None, uy_line=None):
     return o
 
 
+def test_pressure_tensor_of_a_layered_state():
+    """The pressure-tensor diagnostic in closed form for a y-invariant state: with the
+    discrete gradient and Laplacian reducing to central differences, P_xy = 0,
+    P_xx - P_yy = kappa sum_s (d_x rho^s)^2 and, the Flory-Huggins part of the isotropic
+    term vanishing identically (sum rho mu - psi = 0), P_yy = -kappa sum_s (rho^s lap rho^s
+    + (d_x rho^s)^2 / 2), to rounding."""
+    n, nx, ny, kappa = 3, 24, 3, 0.3
+    x = np.arange(nx)
+    base = np.array([0.3, 0.3, 0.4])
+    wave = 0.05 * np.stack([np.sin(2 * np.pi * x / nx), np.cos(4 * np.pi * x / nx),
+                            -np.sin(2 * np.pi * x / nx) - np.cos(4 * np.pi * x / nx)])
+    line = base[:, None] + wave
+    chi = np.array([[0.0, 2.0, 0.5], [2.0, 0.0, 0.3], [0.5, 0.3, 0.0]])
+    o = Oracle(n, nx, ny, 0.9, chi, m=np.array([2.0, 1.0, 1.0]), theta=0.4, kappa=kappa)
+    o.init(np.repeat(line[:, None, :], ny, axis=1), np.zeros((2, ny, nx)))
+    P = o.moments()["P"]
+    dx = 0.5 * (np.roll(line, -1, 1) - np.roll(line, 1, 1))
+    lap = np.roll(line, -1, 1) + np.roll(line, 1, 1) - 2 * line
+    pxx_m_pyy = kappa * (dx ** 2).sum(0)
+    pyy = -kappa * (line * lap + 0.5 * dx ** 2).sum(0)
+    for y in range(ny):
+        np.testing.assert_allclose(P[1, y], 0.0, atol=1e-16)
+        np.testing.assert_allclose(P[0, y] - P[2, y], pxx_m_pyy, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(P[2, y], pyy, rtol=0, atol=1e-14)
+
+
 def test_body_force_on_a_uniform_mixture():
     """A uniform ternary mixture at rest under a body acceleration g: the forcing adds
     rho g of momentum per step (Eqs. ff1-ff3) and nothing else changes, so after t steps
