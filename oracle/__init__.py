@@ -9,9 +9,19 @@ first use into ``oracle/_build``; this module marshals numpy arrays to it.
 ``oracle.thermo`` holds the Flory-Huggins thermodynamics (binodals, critical
 points) the paper compares its simulations against.
 
+Two lattices: D2Q9 (the two-dimensional workloads) and D1Q3, the lattice of the
+paper's own simulations (Sec. 4), each a plain path of its own in the C file.
+Two readings of the velocity in the forcing's second moment (Eq. ff3):
+``forcing_velocity=0`` is the component velocity u^s as printed (the default),
+``forcing_velocity=1`` the barycentric u.
+
 Parity unpinned: none of the lattice-update functions; every stage is pinned
-by tests against moment conditions, closed forms and an independent D1Q3
-transcription.  The paper's printed ternary critical points are not
+by tests against moment conditions, closed forms and independent numpy
+transcriptions.  The floor of the logarithm in Eq. definef is pinned by the
+rho -> lambda rho invariance with the floor binding and by bracketing where it
+binds; the barycentric forcing reading by its transcription and by the one-fluid
+sum of Eq. olso; the D1Q3 path by its moment-solving transcription and by the
+one-row D2Q9 lattice it is the projection of.  The paper's printed ternary critical points are not
 reproduced by the symmetric-chi reading and are reported, not asserted.
 """
 from __future__ import annotations
@@ -38,7 +48,8 @@ class OracleParams(ctypes.Structure):
     _fields_ = [("ncomp", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("tau", ctypes.c_double), ("theta", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
-                ("chi", ctypes.c_double * (NMAX * NMAX)), ("m", ctypes.c_double * NMAX)]
+                ("chi", ctypes.c_double * (NMAX * NMAX)), ("m", ctypes.c_double * NMAX),
+                ("forcing_velocity", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -71,9 +82,12 @@ def _load():
             lib.oracle_mu_bulk.argtypes = [pp, dp, dp]
             lib.oracle_init.argtypes = [pp, dp, dp, dp]
             lib.oracle_run.argtypes = [pp, dp, ctypes.c_long]
-            lib.oracle_fields.argtypes = [pp, dp] + [dp] * 6
             lib.oracle_moments.argtypes = [pp, dp] + [dp] * 4
             lib.oracle_conservation.argtypes = [pp, dp, dp, dp, dp]
+            lib.oracle_d1q3_init.argtypes = [pp, dp, dp, dp]
+            lib.oracle_d1q3_run.argtypes = [pp, dp, ctypes.c_long]
+            lib.oracle_d1q3_moments.argtypes = [pp, dp] + [dp] * 4
+            lib.oracle_d1q3_conservation.argtypes = [pp, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -92,13 +106,20 @@ def nthreads() -> int:
 class Oracle:
     """One oracle simulation: parameters plus the FP64 distribution array.
 
-    ``f`` has shape (N, 9, ny, nx): pre-collision distributions at the current
-    time, D2Q9 velocity order (0,0), (1,0), (0,1), (-1,0), (0,-1), (1,1),
-    (-1,1), (-1,-1), (1,-1).
+    D2Q9: ``f`` has shape (N, 9, ny, nx), pre-collision distributions at the
+    current time, velocity order (0,0), (1,0), (0,1), (-1,0), (0,-1), (1,1),
+    (-1,1), (-1,-1), (1,-1).  D1Q3 (``lattice="d1q3"``, ny must be 1): ``f`` has
+    shape (N, 3, nx), velocity order 0, +1, -1; output fields keep the D2Q9
+    shapes with ny = 1.
     """
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
-                 force=(0.0, 0.0)):
+                 force=(0.0, 0.0), forcing_velocity=0, lattice="d2q9"):
+        if lattice not in ("d2q9", "d1q3"):
+            raise ValueError(f"lattice {lattice!r}")
+        if lattice == "d1q3" and int(ny) != 1:
+            raise ValueError("a D1Q3 lattice has ny = 1")
+        self.lattice = lattice
         self.lib = _load()
         p = OracleParams()
         p.ncomp, p.nx, p.ny = int(ncomp), int(nx), int(ny)
@@ -111,16 +132,23 @@ class Oracle:
         m = np.ones(ncomp) if m is None else np.asarray(m, dtype=np.float64)
         for a in range(ncomp):
             p.m[a] = m[a]
+        p.forcing_velocity = int(forcing_velocity)
         self.p = p
         self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
-        self.f = np.zeros((ncomp, 9, ny, nx))
+        self.f = (np.zeros((ncomp, 3, nx)) if lattice == "d1q3"
+                  else np.zeros((ncomp, 9, ny, nx)))
 
     @classmethod
     def from_problem(cls, prob):
         o = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
-                prob.kappa, prob.force)
+                prob.kappa, prob.force, getattr(prob, "forcing_velocity", 0),
+                getattr(prob, "lattice", "d2q9"))
         o.init(prob.rho, prob.u)
         return o
+
+    @property
+    def _d1(self):
+        return self.lattice == "d1q3"
 
     @property
     def _pp(self):
@@ -129,37 +157,35 @@ class Oracle:
     def init(self, rho, u=None):
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
-        rc = self.lib.oracle_init(self._pp, _ptr(rho), _ptr(uu), _ptr(self.f))
+        if self._d1 and uu is not None:
+            uu = np.ascontiguousarray(uu.reshape(-1)[:self.nx])   # x component only
+        init = self.lib.oracle_d1q3_init if self._d1 else self.lib.oracle_init
+        rc = init(self._pp, _ptr(rho), _ptr(uu), _ptr(self.f))
         if rc:
             raise ValueError(f"oracle_init failed ({rc})")
 
     def set_state(self, f):
-        self.f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(
-            self.ncomp, 9, self.ny, self.nx)).copy()
+        shape = (self.ncomp, 3, self.nx) if self._d1 else (self.ncomp, 9, self.ny, self.nx)
+        self.f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(shape)).copy()
 
     def run(self, nsteps: int) -> int:
-        rc = self.lib.oracle_run(self._pp, _ptr(self.f), int(nsteps))
+        run = self.lib.oracle_d1q3_run if self._d1 else self.lib.oracle_run
+        rc = run(self._pp, _ptr(self.f), int(nsteps))
         if rc < 0:
             raise ValueError(f"oracle_run failed ({rc})")
         return rc
 
-    def fields(self):
-        N, S = self.ncomp, (self.ny, self.nx)
-        rs, nu, ax, ay = (np.zeros((N,) + S) for _ in range(4))
-        ux, uy = np.zeros(S), np.zeros(S)
-        self.lib.oracle_fields(self._pp, _ptr(self.f), _ptr(rs), _ptr(ux), _ptr(uy), _ptr(nu),
-                               _ptr(ax), _ptr(ay))
-        return dict(rho=rs, ux=ux, uy=uy, nu=nu, ax=ax, ay=ay)
-
     def moments(self):
         N, S = self.ncomp, (self.ny, self.nx)
         rho, U, mu, P = np.zeros((N,) + S), np.zeros((2,) + S), np.zeros((N,) + S), np.zeros((3,) + S)
-        self.lib.oracle_moments(self._pp, _ptr(self.f), _ptr(rho), _ptr(U), _ptr(mu), _ptr(P))
+        mom = self.lib.oracle_d1q3_moments if self._d1 else self.lib.oracle_moments
+        mom(self._pp, _ptr(self.f), _ptr(rho), _ptr(U), _ptr(mu), _ptr(P))
         return dict(rho=rho, U=U, mu=mu, P=P)
 
     def conservation(self):
         mass, mom, fs = np.zeros(self.ncomp), np.zeros(2), np.zeros(2)
-        self.lib.oracle_conservation(self._pp, _ptr(self.f), _ptr(mass), _ptr(mom), _ptr(fs))
+        cons = self.lib.oracle_d1q3_conservation if self._d1 else self.lib.oracle_conservation
+        cons(self._pp, _ptr(self.f), _ptr(mass), _ptr(mom), _ptr(fs))
         return dict(mass=mass, mom=mom, force=fs)
 
     # per-site helpers used by the pins

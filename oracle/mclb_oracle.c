@@ -38,7 +38,8 @@
  *     (theta/m^s - 1/3) ln rho^s - (theta/m^s) ln rho, the first term is
  *     dropped when its coefficient is exactly zero and otherwise uses
  *     max(rho^s, 1e-12 rho);
- *   - f^e is built with the bare barycentric u, F with rho^s u^s = j^s;
+ *   - f^e is built with the bare barycentric u, F with rho^s u^s = j^s as
+ *     Eq. ff3 prints it (or, when forcing_velocity = 1, with rho^s u);
  *     the output velocity is U = u + a/2 with rho a = sum_s rho^s a^s;
  *   - initial distributions are the equilibria of the given fields.
  *
@@ -57,11 +58,16 @@
 #define OR_QMAX 9
 #define OR_NMAX 8
 
+/* forcing_velocity selects the velocity in the second moment of the forcing
+ * (Eq. ff3): 0 = the component velocity u^s as printed, rho^s (a^s u^s + u^s a^s);
+ * 1 = the barycentric u, rho^s (a^s u + u a^s), the form whose sum over the
+ * components is the one-fluid forcing moment rho (a u + u a) (Eq. olso). */
 typedef struct {
     int ncomp, nx, ny;
     double tau, theta, kappa, gx, gy;
     double chi[OR_NMAX * OR_NMAX];
     double m[OR_NMAX];
+    int forcing_velocity;
 } oracle_params;
 
 static const int VX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -83,6 +89,7 @@ static int check(const oracle_params* p)
 {
     if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1 || p->ny < 1) return -1;
     if (!(p->tau > 0.5)) return -1;
+    if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
     return 0;
 }
 
@@ -316,9 +323,10 @@ static void stage_collide_stream(const oracle_params* p, const double* f, const 
             for (int s = 0; s < N; ++s) {
                 double fe[9], F[9];
                 double rs = w->rs[s * S + c];
+                double jx = w->jx[s * S + c], jy = w->jy[s * S + c];
+                if (p->forcing_velocity) { jx = rs * w->ux[c]; jy = rs * w->uy[c]; }
                 oracle_equilibrium(rs, w->ux[c], w->uy[c], fe);
-                oracle_forcing(rs, w->jx[s * S + c], w->jy[s * S + c], w->ax[s * S + c],
-                               w->ay[s * S + c], F);
+                oracle_forcing(rs, jx, jy, w->ax[s * S + c], w->ay[s * S + c], F);
                 for (int i = 0; i < 9; ++i) {
                     double fi = f[(long)(s * 9 + i) * S + c];
                     double post = fi + (fe[i] - fi) / tau + F[i];
@@ -373,25 +381,6 @@ int oracle_run(const oracle_params* p, double* f, long nsteps)
     work_free(&w);
     for (long k = 0; k < total; ++k)
         if (!isfinite(f[k])) return 1;
-    return 0;
-}
-
-/* Intermediate fields of one step from state f: rho^s, u, nu^s, a^s (any may be NULL). */
-int oracle_fields(const oracle_params* p, const double* f, double* rs, double* ux, double* uy,
-                  double* nu, double* ax, double* ay)
-{
-    if (check(p)) return -1;
-    work_t w;
-    if (work_alloc(p, &w)) { work_free(&w); return -2; }
-    compute_fields(p, f, &w);
-    long S = w.S, N = p->ncomp;
-    if (rs) memcpy(rs, w.rs, sizeof(double) * N * S);
-    if (ux) memcpy(ux, w.ux, sizeof(double) * S);
-    if (uy) memcpy(uy, w.uy, sizeof(double) * S);
-    if (nu) memcpy(nu, w.nu, sizeof(double) * N * S);
-    if (ax) memcpy(ax, w.ax, sizeof(double) * N * S);
-    if (ay) memcpy(ay, w.ay, sizeof(double) * N * S);
-    work_free(&w);
     return 0;
 }
 
@@ -482,5 +471,258 @@ int oracle_conservation(const oracle_params* p, const double* f, double* mass, d
     if (mom) { mom[0] = mx; mom[1] = my; }
     if (force_sum) { force_sum[0] = fx; force_sum[1] = fy; }
     work_free(&w);
+    return 0;
+}
+
+/* ------------------------------------------------------------------- D1Q3
+ *
+ * The lattice the paper's own simulations use (Sec. 4): velocities v = 0, +1, -1
+ * with weights 2/3, 1/6, 1/6 (c_s^2 = 1/3), one line of nx sites, periodic.  The
+ * same stages as above in the same order; the discrete operators keep their
+ * definition through the lattice's weights, grad g = 3 sum_i w_i v_i g(x + v_i) and
+ * lap g = 6 sum_i w_i (g(x + v_i) - g(x)), i.e. (g(x+1) - g(x-1))/2 and
+ * g(x+1) + g(x-1) - 2 g(x).  The body force is p->gx; p->ny is ignored.
+ *
+ * Layout: f[(s * 3 + i) * nx + x], pre-collision, velocity order 0, +1, -1. */
+
+static const int V1[3] = {0, 1, -1};
+static const double W1[3] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0};
+
+static int check1(const oracle_params* p)
+{
+    if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1) return -1;
+    if (!(p->tau > 0.5)) return -1;
+    if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
+    return 0;
+}
+
+/* f^e_i = w_i rho^s (1 + 3 v u + 9/2 (v u)^2 - 3/2 u^2): moments rho^s, rho^s u,
+ * rho^s/3 + rho^s u^2 (Sec. 3 in one dimension). */
+static void d1_equilibrium(double rs, double u, double* fe)
+{
+    for (int i = 0; i < 3; ++i) {
+        double cu = V1[i] * u;
+        fe[i] = W1[i] * rs * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u * u);
+    }
+}
+
+/* F_i = w_i (3 rho^s v a + 9 (v a)(v j) - 3 a j): moments 0, rho^s a, 2 a j (Eqs.
+ * ff1-ff3 in one dimension). */
+static void d1_forcing(double rs, double j, double a, double* F)
+{
+    for (int i = 0; i < 3; ++i) {
+        double ca = V1[i] * a, cj = V1[i] * j;
+        F[i] = W1[i] * (3.0 * rs * ca + 9.0 * ca * cj - 3.0 * a * j);
+    }
+}
+
+static double d1_grad(const double* g, int nx, int x)
+{
+    double acc = 0.0;
+    for (int i = 0; i < 3; ++i) acc += W1[i] * V1[i] * g[wrap(x + V1[i], nx)];
+    return 3.0 * acc;
+}
+
+static double d1_lap(const double* g, int nx, int x)
+{
+    double acc = 0.0;
+    for (int i = 0; i < 3; ++i) acc += W1[i] * (g[wrap(x + V1[i], nx)] - g[x]);
+    return 6.0 * acc;
+}
+
+typedef struct {
+    double *rs, *j, *rho, *u, *nu, *a;
+} work1_t;
+
+static int work1_alloc(const oracle_params* p, work1_t* w)
+{
+    long nx = p->nx, N = p->ncomp;
+    w->rs = malloc(sizeof(double) * N * nx);
+    w->j = malloc(sizeof(double) * N * nx);
+    w->rho = malloc(sizeof(double) * nx);
+    w->u = malloc(sizeof(double) * nx);
+    w->nu = malloc(sizeof(double) * N * nx);
+    w->a = malloc(sizeof(double) * N * nx);
+    return (w->rs && w->j && w->rho && w->u && w->nu && w->a) ? 0 : -2;
+}
+
+static void work1_free(work1_t* w)
+{
+    free(w->rs); free(w->j); free(w->rho); free(w->u); free(w->nu); free(w->a);
+}
+
+/* Stages 1-3 of one D1Q3 step: moments, potentials nu^s, accelerations a^s. */
+static void d1_fields(const oracle_params* p, const double* f, work1_t* w)
+{
+    int N = p->ncomp, nx = p->nx;
+    double th = p->theta;
+    for (int x = 0; x < nx; ++x) {
+        double rho = 0.0, jt = 0.0;
+        for (int s = 0; s < N; ++s) {
+            double r = 0.0, j = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                double v = f[(long)(s * 3 + i) * nx + x];
+                r += v;
+                j += v * V1[i];
+            }
+            w->rs[s * nx + x] = r;
+            w->j[s * nx + x] = j;
+            rho += r;
+            jt += j;
+        }
+        w->rho[x] = rho;
+        w->u[x] = jt / rho;
+    }
+    for (int x = 0; x < nx; ++x) {
+        double rho = w->rho[x];
+        double phi[OR_NMAX], chiphi[OR_NMAX];
+        double sum_phi_m = 0.0, quad = 0.0;
+        for (int s = 0; s < N; ++s) phi[s] = w->rs[s * nx + x] / rho;
+        for (int s = 0; s < N; ++s) sum_phi_m += phi[s] / p->m[s];
+        for (int s = 0; s < N; ++s) {
+            chiphi[s] = 0.0;
+            for (int t = 0; t < N; ++t) chiphi[s] += p->chi[s * N + t] * phi[t];
+        }
+        for (int s = 0; s < N; ++s) quad += 0.5 * phi[s] * chiphi[s];
+        double lnrho = log(rho);
+        for (int s = 0; s < N; ++s) {
+            double rs = w->rs[s * nx + x];
+            double coef = th / p->m[s] - 1.0 / 3.0;
+            double logs = -(th / p->m[s]) * lnrho;
+            if (coef != 0.0) {
+                double r = rs > LOG_FLOOR * rho ? rs : LOG_FLOOR * rho;
+                logs += coef * log(r);
+            }
+            double bulk = th * (1.0 / p->m[s] - 1.0 - sum_phi_m + chiphi[s] - quad);
+            w->nu[s * nx + x] = logs + bulk - p->kappa * d1_lap(w->rs + s * nx, nx, x);
+        }
+    }
+    double coef = 1.0 - 1.0 / (2.0 * p->tau);
+    for (int x = 0; x < nx; ++x)
+        for (int s = 0; s < N; ++s)
+            w->a[s * nx + x] = -coef * d1_grad(w->nu + s * nx, nx, x) + p->gx;
+}
+
+/* f(x, 0) = f^e(rho^s(x), u(x)); u may be NULL (rest). */
+int oracle_d1q3_init(const oracle_params* p, const double* rho, const double* u, double* f)
+{
+    if (check1(p)) return -1;
+    int N = p->ncomp, nx = p->nx;
+    for (int s = 0; s < N; ++s)
+        for (int x = 0; x < nx; ++x) {
+            double fe[3];
+            d1_equilibrium(rho[s * nx + x], u ? u[x] : 0.0, fe);
+            for (int i = 0; i < 3; ++i) f[(long)(s * 3 + i) * nx + x] = fe[i];
+        }
+    return 0;
+}
+
+/* Advance f (in place) by nsteps D1Q3 timesteps.  Returns 0, -1, -2, or 1 if a
+ * non-finite value appeared. */
+int oracle_d1q3_run(const oracle_params* p, double* f, long nsteps)
+{
+    if (check1(p)) return -1;
+    int N = p->ncomp, nx = p->nx;
+    work1_t w;
+    if (work1_alloc(p, &w)) { work1_free(&w); return -2; }
+    long total = (long)3 * N * nx;
+    double* g = malloc(sizeof(double) * total);
+    if (!g) { work1_free(&w); return -2; }
+    double *cur = f, *nxt = g;
+    double tau = p->tau;
+    for (long t = 0; t < nsteps; ++t) {
+        d1_fields(p, cur, &w);
+        for (int x = 0; x < nx; ++x)
+            for (int s = 0; s < N; ++s) {
+                double fe[3], F[3];
+                double rs = w.rs[s * nx + x];
+                double j = p->forcing_velocity ? rs * w.u[x] : w.j[s * nx + x];
+                d1_equilibrium(rs, w.u[x], fe);
+                d1_forcing(rs, j, w.a[s * nx + x], F);
+                for (int i = 0; i < 3; ++i) {
+                    double fi = cur[(long)(s * 3 + i) * nx + x];
+                    double post = fi + (fe[i] - fi) / tau + F[i];
+                    nxt[(long)(s * 3 + i) * nx + wrap(x + V1[i], nx)] = post;
+                }
+            }
+        double* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (cur != f) memcpy(f, cur, sizeof(double) * total);
+    free(g);
+    work1_free(&w);
+    for (long k = 0; k < total; ++k)
+        if (!isfinite(f[k])) return 1;
+    return 0;
+}
+
+/* Output fields of a D1Q3 state, in the shapes of a D2Q9 state with ny = 1 (any
+ * pointer may be NULL): rho (N*nx); U (2*nx) = (u + a/2, 0); mu (N*nx); P (3*nx) =
+ * (iso + kappa sum_s (d_x rho^s)^2, 0, iso) with iso = sum_s rho^s mu^s - psi -
+ * sum_s (kappa/2) (d_x rho^s)^2. */
+int oracle_d1q3_moments(const oracle_params* p, const double* f, double* rho_out, double* U,
+                        double* mu, double* P)
+{
+    if (check1(p)) return -1;
+    int N = p->ncomp, nx = p->nx;
+    work1_t w;
+    if (work1_alloc(p, &w)) { work1_free(&w); return -2; }
+    d1_fields(p, f, &w);
+    if (rho_out) memcpy(rho_out, w.rs, sizeof(double) * N * nx);
+    for (int x = 0; x < nx; ++x) {
+        if (U) {
+            double fx = 0.0;
+            for (int s = 0; s < N; ++s) fx += w.rs[s * nx + x] * w.a[s * nx + x];
+            U[x] = w.u[x] + 0.5 * fx / w.rho[x];
+            U[nx + x] = 0.0;
+        }
+        if (mu || P) {
+            double rsl[OR_NMAX], mub[OR_NMAX], muf[OR_NMAX];
+            for (int s = 0; s < N; ++s) rsl[s] = w.rs[s * nx + x];
+            oracle_mu_bulk(p, rsl, mub);
+            for (int s = 0; s < N; ++s) muf[s] = mub[s] - p->kappa * d1_lap(w.rs + s * nx, nx, x);
+            if (mu)
+                for (int s = 0; s < N; ++s) mu[s * nx + x] = muf[s];
+            if (P) {
+                double psi = oracle_psi(p, rsl), rmu = 0.0, gg = 0.0, pxx = 0.0;
+                for (int s = 0; s < N; ++s) {
+                    double gx = d1_grad(w.rs + s * nx, nx, x);
+                    rmu += rsl[s] * muf[s];
+                    gg += 0.5 * p->kappa * gx * gx;
+                    pxx += p->kappa * gx * gx;
+                }
+                double iso = rmu - (psi + gg);
+                P[x] = iso + pxx;
+                P[nx + x] = 0.0;
+                P[2 * nx + x] = iso;
+            }
+        }
+    }
+    work1_free(&w);
+    return 0;
+}
+
+/* Global sums of a D1Q3 state: mass^s (N), momentum (2: x, 0), force (2: x, 0). */
+int oracle_d1q3_conservation(const oracle_params* p, const double* f, double* mass,
+                             double* mom, double* force_sum)
+{
+    if (check1(p)) return -1;
+    int N = p->ncomp, nx = p->nx;
+    work1_t w;
+    if (work1_alloc(p, &w)) { work1_free(&w); return -2; }
+    d1_fields(p, f, &w);
+    for (int s = 0; s < N; ++s) {
+        double acc = 0.0;
+        for (int x = 0; x < nx; ++x) acc += w.rs[s * nx + x];
+        if (mass) mass[s] = acc;
+    }
+    double mx = 0.0, fx = 0.0;
+    for (int x = 0; x < nx; ++x)
+        for (int s = 0; s < N; ++s) {
+            mx += w.j[s * nx + x];
+            fx += w.rs[s * nx + x] * w.a[s * nx + x];
+        }
+    if (mom) { mom[0] = mx; mom[1] = 0.0; }
+    if (force_sum) { force_sum[0] = fx; force_sum[1] = 0.0; }
+    work1_free(&w);
     return 0;
 }

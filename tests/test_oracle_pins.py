@@ -137,22 +137,72 @@ def test_momentum_balance():
 
 # ------------------------------------------------ independent transcriptions
 
+@pytest.mark.parametrize("fv", [0, 1], ids=["component_u", "barycentric_u"])
 @pytest.mark.parametrize("shape", [(4, 4), (5, 3), (7, 6)])
-def test_step_matches_hermite_transcription(shape):
+def test_step_matches_hermite_transcription(shape, fv):
     """One to three steps on tiny grids against the generic-Hermite numpy transcription
-    (every site, every population), with every term switched on."""
+    (every site, every population), with every term switched on, for both readings of
+    the velocity in the forcing's second moment (Eq. ff3 as printed, and barycentric)."""
     nx, ny = shape
     n = 3
     chi = _chi(n, 40)
     m = np.array([1.0, 3.0, 10.0])
     rho, u = inputs.random_state(n, nx, ny, seed=41, amp=0.4, umax=0.05)
-    o = Oracle(n, nx, ny, 0.9, chi, m, theta=0.42, kappa=0.05, force=(3e-4, -1e-4))
+    o = Oracle(n, nx, ny, 0.9, chi, m, theta=0.42, kappa=0.05, force=(3e-4, -1e-4),
+               forcing_velocity=fv)
     o.init(rho, u)
     f = o.f.copy()
     for _ in range(3):
         o.run(1)
-        f = tr.step_d2q9(f, chi, m, 0.42, 0.05, 0.9, g=(3e-4, -1e-4))
+        f = tr.step_d2q9(f, chi, m, 0.42, 0.05, 0.9, g=(3e-4, -1e-4), bary=bool(fv))
         np.testing.assert_allclose(o.f, f, rtol=1e-12, atol=1e-14)
+
+
+def _one_fluid_forcing(A, rho, u):
+    """D2Q9 populations with moments 0, A, A u + u A (the overall fluid's forcing with
+    rho a = A, Eq. olso), written out per velocity for 2-vectors A, u."""
+    c = C9.astype(float)
+    out = []
+    for i in range(9):
+        cA = c[i, 0] * A[0] + c[i, 1] * A[1]
+        cu = c[i, 0] * u[0] + c[i, 1] * u[1]
+        Au = A[0] * u[0] + A[1] * u[1]
+        out.append(tr.W9[i] * (3 * cA + 9 * cA * cu - 3 * Au))
+    return np.stack(out)
+
+
+def test_barycentric_forcing_sums_to_one_fluid():
+    """With the barycentric u in the forcing's second moment, summing Eq. ssLB over the
+    components gives exactly the one-fluid update with the overall forcing of Eq. olso
+    (moments 0, rho a, rho (a u + u a), rho a = sum_s rho^s a^s).  The total force comes
+    from the oracle's own output velocity U = u + a/2 (Eq. scon), the rest from the
+    populations, so this pins the option at the level of the whole step.  With Eq. ff3 as
+    printed (component velocities) the same sum differs by sum_s rho^s a^s (u^s - u)
+    terms, which the test also checks is not zero."""
+    n, nx, ny = 3, 9, 7
+    chi = _chi(n, 43)
+    rho, u = inputs.random_state(n, nx, ny, seed=44, amp=0.4, umax=0.05)
+    diffs = []
+    for fv in (1, 0):
+        o = Oracle(n, nx, ny, 0.85, chi, [1.0, 2.0, 1.0], theta=0.4, kappa=0.03,
+                   force=(2e-4, 1e-4), forcing_velocity=fv)
+        o.init(rho, u)
+        o.run(2)  # component velocities differ from u after the first steps
+        f0 = o.f.copy()
+        tot = f0.sum(0)
+        r = tot.sum(0)
+        c = C9.astype(float)
+        uu = np.stack([np.einsum("ixy,i->xy", tot, c[:, 0]), np.einsum("ixy,i->xy", tot, c[:, 1])]) / r
+        A = 2.0 * r * (o.moments()["U"] - uu)
+        feq = np.stack([tr.W9[i] * r * (1 + 3 * (c[i, 0] * uu[0] + c[i, 1] * uu[1])
+                                        + 4.5 * (c[i, 0] * uu[0] + c[i, 1] * uu[1]) ** 2
+                                        - 1.5 * (uu[0] ** 2 + uu[1] ** 2)) for i in range(9)])
+        post = tot + (feq - tot) / 0.85 + _one_fluid_forcing(A, r, uu)
+        want = np.stack([tr.sh(post[i], -C9[i, 0], -C9[i, 1]) for i in range(9)])
+        o.run(1)
+        diffs.append(np.max(np.abs(o.f.sum(0) - want)))
+    assert diffs[0] < 1e-15, diffs
+    assert diffs[1] > 1e-9, diffs
 
 
 def test_single_perturbed_site():
@@ -293,3 +343,171 @@ def test_rotation_symmetry():
     np.testing.assert_allclose(mb["rho"], rot(ma["rho"]), rtol=1e-12, atol=1e-15)
     np.testing.assert_allclose(mb["U"][0], rot(ma["U"][1]), rtol=1e-10, atol=1e-15)
     np.testing.assert_allclose(mb["U"][1], -rot(ma["U"][0]), rtol=1e-10, atol=1e-15)
+
+
+# --------------------------------------------------- floor of the logarithm
+
+def _floored_state(nx, ny, value):
+    """Three components, the third at `value` (times the local total density) on a block
+    of sites and at O(0.1) elsewhere, with a ring of sites at 1e-3 around the block."""
+    rho, u = inputs.random_state(3, nx, ny, seed=61, amp=0.3, umax=0.02)
+    tot = rho.sum(0)
+    rho[2, 2:5, 3:7] = 1e-3 * tot[2:5, 3:7]
+    rho[2, 3, 4:6] = value * tot[3, 4:6]
+    return rho, u
+
+
+@pytest.mark.parametrize("fv", [0, 1])
+def test_log_floor_scale_invariance(fv):
+    """Eq. definef's logarithm of a component that vanishes is taken at max(rho^s,
+    1e-12 rho): the floor is relative to the local total density, so the rho -> lambda rho
+    invariance of the kappa = 0 update (f -> lambda f; every potential shifts by a
+    constant) still holds where the floor binds.  theta/m^s != 1/3 for every component,
+    so the logarithm is evaluated; the third component is exactly 0 at some sites and
+    1e-14 rho at others.  A floor without the factor rho would break this at lambda = 100
+    (the paper's density)."""
+    nx, ny = 10, 8
+    chi = _chi(3, 62)
+    for value in (0.0, 1e-14):
+        rho, u = _floored_state(nx, ny, value)
+        a = Oracle(3, nx, ny, 0.9, chi, [1.0, 2.0, 1.0], theta=0.45, forcing_velocity=fv)
+        a.init(rho, u)
+        b = Oracle(3, nx, ny, 0.9, chi, [1.0, 2.0, 1.0], theta=0.45, forcing_velocity=fv)
+        b.init(100.0 * rho, u)
+        a.run(3)
+        b.run(3)
+        assert np.all(np.isfinite(a.f))
+        np.testing.assert_allclose(b.f, 100.0 * a.f, rtol=1e-11, atol=1e-12)
+
+
+def test_log_floor_binds_below_1e_12():
+    """Below the floor the update does not see the value of the vanishing density: the
+    third component at 0, 1e-14 rho or 5e-13 rho on the same sites gives the same step up
+    to those densities themselves (1e-12).  A missing floor (ln 0) or one lower than
+    5e-13 would change the potentials there by O(1) and the forces on the neighbours."""
+    nx, ny = 10, 8
+    chi = _chi(3, 63)
+    res = []
+    for value in (0.0, 1e-14, 5e-13):
+        rho, u = _floored_state(nx, ny, value)
+        o = Oracle(3, nx, ny, 0.9, chi, [1.0, 2.0, 1.0], theta=0.45, kappa=0.02)
+        o.init(rho, u)
+        o.run(2)
+        assert np.all(np.isfinite(o.f))
+        res.append(o.f)
+    assert np.max(np.abs(res[1] - res[0])) < 1e-12
+    assert np.max(np.abs(res[2] - res[0])) < 1e-11
+
+
+def test_log_floor_inactive_above_1e_12():
+    """Just above the floor (2e-12 rho) the oracle equals the transcription, which takes
+    bare logarithms: the floor does not bind there.  A floor placed higher (1e-11, say)
+    would change the potential of those sites by O(1)."""
+    nx, ny = 10, 8
+    chi = _chi(3, 64)
+    m = np.array([1.0, 2.0, 1.0])
+    rho, u = _floored_state(nx, ny, 2e-12)
+    o = Oracle(3, nx, ny, 0.9, chi, m, theta=0.45, kappa=0.02)
+    o.init(rho, u)
+    f = o.f.copy()
+    o.run(1)
+    want = tr.step_d2q9(f, chi, m, 0.45, 0.02, 0.9)
+    np.testing.assert_allclose(o.f, want, rtol=1e-10, atol=1e-13)
+
+
+def test_log_term_dropped_when_its_coefficient_vanishes():
+    """theta = m^s/3 for every component: the logarithm of rho^s cancels from nu^s
+    exactly (Eq. definef with Eq. lgf), so the oracle drops it and a component that is
+    exactly 0 on some sites needs no floor.  The transcription keeps both logarithms (its
+    complex-step derivative needs a density well above its step 1e-30) and is evaluated
+    with that density at 1e-16 there: the two agree to that density."""
+    nx, ny = 10, 8
+    chi = _chi(3, 65)
+    rho, u = _floored_state(nx, ny, 0.0)
+    o = Oracle(3, nx, ny, 0.9, chi, None, theta=1 / 3, kappa=0.02)
+    o.init(rho, u)
+    f = o.f.copy()
+    o.run(1)
+    assert np.all(np.isfinite(o.f))
+    f_tr = f.copy()
+    zero = f_tr[2].sum(0) == 0.0
+    assert zero.sum() == 2
+    for i in range(9):
+        f_tr[2, i][zero] = tr.W9[i] * 1e-16
+    want = tr.step_d2q9(f_tr, chi, np.ones(3), 1 / 3, 0.02, 0.9)
+    np.testing.assert_allclose(o.f, want, rtol=1e-10, atol=1e-13)
+
+
+# ------------------------------------------------------------ the D1Q3 path
+
+@pytest.mark.parametrize("fv", [0, 1])
+def test_d1q3_path_matches_transcription(fv):
+    """The oracle's own D1Q3 path (Sec. 4's lattice, weights 2/3, 1/6, 1/6) against the
+    transcription that solves the three moment conditions directly, 60 steps with every
+    term on (m != 1, theta != 1/3, kappa, body force), both forcing readings."""
+    n, L = 3, 48
+    chi = np.array([[0.0, 3.0, 0.5], [3.0, 0.0, 0.2], [0.5, 0.2, 0.0]])
+    m = np.array([2.0, 1.0, 1.0])
+    x = np.arange(L)
+    line = np.stack([0.4 + 0.05 * np.sin(2 * np.pi * x / L),
+                     0.35 - 0.05 * np.sin(2 * np.pi * x / L), np.full(L, 0.25)])
+    u0 = 0.02 * np.cos(2 * np.pi * x / L)
+    theta, kappa, tau, g = 0.4, 0.02, 1 / 0.9, 2e-5
+    o = Oracle(n, L, 1, tau, chi, m, theta=theta, kappa=kappa, force=(g, 0.0),
+               forcing_velocity=fv, lattice="d1q3")
+    o.init(line[:, None, :], np.stack([u0, 0 * u0])[:, None, :])
+    f1 = tr.d1q3_init(line, u0)
+    # the transcription orders velocities (-1, 0, +1), the oracle (0, +1, -1)
+    np.testing.assert_allclose(o.f, f1[:, [1, 2, 0]], rtol=1e-14, atol=1e-16)
+    for _ in range(60):
+        f1 = tr.d1q3_step(f1, chi, m, theta, kappa, tau, g=g, bary=bool(fv))
+    o.run(60)
+    np.testing.assert_allclose(o.f, f1[:, [1, 2, 0]], rtol=1e-12, atol=1e-14)
+    assert np.max(np.abs(f1.sum(1) - line)) > 1e-4
+
+
+@pytest.mark.parametrize("fv", [0, 1])
+def test_d1q3_path_equals_one_row_d2q9(fv):
+    """A D2Q9 lattice of one row is y-invariant, and D1Q3 is its projection (the rest,
+    +x and -x populations summed over v_y): the oracle's two paths give the same
+    densities, velocities, potentials and pressure tensor, and the projected populations,
+    over 100 steps of a phase-separating polymer mixture."""
+    n, L = 3, 40
+    chi = np.array([[0.0, 2.6, 1.0], [2.6, 0.0, 0.4], [1.0, 0.4, 0.0]])
+    m = np.array([3.0, 1.0, 1.0])
+    rho, u = inputs.random_state(n, L, 1, seed=66, amp=0.4, umax=0.03)
+    u[1] = 0.0
+    kw = dict(m=m, theta=0.38, kappa=0.03, force=(1e-5, 0.0), forcing_velocity=fv)
+    a = Oracle(n, L, 1, 0.8, chi, lattice="d1q3", **kw)
+    b = Oracle(n, L, 1, 0.8, chi, **kw)
+    a.init(rho, u)
+    b.init(rho, u)
+    a.run(100)
+    b.run(100)
+    proj = np.stack([b.f[:, [0, 2, 4]].sum(1), b.f[:, [1, 5, 8]].sum(1),
+                     b.f[:, [3, 6, 7]].sum(1)], axis=1)[:, :, 0, :]
+    np.testing.assert_allclose(a.f, proj, rtol=1e-12, atol=1e-15)
+    ma, mb = a.moments(), b.moments()
+    for k in ("rho", "U", "mu", "P"):
+        np.testing.assert_allclose(ma[k], mb[k], rtol=1e-11, atol=1e-14, err_msg=k)
+    ca, cb = a.conservation(), b.conservation()
+    for k in ("mass", "mom", "force"):
+        np.testing.assert_allclose(ca[k], cb[k], rtol=1e-11, atol=1e-15, err_msg=k)
+
+
+def test_d1q3_conservation_and_momentum_balance():
+    """D1Q3: per-component mass kept to rounding (Eq. ff1) and the momentum changed by
+    exactly the summed force (Eq. ff2) each step."""
+    n, L = 2, 64
+    rho, u = inputs.random_state(n, L, 1, seed=67, amp=0.3, umax=0.03)
+    o = Oracle(n, L, 1, 0.9, np.array([[0.0, 1.3], [1.3, 0.0]]), [4.0, 1.0], theta=0.5,
+               kappa=0.01, force=(3e-5, 0.0), lattice="d1q3")
+    o.init(rho, u)
+    m0 = o.conservation()["mass"]
+    for _ in range(5):
+        c0 = o.conservation()
+        o.run(1)
+        c1 = o.conservation()
+        np.testing.assert_allclose(c1["mom"] - c0["mom"], c0["force"], rtol=1e-10, atol=1e-16)
+    o.run(500)
+    np.testing.assert_allclose(o.conservation()["mass"], m0, rtol=1e-13)

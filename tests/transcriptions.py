@@ -13,6 +13,9 @@ a disagreement:
   rho^s a^s, rho^s (a^s u^s + u^s a^s));
 * the D1Q3 update (the paper's own lattice, Sec. 4) solves the three moment
   conditions for the three populations directly;
+* ``bary=True`` puts the barycentric u in place of the component velocity in the
+  forcing's second moment (rho^s (a^s u + u a^s) instead of Eq. ff3's
+  rho^s (a^s u^s + u^s a^s));
 * streaming uses numpy.roll, the stencils are the explicit 9-point forms.
 """
 from __future__ import annotations
@@ -89,7 +92,7 @@ def hermite2(zeroth, first, second):
     return np.stack(out)
 
 
-def step_d2q9(f, chi, m, theta, kappa, tau, g=(0.0, 0.0)):
+def step_d2q9(f, chi, m, theta, kappa, tau, g=(0.0, 0.0), bary=False):
     """One update of f (N, 9, ny, nx) by the alternative formulation above."""
     N = f.shape[0]
     rs = f.sum(1)
@@ -108,9 +111,11 @@ def step_d2q9(f, chi, m, theta, kappa, tau, g=(0.0, 0.0)):
                        [[rs[s] / 3 + rs[s] * ux * ux, rs[s] * ux * uy],
                         [rs[s] * uy * ux, rs[s] / 3 + rs[s] * uy * uy]])
         zero = np.zeros_like(rs[s])
+        # second moment rho^s (a v + v a) with v = u^s (jx/rho^s) or the barycentric u
+        vx_, vy_ = (ux, uy) if bary else (jx[s] / rs[s], jy[s] / rs[s])
         F = hermite2(zero, (rs[s] * ax, rs[s] * ay),
-                     [[2 * ax * jx[s], ax * jy[s] + ay * jx[s]],
-                      [ay * jx[s] + ax * jy[s], 2 * ay * jy[s]]])
+                     [[rs[s] * 2 * ax * vx_, rs[s] * (ax * vy_ + ay * vx_)],
+                      [rs[s] * (ay * vx_ + ax * vy_), rs[s] * 2 * ay * vy_]])
         post = f[s] + (feq - f[s]) / tau + F
         for i in range(9):
             fnew[s, i] = sh(post[i], -C9[i, 0], -C9[i, 1])
@@ -126,7 +131,8 @@ def d1q3_equilibrium(rs, u):
 
 
 def d1q3_forcing(rs, j, a):
-    """Populations with moments 0, rho a, 2 a j (Eqs. ff1-ff3 in one dimension)."""
+    """Populations with moments 0, rho a, 2 a j (Eqs. ff1-ff3 in one dimension; j is
+    rho^s times the velocity of the second moment)."""
     p2 = 2.0 * a * j
     return np.stack([(p2 - rs * a) / 2.0, -p2, (p2 + rs * a) / 2.0])
 
@@ -135,8 +141,8 @@ def d1q3_init(rho_s, u):
     return np.stack([d1q3_equilibrium(rho_s[s], u) for s in range(rho_s.shape[0])])
 
 
-def d1q3_step(f, chi, m, theta, kappa, tau, g=0.0):
-    """One update of f (N, 3, nx) on the D1Q3 lattice of Sec. 4."""
+def d1q3_step(f, chi, m, theta, kappa, tau, g=0.0, bary=False):
+    """One update of f (N, 3, nx) on the D1Q3 lattice of Sec. 4 (velocities -1, 0, +1)."""
     N = f.shape[0]
     v = np.array([-1.0, 0.0, 1.0])
     rs = f.sum(1)
@@ -150,7 +156,8 @@ def d1q3_step(f, chi, m, theta, kappa, tau, g=0.0):
         nu = mu[s] - kappa * lap - np.log(rs[s]) / 3.0
         grad = (np.roll(nu, -1) - np.roll(nu, 1)) / 2.0
         a = -(1.0 - 1.0 / (2.0 * tau)) * grad + g
-        post = f[s] + (d1q3_equilibrium(rs[s], u) - f[s]) / tau + d1q3_forcing(rs[s], j[s], a)
+        js = rs[s] * u if bary else j[s]
+        post = f[s] + (d1q3_equilibrium(rs[s], u) - f[s]) / tau + d1q3_forcing(rs[s], js, a)
         out[s, 0] = np.roll(post[0], -1)
         out[s, 1] = post[1]
         out[s, 2] = np.roll(post[2], 1)
