@@ -2,7 +2,8 @@
  * mclb.h -- C ABI of the GB300 (sm_103a) multicomponent lattice Boltzmann library.
  *
  * The library advances the symmetric free-energy multicomponent lattice
- * Boltzmann method of Li & Wagner (arXiv:0704.3444) on a periodic D2Q9 lattice:
+ * Boltzmann method of Li & Wagner (arXiv:0704.3444) on a periodic D2Q9 lattice, or
+ * on the D1Q3 lattice of the paper's own simulations (Sec. 4):
  * one lattice Boltzmann equation per component with BGK relaxation towards an
  * equilibrium built on the shared barycentric velocity, plus the forcing term
  *     rho^s a^s = -(1 - 1/(2 tau)) rho^s grad( mu^s - (1/3) ln rho^s )   (Eq. definef)
@@ -21,6 +22,13 @@
  *     storage precision.
  *   - D2Q9 velocity order: v_0 = (0,0); v_1..4 = (1,0), (0,1), (-1,0), (0,-1);
  *     v_5..8 = (1,1), (-1,1), (-1,-1), (1,-1).  Weights 4/9, 1/9, 1/36.
+ *   - D1Q3 (params.lattice = MCLB_D1Q3, ny = 1): v_0 = 0, v_1 = +1, v_2 = -1, weights
+ *     2/3, 1/6, 1/6; the discrete gradient and Laplacian are (g(x+1) - g(x-1))/2 and
+ *     g(x+1) + g(x-1) - 2 g(x).  Field arrays keep the D2Q9 shapes with ny = 1
+ *     (velocity-like [2][1][nx] with a zero y component).
+ *   - In FP32 the weights are rounded so that they sum to exactly 1 (w_5..8 of D2Q9 and
+ *     w_1,2 of D1Q3 sit one unit in the last place below the nearest float), so that
+ *     the equilibria keep every site's mass to rounding.
  *   - All device work of a handle is ordered on the stream given at creation
  *     (NULL: the legacy default stream).  Calls that return host data
  *     synchronise that stream.  Handles are not thread-safe.
@@ -69,6 +77,23 @@ typedef enum {
                                potential fields in device scratch memory            */
 } mclb_kernel;
 
+/* Velocity in the second moment of the forcing term (Eq. ff3). */
+typedef enum {
+    MCLB_FORCING_COMPONENT = 0,   /* rho^s (a^s u^s + u^s a^s), u^s = j^s / rho^s, as Eq. ff3
+                                     prints it (the default)                             */
+    MCLB_FORCING_BARYCENTRIC = 1  /* rho^s (a^s u + u a^s) with the barycentric u: a reading
+                                     whose sum over the components is the one-fluid forcing
+                                     moment rho (a u + u a) of Eq. olso; the paper's remark
+                                     after Eq. olso calls the difference higher order     */
+} mclb_forcing_velocity;
+
+/* Lattice. */
+typedef enum {
+    MCLB_D2Q9 = 0,   /* two-dimensional, nine velocities (see the conventions above)      */
+    MCLB_D1Q3 = 1    /* the one-dimensional lattice of the paper's simulations (Sec. 4):
+                        v_0 = 0, v_1 = +1, v_2 = -1, weights 2/3, 1/6, 1/6; ny must be 1   */
+} mclb_lattice;
+
 /* Problem statement (Sec. 3 and Sec. 4 of the paper).
  *   ncomp      N, number of components, 1..MCLB_NMAX
  *   nx, ny     periodic lattice size, >= 1 each
@@ -82,7 +107,9 @@ typedef enum {
  *   force      body acceleration g (Eq. NSEeq), added to every a^s
  *   precision  mclb_precision
  *   kernel     mclb_kernel
- *   stream     cudaStream_t to order all work on, or NULL */
+ *   stream     cudaStream_t to order all work on, or NULL
+ *   forcing_velocity  mclb_forcing_velocity (0: Eq. ff3 as printed)
+ *   lattice    mclb_lattice (0: D2Q9) */
 typedef struct {
     int ncomp;
     int nx, ny;
@@ -95,12 +122,18 @@ typedef struct {
     int precision;
     int kernel;
     void* stream;
+    int forcing_velocity;
+    int lattice;
 } mclb_params;
 
 typedef struct mclb_handle_s* mclb_handle;
 
 /* Validate params and allocate the device state of one simulation.  The
  * distributions start at zero: call mclb_init_fields or mclb_set_state next.
+ * A D1Q3 lattice needs ny = 1 and FP64 or FP32 storage; params->kernel is ignored
+ * there (lines of up to a few hundred to 1024 sites, depending on N and precision,
+ * live in one CTA's shared memory and advance up to 4096 timesteps per launch; longer
+ * lines advance one timestep per launch).
  * Errors: EINVAL (any parameter out of range, asymmetric or non-finite chi),
  * ENOMEM, ECUDA.  *out is set to NULL on failure. */
 int mclb_create(const mclb_params* params, mclb_handle* out);
@@ -158,7 +191,7 @@ int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_su
 int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi);
 
 /* Copy the distributions in or out as FP64 pre-collision values f^s_i(r, t), layout
- * [s][i][y][x] (count must equal N*9*ny*nx).  Host pointers, synchronous.  Getting
+ * [s][i][y][x] (count must equal N*9*ny*nx; on D1Q3 [s][i][x], count N*3*nx).  Host pointers, synchronous.  Getting
  * and setting a state is exact in FP64 and FP32; in the shifted modes setting
  * stores the state as R and 16-bit deviations (see mclb_precision), so a state
  * read back differs by the rounding of the deviations.  set_state checks the values
@@ -180,11 +213,12 @@ int mclb_test_withhold_copies(mclb_handle h, int on);
 
 /* HBM bytes one timestep must move at least: every stored value read once and
  * written once, 2 * N * ny * nx * (9 * storage size) in FP64 and FP32 and
- * 2 * N * ny * nx * (9 * 2 + 4) in the shifted modes. */
+ * 2 * N * ny * nx * (9 * 2 + 4) in the shifted modes (3 in place of 9 on D1Q3). */
 double mclb_bytes_per_step(mclb_handle h);
 
 /* Kernel launches one timestep issues (2 for the fused schedule: the single pass and
- * the refresh of the periodic ghost columns; 3 for the staged). */
+ * the refresh of the periodic ghost columns; 3 for the staged; 1 on D1Q3, where one
+ * launch advances a resident line by up to 4096 timesteps). */
 int mclb_launches_per_step(mclb_handle h);
 
 /* Release everything the handle owns.  NULL is accepted.  Synchronises. */
@@ -201,21 +235,25 @@ const char* mclb_last_error(void);
  * break the caller's own overlap of work.)
  *
  * mclb_step_noalloc advances the distributions by one timestep with the staged
- * schedule in FP64 (params->precision must be MCLB_FP64; params->kernel is ignored).
+ * schedule in FP64 on the D2Q9 lattice (params->precision must be MCLB_FP64 and
+ * params->lattice MCLB_D2Q9; params->kernel is ignored).
  * Its two scratch fields live in one fixed array inside the library (a static device
  * array of 2 * MCLB_NOALLOC_MAX_COMP_SITES doubles, 8 MiB, which every GPU that loads
  * the library holds until the process exits); the call allocates nothing.
  *   f_in   device array, N*9*ny*nx doubles, pre-collision f^s_i(r, t) in the layout of
  *          mclb_get_state ([s][i][y][x]); read only
- *   f_out  device array of the same size, distinct from f_in; receives f^s_i(r, t + 1)
+ *   f_out  device array of the same size that shares no byte with f_in; receives
+ *          f^s_i(r, t + 1)
  * Work is enqueued on params->stream (NULL: the legacy default stream) and the call
  * returns without waiting.  Errors: EINVAL for invalid params, a precision other than
- * FP64, NULL or identical arrays, or N*nx*ny above MCLB_NOALLOC_MAX_COMP_SITES; ECUDA
- * if no device is usable or a launch fails.  Non-finite values are not reported.
- * The first call on a device looks up the array's device address (once per device);
- * make that first call before any stream capture.  All calls share the one array,
- * so calls that overlap on the GPU (on different streams, or from several threads)
- * race with each other; serialise them.
+ * FP64, another lattice, NULL or overlapping arrays, or N*nx*ny above
+ * MCLB_NOALLOC_MAX_COMP_SITES; ECUDA if no device is usable or a launch fails.
+ * Non-finite values are not reported.  Every call made outside a stream capture looks
+ * up the array's device address on the current device (so a device reset is followed);
+ * a call inside a capture reuses the address of the last call outside one, so make the
+ * first call on a device before any stream capture (EINVAL otherwise).  All calls share
+ * the one array, so calls that overlap on the GPU (on different streams, or from
+ * several threads) race with each other; serialise them.
  * ------------------------------------------------------------------------- */
 #define MCLB_NOALLOC_MAX_COMP_SITES 524288 /* largest N * nx * ny */
 int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_out);
@@ -229,8 +267,10 @@ int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_o
  * falls back to the staged schedule (three launches).  The first step after the batch
  * is (re)built picks each group's partition into row segments by timing a few
  * candidates on the current state (the state is not changed; the call synchronises).
- * Steps are replayed from a CUDA graph in chunks of 32.  precision and stream are taken from params[0]; kernel is
- * ignored.  Instances share no data.  Every instance must be initialised
+ * Steps are replayed from a CUDA graph in chunks of 32.  D1Q3 instances of one N
+ * advance together in one launch per 4096 timesteps (one CTA per line, the line in
+ * shared memory; lines too long for that step one launch per timestep).  precision
+ * and stream are taken from params[0]; kernel is ignored.  Instances share no data.  Every instance must be initialised
  * (mclb_batch_init_fields) before the first mclb_batch_step.  Errors as for the
  * single-simulation calls, and EINVAL for an index outside 0..count-1.
  * ------------------------------------------------------------------------- */
@@ -241,7 +281,8 @@ int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const dou
 /* Enqueue nsteps timesteps of every instance; returns without waiting. */
 int mclb_batch_step(mclb_batch b, long nsteps);
 /* Kernel launches one batched timestep issues (2 per distinct N, 3 for a group on the
- * staged schedule). */
+ * staged schedule; D1Q3 lines: 1 per distinct N, plus 1 per line too long for shared
+ * memory). */
 int mclb_batch_launches_per_step(mclb_batch b);
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P);
 int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count);

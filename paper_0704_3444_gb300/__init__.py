@@ -23,10 +23,14 @@ from ._build import LIB as _LIB_PATH
 from ._build import build as _build
 
 __all__ = ["build", "load", "Simulation", "Batch", "MclbError", "FP64", "FP32", "BF16_SHIFTED",
-           "FP16_SHIFTED", "KERNEL_AUTO", "KERNEL_FUSED", "KERNEL_STAGED"]
+           "FP16_SHIFTED", "KERNEL_AUTO", "KERNEL_FUSED", "KERNEL_STAGED", "FORCING_COMPONENT",
+           "FORCING_BARYCENTRIC", "D2Q9", "D1Q3"]
 
 FP64, FP32, BF16_SHIFTED, FP16_SHIFTED = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_STAGED = 0, 1, 2
+FORCING_COMPONENT, FORCING_BARYCENTRIC = 0, 1
+D2Q9, D1Q3 = 0, 1
+LATTICES = {"d2q9": D2Q9, "d1q3": D1Q3}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SHIFTED, "fp16": FP16_SHIFTED}
 NMAX = 8
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
@@ -48,7 +52,8 @@ class mclb_params(ctypes.Structure):
                 ("m", ctypes.POINTER(ctypes.c_double)), ("theta", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("force", ctypes.c_double * 2),
                 ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("forcing_velocity", ctypes.c_int),
+                ("lattice", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -143,7 +148,8 @@ def _fields(rho, u, ncomp, ny, nx, device=False):
 
 
 def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, force=(0.0, 0.0),
-                precision="fp32", kernel=KERNEL_AUTO, stream=None):
+                precision="fp32", kernel=KERNEL_AUTO, stream=None, forcing_velocity=0,
+                lattice="d2q9"):
     """Build an mclb_params struct; returns (struct, keep-alive arrays)."""
     chi = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp))
     marr = None if m is None else np.ascontiguousarray(np.asarray(m, dtype=np.float64))
@@ -156,6 +162,8 @@ def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, for
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.kernel = int(kernel)
     p.stream = ctypes.c_void_p(stream) if stream else None
+    p.forcing_velocity = int(forcing_velocity)
+    p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     return p, (chi, marr)
 
 
@@ -163,11 +171,13 @@ class Simulation:
     """One simulation handle (mclb_create ... mclb_destroy)."""
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
-                 force=(0.0, 0.0), precision="fp32", kernel=KERNEL_AUTO, stream=None):
+                 force=(0.0, 0.0), precision="fp32", kernel=KERNEL_AUTO, stream=None,
+                 forcing_velocity=0, lattice="d2q9"):
         self.lib = load()
         self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
         p, keep = make_params(ncomp, nx, ny, tau, chi, m, theta, kappa, force, precision, kernel,
-                              stream)
+                              stream, forcing_velocity, lattice)
+        self.q = 3 if p.lattice == D1Q3 else 9
         h = ctypes.c_void_p()
         _check(self.lib.mclb_create(ctypes.byref(p), ctypes.byref(h)), "mclb_create")
         self.h = h
@@ -175,7 +185,8 @@ class Simulation:
     @classmethod
     def from_problem(cls, prob, precision=None, kernel=KERNEL_AUTO, stream=None):
         s = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta, prob.kappa,
-                prob.force, precision or prob.precision, kernel, stream)
+                prob.force, precision or prob.precision, kernel, stream,
+                getattr(prob, "forcing_velocity", 0), getattr(prob, "lattice", "d2q9"))
         s.init_fields(prob.rho, prob.u)
         return s
 
@@ -242,7 +253,8 @@ class Simulation:
         return out
 
     def get_state(self):
-        f = np.empty((self.ncomp, 9, self.ny, self.nx))
+        """Pre-collision populations: (N, 9, ny, nx) on D2Q9, (N, 3, nx) on D1Q3."""
+        f = np.empty((self.ncomp, 3, self.nx) if self.q == 3 else (self.ncomp, 9, self.ny, self.nx))
         _check(self.lib.mclb_get_state(self.h, _dp(f), f.size), "mclb_get_state")
         return f
 
@@ -277,7 +289,8 @@ class Batch:
         self._keep = []
         for k, pr in enumerate(self.problems):
             p, keep = make_params(pr.ncomp, pr.nx, pr.ny, pr.tau, pr.chi, pr.m, pr.theta, pr.kappa,
-                                  pr.force, precision, KERNEL_AUTO, stream)
+                                  pr.force, precision, KERNEL_AUTO, stream,
+                                  getattr(pr, "forcing_velocity", 0), getattr(pr, "lattice", "d2q9"))
             arr[k] = p
             self._keep.append(keep)
         h = ctypes.c_void_p()
@@ -319,7 +332,8 @@ class Batch:
 
     def get_state(self, index):
         pr = self.problems[index]
-        f = np.empty((pr.ncomp, 9, pr.ny, pr.nx))
+        q = 3 if getattr(pr, "lattice", "d2q9") == "d1q3" else 9
+        f = np.empty((pr.ncomp, q, pr.nx) if q == 3 else (pr.ncomp, 9, pr.ny, pr.nx))
         _check(self.lib.mclb_batch_get_state(self.h, int(index), _dp(f), f.size),
                "mclb_batch_get_state")
         return f

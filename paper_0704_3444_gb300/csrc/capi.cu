@@ -102,12 +102,21 @@ int validate(const mclb_params* p)
         return fail(MCLB_EINVAL, "precision=%d unknown", p->precision);
     if (p->kernel < MCLB_KERNEL_AUTO || p->kernel > MCLB_KERNEL_STAGED)
         return fail(MCLB_EINVAL, "kernel=%d unknown", p->kernel);
+    if (p->forcing_velocity != MCLB_FORCING_COMPONENT && p->forcing_velocity != MCLB_FORCING_BARYCENTRIC)
+        return fail(MCLB_EINVAL, "forcing_velocity=%d unknown", p->forcing_velocity);
+    if (p->lattice != MCLB_D2Q9 && p->lattice != MCLB_D1Q3)
+        return fail(MCLB_EINVAL, "lattice=%d unknown", p->lattice);
+    if (p->lattice == MCLB_D1Q3) {
+        if (p->ny != 1) return fail(MCLB_EINVAL, "lattice D1Q3 needs ny = 1 (ny=%d)", p->ny);
+        if (p->precision != MCLB_FP64 && p->precision != MCLB_FP32)
+            return fail(MCLB_EINVAL, "lattice D1Q3 stores FP64 or FP32 (precision=%d)", p->precision);
+    }
     return MCLB_OK;
 }
 
 void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
 {
-    const int hx = tab.hx;
+    const int hx = p->lattice == MCLB_D1Q3 ? 0 : tab.hx;
     memset(&P, 0, sizeof(P));
     P.N = p->ncomp;
     P.nx = p->nx;
@@ -116,6 +125,11 @@ void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
     P.hx = hx;
     P.pitch = 2LL * hx + (long long)((p->nx + ROW_ALIGN - 1) / ROW_ALIGN) * ROW_ALIGN;
     P.plane = P.pitch * Q * p->ny;
+    P.lattice = p->lattice;
+    if (P.lattice == MCLB_D1Q3) {   // compact [s][3][nx], no ghost columns
+        P.pitch = p->nx;
+        P.plane = 3LL * p->nx;
+    }
     // 16-bit formats: the FP32 density lines follow the deviations, 256-byte aligned
     P.rbytes = tab.shifted ? (long long)((P.plane * P.N * (long long)tab.storage_bytes + 255) / 256 * 256) : 0;
     P.tau = p->tau;
@@ -123,6 +137,7 @@ void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
     P.kappa = p->kappa;
     P.gx = p->force[0];
     P.gy = p->force[1];
+    P.forcing_velocity = p->forcing_velocity;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) P.chi[a * P.N + b] = p->chi[a * P.N + b];
         P.m[a] = p->m ? p->m[a] : 1.0;
@@ -145,6 +160,7 @@ struct mclb_handle_s {
     Scratch sc;
     FusedPlan plan;
     bool fused;
+    const Line3Table* line3;      // D1Q3 handles: their kernels (null for D2Q9)
     cudaStream_t stream;
     bool own_stream;
     void* f[2];
@@ -359,6 +375,10 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     }
     h->fbytes = (size_t)P.plane * P.N * h->tab->storage_bytes;
     if (h->tab->shifted) h->fbytes = (size_t)P.rbytes + (size_t)P.N * P.ny * P.pitch * sizeof(float);
+    if (P.lattice == MCLB_D1Q3) {
+        h->line3 = h->tab->line3;
+        if (!h->line3) return bail(fail(MCLB_EINVAL, "no D1Q3 kernels for this precision"));
+    }
     const size_t cbytes = (h->precision == MCLB_FP64) ? sizeof(double) : sizeof(float);
     for (int b = 0; b < 2; ++b) {
         if (cudaMalloc(&h->f[b], h->fbytes) != cudaSuccess)
@@ -384,7 +404,12 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaStreamCreateWithFlags(&h->status_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
     h->fused = false;
-    if (h->kernel != MCLB_KERNEL_STAGED) {
+    if (h->line3) {
+        if (cudaMalloc(&h->sc.line_item, h->line3->item_bytes) != cudaSuccess)
+            return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));
+        if (h->line3->prepare(P, h->sc, h->f) != cudaSuccess)
+            return bail(fail(MCLB_ECUDA, "D1Q3 line description upload failed"));
+    } else if (h->kernel != MCLB_KERNEL_STAGED) {
         h->plan = h->tab->plan_fused(P, sms);
         if (h->plan.ok && make_tmap(h, 0) == MCLB_OK && make_tmap(h, 1) == MCLB_OK) h->fused = true;
         if (!h->fused && h->kernel == MCLB_KERNEL_FUSED)
@@ -411,6 +436,7 @@ int mclb_destroy(mclb_handle h)
     if (h->sc.nu) cudaFree(h->sc.nu);
     if (h->sc.partial) cudaFree(h->sc.partial);
     if (h->sc.status) cudaFree(h->sc.status);
+    if (h->sc.line_item) cudaFree(h->sc.line_item);
     if (h->dtmp) cudaFree(h->dtmp);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->status_event) cudaEventDestroy(h->status_event);
@@ -427,7 +453,10 @@ static int init_common(mclb_handle h, const double* rho_d, const double* u_d)
     int rc = settle_status(h);
     if (rc) return rc;
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
-    CK(h->tab->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
+    if (h->line3)
+        CK(h->line3->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
+    else
+        CK(h->tab->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
     h->cur = 0;
     h->steps = 0;
     return MCLB_OK;
@@ -489,6 +518,15 @@ int mclb_step(mclb_handle h, long nsteps)
         prev = status_code(*h->status_host);
     }
     cudaGetLastError();
+    if (h->line3) {
+        CK(h->line3->step(h->P, h->sc, h->f, &h->cur, nsteps, h->stream));
+        h->steps += nsteps;
+        if (nsteps > 0) {
+            rc = enqueue_status_copy(h);
+            if (rc) return rc;
+        }
+        return prev;
+    }
     long left = nsteps;
     while (left >= GRAPH_STEPS && !h->P.withhold) {
         if (!h->graph_tried[h->cur]) try_capture(h, h->cur);
@@ -528,13 +566,15 @@ int mclb_test_withhold_copies(mclb_handle h, int on)
 double mclb_bytes_per_step(mclb_handle h)
 {
     if (check_handle(h)) return -1.0;
-    const double per = Q * (double)h->tab->storage_bytes + (h->tab->shifted ? sizeof(float) : 0.0);
+    const double q = h->line3 ? 3.0 : (double)Q;
+    const double per = q * (double)h->tab->storage_bytes + (h->tab->shifted ? sizeof(float) : 0.0);
     return 2.0 * h->P.N * (double)h->P.S * per;
 }
 
 int mclb_launches_per_step(mclb_handle h)
 {
     if (check_handle(h)) return -1;
+    if (h->line3) return 1;
     return h->fused ? 2 : 3;
 }
 
@@ -543,7 +583,10 @@ int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, doubl
     int rc = check_handle(h);
     if (rc) return rc;
     if (!rho && !U && !mu && !P) return MCLB_OK;
-    CK(h->tab->moments(h->P, h->sc, h->f[h->cur], rho, U, mu, P, h->stream));
+    if (h->line3)
+        CK(h->line3->moments(h->P, h->sc, h->f[h->cur], rho, U, mu, P, h->stream));
+    else
+        CK(h->tab->moments(h->P, h->sc, h->f[h->cur], rho, U, mu, P, h->stream));
     return MCLB_OK;
 }
 
@@ -576,7 +619,10 @@ int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_su
     const int N = h->P.N;
     rc = ensure_dtmp(h, NMAX + 4);
     if (rc) return rc;
-    CK(h->tab->conservation(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    if (h->line3)
+        CK(h->line3->conservation(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    else
+        CK(h->tab->conservation(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
     double out[NMAX + 4];
     CK(cudaMemcpyAsync(out, h->dtmp, sizeof(double) * (N + 4), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -590,11 +636,14 @@ int mclb_get_state(mclb_handle h, double* f, size_t count)
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    const size_t want = (size_t)h->P.N * Q * h->P.S;
+    const size_t want = (size_t)h->P.N * (h->line3 ? 3 : Q) * h->P.S;
     if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
     rc = ensure_dtmp(h, want);
     if (rc) return rc;
-    CK(h->tab->get_state(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    if (h->line3)
+        CK(h->line3->get_state(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    else
+        CK(h->tab->get_state(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
     CK(cudaMemcpyAsync(f, h->dtmp, sizeof(double) * want, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return MCLB_OK;
@@ -605,7 +654,7 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
     int rc = check_handle(h);
     if (rc) return rc;
     const Problem& P = h->P;
-    const size_t want = (size_t)P.N * Q * P.S;
+    const size_t want = (size_t)P.N * (h->line3 ? 3 : Q) * P.S;
     if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
     rc = ensure_dtmp(h, want + 1);
     if (rc) return rc;
@@ -619,7 +668,10 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
     rc = settle_status(h);
     if (rc) return rc;
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
-    CK(h->tab->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
+    if (h->line3)
+        CK(h->line3->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
+    else
+        CK(h->tab->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->cur = 0;
     h->steps = 0;
@@ -638,7 +690,10 @@ int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi)
     if (rc) return rc;
     double* d_phi = h->dtmp;
     double* d_bulk = h->dtmp + P.N * S;
-    CK(h->tab->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
+    if (h->line3)
+        CK(h->line3->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
+    else
+        CK(h->tab->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
     std::vector<double> hphi((size_t)P.N * S), hbulk(S);
     CK(cudaMemcpyAsync(hphi.data(), d_phi, sizeof(double) * P.N * S, cudaMemcpyDeviceToHost,
                        h->stream));
@@ -702,8 +757,10 @@ struct mclb_batch_s {
     bool own_stream;
     const KernelTable* tab;
     std::vector<void*> groups;        // batched launches, one group per distinct N
+    std::vector<void*> lgroups;       // D1Q3 instances, one group per distinct N
     bool dirty;                       // groups must be rebuilt before the next step
-    int parity;                       // buffer holding every instance's current state
+    int parity;                       // buffer holding every D2Q9 instance's current state
+    int lparity;                      // the same for the D1Q3 instances
     cudaGraphExec_t graph[2];
     bool graph_tried[2];
     // a group's ghost refresh runs on the side stream, overlapping the next group's march;
@@ -718,6 +775,8 @@ void batch_drop(mclb_batch b)
 {
     for (void* g : b->groups) b->tab->batch_destroy(g);
     b->groups.clear();
+    for (void* g : b->lgroups) b->tab->line3->batch_destroy(g);
+    b->lgroups.clear();
     for (cudaEvent_t e : b->ev_main) cudaEventDestroy(e);
     for (cudaEvent_t e : b->ev_side) cudaEventDestroy(e);
     b->ev_main.clear();
@@ -738,8 +797,27 @@ int batch_build(mclb_batch b)
         std::vector<void*> fa, fb;
         std::vector<CUtensorMap> maps;
         bool fused = true;
+        std::vector<Problem> lprobs;
+        std::vector<Scratch> lscs;
+        std::vector<void*> la, lb;
         for (auto h : b->items)
-            if (h->P.N == n) {
+            if (h->P.N == n && h->line3) {
+                lprobs.push_back(h->P);
+                lscs.push_back(h->sc);
+                la.push_back(h->f[0]);
+                lb.push_back(h->f[1]);
+            }
+        if (!lprobs.empty()) {
+            void* g = b->tab->line3->batch_create(n, (int)lprobs.size(), lprobs.data(), lscs.data(),
+                                                  la.data(), lb.data(), b->stream);
+            if (!g) {
+                batch_drop(b);
+                return fail(MCLB_ENOMEM, "D1Q3 batch tables for N=%d could not be built", n);
+            }
+            b->lgroups.push_back(g);
+        }
+        for (auto h : b->items)
+            if (h->P.N == n && !h->line3) {
                 probs.push_back(h->P);
                 scs.push_back(h->sc);
                 fa.push_back(h->f[0]);
@@ -857,6 +935,7 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
     b->own_stream = false;
     b->dirty = true;
     b->parity = 0;
+    b->lparity = 0;
     if (!b->stream) {
         if (cudaStreamCreate(&b->stream) != cudaSuccess) {
             delete b;
@@ -903,7 +982,7 @@ int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const dou
     if (rc) return rc;
     rc = mclb_init_fields(h, rho, u);  // writes buffer 0
     if (rc) return rc;
-    if (b->parity == 1) {              // every instance's state lives in the batch's buffer
+    if ((h->line3 ? b->lparity : b->parity) == 1) {   // the state lives in the batch's buffer
         CK(cudaMemcpyAsync(h->f[1], h->f[0], h->fbytes, cudaMemcpyDeviceToDevice, b->stream));
         CK(cudaStreamSynchronize(b->stream));
         h->cur = 1;
@@ -923,7 +1002,15 @@ int mclb_batch_step(mclb_batch b, long nsteps)
     cudaGetLastError();
     if (nsteps > 0)
         for (void* g : b->groups) CK(b->tab->batch_tune(g, b->parity, b->stream));
-    long left = nsteps;
+    // D1Q3 lines: every group in chunks of resident steps (each chunk moves the lines to
+    // the other buffer)
+    for (long left = b->lgroups.empty() ? 0 : nsteps; left > 0;) {
+        const int k = (int)(left < LINE3_CHUNK ? left : LINE3_CHUNK);
+        for (void* g : b->lgroups) CK(b->tab->line3->batch_step(g, b->lparity, k, b->stream));
+        b->lparity ^= 1;
+        left -= k;
+    }
+    long left = b->groups.empty() ? 0 : nsteps;
     while (left >= GRAPH_STEPS) {
         if (!b->graph_tried[b->parity]) batch_capture(b, b->parity);
         if (!b->graph[b->parity]) break;
@@ -936,7 +1023,7 @@ int mclb_batch_step(mclb_batch b, long nsteps)
     }
     CK(batch_join(b));   // later work on the batch's stream sees every ghost refresh
     for (auto h : b->items) {
-        h->cur = b->parity;
+        h->cur = h->line3 ? b->lparity : b->parity;
         h->steps += nsteps;
     }
     return MCLB_OK;
@@ -948,6 +1035,7 @@ int mclb_batch_launches_per_step(mclb_batch b)
     if (b->dirty && batch_build(b)) return -1;
     int n = 0;
     for (const void* g : b->groups) n += b->tab->batch_launches(g);
+    for (const void* g : b->lgroups) n += b->tab->line3->batch_launches(g);
     return n;
 }
 

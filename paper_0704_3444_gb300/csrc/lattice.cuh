@@ -26,6 +26,18 @@ __host__ __device__ __forceinline__ constexpr C wq(int i)
 {
     return i == 0 ? C(4.0 / 9.0) : (i < 5 ? C(1.0 / 9.0) : C(1.0 / 36.0));
 }
+// FP32 weights whose exact sum is 1.  The floats nearest to 4/9, 1/9 and 1/36 sum to
+// 1 + 7.45e-9, and every step would add that fraction of each site's mass through the
+// equilibria (sum_i f^e_i = rho^s sum_i w_i, Sec. 3) and, in the 16-bit formats, again
+// when the populations are rebuilt from the reference density: a steady drift of the
+// component masses (3e-4 after 40 000 steps).  Taking w_5..8 one unit in the last place
+// below the nearest float to 1/36 (14913080 * 2^-29) makes w_0 + 4 w_1 + 4 w_5 = 1
+// exactly, with w_0 and w_1 the nearest floats.
+template <>
+__host__ __device__ __forceinline__ constexpr float wq<float>(int i)
+{
+    return i == 0 ? float(4.0 / 9.0) : (i < 5 ? float(1.0 / 9.0) : 14913080.0f * 0x1p-29f);
+}
 
 // Storage precisions.  C is the arithmetic type.  The 16-bit formats ("shifted") hold,
 // per site and component, the deviations f_i - w_i R in 16 bits and the reference
@@ -93,6 +105,7 @@ struct StepParams {
     C gx, gy;             // body acceleration
     C kappa, theta;
     C log_floor;          // floor of rho^s / rho inside a logarithm
+    int bary;             // 1: barycentric u in the forcing's second moment, 0: u^s (Eq. ff3)
     C chi[NMAX * NMAX];
     C th_m[NMAX];         // theta / m^s
     C logc[NMAX];         // theta / m^s - 1/3: coefficient of ln rho^s in nu^s
@@ -122,6 +135,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
     p.kappa = C(P.kappa);
     p.theta = C(P.theta);
     p.log_floor = C(1e-12);
+    p.bary = P.forcing_velocity;
     p.log_mask = 0;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) p.chi[a * P.N + b] = C(P.chi[a * P.N + b]);

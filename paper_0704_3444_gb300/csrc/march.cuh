@@ -368,10 +368,11 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                     const C gy = Tn[c] - T2[c];
                     const C ax = -p.fcoef * (C(3) * gx) + p.gx;
                     const C ay = -p.fcoef * (C(3) * gy) + p.gy;
-                    C out[Q];
+                    C out[Q], fjx, fjy;
+                    forcing_momentum(p, R2[c], X2[c], Y2[c], ux2, uy2, fjx, fjy);
                     // 16-bit box stores: out_i is already the deviation f*_i - w_i M, with M
                     // the site's pre-collision mass rho^s, which the collision conserves
-                    collide(p, f, e, R2[c], X2[c], Y2[c], ax, ay, out,
+                    collide(p, f, e, R2[c], fjx, fjy, ax, ay, out,
                             G::CTA_STORE ? R2[c] : C(0));
                     if constexpr (G::TMA_STORE) {
                         if (lane >= 2 && lane < 30) {

@@ -35,6 +35,8 @@ struct Problem {
     double tau, theta, kappa, gx, gy;
     double chi[NMAX * NMAX];
     double m[NMAX];
+    int forcing_velocity;   // MCLB_FORCING_COMPONENT (0) or MCLB_FORCING_BARYCENTRIC (1)
+    int lattice;            // MCLB_D2Q9 (0) or MCLB_D1Q3 (1: ny = 1, layout [s][i][x], no ghosts)
     int withhold;           // test hook: the single-pass kernel issues no copies
     long long rbytes;       // 16-bit formats: byte offset of the FP32 density lines
                             // ([s][y][pitch], same ghosts) after the deviations; else 0
@@ -49,6 +51,7 @@ struct Scratch {
     double* partial;        // reduction partials
     size_t partial_cap;     // capacity in doubles
     unsigned int* status;   // device status bits (see STATUS_*)
+    void* line_item;        // D1Q3 handles: the device description the resident kernel reads
 };
 
 enum : unsigned int {
@@ -67,6 +70,40 @@ struct FusedPlan {
     size_t smem;
     bool ok;
 };
+
+// Kernels of the D1Q3 lattice (line3.cuh) for one storage type (FP64 and FP32 only).
+// Distributions: post-collision values [s][3][nx]; pre-collision f_i(x) = f*_i(x - v_i).
+struct Line3Table {
+    int (*max_resident)(int N);   // longest line the resident (shared-memory) kernel holds
+    size_t item_bytes;            // size of the device description at Scratch::line_item
+    // write the description of buffers f[0], f[1] to sc.line_item (synchronous)
+    cudaError_t (*prepare)(const Problem&, const Scratch&, void* const* f);
+    cudaError_t (*init)(const Problem&, const Scratch&, const double* rho, const double* u,
+                        void* f, cudaStream_t st);
+    // nsteps timesteps from f[*cur]; *cur receives the buffer holding the result
+    cudaError_t (*step)(const Problem&, const Scratch&, void* const* f, int* cur, long nsteps,
+                        cudaStream_t st);
+    cudaError_t (*moments)(const Problem&, const Scratch&, const void* f, double* rho,
+                           double* U, double* mu, double* P, cudaStream_t st);
+    cudaError_t (*conservation)(const Problem&, const Scratch&, const void* f, double* out,
+                                cudaStream_t st);
+    cudaError_t (*compositions)(const Problem&, const Scratch&, const void* f, double* phi,
+                                double* bulk, double tol, cudaStream_t st);
+    cudaError_t (*get_state)(const Problem&, const Scratch&, const void* f, double* out,
+                             cudaStream_t st);
+    cudaError_t (*set_state)(const Problem&, const Scratch&, const double* in, void* f,
+                             cudaStream_t st);
+    // batches: every line of one N; a step of k <= L3_CHUNK timesteps reads buffer
+    // `parity` of every line and leaves the result in buffer parity ^ 1 (lines that fit
+    // share one resident launch, one CTA each; longer ones step with the tile kernel)
+    void* (*batch_create)(int N, int count, const Problem* probs, const Scratch* scs,
+                          void* const* fa, void* const* fb, cudaStream_t st);
+    cudaError_t (*batch_step)(void* group, int parity, int nsteps, cudaStream_t st);
+    int (*batch_launches)(const void* group);
+    void (*batch_destroy)(void* group);
+};
+
+constexpr int LINE3_CHUNK = 4096;   // most timesteps one resident D1Q3 launch advances
 
 struct KernelTable {
     size_t storage_bytes;   // bytes of one stored distribution value
@@ -117,6 +154,7 @@ struct KernelTable {
     cudaError_t (*batch_tune)(void* group, int parity, cudaStream_t st);
     int (*batch_waves)(const void* group);      // waves of the partition in use, 0 if staged
     void (*batch_destroy)(void* group);
+    const Line3Table* line3;    // D1Q3 kernels (null for the 16-bit formats)
 };
 
 // Device checks of FP64 boundary data (checks.cu).  *first_bad receives the smallest

@@ -7,6 +7,7 @@
 // distributions are caller-owned device arrays in the compact pre-collision layout
 // of mclb_get_state ([s][i][y][x], FP64): f_in is read, f_out is written (streamed,
 // i.e. the pre-collision state of the next time level).
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -25,21 +26,32 @@ namespace {
 constexpr long long NOALLOC_MAX = MCLB_NOALLOC_MAX_COMP_SITES;
 static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX];
 
-// Device address of g_noalloc_scratch, resolved once per device (host code must not
-// pass the symbol itself to a kernel: on the host it only names a stand-in).
+// Device address of g_noalloc_scratch per device (host code must not pass the symbol
+// itself to a kernel: on the host it only names a stand-in).  It is looked up again on
+// every call made outside a stream capture, so that a device reset or a new context on
+// the same device (which reloads the module at another address) is followed; inside a
+// capture the address of the last call outside one is used.
 constexpr int MAX_DEVICES = 64;
 void* g_scratch_addr[MAX_DEVICES];
 std::mutex g_scratch_mu;
 
-int scratch_for_current_device(double** out)
+int scratch_for_current_device(cudaStream_t st, double** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();
         return report(MCLB_ECUDA, "mclb_step_noalloc: no usable CUDA device");
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return report(MCLB_ECUDA, "mclb_step_noalloc: cudaStreamIsCapturing failed");
+    }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cap != cudaStreamCaptureStatusNone && !g_scratch_addr[dev])
+        return report(MCLB_EINVAL, "mclb_step_noalloc: the first call on a device must come "
+                                   "before any stream capture");
+    if (cap == cudaStreamCaptureStatusNone) {
         void* ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) {
@@ -106,8 +118,9 @@ k_na_collide(const double* __restrict__ fin, double* __restrict__ fout, const do
     for (int s = 0; s < N; ++s) {
         double gx, gy;
         field_grad(nu + s * p.S, p, x, y, gx, gy);
-        double out[Q];
-        collide(p, f[s], e, r[s], jx[s], jy[s], -p.fcoef * gx + p.gx, -p.fcoef * gy + p.gy, out);
+        double out[Q], fjx, fjy;
+        forcing_momentum(p, r[s], jx[s], jy[s], jxt / rho, jyt / rho, fjx, fjy);
+        collide(p, f[s], e, r[s], fjx, fjy, -p.fcoef * gx + p.gx, -p.fcoef * gy + p.gy, out);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
@@ -140,9 +153,11 @@ extern "C" int mclb_step_noalloc(const mclb_params* params, const double* f_in, 
     if (rc) return rc;
     if (params->precision != MCLB_FP64)
         return report(MCLB_EINVAL, "mclb_step_noalloc: only precision MCLB_FP64 is supported");
-    if (!f_in || !f_out || f_in == f_out)
-        return report(MCLB_EINVAL, "mclb_step_noalloc: f_in and f_out must be distinct device arrays");
+    if (params->lattice != MCLB_D2Q9)
+        return report(MCLB_EINVAL, "mclb_step_noalloc: only the D2Q9 lattice is supported");
     const long long S = (long long)params->nx * params->ny;
+    if (!f_in || !f_out)
+        return report(MCLB_EINVAL, "mclb_step_noalloc: f_in and f_out must be device arrays");
     if ((long long)params->ncomp * S > NOALLOC_MAX) {
         char msg[256];
         snprintf(msg, sizeof(msg),
@@ -150,8 +165,16 @@ extern "C" int mclb_step_noalloc(const mclb_params* params, const double* f_in, 
                  (long long)params->ncomp * S, NOALLOC_MAX);
         return report(MCLB_EINVAL, msg);
     }
+    {
+        // the collision scatters into f_out while other threads still read f_in: the two
+        // ranges of N * 9 * nx * ny doubles must not overlap at all
+        const unsigned long long n = (unsigned long long)params->ncomp * Q * (unsigned long long)S;
+        const uintptr_t a = reinterpret_cast<uintptr_t>(f_in), b = reinterpret_cast<uintptr_t>(f_out);
+        if (a < b + n * sizeof(double) && b < a + n * sizeof(double))
+            return report(MCLB_EINVAL, "mclb_step_noalloc: f_in and f_out overlap");
+    }
     double* scratch = nullptr;
-    rc = scratch_for_current_device(&scratch);
+    rc = scratch_for_current_device((cudaStream_t)params->stream, &scratch);
     if (rc) return rc;
 
     Problem P;
@@ -167,6 +190,7 @@ extern "C" int mclb_step_noalloc(const mclb_params* params, const double* f_in, 
     P.kappa = params->kappa;
     P.gx = params->force[0];
     P.gy = params->force[1];
+    P.forcing_velocity = params->forcing_velocity;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) P.chi[a * P.N + b] = params->chi[a * P.N + b];
         P.m[a] = params->m ? params->m[a] : 1.0;

@@ -140,12 +140,15 @@ struct VDots {
 };
 
 // Velocity-dependent part of the equilibrium, shared by every component:
-// e_i = w_i (1 + 3 v_i.u + 9/2 (v_i.u)^2 - 3/2 u.u), so that f^{s,e}_i = rho^s e_i
-// (Sec. 3 equilibrium moments, all components built on the barycentric u).
+// e_i = w_i (3 v_i.u + 9/2 (v_i.u)^2 - 3/2 u.u), so that f^{s,e}_i = rho^s (w_i + e_i)
+// (Sec. 3 equilibrium moments, all components built on the barycentric u).  The constant
+// w_i is added by collide() through its forcing bracket, so that 1 - 3/2 u.u is never
+// rounded: in FP32 that rounding has a sign set by u and changed the component masses
+// systematically (by up to 3e-8 of the density per step).
 template <typename C>
 __device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
 {
-    const C base = C(1) - C(1.5) * (ux * ux + uy * uy);
+    const C base = C(-1.5) * (ux * ux + uy * uy);
     const VDots<C> du(ux, uy);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -158,20 +161,31 @@ __device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
     }
 }
 
+// Momentum of the forcing's second moment (Eq. ff3): j^s = rho^s u^s as printed, or
+// rho^s u with the barycentric u when the barycentric reading is selected.
+template <typename C>
+__device__ __forceinline__ void forcing_momentum(const StepParams<C>& p, C r, C jx, C jy, C ux,
+                                                 C uy, C& fx, C& fy)
+{
+    fx = p.bary ? r * ux : jx;
+    fy = p.bary ? r * uy : jy;
+}
+
 // Post-collision populations of one component (Eq. ssLB):
-//   f* = f + (f^e - f)/tau + F,  f^e_i = rho^s e_i,
-//   F_i = w_i [3 rho^s (v_i.a) + 9 (v_i.a)(v_i.j) - 3 a.j]   (Eqs. ff1-ff3, j = rho^s u^s),
-// evaluated as f (1 - 1/tau) + (rho^s/tau) e_i + w_i [(v_i.a)(9 v_i.j + 3 rho^s) - 3 a.j].
-// With a nonzero `shift` M it returns f*_i - w_i M instead (the deviations the 16-bit
-// formats store), the subtraction folded into the forcing bracket.
+//   f* = f + (f^e - f)/tau + F,  f^e_i = rho^s (w_i + e_i),
+//   F_i = w_i [3 rho^s (v_i.a) + 9 (v_i.a)(v_i.j) - 3 a.j]   (Eqs. ff1-ff3, j from
+//   forcing_momentum),
+// evaluated as f (1 - 1/tau) + (rho^s/tau) e_i + w_i [(v_i.a)(9 v_i.j + 3 rho^s) - 3 a.j
+// + rho^s/tau].  With a nonzero `shift` M it returns f*_i - w_i M instead (the deviations
+// the 16-bit formats store), the subtraction folded into the same bracket.
 template <typename C>
 __device__ __forceinline__ void collide(const StepParams<C>& p, const C (&f)[Q], const C (&e)[Q],
                                         C r, C jx, C jy, C ax, C ay, C (&out)[Q], C shift = C(0))
 {
     const VDots<C> da(ax, ay), dj(jx, jy);
-    const C m3aj = C(-3) * (ax * jx + ay * jy) - shift;
     const C r3 = C(3) * r;
     const C omr = p.omega * r;
+    const C m3aj = fma(C(-3), ax * jx + ay * jy, omr - shift);
     const C keep = C(1) - p.omega;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

@@ -154,8 +154,9 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
         field_grad(nu + s * p.S, p, x, y, gx, gy);
         const C ax = -p.fcoef * gx + p.gx;
         const C ay = -p.fcoef * gy + p.gy;
-        C out[Q];
-        collide(p, f[s], e, r[s], jx[s], jy[s], ax, ay, out);
+        C out[Q], fjx, fjy;
+        forcing_momentum(p, r[s], jx[s], jy[s], ux, uy, fjx, fjy);
+        collide(p, f[s], e, r[s], fjx, fjy, ax, ay, out);
         store_site(fout, p, s, y, x, out);
     }
     if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);

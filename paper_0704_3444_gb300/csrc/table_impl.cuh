@@ -5,6 +5,7 @@
 
 #include "batch.cuh"
 #include "ghosts.cuh"
+#include "line3.cuh"
 #include "march.cuh"
 #include "staged.cuh"
 
@@ -197,6 +198,247 @@ struct Launch {
     }
 };
 
+// Launchers of the D1Q3 kernels (line3.cuh) for one storage type.
+template <typename T>
+struct Line3Launch {
+    using C = typename Storage<T>::C;
+    static constexpr size_t SMEM_CAP = 227 * 1024 - sizeof(StepParams<C>) - 256;
+
+    static int max_resident(int N)
+    {
+        const size_t per = (size_t)5 * N * sizeof(C);
+        return (int)std::min<size_t>(SMEM_CAP / per, (size_t)L3_MAX_SITES);
+    }
+
+    static Line3Item<T> item(const Problem& P, const Scratch& sc, void* f0, void* f1)
+    {
+        Line3Item<T> it{};
+        it.p = make_params<C>(P, sc.status);
+        it.f[0] = (T*)f0;
+        it.f[1] = (T*)f1;
+        return it;
+    }
+
+    static cudaError_t prepare(const Problem& P, const Scratch& sc, void* const* f)
+    {
+        const Line3Item<T> it = item(P, sc, f[0], f[1]);
+        return cudaMemcpy(sc.line_item, &it, sizeof(it), cudaMemcpyHostToDevice);
+    }
+
+    template <int N>
+    static cudaError_t resident(const Line3Item<T>* items, int count, int nxmax, int parity,
+                                int nsteps, cudaStream_t st)
+    {
+        static const cudaError_t attr = cudaFuncSetAttribute(
+            k_line3_resident<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_CAP);
+        if (attr != cudaSuccess) return attr;
+        const size_t smem = Line3Smem<T, N>::bytes(nxmax);
+        const int threads = (nxmax + 31) / 32 * 32;
+        k_line3_resident<T, N><<<count, threads, smem, st>>>(items, parity, nsteps);
+        return cudaGetLastError();
+    }
+
+    template <int N>
+    static cudaError_t tile(const StepParams<C>& p, const void* fin, void* fout, cudaStream_t st)
+    {
+        const unsigned blocks = (unsigned)((p.nx + L3_TILE - 5) / (L3_TILE - 4));
+        k_line3_tile<T, N><<<blocks, L3_TILE, 0, st>>>((const T*)fin, (T*)fout, p);
+        return cudaGetLastError();
+    }
+
+    static unsigned line_blocks(int nx) { return (unsigned)((nx + SITE_THREADS - 1) / SITE_THREADS); }
+
+    static cudaError_t init(const Problem& P, const Scratch& sc, const double* rho, const double* u,
+                            void* f, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k_line3_init<T, NN><<<line_blocks(P.nx), SITE_THREADS, 0, st>>>(rho, u, (T*)f, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t step(const Problem& P, const Scratch& sc, void* const* f, int* cur,
+                            long nsteps, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        const bool res = P.nx <= max_resident(P.N);
+        MCLB_DISPATCH_N(P.N, {
+            while (nsteps > 0) {
+                cudaError_t e;
+                if (res) {
+                    const int k = (int)std::min<long>(nsteps, L3_CHUNK);
+                    e = resident<NN>((const Line3Item<T>*)sc.line_item, 1, P.nx, *cur, k, st);
+                    nsteps -= k;
+                } else {
+                    e = tile<NN>(p, f[*cur], f[*cur ^ 1], st);
+                    nsteps -= 1;
+                }
+                if (e != cudaSuccess) return e;
+                *cur ^= 1;
+            }
+            return cudaSuccess;
+        });
+    }
+
+    static cudaError_t moments(const Problem& P, const Scratch& sc, const void* f, double* rho,
+                               double* U, double* mu, double* Pt, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k_line3_moments<T, NN><<<line_blocks(P.nx), SITE_THREADS, 0, st>>>((const T*)f, rho, U,
+                                                                               mu, Pt, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t conservation(const Problem& P, const Scratch& sc, const void* f, double* out,
+                                    cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            if (sc.partial_cap < (size_t)REDUCE_BLOCKS * (NN + 4)) return cudaErrorInvalidValue;
+            k_line3_conservation<T, NN><<<REDUCE_BLOCKS, SITE_THREADS, 0, st>>>((const T*)f,
+                                                                                sc.partial, p);
+            k_reduce_partials<<<1, SITE_THREADS, 0, st>>>(sc.partial, REDUCE_BLOCKS, NN + 4, out);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t compositions(const Problem& P, const Scratch& sc, const void* f, double* phi,
+                                    double* bulk, double tol, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k_line3_compositions<T, NN><<<line_blocks(P.nx), SITE_THREADS, 0, st>>>(
+                (const T*)f, phi, bulk, tol, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t get_state(const Problem& P, const Scratch& sc, const void* f, double* out,
+                                 cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k_line3_get_state<T, NN><<<line_blocks(P.nx), SITE_THREADS, 0, st>>>((const T*)f, out, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t set_state(const Problem& P, const Scratch& sc, const double* in, void* f,
+                                 cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k_line3_set_state<T, NN><<<line_blocks(P.nx), SITE_THREADS, 0, st>>>(in, (T*)f, p);
+            return cudaGetLastError();
+        });
+    }
+
+    // ---- batches of lines with one N
+    struct Group {
+        int N = 0;
+        Line3Item<T>* d_items = nullptr;     // lines the resident kernel holds
+        int nres = 0, nxmax = 1;
+        std::vector<Line3Item<T>> longs;     // lines stepped with the tile kernel
+        std::vector<size_t> long_bytes;
+    };
+
+    static void* batch_create(int N, int count, const Problem* probs, const Scratch* scs,
+                              void* const* fa, void* const* fb, cudaStream_t st)
+    {
+        auto* g = new (std::nothrow) Group();
+        if (!g) return nullptr;
+        g->N = N;
+        std::vector<Line3Item<T>> res;
+        for (int k = 0; k < count; ++k) {
+            const Line3Item<T> it = item(probs[k], scs[k], fa[k], fb[k]);
+            if (probs[k].nx <= max_resident(N)) {
+                res.push_back(it);
+                g->nxmax = std::max(g->nxmax, probs[k].nx);
+            } else {
+                g->longs.push_back(it);
+                g->long_bytes.push_back((size_t)N * 3 * probs[k].nx * sizeof(T));
+            }
+        }
+        g->nres = (int)res.size();
+        if (g->nres > 0) {
+            if (cudaMalloc(&g->d_items, sizeof(Line3Item<T>) * res.size()) != cudaSuccess ||
+                cudaMemcpyAsync(g->d_items, res.data(), sizeof(Line3Item<T>) * res.size(),
+                                cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                cudaGetLastError();
+                batch_destroy(g);
+                return nullptr;
+            }
+        }
+        return g;
+    }
+
+    static cudaError_t batch_step(void* gv, int parity, int nsteps, cudaStream_t st)
+    {
+        auto* g = static_cast<Group*>(gv);
+        MCLB_DISPATCH_N(g->N, {
+            if (g->nres > 0) {
+                cudaError_t e = resident<NN>(g->d_items, g->nres, g->nxmax, parity, nsteps, st);
+                if (e != cudaSuccess) return e;
+            }
+            for (size_t k = 0; k < g->longs.size(); ++k) {
+                const Line3Item<T>& it = g->longs[k];
+                int c = parity;
+                for (int t = 0; t < nsteps; ++t, c ^= 1) {
+                    cudaError_t e = tile<NN>(it.p, it.f[c], it.f[c ^ 1], st);
+                    if (e != cudaSuccess) return e;
+                }
+                if (c == parity) {   // an even number of steps: the result goes to parity ^ 1
+                    cudaError_t e = cudaMemcpyAsync(it.f[parity ^ 1], it.f[parity], g->long_bytes[k],
+                                                    cudaMemcpyDeviceToDevice, st);
+                    if (e != cudaSuccess) return e;
+                }
+            }
+            return cudaSuccess;
+        });
+    }
+
+    static int batch_launches(const void* gv)
+    {
+        auto* g = static_cast<const Group*>(gv);
+        return (g->nres > 0 ? 1 : 0) + (int)g->longs.size();
+    }
+
+    static void batch_destroy(void* gv)
+    {
+        auto* g = static_cast<Group*>(gv);
+        if (!g) return;
+        if (g->d_items) cudaFree(g->d_items);
+        delete g;
+    }
+
+    static const Line3Table* table()
+    {
+        static const Line3Table t = [] {
+            Line3Table x{};
+            x.max_resident = &max_resident;
+            x.item_bytes = sizeof(Line3Item<T>);
+            x.prepare = &prepare;
+            x.init = &init;
+            x.step = &step;
+            x.moments = &moments;
+            x.conservation = &conservation;
+            x.compositions = &compositions;
+            x.get_state = &get_state;
+            x.set_state = &set_state;
+            x.batch_create = &batch_create;
+            x.batch_step = &batch_step;
+            x.batch_launches = &batch_launches;
+            x.batch_destroy = &batch_destroy;
+            return x;
+        }();
+        return &t;
+    }
+};
+
 template <typename T>
 inline KernelTable make_table(CUtensorMapDataType tt)
 {
@@ -220,6 +462,8 @@ inline KernelTable make_table(CUtensorMapDataType tt)
     t.batch_tune = &batch_group_tune<T>;
     t.batch_waves = &batch_group_waves<T>;
     t.batch_destroy = &batch_group_destroy<T>;
+    if constexpr (!Storage<T>::shifted) t.line3 = Line3Launch<T>::table();
+    else t.line3 = nullptr;
     return t;
 }
 

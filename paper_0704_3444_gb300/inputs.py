@@ -82,6 +82,8 @@ class Problem:
     steps: int = 0
     precision: str = "fp32"
     meta: dict = field(default_factory=dict)
+    forcing_velocity: int = 0      # 0: Eq. ff3 as printed, 1: barycentric reading
+    lattice: str = "d2q9"          # or "d1q3" (ny = 1)
 
     @property
     def sites(self) -> int:
@@ -147,6 +149,33 @@ def ternary_gauss(nx=256, ny=256, *, chi=2.4, tau=0.8, kappa=0.01, sigma=0.005, 
     s = nx * ny
     noise = np.stack([sigma * gaussian(seed, s, k) for k in range(3)])
     phi = (1.0 / 3.0 + _mass_neutral(noise)).reshape(3, ny, nx)
+    return _problem(name, 3, nx, ny, tau, uniform_chi(3, chi), phi, kappa=kappa, steps=steps,
+                    precision=precision)
+
+
+def ternary_droplets(nx=256, ny=256, *, chi=2.4, tau=0.8, kappa=0.01, sigma=0.005, seed=12,
+                     ndrop=6, steps=100, precision="fp32", name="ternary_droplets") -> Problem:
+    """The ternary workload's parameters (chi_ij = 2.4, tau = 0.8, kappa = 0.01) started
+    phase separated: `ndrop` discs rich in component 0, phi = (0.8, 0.15, 0.05), in a
+    matrix rich in component 1, (0.15, 0.8, 0.05), with tanh edges of width 2 and
+    Gaussian noise sigma made mass neutral; disc centres and radii (8..24) drawn from
+    the seed, periodic images included.  (At chi = 2.4 the A-B pair coexists near
+    0.17 / 0.83, so the discs stay: a state with interfaces everywhere.)
+    """
+    s = nx * ny
+    r = uniform(seed, 3 * ndrop, 5).reshape(ndrop, 3)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    inside = np.zeros((ny, nx))
+    for k in range(ndrop):
+        cx, cy, rad = r[k, 0] * nx, r[k, 1] * ny, 8.0 + 16.0 * r[k, 2]
+        dx = np.minimum(np.abs(x - cx), nx - np.abs(x - cx))
+        dy = np.minimum(np.abs(y - cy), ny - np.abs(y - cy))
+        w = 0.5 * (1.0 - np.tanh((np.sqrt(dx * dx + dy * dy) - rad) / 2.0))
+        inside = np.maximum(inside, w)
+    a, b = np.array([0.8, 0.15, 0.05]), np.array([0.15, 0.8, 0.05])
+    phi = a[:, None, None] * inside[None] + b[:, None, None] * (1.0 - inside[None])
+    noise = np.stack([sigma * gaussian(seed, s, k) for k in range(3)]).reshape(3, ny, nx)
+    phi = phi + _mass_neutral(noise)
     return _problem(name, 3, nx, ny, tau, uniform_chi(3, chi), phi, kappa=kappa, steps=steps,
                     precision=precision)
 

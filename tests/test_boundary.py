@@ -56,6 +56,10 @@ def _params(**kw):
     (dict(kappa=-1.0), "kappa"),
     (dict(precision=7), "precision"),
     (dict(kernel=5), "kernel"),
+    (dict(forcing_velocity=2), "forcing_velocity"),
+    (dict(lattice=2), "lattice"),
+    (dict(lattice="d1q3", ny=2), "ny = 1"),
+    (dict(lattice="d1q3", ny=1, precision="bf16"), "FP64 or FP32"),
 ])
 def test_invalid_parameters_are_rejected(lib, kw, frag):
     p, keep = _params(**kw)

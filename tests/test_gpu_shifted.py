@@ -11,7 +11,8 @@ R = M - sum_i d_i.  The tests check what that format promises and what it is for
   * Sec. 4 use: coexisting bulk compositions of a binary flat interface (chi = 2.2,
     40000 steps) and the densities of the polymer/solvent/non-solvent slab after 3000
     steps agree with the oracle to 1e-3, the accuracy asked of reduced-precision
-    storage; total mass of each component drifts by less than 1e-3 over 40000 steps.
+    storage; total mass of each component drifts by less than 2e-5 (BF16), 6e-5 (FP16)
+    and 1e-4 (FP32) over 40000 steps.
 """
 import numpy as np
 import pytest
@@ -78,12 +79,19 @@ def test_shifted_storage_bounds(precision, kernel):
     np.testing.assert_allclose(back.sum(axis=1), M[:, 0], rtol=1e-6, atol=0)
 
 
+MASS_DRIFT = {"bf16": 2e-5, "fp16": 6e-5, "fp32": 1e-4}
+
+
 @pytest.mark.parametrize("precision", SHIFTED + ["fp32"])
 def test_shifted_flat_interface_compositions(precision, flat_oracle):
     """Bulk compositions of the binary flat interface after 40000 steps match the
-    oracle's to 1e-3, and each component's mass drifts by less than 1e-3.  Only the
-    plateaus are compared: where the interfaces settle is decided by rounding (the
-    lattice is translation invariant), not by the method."""
+    oracle's to 1e-3, and each component's mass drifts by less than MASS_DRIFT (relative;
+    measured 8.5e-6 BF16, 3.0e-5 FP16, 1.6e-5 FP32 -- up to 6.9e-5 along the way).  The
+    FP32 weights sum to exactly 1 and the equilibrium's constant part is never rounded
+    with its velocity terms, so no rounding has a fixed sign; what remains is the
+    rounding of each site's sums, which repeats step after step once the state is
+    stationary.  Only the plateaus are compared: where the interfaces settle is decided by
+    rounding (the lattice is translation invariant), not by the method."""
     p, phi_ref = flat_oracle
     sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
     m0 = sim.conservation()["mass"]
@@ -94,7 +102,7 @@ def test_shifted_flat_interface_compositions(precision, flat_oracle):
     assert abs(phi.max() - phi_ref.max()) < 1e-3
     assert abs(phi.min() - phi_ref.min()) < 1e-3
     m1 = sim.conservation()["mass"]
-    assert np.all(np.abs(m1 / m0 - 1.0) < 1e-3)
+    assert np.all(np.abs(m1 / m0 - 1.0) < MASS_DRIFT[precision]), np.abs(m1 / m0 - 1.0)
 
 
 @pytest.mark.parametrize("precision", SHIFTED)
