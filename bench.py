@@ -86,14 +86,18 @@ def hbm_peak():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples (every 20 ms) of SM clock, utilisation and throttle reasons over a
+    window of GPU work; the summary keeps the samples taken under load (utilisation
+    >= 50 %)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "utilization.gpu")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 20):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
         self.path = None
 
@@ -103,7 +107,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -122,7 +126,7 @@ class ClockSampler:
         try:
             for line in open(self.path):
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 8:
+                if len(parts) >= 9:
                     rows.append(parts)
         finally:
             try:
@@ -137,6 +141,8 @@ class ClockSampler:
                 return float(x)
             except ValueError:
                 return None
+        total = len(rows)
+        rows = [r for r in rows if (num(r[8]) or 0.0) >= 50.0] or rows
         sm = [num(r[0]) for r in rows if num(r[0]) is not None]
         mx = [num(r[1]) for r in rows if num(r[1]) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -145,7 +151,8 @@ class ClockSampler:
         pw = [num(r[2]) for r in rows if num(r[2]) is not None]
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "power_w_max": max(pw) if pw else None, "samples": len(rows)}
+                "power_w_max": max(pw) if pw else None, "samples": len(rows),
+                "samples_total": total}
 
 
 def gpu_index(local_rank: int) -> int:
@@ -183,10 +190,15 @@ def job_rate(torch, dist, work, elapsed, world, device):
     return world * work / elapsed / 1e6, elapsed
 
 
-def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=50):
+def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=1000):
     """512 independent binary/ternary FP32 simulations of uneven size advanced together
-    (one batch handle, graph-replayed launches) against the same instances advanced one
-    after another, each with its own handle on the plain FP32 single-pass path."""
+    for the workload's 1000 steps (one batch handle, graph-replayed launches) against the
+    same instances advanced one after another, each with its own handle on the plain FP32
+    single-pass path.  Instances whose density turned non-finite are counted at the end
+    (the recipe's chi range reaches past the method's stability limit for its strongest
+    binaries); the rate is also given over the instances that stayed finite, and the
+    two-phase fits of those are compared between the batch and the single handles."""
+    import numpy as np
     from paper_0704_3444_gb300 import inputs
     probs = inputs.batch(512)
     work = sum(p.sites * p.ncomp for p in probs)
@@ -202,9 +214,8 @@ def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=50):
     torch.cuda.synchronize()
     tb = start.elapsed_time(stop) / 1e3
     per = b.status()[1]
-    diverged = [k for k, v in enumerate(per) if v != 0]
+    finite = [k for k, v in enumerate(per) if v == 0]
     launches = b.launches_per_step
-    b.close()
     sims = [mclb.Simulation.from_problem(p, precision="fp32", kernel=mclb.KERNEL_FUSED, stream=sptr)
             for p in probs]
     for sm in sims:
@@ -216,15 +227,33 @@ def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=50):
     stop.record(stream)
     torch.cuda.synchronize()
     ts = start.elapsed_time(stop) / 1e3
-    diverged_one = sum(1 for sm in sims if sm.status() != 0)
+    finite_one = [k for k, sm in enumerate(sims) if sm.status() == 0]
+    # two-phase bulk compositions of the instances that stayed finite and have separated
+    # into two phases (fitted phases at least 0.3 apart in some component: below that the
+    # two clusters only split the noise of a still mixed state), batch vs handles
+    fit_err, fitted = 0.0, 0
+    for k in sorted(set(finite) & set(finite_one)):
+        try:
+            fb = b.fit_equilibrium(k, 2)
+            fs = sims[k].fit_equilibrium(2)
+        except mclb.MclbError:       # no bulk site (still mixing): nothing to compare
+            continue
+        if min(np.max(np.abs(fb[0] - fb[1])), np.max(np.abs(fs[0] - fs[1]))) < 0.3:
+            continue
+        fit_err = max(fit_err, float(np.max(np.abs(fb - fs))))
+        fitted += 1
+    b.close()
     for sm in sims:
         sm.close()
+    work_finite = sum(probs[k].sites * probs[k].ncomp for k in finite)
     vb, vs = work * steps / tb / 1e6, work * steps / ts / 1e6
     return {"value": vb, "steps": steps, "instances": len(probs),
-            "diverged": len(diverged), "diverged_one_by_one": diverged_one,
+            "diverged": len(probs) - len(finite), "diverged_one_by_one": len(probs) - len(finite_one),
+            "value_finite_instances": work_finite * steps / tb / 1e6,
             "diverged_note": "binary instances with chi >= ~1.39 x critical leave the method's "
-                             "stability range at kappa = 0.01 (non-finite density); the same "
-                             "work is timed either way",
+                             "stability range at kappa = 0.01 (non-finite density) within the "
+                             "1000 steps; the same work is timed either way",
+            "fit_max_abs_diff_vs_one_by_one": fit_err, "fit_two_phase_instances_compared": fitted,
             "sites": sum(p.sites for p in probs), "launches_per_step": launches,
             "one_by_one_fp32_value": vs, "speedup_vs_one_by_one": vb / vs,
             "speedup_vs_fp32": vb / fp32_value}
@@ -334,32 +363,37 @@ def main():
     sim = mclb.Simulation.from_problem(prob, precision=args.precision, kernel=kern, stream=sptr)
     launches = sim.launches_per_step
     bytes_step = sim.bytes_per_step
+    # the clock sampler covers the warm-up, the timed steps, the end-to-end job and the
+    # variants: the timed region alone can be shorter than one sampling interval
+    clk = ClockSampler(gpu_index(local_rank))
+    clk.__enter__()
     sim.step(args.warmup)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(gpu_index(local_rank)) as clk:
-        start.record(stream)
-        sim.step(args.steps)
-        stop.record(stream)
-        torch.cuda.synchronize()
+    start.record(stream)
+    sim.step(args.steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
     elapsed = start.elapsed_time(stop) / 1e3
     value, elapsed = job_rate(torch, dist, S * N * args.steps, elapsed, world, "cuda")
     status = sim.status()
     if status != 0:
         raise SystemExit(f"device status {status} after the timed steps")
-    clocks = clk.summary()
     per_launch = elapsed / args.steps
     peak, peak_src = hbm_peak()
     achieved = bytes_step / per_launch / 1e9
     traffic = profiled_traffic() if args.precision == "fp32" and args.workload == "n5_2048x2048" else None
 
-    # end to end through the C ABI with host buffers: H2D of the initial fields from pinned
-    # memory, every step's status word back, and the final rho/U fields to the host
+    # end to end through the C ABI with host buffers, one job of the workload's horizon
+    # (2000 steps for the N = 5 workload, or --steps if longer): the initial fields from
+    # pinned memory to the device, every step's status word back (mclb_step returns the
+    # previous step's), and the final rho and U fields to the host
     e2e = None
     if not args.no_e2e:
+        job = max(args.steps, int(prob.steps or 0))
         rho_h = torch.from_numpy(prob.rho).pin_memory().numpy()
         u_h = torch.from_numpy(prob.u).pin_memory().numpy()
         out_rho = torch.empty(prob.rho.shape, dtype=torch.float64).pin_memory().numpy()
@@ -371,21 +405,25 @@ def main():
         sim2.status()
         t0 = time.perf_counter()
         sim2.init_fields(rho_h, u_h)
-        for _ in range(args.steps):
+        for _ in range(job):
             sim2.step(1)
         rc = sim2.lib.mclb_moments(sim2.h, mclb._dp(out_rho), mclb._dp(out_u), None, None)
         rc2 = sim2.status()
         t_e2e = time.perf_counter() - t0
         sim2.close()
         if rc == 0 and rc2 == 0:
-            io = (prob.rho.nbytes + prob.u.nbytes)
-            e2e = {"value": S * N * args.steps / t_e2e / 1e6 * world, "unit": UNIT,
-                   "h2d_bytes_per_step": io / args.steps,
-                   "d2h_bytes_per_step": 4 + io / args.steps}
+            h2d = prob.rho.nbytes + prob.u.nbytes
+            d2h = out_rho.nbytes + out_u.nbytes
+            e2e = {"value": S * N * job / t_e2e / 1e6 * world, "unit": UNIT,
+                   "h2d_bytes_per_step": h2d / job, "d2h_bytes_per_step": 4 + d2h / job,
+                   "job_steps": job,
+                   "note": "one job: upload of the initial fields, one mclb_step(1) call per "
+                           "step (each returns the previous step's 4-byte status word), "
+                           "download of rho and U; bytes per step are the job's copies / steps"}
 
     variants = {}
     if not args.no_variants and rank == 0 and args.precision == "fp32":
-        ks = min(args.steps, 500)
+        ks = 500
         for prec in ("bf16", "fp16"):
             v = mclb.Simulation.from_problem(prob, precision=prec, kernel=mclb.KERNEL_FUSED,
                                              stream=sptr)
@@ -398,12 +436,32 @@ def main():
             v.close()
         v = mclb.Simulation.from_problem(prob, precision="fp32", kernel=mclb.KERNEL_STAGED,
                                          stream=sptr)
-        t = time_steps(torch, v, min(ks, 200), args.warmup, stream)
+        t = time_steps(torch, v, 200, args.warmup, stream)
         variants["fp32_staged_3_launches"] = {
-            "value": S * N * min(ks, 200) / t / 1e6, "steps": min(ks, 200),
-            "speedup_vs_fp32": (S * N * min(ks, 200) / t / 1e6) / (value / world)}
+            "value": S * N * 200 / t / 1e6, "steps": 200,
+            "speedup_vs_fp32": (S * N * 200 / t / 1e6) / (value / world)}
         v.close()
+        # the 8192 x 2048 ternary slab (polymer / solvent against non-solvent) in FP32 and
+        # in BF16-shifted storage
+        slab = workloads()["slab_8192x2048"]()
+        slab_fp32 = None
+        for prec in ("fp32", "bf16"):
+            v = mclb.Simulation.from_problem(slab, precision=prec, kernel=mclb.KERNEL_FUSED,
+                                             stream=sptr)
+            t = time_steps(torch, v, 200, args.warmup, stream)
+            val = slab.sites * slab.ncomp * 200 / t / 1e6
+            slab_fp32 = val if prec == "fp32" else slab_fp32
+            variants[f"slab_8192x2048_{prec}"] = {
+                "value": val, "steps": 200, "status_ok": v.status() == 0,
+                "hbm_gbs_algorithmic": v.bytes_per_step / (t / 200) / 1e9,
+                "hbm_frac_of_measured": v.bytes_per_step / (t / 200) / 1e9 / peak,
+                "speedup_vs_fp32": val / slab_fp32}
+            v.close()
         variants["batched_512"] = run_batched(torch, mclb, sptr, stream, args.warmup, value / world)
+    clk.__exit__()
+    clocks = clk.summary()
+    clocks["window"] = ("nvidia-smi every 20 ms from the warm-up of the timed steps through "
+                        "the end-to-end job and the variants; samples at >= 50 % utilisation")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

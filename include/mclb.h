@@ -181,11 +181,11 @@ int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, doubl
 int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_sum);
 
 /* Mean compositions phi^s = rho^s / rho of the nphase bulk phases of the current
- * state: the compositions and the bulk mask (sites whose largest composition
- * difference to a neighbour is below 1e-3) are computed on the device in FP64; the
- * bulk sites are clustered on the host into nphase groups by k-means, group c
- * started at the bulk site richest in component c.  phi receives nphase*N values,
- * group c first.  nphase in 1..N.  Synchronises.  Errors: EHANDLE, EINVAL (nphase out
+ * state, all computed on the device in FP64: the compositions, the bulk mask (sites
+ * whose composition gradient is below 1e-3 in every component) and a k-means of the
+ * bulk sites into nphase groups, group c started at the bulk site richest in component
+ * c, with sums in a fixed order (the result is deterministic); only the nphase*N means
+ * come back.  phi receives nphase*N values, group c first.  nphase in 1..N.  Synchronises.  Errors: EHANDLE, EINVAL (nphase out
  * of range, no bulk site), ENOMEM, ECUDA.  Sec. 4 compares these coexisting
  * compositions with the Flory-Huggins binodal. */
 int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi);
@@ -285,6 +285,8 @@ int mclb_batch_step(mclb_batch b, long nsteps);
  * memory). */
 int mclb_batch_launches_per_step(mclb_batch b);
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P);
+/* mclb_fit_equilibrium of one instance (Sec. 4 coexisting compositions). */
+int mclb_batch_fit_equilibrium(mclb_batch b, int index, int nphase, double* phi);
 int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count);
 /* per_instance (count ints, may be NULL) receives each instance's status; the
  * return value is the first non-OK status or OK.  Synchronises. */

@@ -96,6 +96,7 @@ def load():
             "mclb_batch_step": ([H, ctypes.c_long], ctypes.c_int),
             "mclb_batch_moments": ([H, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
             "mclb_batch_get_state": ([H, ctypes.c_int, dp, ctypes.c_size_t], ctypes.c_int),
+            "mclb_batch_fit_equilibrium": ([H, ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
             "mclb_batch_status": ([H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "mclb_batch_bytes_per_step": ([H], ctypes.c_double),
             "mclb_batch_launches_per_step": ([H], ctypes.c_int),
@@ -329,6 +330,12 @@ class Batch:
         _check(self.lib.mclb_batch_moments(self.h, int(index), _dp(rho), _dp(U), None, None),
                "mclb_batch_moments")
         return dict(rho=rho, U=U)
+
+    def fit_equilibrium(self, index, nphase: int):
+        out = np.empty((nphase, self.problems[index].ncomp))
+        _check(self.lib.mclb_batch_fit_equilibrium(self.h, int(index), int(nphase), _dp(out)),
+               "mclb_batch_fit_equilibrium")
+        return out
 
     def get_state(self, index):
         pr = self.problems[index]

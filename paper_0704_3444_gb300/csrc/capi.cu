@@ -686,63 +686,21 @@ int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi)
     if (nphase < 1 || nphase > P.N || !phi)
         return fail(MCLB_EINVAL, "nphase=%d must be in 1..N=%d (phi non-NULL)", nphase, P.N);
     const long long S = P.S;
-    rc = ensure_dtmp(h, (size_t)(P.N + 1) * S);
+    rc = ensure_dtmp(h, (size_t)(P.N + 1) * S + fit_work_doubles());
     if (rc) return rc;
     double* d_phi = h->dtmp;
     double* d_bulk = h->dtmp + P.N * S;
+    double* d_work = d_bulk + S;
     if (h->line3)
         CK(h->line3->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
     else
         CK(h->tab->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
-    std::vector<double> hphi((size_t)P.N * S), hbulk(S);
-    CK(cudaMemcpyAsync(hphi.data(), d_phi, sizeof(double) * P.N * S, cudaMemcpyDeviceToHost,
-                       h->stream));
-    CK(cudaMemcpyAsync(hbulk.data(), d_bulk, sizeof(double) * S, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    // k-means over the bulk sites; phase c is seeded at the bulk site richest in component c
-    std::vector<double> cen((size_t)nphase * P.N);
-    long long nbulk = 0;
-    for (int c = 0; c < nphase; ++c) {
-        double best = -1.0;
-        long long arg = -1;
-        for (long long t = 0; t < S; ++t)
-            if (hbulk[t] > 0.5 && hphi[(size_t)c * S + t] > best) {
-                best = hphi[(size_t)c * S + t];
-                arg = t;
-            }
-        if (arg < 0) return fail(MCLB_EINVAL, "no bulk sites (composition gradients all >= 1e-3)");
-        for (int s = 0; s < P.N; ++s) cen[(size_t)c * P.N + s] = hphi[(size_t)s * S + arg];
-    }
-    std::vector<int> lab(S, -1);
-    for (int it = 0; it < 100; ++it) {
-        bool changed = false;
-        std::vector<double> acc((size_t)nphase * P.N, 0.0);
-        std::vector<long long> cnt(nphase, 0);
-        nbulk = 0;
-        for (long long t = 0; t < S; ++t) {
-            if (hbulk[t] < 0.5) continue;
-            ++nbulk;
-            int best = 0;
-            double bd = 1e300;
-            for (int c = 0; c < nphase; ++c) {
-                double d = 0.0;
-                for (int s = 0; s < P.N; ++s) {
-                    const double e = hphi[(size_t)s * S + t] - cen[(size_t)c * P.N + s];
-                    d += e * e;
-                }
-                if (d < bd) { bd = d; best = c; }
-            }
-            if (lab[t] != best) changed = true;
-            lab[t] = best;
-            ++cnt[best];
-            for (int s = 0; s < P.N; ++s) acc[(size_t)best * P.N + s] += hphi[(size_t)s * S + t];
-        }
-        for (int c = 0; c < nphase; ++c)
-            if (cnt[c] > 0)
-                for (int s = 0; s < P.N; ++s) cen[(size_t)c * P.N + s] = acc[(size_t)c * P.N + s] / cnt[c];
-        if (!changed) break;
-    }
-    memcpy(phi, cen.data(), sizeof(double) * nphase * P.N);
+    // k-means of the bulk sites on the device; only the centroids come back
+    std::vector<double> out((size_t)nphase * P.N + 1);
+    int found = 0;
+    CK(fit_phases(d_phi, d_bulk, P.N, S, nphase, d_work, out.data(), &found, h->stream));
+    if (!found) return fail(MCLB_EINVAL, "no bulk sites (composition gradients all >= 1e-3)");
+    memcpy(phi, out.data(), sizeof(double) * nphase * P.N);
     return MCLB_OK;
 }
 
@@ -1044,6 +1002,13 @@ int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* 
     mclb_handle h;
     int rc = batch_item(b, index, &h);
     return rc ? rc : mclb_moments(h, rho, U, mu, P);
+}
+
+int mclb_batch_fit_equilibrium(mclb_batch b, int index, int nphase, double* phi)
+{
+    mclb_handle h;
+    int rc = batch_item(b, index, &h);
+    return rc ? rc : mclb_fit_equilibrium(h, nphase, phi);
 }
 
 int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count)

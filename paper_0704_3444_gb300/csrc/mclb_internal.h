@@ -166,6 +166,14 @@ cudaError_t check_fields(const double* rho, const double* u, int N, long long S,
 cudaError_t check_finite(const double* a, long long n, unsigned long long* first_bad,
                          cudaStream_t st);
 
+// Bulk-phase fit on the device (fit.cu): k-means of the bulk sites' compositions into
+// nphase phases in FP64 with fixed-order sums.  phi: N * S, bulk: S (device).  work:
+// fit_work_doubles() device doubles.  host_out: nphase * N + 1 host doubles; receives the
+// centroids, phase c first.  *found = 0 if there is no bulk site.  Synchronises st.
+size_t fit_work_doubles();
+cudaError_t fit_phases(const double* phi, const double* bulk, int N, long long S, int nphase,
+                       double* work, double* host_out, int* found, cudaStream_t st);
+
 const KernelTable& table_fp64();
 const KernelTable& table_fp32();
 const KernelTable& table_bf16();

@@ -267,3 +267,43 @@ def test_batch_ternary_sweep_matches_oracle():
         gaps.append(np.max(np.abs(got[:, 0, nx // 2] - ties[k][0])))
     assert gaps[0] < gaps[1] < gaps[2], gaps
     b.close()
+
+
+def _fit_by_definition(rho, nphase):
+    """mclb_fit_equilibrium written out in numpy: compositions; bulk sites where every
+    component's D2Q9 gradient 3 sum_i w_i v_i phi(x + v_i) is below 1e-3 in magnitude;
+    k-means seeded at the bulk site richest in component c (first on ties), nearest
+    centroid by squared distance (lower phase on ties), until the centroids stop moving."""
+    phi = rho / rho.sum(0)
+    cx = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    cy = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    w = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+    gx = sum(3 * w[i] * cx[i] * np.roll(phi, (-cy[i], -cx[i]), axis=(1, 2)) for i in range(9))
+    gy = sum(3 * w[i] * cy[i] * np.roll(phi, (-cy[i], -cx[i]), axis=(1, 2)) for i in range(9))
+    bulk = np.all(gx * gx + gy * gy < 1e-6, axis=0).ravel()
+    pts = phi.reshape(phi.shape[0], -1)[:, bulk].T
+    cen = np.stack([pts[np.argmax(pts[:, c])] for c in range(nphase)])
+    for _ in range(100):
+        d = ((pts[:, None, :] - cen[None]) ** 2).sum(-1)
+        lab = np.argmin(d, axis=1)
+        new = np.stack([pts[lab == c].mean(0) if np.any(lab == c) else cen[c]
+                        for c in range(nphase)])
+        if np.array_equal(new, cen):
+            break
+        cen = new
+    return cen
+
+
+@pytest.mark.parametrize("nphase", [2, 3])
+def test_fit_equilibrium_matches_its_definition(nphase):
+    """The device k-means of mclb_fit_equilibrium against the same fit written out in
+    numpy on the handle's own densities (FP64 state of the ternary droplet workload after
+    1500 steps): equal to 1e-12 for two and three phases."""
+    p = inputs.ternary_droplets(256, 192)
+    sim = mclb.Simulation.from_problem(p, precision="fp64")
+    sim.step(1500)
+    assert sim.status() == 0
+    got = sim.fit_equilibrium(nphase)
+    want = _fit_by_definition(sim.moments(U=False, mu=False, P=False)["rho"], nphase)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
+    sim.close()

@@ -40,5 +40,8 @@ def test_bench_json_line():
     e2e = d["e2e"]
     assert e2e["unit"] == d["unit"] and e2e["value"] > 0
     assert e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
+    assert e2e["job_steps"] == 2000
+    assert abs(e2e["h2d_bytes_per_step"] - (5 + 2) * 2048 * 2048 * 8 / 2000) < 1e-6 * e2e["h2d_bytes_per_step"]
     assert d["gpu_launches"] == 2 * d["steps"]
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+    assert d["clocks"]["samples"] > 0 and d["clocks"]["sm_mhz"] > 0

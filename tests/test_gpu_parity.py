@@ -443,3 +443,25 @@ def test_n5_recipe_long_horizon_per_field():
         assert np.abs(g["rho"] - ref2000["rho"]).max() < brho, prec
         assert np.abs(g["mu"] - ref2000["mu"]).max() < bmu, prec
         sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_resume_equals_uninterrupted(precision, kernel):
+    """Checkpoint and resume: get_state after 37 steps, set_state into a new handle, and 45
+    more steps there (one 32-step graph chunk and 13 single steps, from the other buffer
+    parity) equal 45 more steps of the original handle, bitwise."""
+    p = inputs.ternary_droplets(128, 96)
+    a = mclb.Simulation.from_problem(p, precision=precision, kernel=kernel)
+    a.step(37)
+    f = a.get_state()
+    b = mclb.Simulation(p.ncomp, p.nx, p.ny, p.tau, p.chi, p.m, p.theta, p.kappa, p.force,
+                        precision, kernel)
+    b.set_state(f)
+    assert b.step_count == 0
+    a.step(45)
+    b.step(45)
+    assert a.status() == 0 and b.status() == 0
+    assert np.array_equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
