@@ -32,6 +32,8 @@
 // and the step waits for the slowest CTA.)
 #pragma once
 
+#include <type_traits>
+
 #include "tma.cuh"
 
 namespace mclb {
@@ -238,6 +240,8 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
         return v;
     };
 
+    // FP32 storage collides two components at a time with the packed pair instructions
+    constexpr bool PAIRS = std::is_same<T, float>::value && N >= 2;
     const C theta = p.theta, kappa6 = C(6) * p.kappa;
     const C c9 = C(1.0 / 9.0), c36 = C(1.0 / 36.0), c59 = C(5.0 / 9.0);
 
@@ -342,8 +346,6 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                     if (lane == 0) bulk_wait_read();
                     __syncwarp();
                 }
-                C e[Q];
-                eq_weights(ux2, uy2, e);
                 [[maybe_unused]] const RLines Lc = rlines(k - 2);
                 if constexpr (G::CTA_STORE && G::NB == 1) {
                     // the box stored one row earlier has left the staging buffer
@@ -358,22 +360,9 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                         }
                     }
                 }
-#pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    const int s = c;
-                    C f[Q];
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) f[i] = pulled(sc, Lc, i, s);
-                    const C gx = GX[c] + Dn[c] * c36;
-                    const C gy = Tn[c] - T2[c];
-                    const C ax = -p.fcoef * (C(3) * gx) + p.gx;
-                    const C ay = -p.fcoef * (C(3) * gy) + p.gy;
-                    C out[Q], fjx, fjy;
-                    forcing_momentum(p, R2[c], X2[c], Y2[c], ux2, uy2, fjx, fjy);
-                    // 16-bit box stores: out_i is already the deviation f*_i - w_i M, with M
-                    // the site's pre-collision mass rho^s, which the collision conserves
-                    collide(p, f, e, R2[c], fjx, fjy, ax, ay, out,
-                            G::CTA_STORE ? R2[c] : C(0));
+                // post-collision values of component s to the store path of this format
+                auto store_out = [&](const int s, C (&out)[Q]) {
+                    const int c = s;
                     if constexpr (G::TMA_STORE) {
                         if (lane >= 2 && lane < 30) {
 #pragma unroll
@@ -399,20 +388,86 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                         }
                     } else if (out_lane) {
                         T* line = fout + line_off(p, s, r, 0) + G::HX;
-                        [[maybe_unused]] C rref = C(0);
                         if constexpr (G::SHIFTED) {
-                            const C M = R2[c];   // pre-collision mass, conserved by the collision
+                            // out_i is the deviation f*_i - w_i M already (see below): rounded
+                            // once, stored, and summed for the compensated reference density
+                            const C M = R2[c];
                             C dsum = C(0);
 #pragma unroll
                             for (int i = 0; i < Q; ++i) {
-                                out[i] = Storage<T>::round(out[i] - wq<C>(i) * M);
-                                dsum += out[i];
+                                const T d = Storage<T>::pack(out[i]);
+                                dsum = add_wide<T>(dsum, d);
+                                line[i * p.pitch + X] = d;
                             }
-                            rref = M - dsum;
-                        }
+                            rho_line(fout, p, s, r)[G::HX + X] = float(M - dsum);
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < Q; ++i) Storage<T>::store(line + i * p.pitch + X, out[i]);
-                        if constexpr (G::SHIFTED) rho_line(fout, p, s, r)[G::HX + X] = rref;
+                            for (int i = 0; i < Q; ++i) Storage<T>::store(line + i * p.pitch + X, out[i]);
+                        }
+                    }
+                };
+                // acceleration a^s of row r (Eq. definef plus the body force)
+                auto accel = [&](const int c, C& ax, C& ay) {
+                    const C gx = GX[c] + Dn[c] * c36;
+                    const C gy = Tn[c] - T2[c];
+                    ax = -p.fcoef * (C(3) * gx) + p.gx;
+                    ay = -p.fcoef * (C(3) * gy) + p.gy;
+                };
+                // 16-bit formats: out_i is already the deviation f*_i - w_i M, with M the
+                // site's pre-collision mass rho^s, which the collision conserves
+                if constexpr (PAIRS) {
+                    // FP32: components (c, c + 1) together with the packed pair instructions
+                    float2 e2[Q];
+                    eq_weights2(ux2, uy2, e2);
+#pragma unroll
+                    for (int c = 0; c + 1 < N; c += 2) {
+                        float2 f2[Q], out2[Q];
+#pragma unroll
+                        for (int i = 0; i < Q; ++i)
+                            f2[i] = make_float2(pulled(sc, Lc, i, c), pulled(sc, Lc, i, c + 1));
+                        C ax0, ay0, ax1, ay1, jx0, jy0, jx1, jy1;
+                        accel(c, ax0, ay0);
+                        accel(c + 1, ax1, ay1);
+                        forcing_momentum(p, R2[c], X2[c], Y2[c], ux2, uy2, jx0, jy0);
+                        forcing_momentum(p, R2[c + 1], X2[c + 1], Y2[c + 1], ux2, uy2, jx1, jy1);
+                        const float2 r2 = make_float2(R2[c], R2[c + 1]);
+                        collide2(p, f2, e2, r2, make_float2(jx0, jx1), make_float2(jy0, jy1),
+                                 make_float2(ax0, ax1), make_float2(ay0, ay1), out2,
+                                 G::SHIFTED ? r2 : pdup(0.0f));
+                        C o0[Q], o1[Q];
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            o0[i] = out2[i].x;
+                            o1[i] = out2[i].y;
+                        }
+                        store_out(c, o0);
+                        store_out(c + 1, o1);
+                    }
+                    if constexpr (N % 2 == 1) {
+                        constexpr int c = N - 1;
+                        C f[Q], e[Q], out[Q], ax, ay, fjx, fjy;
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) {
+                            f[i] = pulled(sc, Lc, i, c);
+                            e[i] = e2[i].x;
+                        }
+                        accel(c, ax, ay);
+                        forcing_momentum(p, R2[c], X2[c], Y2[c], ux2, uy2, fjx, fjy);
+                        collide(p, f, e, R2[c], fjx, fjy, ax, ay, out, G::SHIFTED ? R2[c] : C(0));
+                        store_out(c, out);
+                    }
+                } else {
+                    C e[Q];
+                    eq_weights(ux2, uy2, e);
+#pragma unroll
+                    for (int c = 0; c < N; ++c) {
+                        C f[Q], out[Q], ax, ay, fjx, fjy;
+#pragma unroll
+                        for (int i = 0; i < Q; ++i) f[i] = pulled(sc, Lc, i, c);
+                        accel(c, ax, ay);
+                        forcing_momentum(p, R2[c], X2[c], Y2[c], ux2, uy2, fjx, fjy);
+                        collide(p, f, e, R2[c], fjx, fjy, ax, ay, out, G::SHIFTED ? R2[c] : C(0));
+                        store_out(c, out);
                     }
                 }
             }

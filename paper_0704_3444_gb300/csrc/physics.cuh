@@ -195,4 +195,66 @@ __device__ __forceinline__ void collide(const StepParams<C>& p, const C (&f)[Q],
     }
 }
 
+// ---------------------------------------------------------------- component pairs
+//
+// In FP32 two components of a site are collided together with the packed pair
+// instructions of sm_100 and later (fma/add/mul .f32x2: one instruction for both), which
+// halves the issue slots of the collision.  The pair layout is (component c, c + 1).
+
+__device__ __forceinline__ float2 pdup(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// eq_weights for a pair of components: the same per-site values in both halves.
+__device__ __forceinline__ void eq_weights2(float ux, float uy, float2 (&e)[Q])
+{
+    const float2 u = pdup(ux), v = pdup(uy);
+    const float2 base = pmul(pdup(-1.5f), pfma(u, u, pmul(v, v)));
+    const float2 sp = padd(u, v), sm = pfma(v, pdup(-1.0f), u);
+    const float2 k45 = pdup(4.5f), k3 = pdup(3.0f), km3 = pdup(-3.0f);
+    e[0] = pmul(pdup(wq<float>(0)), base);
+    // v_i . u and its opposite -v_i . u share (v_i.u)^2: 4.5 x^2 + 3 x and 4.5 x^2 - 3 x
+    auto two = [&](int i, int j, float2 x) {
+        const float2 q = pfma(pmul(k45, x), x, base);
+        e[i] = pmul(pdup(wq<float>(i)), pfma(k3, x, q));
+        e[j] = pmul(pdup(wq<float>(j)), pfma(km3, x, q));
+    };
+    two(1, 3, u);
+    two(2, 4, v);
+    two(5, 7, sp);
+    two(8, 6, sm);
+}
+
+// collide() for the pair of components (c, c + 1): every argument but e holds the two
+// components' values.  The opposite velocity of i gets the same bracket with the sign of
+// the 3 rho^s term flipped, (-v.a)(9 (-v.j) + 3 rho) = (v.a)(9 v.j - 3 rho), so no operand
+// needs negating.
+__device__ __forceinline__ void collide2(const StepParams<float>& p, const float2 (&f)[Q],
+                                         const float2 (&e)[Q], float2 r, float2 jx, float2 jy,
+                                         float2 ax, float2 ay, float2 (&out)[Q], float2 shift)
+{
+    const float2 mone = pdup(-1.0f);
+    const float2 sa = padd(ax, ay), da = pfma(ay, mone, ax);
+    const float2 sj = padd(jx, jy), dj = pfma(jy, mone, jx);
+    const float2 omr = pmul(pdup(p.omega), r);
+    const float2 r3 = pmul(pdup(3.0f), r), r3n = pmul(pdup(-3.0f), r);
+    const float2 aj = pfma(ay, jy, pmul(ax, jx));
+    const float2 m3aj = pfma(pdup(-3.0f), aj, pfma(shift, mone, omr));
+    const float2 keep = pdup(1.0f - p.omega), nine = pdup(9.0f);
+    out[0] = pfma(keep, f[0], pfma(omr, e[0], pmul(pdup(wq<float>(0)), m3aj)));
+    auto term = [&](int i, float2 a, float2 j, float2 r3s) {
+        const float2 F = pmul(pdup(wq<float>(i)), pfma(a, pfma(nine, j, r3s), m3aj));
+        out[i] = pfma(keep, f[i], pfma(omr, e[i], F));
+    };
+    term(1, ax, jx, r3);
+    term(3, ax, jx, r3n);
+    term(2, ay, jy, r3);
+    term(4, ay, jy, r3n);
+    term(5, sa, sj, r3);
+    term(7, sa, sj, r3n);
+    term(8, da, dj, r3);
+    term(6, da, dj, r3n);
+}
+
 }  // namespace mclb
