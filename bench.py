@@ -335,6 +335,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run only the 512-instance batch variant and print its record")
+    ap.add_argument("--batch-steps", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -356,6 +359,10 @@ def main():
     mclb.load()
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
+    if args.only_batch:
+        print(json.dumps(run_batched(torch, mclb, sptr, stream, args.warmup, float("nan"),
+                                     args.batch_steps)), flush=True)
+        return
     prob = workloads()[args.workload]()
     N, S = prob.ncomp, prob.sites
 
