@@ -13,7 +13,9 @@ Two lattices: D2Q9 (the two-dimensional workloads) and D1Q3, the lattice of the
 paper's own simulations (Sec. 4), each a plain path of its own in the C file.
 Two readings of the velocity in the forcing's second moment (Eq. ff3):
 ``forcing_velocity=0`` is the component velocity u^s as printed (the default),
-``forcing_velocity=1`` the barycentric u.
+``forcing_velocity=1`` the barycentric u.  Two readings of the sum of the component
+forces of Eq. definef: ``force_form=0`` as printed (the default), ``force_form=1`` the
+Gibbs-Duhem total (kappa = 0 only).
 
 Parity unpinned: none of the lattice-update functions; every stage is pinned
 by tests against moment conditions, closed forms and independent numpy
@@ -49,7 +51,7 @@ class OracleParams(ctypes.Structure):
                 ("tau", ctypes.c_double), ("theta", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
                 ("chi", ctypes.c_double * (NMAX * NMAX)), ("m", ctypes.c_double * NMAX),
-                ("forcing_velocity", ctypes.c_int)]
+                ("forcing_velocity", ctypes.c_int), ("force_form", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -114,7 +116,7 @@ class Oracle:
     """
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
-                 force=(0.0, 0.0), forcing_velocity=0, lattice="d2q9"):
+                 force=(0.0, 0.0), forcing_velocity=0, lattice="d2q9", force_form=0):
         if lattice not in ("d2q9", "d1q3"):
             raise ValueError(f"lattice {lattice!r}")
         if lattice == "d1q3" and int(ny) != 1:
@@ -133,6 +135,7 @@ class Oracle:
         for a in range(ncomp):
             p.m[a] = m[a]
         p.forcing_velocity = int(forcing_velocity)
+        p.force_form = int(force_form)
         self.p = p
         self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
         self.f = (np.zeros((ncomp, 3, nx)) if lattice == "d1q3"
@@ -142,7 +145,7 @@ class Oracle:
     def from_problem(cls, prob):
         o = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
                 prob.kappa, prob.force, getattr(prob, "forcing_velocity", 0),
-                getattr(prob, "lattice", "d2q9"))
+                getattr(prob, "lattice", "d2q9"), getattr(prob, "force_form", 0))
         o.init(prob.rho, prob.u)
         return o
 

@@ -40,6 +40,9 @@
  *     max(rho^s, 1e-12 rho);
  *   - f^e is built with the bare barycentric u, F with rho^s u^s = j^s as
  *     Eq. ff3 prints it (or, when forcing_velocity = 1, with rho^s u);
+ *   - the forces are those of Eq. definef for each component (or, when
+ *     force_form = 1 and kappa = 0, shifted so that their sum is the Gibbs-Duhem
+ *     total (1 - 1/(2 tau)) (1/3) grad rho);
  *     the output velocity is U = u + a/2 with rho a = sum_s rho^s a^s;
  *   - initial distributions are the equilibria of the given fields.
  *
@@ -62,12 +65,18 @@
  * (Eq. ff3): 0 = the component velocity u^s as printed, rho^s (a^s u^s + u^s a^s);
  * 1 = the barycentric u, rho^s (a^s u + u a^s), the form whose sum over the
  * components is the one-fluid forcing moment rho (a u + u a) (Eq. olso). */
+/* force_form selects how the component forces of Eq. definef are summed: 0 = each
+ * component's force as Eq. definef prints it; 1 = the Gibbs-Duhem reading (kappa = 0
+ * only): the forces keep their differences but their sum over the components is
+ * replaced by the continuum total that Gibbs-Duhem gives for the Flory-Huggins free
+ * energy (whose pressure sum rho mu - psi vanishes), (1 - 1/(2 tau)) (1/3) grad rho. */
 typedef struct {
     int ncomp, nx, ny;
     double tau, theta, kappa, gx, gy;
     double chi[OR_NMAX * OR_NMAX];
     double m[OR_NMAX];
     int forcing_velocity;
+    int force_form;
 } oracle_params;
 
 static const int VX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -90,6 +99,8 @@ static int check(const oracle_params* p)
     if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1 || p->ny < 1) return -1;
     if (!(p->tau > 0.5)) return -1;
     if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
+    if (p->force_form != 0 && p->force_form != 1) return -1;
+    if (p->force_form == 1 && p->kappa != 0.0) return -1;
     return 0;
 }
 
@@ -307,6 +318,29 @@ static void stage_forces(const oracle_params* p, work_t* w)
             }
         }
     }
+    if (p->force_form == 1) {
+        /* Gibbs-Duhem reading: every a^s shifted by the same (A_c - A)/rho, where
+         * A = sum_s rho^s (a^s - g) and A_c = (1 - 1/(2 tau)) (1/3) grad rho, so that the
+         * components' forces sum to A_c + rho g and their differences are kept */
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                long c = (long)y * nx + x;
+                double Ax = 0.0, Ay = 0.0, gx, gy;
+                for (int s = 0; s < N; ++s) {
+                    Ax += w->rs[s * S + c] * (w->ax[s * S + c] - p->gx);
+                    Ay += w->rs[s * S + c] * (w->ay[s * S + c] - p->gy);
+                }
+                grad_at(w->rho, nx, ny, x, y, &gx, &gy);
+                double dx = (coef * gx / 3.0 - Ax) / w->rho[c];
+                double dy = (coef * gy / 3.0 - Ay) / w->rho[c];
+                for (int s = 0; s < N; ++s) {
+                    w->ax[s * S + c] += dx;
+                    w->ay[s * S + c] += dy;
+                }
+            }
+        }
+    }
 }
 
 /* Stages 4 and 5: BGK collision with forcing, then streaming (Eq. ssLB). */
@@ -493,6 +527,8 @@ static int check1(const oracle_params* p)
     if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1) return -1;
     if (!(p->tau > 0.5)) return -1;
     if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
+    if (p->force_form != 0 && p->force_form != 1) return -1;
+    if (p->force_form == 1 && p->kappa != 0.0) return -1;
     return 0;
 }
 
@@ -601,6 +637,14 @@ static void d1_fields(const oracle_params* p, const double* f, work1_t* w)
     for (int x = 0; x < nx; ++x)
         for (int s = 0; s < N; ++s)
             w->a[s * nx + x] = -coef * d1_grad(w->nu + s * nx, nx, x) + p->gx;
+    if (p->force_form == 1) {   /* Gibbs-Duhem reading, as in stage_forces */
+        for (int x = 0; x < nx; ++x) {
+            double A = 0.0;
+            for (int s = 0; s < N; ++s) A += w->rs[s * nx + x] * (w->a[s * nx + x] - p->gx);
+            double d = (coef * d1_grad(w->rho, nx, x) / 3.0 - A) / w->rho[x];
+            for (int s = 0; s < N; ++s) w->a[s * nx + x] += d;
+        }
+    }
 }
 
 /* f(x, 0) = f^e(rho^s(x), u(x)); u may be NULL (rest). */

@@ -16,6 +16,9 @@ a disagreement:
 * ``bary=True`` puts the barycentric u in place of the component velocity in the
   forcing's second moment (rho^s (a^s u + u a^s) instead of Eq. ff3's
   rho^s (a^s u^s + u^s a^s));
+* ``gd=True`` (kappa = 0) keeps the differences of the component accelerations and
+  makes their density-weighted sum the Gibbs-Duhem total (1 - 1/(2 tau)) (1/3) grad rho
+  (plus rho g), by adding the same vector to every a^s;
 * streaming uses numpy.roll, the stencils are the explicit 9-point forms.
 """
 from __future__ import annotations
@@ -92,7 +95,7 @@ def hermite2(zeroth, first, second):
     return np.stack(out)
 
 
-def step_d2q9(f, chi, m, theta, kappa, tau, g=(0.0, 0.0), bary=False):
+def step_d2q9(f, chi, m, theta, kappa, tau, g=(0.0, 0.0), bary=False, gd=False):
     """One update of f (N, 9, ny, nx) by the alternative formulation above."""
     N = f.shape[0]
     rs = f.sum(1)
@@ -102,11 +105,21 @@ def step_d2q9(f, chi, m, theta, kappa, tau, g=(0.0, 0.0), bary=False):
     ux, uy = jx.sum(0) / rho, jy.sum(0) / rho
     mu = mu_complex_step(rs, chi, m, theta)
     fnew = np.empty_like(f)
+    c = 1.0 - 1.0 / (2.0 * tau)
+    acc = []
     for s in range(N):
         nu = mu[s] - kappa * lap9(rs[s]) - np.log(rs[s]) / 3.0
         gx, gy = grad9(nu)
-        c = 1.0 - 1.0 / (2.0 * tau)
-        ax, ay = -c * gx + g[0], -c * gy + g[1]
+        acc.append([-c * gx, -c * gy])
+    if gd:
+        Ax = sum(rs[s] * acc[s][0] for s in range(N))
+        Ay = sum(rs[s] * acc[s][1] for s in range(N))
+        rgx, rgy = grad9(rho)
+        for s in range(N):
+            acc[s][0] = acc[s][0] + (c * rgx / 3.0 - Ax) / rho
+            acc[s][1] = acc[s][1] + (c * rgy / 3.0 - Ay) / rho
+    for s in range(N):
+        ax, ay = acc[s][0] + g[0], acc[s][1] + g[1]
         feq = hermite2(rs[s], (rs[s] * ux, rs[s] * uy),
                        [[rs[s] / 3 + rs[s] * ux * ux, rs[s] * ux * uy],
                         [rs[s] * uy * ux, rs[s] / 3 + rs[s] * uy * uy]])
@@ -141,7 +154,7 @@ def d1q3_init(rho_s, u):
     return np.stack([d1q3_equilibrium(rho_s[s], u) for s in range(rho_s.shape[0])])
 
 
-def d1q3_step(f, chi, m, theta, kappa, tau, g=0.0, bary=False):
+def d1q3_step(f, chi, m, theta, kappa, tau, g=0.0, bary=False, gd=False):
     """One update of f (N, 3, nx) on the D1Q3 lattice of Sec. 4 (velocities -1, 0, +1)."""
     N = f.shape[0]
     v = np.array([-1.0, 0.0, 1.0])
@@ -151,11 +164,18 @@ def d1q3_step(f, chi, m, theta, kappa, tau, g=0.0, bary=False):
     u = j.sum(0) / rho
     mu = mu_complex_step(rs, chi, m, theta)
     out = np.empty_like(f)
+    c = 1.0 - 1.0 / (2.0 * tau)
+    d1 = lambda q: (np.roll(q, -1) - np.roll(q, 1)) / 2.0
+    acc = []
     for s in range(N):
         lap = np.roll(rs[s], -1) + np.roll(rs[s], 1) - 2 * rs[s]
         nu = mu[s] - kappa * lap - np.log(rs[s]) / 3.0
-        grad = (np.roll(nu, -1) - np.roll(nu, 1)) / 2.0
-        a = -(1.0 - 1.0 / (2.0 * tau)) * grad + g
+        acc.append(-c * d1(nu))
+    if gd:
+        A = sum(rs[s] * acc[s] for s in range(N))
+        acc = [a + (c * d1(rho) / 3.0 - A) / rho for a in acc]
+    for s in range(N):
+        a = acc[s] + g
         js = rs[s] * u if bary else j[s]
         post = f[s] + (d1q3_equilibrium(rs[s], u) - f[s]) / tau + d1q3_forcing(rs[s], js, a)
         out[s, 0] = np.roll(post[0], -1)
