@@ -87,6 +87,20 @@ typedef enum {
                                      after Eq. olso calls the difference higher order     */
 } mclb_forcing_velocity;
 
+/* How the component forces of Eq. definef are summed. */
+typedef enum {
+    MCLB_FORCE_COMPONENT = 0,     /* each component's force as Eq. definef prints it (the
+                                     default)                                              */
+    MCLB_FORCE_GIBBS_DUHEM = 1    /* a reading for kappa = 0 (the paper's setting): every
+                                     component's acceleration gets the same shift, so that
+                                     their differences are kept and their density-weighted
+                                     sum is the continuum total (1 - 1/(2 tau)) (1/3) grad rho
+                                     that Gibbs-Duhem gives for the Flory-Huggins free energy
+                                     (its pressure sum rho mu - psi vanishes); the total force
+                                     is then a discrete gradient and total momentum is kept.
+                                     Runs on the staged schedule (D2Q9) and on D1Q3          */
+} mclb_force_form;
+
 /* Lattice. */
 typedef enum {
     MCLB_D2Q9 = 0,   /* two-dimensional, nine velocities (see the conventions above)      */
@@ -109,7 +123,8 @@ typedef enum {
  *   kernel     mclb_kernel
  *   stream     cudaStream_t to order all work on, or NULL
  *   forcing_velocity  mclb_forcing_velocity (0: Eq. ff3 as printed)
- *   lattice    mclb_lattice (0: D2Q9) */
+ *   lattice    mclb_lattice (0: D2Q9)
+ *   force_form mclb_force_form (0: Eq. definef as printed) */
 typedef struct {
     int ncomp;
     int nx, ny;
@@ -124,6 +139,7 @@ typedef struct {
     void* stream;
     int forcing_velocity;
     int lattice;
+    int force_form;
 } mclb_params;
 
 typedef struct mclb_handle_s* mclb_handle;

@@ -24,11 +24,12 @@ from ._build import build as _build
 
 __all__ = ["build", "load", "Simulation", "Batch", "MclbError", "FP64", "FP32", "BF16_SHIFTED",
            "FP16_SHIFTED", "KERNEL_AUTO", "KERNEL_FUSED", "KERNEL_STAGED", "FORCING_COMPONENT",
-           "FORCING_BARYCENTRIC", "D2Q9", "D1Q3"]
+           "FORCING_BARYCENTRIC", "FORCE_COMPONENT", "FORCE_GIBBS_DUHEM", "D2Q9", "D1Q3"]
 
 FP64, FP32, BF16_SHIFTED, FP16_SHIFTED = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_STAGED = 0, 1, 2
 FORCING_COMPONENT, FORCING_BARYCENTRIC = 0, 1
+FORCE_COMPONENT, FORCE_GIBBS_DUHEM = 0, 1
 D2Q9, D1Q3 = 0, 1
 LATTICES = {"d2q9": D2Q9, "d1q3": D1Q3}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SHIFTED, "fp16": FP16_SHIFTED}
@@ -53,7 +54,7 @@ class mclb_params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("force", ctypes.c_double * 2),
                 ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("forcing_velocity", ctypes.c_int),
-                ("lattice", ctypes.c_int)]
+                ("lattice", ctypes.c_int), ("force_form", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -150,7 +151,7 @@ def _fields(rho, u, ncomp, ny, nx, device=False):
 
 def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, force=(0.0, 0.0),
                 precision="fp32", kernel=KERNEL_AUTO, stream=None, forcing_velocity=0,
-                lattice="d2q9"):
+                lattice="d2q9", force_form=0):
     """Build an mclb_params struct; returns (struct, keep-alive arrays)."""
     chi = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp))
     marr = None if m is None else np.ascontiguousarray(np.asarray(m, dtype=np.float64))
@@ -165,6 +166,7 @@ def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, for
     p.stream = ctypes.c_void_p(stream) if stream else None
     p.forcing_velocity = int(forcing_velocity)
     p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    p.force_form = int(force_form)
     return p, (chi, marr)
 
 
@@ -173,11 +175,11 @@ class Simulation:
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
                  force=(0.0, 0.0), precision="fp32", kernel=KERNEL_AUTO, stream=None,
-                 forcing_velocity=0, lattice="d2q9"):
+                 forcing_velocity=0, lattice="d2q9", force_form=0):
         self.lib = load()
         self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
         p, keep = make_params(ncomp, nx, ny, tau, chi, m, theta, kappa, force, precision, kernel,
-                              stream, forcing_velocity, lattice)
+                              stream, forcing_velocity, lattice, force_form)
         self.q = 3 if p.lattice == D1Q3 else 9
         h = ctypes.c_void_p()
         _check(self.lib.mclb_create(ctypes.byref(p), ctypes.byref(h)), "mclb_create")
@@ -187,7 +189,8 @@ class Simulation:
     def from_problem(cls, prob, precision=None, kernel=KERNEL_AUTO, stream=None):
         s = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta, prob.kappa,
                 prob.force, precision or prob.precision, kernel, stream,
-                getattr(prob, "forcing_velocity", 0), getattr(prob, "lattice", "d2q9"))
+                getattr(prob, "forcing_velocity", 0), getattr(prob, "lattice", "d2q9"),
+                getattr(prob, "force_form", 0))
         s.init_fields(prob.rho, prob.u)
         return s
 
@@ -291,7 +294,8 @@ class Batch:
         for k, pr in enumerate(self.problems):
             p, keep = make_params(pr.ncomp, pr.nx, pr.ny, pr.tau, pr.chi, pr.m, pr.theta, pr.kappa,
                                   pr.force, precision, KERNEL_AUTO, stream,
-                                  getattr(pr, "forcing_velocity", 0), getattr(pr, "lattice", "d2q9"))
+                                  getattr(pr, "forcing_velocity", 0), getattr(pr, "lattice", "d2q9"),
+                                  getattr(pr, "force_form", 0))
             arr[k] = p
             self._keep.append(keep)
         h = ctypes.c_void_p()

@@ -52,7 +52,7 @@ kb_collide(const BatchItem<T>* __restrict__ items, const int* __restrict__ blk2i
     const BatchItem<T>& it = items[blk2inst[blockIdx.x]];
     const long long site = (long long)(blockIdx.x - it.block0) * SITE_THREADS + threadIdx.x;
     if (site >= it.p.S) return;
-    collide_site<T, N>(it.f[parity], it.f[parity ^ 1], it.nu, it.p, site);
+    collide_site<T, N>(it.f[parity], it.f[parity ^ 1], it.rs, it.nu, it.p, site);
 }
 
 // Device-side description of one instance for the batched march: its tensor maps

@@ -106,6 +106,15 @@ int validate(const mclb_params* p)
         return fail(MCLB_EINVAL, "forcing_velocity=%d unknown", p->forcing_velocity);
     if (p->lattice != MCLB_D2Q9 && p->lattice != MCLB_D1Q3)
         return fail(MCLB_EINVAL, "lattice=%d unknown", p->lattice);
+    if (p->force_form != MCLB_FORCE_COMPONENT && p->force_form != MCLB_FORCE_GIBBS_DUHEM)
+        return fail(MCLB_EINVAL, "force_form=%d unknown", p->force_form);
+    if (p->force_form == MCLB_FORCE_GIBBS_DUHEM) {
+        if (p->kappa != 0.0)
+            return fail(MCLB_EINVAL, "the Gibbs-Duhem force form is defined for kappa = 0");
+        if (p->lattice == MCLB_D2Q9 && p->kernel == MCLB_KERNEL_FUSED)
+            return fail(MCLB_EINVAL, "the Gibbs-Duhem force form runs on the staged schedule "
+                                     "(kernel AUTO or STAGED) on D2Q9");
+    }
     if (p->lattice == MCLB_D1Q3) {
         if (p->ny != 1) return fail(MCLB_EINVAL, "lattice D1Q3 needs ny = 1 (ny=%d)", p->ny);
         if (p->precision != MCLB_FP64 && p->precision != MCLB_FP32)
@@ -138,6 +147,7 @@ void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
     P.gx = p->force[0];
     P.gy = p->force[1];
     P.forcing_velocity = p->forcing_velocity;
+    P.force_form = p->force_form;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) P.chi[a * P.N + b] = p->chi[a * P.N + b];
         P.m[a] = p->m ? p->m[a] : 1.0;
@@ -404,6 +414,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaStreamCreateWithFlags(&h->status_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
     h->fused = false;
+    if (P.force_form == MCLB_FORCE_GIBBS_DUHEM && !h->line3) h->kernel = MCLB_KERNEL_STAGED;
     if (h->line3) {
         if (cudaMalloc(&h->sc.line_item, h->line3->item_bytes) != cudaSuccess)
             return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));

@@ -106,6 +106,7 @@ struct StepParams {
     C kappa, theta;
     C log_floor;          // floor of rho^s / rho inside a logarithm
     int bary;             // 1: barycentric u in the forcing's second moment, 0: u^s (Eq. ff3)
+    int gd;               // 1: Gibbs-Duhem total force (kappa = 0), 0: Eq. definef as printed
     C chi[NMAX * NMAX];
     C th_m[NMAX];         // theta / m^s
     C logc[NMAX];         // theta / m^s - 1/3: coefficient of ln rho^s in nu^s
@@ -136,6 +137,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
     p.theta = C(P.theta);
     p.log_floor = C(1e-12);
     p.bary = P.forcing_velocity;
+    p.gd = P.force_form;
     p.log_mask = 0;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) p.chi[a * P.N + b] = C(P.chi[a * P.N + b]);

@@ -94,6 +94,20 @@ __device__ __forceinline__ void nu3(const StepParams<C>& p, const C (&rl)[N], co
     site_nu<C, N>(p, rc, lap, nu);
 }
 
+// Gibbs-Duhem reading of the sum of the component forces (kappa = 0) on D1Q3: every a^s
+// shifted by (A_c - A) / rho, A = sum_s rho^s (a^s - g), A_c = (1 - 1/(2 tau)) (1/3) d_x rho.
+template <typename C, int N>
+__device__ __forceinline__ void gibbs_duhem3(const StepParams<C>& p, const C (&r)[N], C rho,
+                                             C grad_rho, C (&a)[N])
+{
+    C A = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) A += r[s] * (a[s] - p.gx);
+    const C d = (p.fcoef * grad_rho / C(3) - A) / rho;
+#pragma unroll
+    for (int s = 0; s < N; ++s) a[s] += d;
+}
+
 // One instance of a resident launch: buffers and parameters.
 template <typename T>
 struct Line3Item {
@@ -165,12 +179,26 @@ k_line3_resident(const Line3Item<T>* __restrict__ items, int parity, int nsteps)
         }
         __syncthreads();
         if (act) {
+            C a[N], rho = C(0);
 #pragma unroll
             for (int s = 0; s < N; ++s) {
-                const C a = -p.fcoef * (C(0.5) * (NU[s * nx + xr] - NU[s * nx + xl])) + p.gx;
+                a[s] = -p.fcoef * (C(0.5) * (NU[s * nx + xr] - NU[s * nx + xl])) + p.gx;
+                rho += r[s];
+            }
+            if (p.gd) {
+                C rl = C(0), rr = C(0);
+#pragma unroll
+                for (int s = 0; s < N; ++s) {
+                    rl += R[s * nx + xl];
+                    rr += R[s * nx + xr];
+                }
+                gibbs_duhem3<C, N>(p, r, rho, C(0.5) * (rr - rl), a);
+            }
+#pragma unroll
+            for (int s = 0; s < N; ++s) {
                 const C jf = p.bary ? r[s] * u : j[s];
                 C out[3];
-                collide3(p, f[s], r[s], jf, u, a, out);
+                collide3(p, f[s], r[s], jf, u, a[s], out);
 #pragma unroll
                 for (int i = 0; i < 3; ++i) A[(s * 3 + i) * nx + x] = out[i];
             }
@@ -225,12 +253,23 @@ k_line3_tile(const T* __restrict__ fin, T* __restrict__ fout,
     const int xo = x0 - 2 + t;
     if (t >= 2 && t < L3_TILE - 2 && xo < nx) {
         if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
+        C a[N];
+#pragma unroll
+        for (int s = 0; s < N; ++s) a[s] = -p.fcoef * (C(0.5) * (NU[s][t + 1] - NU[s][t - 1])) + p.gx;
+        if (p.gd) {
+            C rl = C(0), rr = C(0);
+#pragma unroll
+            for (int s = 0; s < N; ++s) {
+                rl += R[s][t - 1];
+                rr += R[s][t + 1];
+            }
+            gibbs_duhem3<C, N>(p, r, rho, C(0.5) * (rr - rl), a);
+        }
 #pragma unroll
         for (int s = 0; s < N; ++s) {
-            const C a = -p.fcoef * (C(0.5) * (NU[s][t + 1] - NU[s][t - 1])) + p.gx;
             const C jf = p.bary ? r[s] * u : j[s];
             C out[3];
-            collide3(p, f[s], r[s], jf, u, a, out);
+            collide3(p, f[s], r[s], jf, u, a[s], out);
 #pragma unroll
             for (int i = 0; i < 3; ++i) fout[(long long)(s * 3 + i) * nx + xo] = T(out[i]);
         }
@@ -315,10 +354,23 @@ struct Line3Site {
             jt += j[s];
         }
         u = jt / rho;
+        // Gibbs-Duhem reading: the common shift of every a^s
+        shift = C(0);
+        if (p.gd) {
+            C A = C(0), rl = C(0), rr = C(0);
+#pragma unroll
+            for (int s = 0; s < N; ++s) {
+                A += r[2][s] * (-p.fcoef * (C(0.5) * (nu[2][s] - nu[0][s])));
+                rl += r[1][s];
+                rr += r[3][s];
+            }
+            shift = (p.fcoef * (C(0.5) * (rr - rl)) / C(3) - A) / rho;
+        }
     }
+    C shift;
     __device__ __forceinline__ C accel(const StepParams<C>& p, int s) const
     {
-        return -p.fcoef * (C(0.5) * (nu[2][s] - nu[0][s])) + p.gx;
+        return -p.fcoef * (C(0.5) * (nu[2][s] - nu[0][s])) + p.gx + shift;
     }
 };
 

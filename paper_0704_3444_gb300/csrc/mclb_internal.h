@@ -37,6 +37,7 @@ struct Problem {
     double m[NMAX];
     int forcing_velocity;   // MCLB_FORCING_COMPONENT (0) or MCLB_FORCING_BARYCENTRIC (1)
     int lattice;            // MCLB_D2Q9 (0) or MCLB_D1Q3 (1: ny = 1, layout [s][i][x], no ghosts)
+    int force_form;         // MCLB_FORCE_COMPONENT (0) or MCLB_FORCE_GIBBS_DUHEM (1)
     int withhold;           // test hook: the single-pass kernel issues no copies
     long long rbytes;       // 16-bit formats: byte offset of the FP32 density lines
                             // ([s][y][pitch], same ghosts) after the deviations; else 0

@@ -155,6 +155,8 @@ extern "C" int mclb_step_noalloc(const mclb_params* params, const double* f_in, 
         return report(MCLB_EINVAL, "mclb_step_noalloc: only precision MCLB_FP64 is supported");
     if (params->lattice != MCLB_D2Q9)
         return report(MCLB_EINVAL, "mclb_step_noalloc: only the D2Q9 lattice is supported");
+    if (params->force_form != MCLB_FORCE_COMPONENT)
+        return report(MCLB_EINVAL, "mclb_step_noalloc: only the component forces of Eq. definef");
     const long long S = (long long)params->nx * params->ny;
     if (!f_in || !f_out)
         return report(MCLB_EINVAL, "mclb_step_noalloc: f_in and f_out must be device arrays");

@@ -161,6 +161,30 @@ __device__ __forceinline__ void eq_weights(C ux, C uy, C (&e)[Q])
     }
 }
 
+// Gibbs-Duhem reading of the sum of the component forces (kappa = 0): every a^s gets
+// the same shift (A_c - A) / rho, with A = sum_s rho^s (a^s - g) the sum of the Eq. definef
+// forces and A_c = (1 - 1/(2 tau)) (1/3) grad rho their continuum total for the
+// Flory-Huggins free energy (Gibbs-Duhem with the pressure sum rho mu - psi = 0); the
+// differences between the components' accelerations are kept.
+template <typename C, int N>
+__device__ __forceinline__ void gibbs_duhem_shift(const StepParams<C>& p, const C (&r)[N], C rho,
+                                                  C grx, C gry, C (&ax)[N], C (&ay)[N])
+{
+    C Ax = C(0), Ay = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        Ax += r[s] * (ax[s] - p.gx);
+        Ay += r[s] * (ay[s] - p.gy);
+    }
+    const C dx = (p.fcoef * grx / C(3) - Ax) / rho;
+    const C dy = (p.fcoef * gry / C(3) - Ay) / rho;
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        ax[s] += dx;
+        ay[s] += dy;
+    }
+}
+
 // Momentum of the forcing's second moment (Eq. ff3): j^s = rho^s u^s as printed, or
 // rho^s u with the barycentric u when the barycentric reading is selected.
 template <typename C>

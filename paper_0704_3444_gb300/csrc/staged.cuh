@@ -114,10 +114,51 @@ __device__ __forceinline__ void field_grad(const C* __restrict__ g, const StepPa
     gy = C(3) * ay;
 }
 
+// grad rho = 3 sum_i w_i v_i rho(r + v_i) of the total density, from the N density fields
+template <typename C, int N>
+__device__ __forceinline__ void rho_grad(const C* __restrict__ rs, const StepParams<C>& p, int x,
+                                         int y, C& gx, C& gy)
+{
+    C ax = C(0), ay = C(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        C r = C(0);
+#pragma unroll
+        for (int s = 0; s < N; ++s) r += rs[s * p.S + (long long)yy * p.nx + xx];
+        ax += wq<C>(i) * C(vx(i)) * r;
+        ay += wq<C>(i) * C(vy(i)) * r;
+    }
+    gx = C(3) * ax;
+    gy = C(3) * ay;
+}
+
+// Accelerations a^s at (x, y) from the potential fields (Eq. definef plus the body force;
+// with p.gd the Gibbs-Duhem shift).  r: the site's rho^s, rho their sum.
+template <typename C, int N>
+__device__ __forceinline__ void site_accel(const C* __restrict__ rs, const C* __restrict__ nu,
+                                           const StepParams<C>& p, int x, int y, const C (&r)[N],
+                                           C rho, C (&ax)[N], C (&ay)[N])
+{
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C gx, gy;
+        field_grad(nu + s * p.S, p, x, y, gx, gy);
+        ax[s] = -p.fcoef * gx + p.gx;
+        ay[s] = -p.fcoef * gy + p.gy;
+    }
+    if (p.gd) {
+        C grx, gry;
+        rho_grad<C, N>(rs, p, x, y, grx, gry);
+        gibbs_duhem_shift<C, N>(p, r, rho, grx, gry, ax, ay);
+    }
+}
+
 // Collision at one site from the pulled populations and the potential fields; the
 // post-collision values are stored in place (pull scheme), ghosts included.
 template <typename T, int N>
 __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __restrict__ fout,
+                                             const typename Storage<T>::C* __restrict__ rs,
                                              const typename Storage<T>::C* __restrict__ nu,
                                              const StepParams<typename Storage<T>::C>& p,
                                              long long site)
@@ -148,15 +189,13 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
     const C ux = jxt / rho, uy = jyt / rho;
     C e[Q];
     eq_weights(ux, uy, e);
+    C ax[N], ay[N];
+    site_accel<C, N>(rs, nu, p, x, y, r, rho, ax, ay);
 #pragma unroll
     for (int s = 0; s < N; ++s) {
-        C gx, gy;
-        field_grad(nu + s * p.S, p, x, y, gx, gy);
-        const C ax = -p.fcoef * gx + p.gx;
-        const C ay = -p.fcoef * gy + p.gy;
         C out[Q], fjx, fjy;
         forcing_momentum(p, r[s], jx[s], jy[s], ux, uy, fjx, fjy);
-        collide(p, f[s], e, r[s], fjx, fjy, ax, ay, out);
+        collide(p, f[s], e, r[s], fjx, fjy, ax[s], ay[s], out);
         store_site(fout, p, s, y, x, out);
     }
     if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
@@ -165,12 +204,13 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
 template <typename T, int N>
 __global__ void __launch_bounds__(SITE_THREADS)
 k_collide(const T* __restrict__ fin, T* __restrict__ fout,
+          const typename Storage<T>::C* __restrict__ rs,
           const typename Storage<T>::C* __restrict__ nu,
           const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
-    collide_site<T, N>(fin, fout, nu, p, site);
+    collide_site<T, N>(fin, fout, rs, nu, p, site);
 }
 
 // ---------------------------------------------------------------- diagnostics
@@ -262,6 +302,8 @@ k_moments(const T* __restrict__ f, const typename Storage<T>::C* __restrict__ rs
         for (int s = 0; s < N; ++s) rho_out[s * p.S + site] = (double)r[s];
     if (U) {
         C jxt = C(0), jyt = C(0), fx = C(0), fy = C(0);
+        C ax[N], ay[N];
+        site_accel<C, N>(rs, nu, p, x, y, r, rho, ax, ay);
 #pragma unroll
         for (int s = 0; s < N; ++s) {
 #pragma unroll
@@ -270,10 +312,8 @@ k_moments(const T* __restrict__ f, const typename Storage<T>::C* __restrict__ rs
                 jxt += v * C(vx(i));
                 jyt += v * C(vy(i));
             }
-            C gx, gy;
-            field_grad(nu + s * p.S, p, x, y, gx, gy);
-            fx += r[s] * (-p.fcoef * gx + p.gx);
-            fy += r[s] * (-p.fcoef * gy + p.gy);
+            fx += r[s] * ax[s];
+            fy += r[s] * ay[s];
         }
         U[site] = (double)(jxt / rho + C(0.5) * fx / rho);
         U[p.S + site] = (double)(jyt / rho + C(0.5) * fy / rho);
@@ -338,9 +378,17 @@ k_conservation(const T* __restrict__ f, const typename Storage<T>::C* __restrict
     for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < p.S;
          site += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
+        C rl[N], ax[N], ay[N];
+        C rho = C(0);
 #pragma unroll
         for (int s = 0; s < N; ++s) {
-            const C r = rs[s * p.S + site];
+            rl[s] = rs[s * p.S + site];
+            rho += rl[s];
+        }
+        site_accel<C, N>(rs, nu, p, x, y, rl, rho, ax, ay);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            const C r = rl[s];
             acc[s] += (double)r;
             double jx = 0.0, jy = 0.0;
 #pragma unroll
@@ -351,10 +399,8 @@ k_conservation(const T* __restrict__ f, const typename Storage<T>::C* __restrict
             }
             acc[N] += jx;
             acc[N + 1] += jy;
-            C gx, gy;
-            field_grad(nu + s * p.S, p, x, y, gx, gy);
-            acc[N + 2] += (double)r * (double)(-p.fcoef * gx + p.gx);
-            acc[N + 3] += (double)r * (double)(-p.fcoef * gy + p.gy);
+            acc[N + 2] += (double)r * (double)ax[s];
+            acc[N + 3] += (double)r * (double)ay[s];
         }
     }
     block_reduce_store<K>(acc, partial);

@@ -58,7 +58,7 @@ struct Launch {
             cudaError_t e = fields_n<NN>(p, sc, (const T*)fin, st);
             if (e != cudaSuccess) return e;
             k_collide<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(
-                (const T*)fin, (T*)fout, (const C*)sc.nu, p);
+                (const T*)fin, (T*)fout, (const C*)sc.rho_s, (const C*)sc.nu, p);
             return cudaGetLastError();
         });
     }

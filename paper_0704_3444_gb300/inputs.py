@@ -84,6 +84,7 @@ class Problem:
     meta: dict = field(default_factory=dict)
     forcing_velocity: int = 0      # 0: Eq. ff3 as printed, 1: barycentric reading
     lattice: str = "d2q9"          # or "d1q3" (ny = 1)
+    force_form: int = 0            # 0: Eq. definef as printed, 1: Gibbs-Duhem total (kappa = 0)
 
     @property
     def sites(self) -> int:

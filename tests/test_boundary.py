@@ -60,6 +60,9 @@ def _params(**kw):
     (dict(lattice=2), "lattice"),
     (dict(lattice="d1q3", ny=2), "ny = 1"),
     (dict(lattice="d1q3", ny=1, precision="bf16"), "FP64 or FP32"),
+    (dict(force_form=2), "force_form"),
+    (dict(force_form=1, kappa=0.01), "kappa = 0"),
+    (dict(force_form=1, kernel=1), "staged schedule"),
 ])
 def test_invalid_parameters_are_rejected(lib, kw, frag):
     p, keep = _params(**kw)
