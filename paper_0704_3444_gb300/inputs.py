@@ -208,6 +208,25 @@ def multi_uniform(nx=2048, ny=2048, *, ncomp=5, tau=1.0, kappa=0.01, amp=0.01, s
                     kappa=kappa, steps=steps, precision=precision)
 
 
+def multi_spinodal(nx=256, ny=256, *, ncomp=5, tau=1.0, kappa=0.01, amp=0.01, seed=3,
+                   steps=2000, precision="fp32", name="n5_spinodal") -> Problem:
+    """The N-component workload's interactions (random symmetric chi in [0.8, 1.5] x
+    critical, same seed) with a mean composition inside the spinodal: the pair with the
+    largest chi at 0.4 each, the other components sharing 0.2, plus mass-neutral uniform
+    noise of amplitude `amp`.  (At the equimolar composition that chi set is stable; here
+    the pair's composition mode grows and the mixture separates into two phases.)
+    """
+    chi = random_chi(ncomp, 0.8, 1.5, seed)
+    a, b = np.unravel_index(np.argmax(chi), chi.shape)
+    phi0 = np.full(ncomp, 0.2 / (ncomp - 2))
+    phi0[a] = phi0[b] = 0.4
+    s = nx * ny
+    noise = np.stack([amp * (2.0 * uniform(seed + 17, s, k) - 1.0) for k in range(ncomp)])
+    phi = (phi0[:, None] + _mass_neutral(noise)).reshape(ncomp, ny, nx)
+    return _problem(name, ncomp, nx, ny, tau, chi, phi, kappa=kappa, steps=steps,
+                    precision=precision, meta={"pair": (int(a), int(b))})
+
+
 def slab(nx=8192, ny=2048, *, tau=1.0 / 0.9, kappa=0.01, amp=0.01, seed=5, steps=20000,
          precision="fp32", name="slab_8192x2048") -> Problem:
     """Polymer (P) / solvent (S) mixture 0.3/0.7 on the left half against pure

@@ -465,3 +465,45 @@ def test_resume_equals_uninterrupted(precision, kernel):
     assert np.array_equal(a.get_state(), b.get_state())
     a.close()
     b.close()
+
+
+def test_n5_spinodal_per_field():
+    """The N = 5 workload's interactions at a mean composition inside the spinodal (the
+    strongest pair at 0.4 each, inputs.multi_spinodal): the mixture separates into two
+    phases, so rho, U, mu and P are compared across interfaces rather than on a uniform
+    state.  256 x 256 against the FP64 oracle.  FP64 after 2000 steps: every field within
+    10x the oracle's own divergence from a start perturbed by 2^-52 (floored at 8 units of
+    roundoff of the field's scale).  After 500 steps (before the growing composition mode
+    has amplified rounding by more than a few times): FP32 within 1e-5 on all four fields,
+    BF16 and FP16 within 2e-5 on rho, U and mu and 1e-6 on P."""
+    p = inputs.multi_spinodal(256, 256)
+    o = Oracle.from_problem(p)
+    o.run(500)
+    ref500 = o.moments()
+    o.run(1500)
+    ref2000 = o.moments()
+    rng = np.random.default_rng(7)
+    q = Oracle.from_problem(p)
+    q.init(p.rho * (1 + 2.0 ** -52 * rng.uniform(-1, 1, p.rho.shape)), p.u)
+    q.run(2000)
+    self2000 = q.moments()
+    assert np.abs(ref2000["rho"][p.meta["pair"][0]]).max() > 0.6   # separated
+    sim = mclb.Simulation.from_problem(p, precision="fp64", kernel=mclb.KERNEL_FUSED)
+    sim.step(2000)
+    assert sim.status() == 0
+    g = sim.moments()
+    for k in ("rho", "U", "mu", "P"):
+        floor = 8 * 2.0 ** -52 * np.abs(ref2000[k]).max()
+        sens = max(np.abs(self2000[k] - ref2000[k]).max(), floor)
+        assert np.abs(g[k] - ref2000[k]).max() <= 10 * sens, k
+    sim.close()
+    bounds = {"fp32": (1e-5, 1e-5), "bf16": (2e-5, 1e-6), "fp16": (2e-5, 1e-6)}
+    for prec, (b, bp) in bounds.items():
+        sim = mclb.Simulation.from_problem(p, precision=prec, kernel=mclb.KERNEL_FUSED)
+        sim.step(500)
+        assert sim.status() == 0
+        g = sim.moments()
+        for k in ("rho", "U", "mu"):
+            assert np.abs(g[k] - ref500[k]).max() < b, (prec, k)
+        assert np.abs(g["P"] - ref500["P"]).max() < bp, prec
+        sim.close()
