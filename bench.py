@@ -441,6 +441,14 @@ def main():
                 "speedup_vs_fp32": (S * N * ks / t / 1e6) / (value / world),
                 "hbm_gbs_algorithmic": v.bytes_per_step / (t / ks) / 1e9}
             v.close()
+            # the same with the per-component mass compensation after every 64 steps
+            v = mclb.Simulation.from_problem(prob, precision=prec, kernel=mclb.KERNEL_FUSED,
+                                             stream=sptr, mass_every=64)
+            t = time_steps(torch, v, 512, 64, stream)
+            variants[f"{prec}_shifted"]["mass_every_64"] = {
+                "value": S * N * 512 / t / 1e6, "steps": 512, "status_ok": v.status() == 0,
+                "speedup_vs_fp32": (S * N * 512 / t / 1e6) / (value / world)}
+            v.close()
         v = mclb.Simulation.from_problem(prob, precision="fp32", kernel=mclb.KERNEL_STAGED,
                                          stream=sptr)
         t = time_steps(torch, v, 200, args.warmup, stream)

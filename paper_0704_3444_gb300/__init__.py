@@ -54,7 +54,8 @@ class mclb_params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("force", ctypes.c_double * 2),
                 ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("forcing_velocity", ctypes.c_int),
-                ("lattice", ctypes.c_int), ("force_form", ctypes.c_int)]
+                ("lattice", ctypes.c_int), ("force_form", ctypes.c_int),
+                ("mass_every", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -151,7 +152,7 @@ def _fields(rho, u, ncomp, ny, nx, device=False):
 
 def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, force=(0.0, 0.0),
                 precision="fp32", kernel=KERNEL_AUTO, stream=None, forcing_velocity=0,
-                lattice="d2q9", force_form=0):
+                lattice="d2q9", force_form=0, mass_every=0):
     """Build an mclb_params struct; returns (struct, keep-alive arrays)."""
     chi = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp))
     marr = None if m is None else np.ascontiguousarray(np.asarray(m, dtype=np.float64))
@@ -167,6 +168,7 @@ def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, for
     p.forcing_velocity = int(forcing_velocity)
     p.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     p.force_form = int(force_form)
+    p.mass_every = int(mass_every)
     return p, (chi, marr)
 
 
@@ -175,22 +177,22 @@ class Simulation:
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
                  force=(0.0, 0.0), precision="fp32", kernel=KERNEL_AUTO, stream=None,
-                 forcing_velocity=0, lattice="d2q9", force_form=0):
+                 forcing_velocity=0, lattice="d2q9", force_form=0, mass_every=0):
         self.lib = load()
         self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
         p, keep = make_params(ncomp, nx, ny, tau, chi, m, theta, kappa, force, precision, kernel,
-                              stream, forcing_velocity, lattice, force_form)
+                              stream, forcing_velocity, lattice, force_form, mass_every)
         self.q = 3 if p.lattice == D1Q3 else 9
         h = ctypes.c_void_p()
         _check(self.lib.mclb_create(ctypes.byref(p), ctypes.byref(h)), "mclb_create")
         self.h = h
 
     @classmethod
-    def from_problem(cls, prob, precision=None, kernel=KERNEL_AUTO, stream=None):
+    def from_problem(cls, prob, precision=None, kernel=KERNEL_AUTO, stream=None, mass_every=0):
         s = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta, prob.kappa,
                 prob.force, precision or prob.precision, kernel, stream,
                 getattr(prob, "forcing_velocity", 0), getattr(prob, "lattice", "d2q9"),
-                getattr(prob, "force_form", 0))
+                getattr(prob, "force_form", 0), mass_every)
         s.init_fields(prob.rho, prob.u)
         return s
 

@@ -115,6 +115,7 @@ int validate(const mclb_params* p)
             return fail(MCLB_EINVAL, "the Gibbs-Duhem force form runs on the staged schedule "
                                      "(kernel AUTO or STAGED) on D2Q9");
     }
+    if (p->mass_every < 0) return fail(MCLB_EINVAL, "mass_every=%d must be >= 0", p->mass_every);
     if (p->lattice == MCLB_D1Q3) {
         if (p->ny != 1) return fail(MCLB_EINVAL, "lattice D1Q3 needs ny = 1 (ny=%d)", p->ny);
         if (p->precision != MCLB_FP64 && p->precision != MCLB_FP32)
@@ -148,6 +149,7 @@ void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
     P.gy = p->force[1];
     P.forcing_velocity = p->forcing_velocity;
     P.force_form = p->force_form;
+    P.mass_every = p->mass_every;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) P.chi[a * P.N + b] = p->chi[a * P.N + b];
         P.m[a] = p->m ? p->m[a] : 1.0;
@@ -180,6 +182,7 @@ struct mclb_handle_s {
     CUtensorMap tmapwr[2];        // the same for the density lines of the 16-bit formats
     int cur;                      // buffer holding the current state
     long steps;
+    long since_mass;              // steps since the last mass compensation
     size_t fbytes;                // bytes of one distribution buffer
     unsigned int* status_host;    // pinned mirror of the device status word
     cudaEvent_t status_event;     // the mirror's copy has landed
@@ -336,6 +339,35 @@ int settle_status(mclb_handle h)
     return MCLB_OK;
 }
 
+// The mass compensation's reference: each component's mass of the state just set.
+int record_mass(mclb_handle h)
+{
+    h->since_mass = 0;
+    if (h->P.mass_every > 0) CK(h->tab->mass(h->P, h->sc, h->f[h->cur], 1, h->stream));
+    return MCLB_OK;
+}
+
+// nsteps timesteps, graph-replayed in GRAPH_STEPS chunks where possible.
+int advance(mclb_handle h, long nsteps)
+{
+    if (h->line3) {
+        CK(h->line3->step(h->P, h->sc, h->f, &h->cur, nsteps, h->stream));
+        return MCLB_OK;
+    }
+    long left = nsteps;
+    while (left >= GRAPH_STEPS && !h->P.withhold) {
+        if (!h->graph_tried[h->cur]) try_capture(h, h->cur);
+        if (!h->graph[h->cur]) break;
+        CK(cudaGraphLaunch(h->graph[h->cur], h->stream));
+        left -= GRAPH_STEPS;
+    }
+    for (; left > 0; --left) {
+        CK(launch_one_step(h, h->cur));
+        h->cur ^= 1;
+    }
+    return MCLB_OK;
+}
+
 int sync_status(mclb_handle h)
 {
     int rc = enqueue_status_copy(h);
@@ -401,7 +433,8 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
         return bail(fail(MCLB_ENOMEM, "scratch fields"));
     h->sc.partial_cap = (size_t)REDUCE_BLOCKS * (NMAX + 4) + 64;
     if (cudaMalloc(&h->sc.partial, h->sc.partial_cap * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&h->sc.status, sizeof(unsigned int)) != cudaSuccess)
+        cudaMalloc(&h->sc.status, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&h->sc.mass_ref, NMAX * sizeof(double)) != cudaSuccess)
         return bail(fail(MCLB_ENOMEM, "reduction scratch"));
     if (cudaMemset(h->sc.status, 0, sizeof(unsigned int)) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaMemset failed"));
@@ -448,6 +481,7 @@ int mclb_destroy(mclb_handle h)
     if (h->sc.partial) cudaFree(h->sc.partial);
     if (h->sc.status) cudaFree(h->sc.status);
     if (h->sc.line_item) cudaFree(h->sc.line_item);
+    if (h->sc.mass_ref) cudaFree(h->sc.mass_ref);
     if (h->dtmp) cudaFree(h->dtmp);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->status_event) cudaEventDestroy(h->status_event);
@@ -470,7 +504,7 @@ static int init_common(mclb_handle h, const double* rho_d, const double* u_d)
         CK(h->tab->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
     h->cur = 0;
     h->steps = 0;
-    return MCLB_OK;
+    return record_mass(h);
 }
 
 int mclb_init_fields(mclb_handle h, const double* rho, const double* u)
@@ -529,25 +563,19 @@ int mclb_step(mclb_handle h, long nsteps)
         prev = status_code(*h->status_host);
     }
     cudaGetLastError();
-    if (h->line3) {
-        CK(h->line3->step(h->P, h->sc, h->f, &h->cur, nsteps, h->stream));
-        h->steps += nsteps;
-        if (nsteps > 0) {
-            rc = enqueue_status_copy(h);
-            if (rc) return rc;
-        }
-        return prev;
-    }
+    // with the mass compensation on, every mass_every-th step (counted since the state
+    // was set) is followed by the compensation
+    const long every = h->P.mass_every;
     long left = nsteps;
-    while (left >= GRAPH_STEPS && !h->P.withhold) {
-        if (!h->graph_tried[h->cur]) try_capture(h, h->cur);
-        if (!h->graph[h->cur]) break;
-        CK(cudaGraphLaunch(h->graph[h->cur], h->stream));
-        left -= GRAPH_STEPS;
-    }
-    for (; left > 0; --left) {
-        CK(launch_one_step(h, h->cur));
-        h->cur ^= 1;
+    while (left > 0) {
+        const long chunk = every > 0 ? std::min(left, every - h->since_mass) : left;
+        rc = advance(h, chunk);
+        if (rc) return rc;
+        left -= chunk;
+        if (every > 0 && (h->since_mass += chunk) == every) {
+            CK(h->tab->mass(h->P, h->sc, h->f[h->cur], 0, h->stream));
+            h->since_mass = 0;
+        }
     }
     h->steps += nsteps;
     if (nsteps > 0) {
@@ -683,9 +711,11 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
         CK(h->line3->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
     else
         CK(h->tab->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
-    CK(cudaStreamSynchronize(h->stream));
     h->cur = 0;
     h->steps = 0;
+    rc = record_mass(h);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream));
     return MCLB_OK;
 }
 
@@ -896,6 +926,9 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
     if (!out) return fail(MCLB_EINVAL, "out is NULL");
     *out = nullptr;
     if (!params || count < 1) return fail(MCLB_EINVAL, "count=%d must be >= 1", count);
+    for (int k = 0; k < count; ++k)
+        if (params[k].mass_every != 0)
+            return fail(MCLB_EINVAL, "instance %d: mass_every must be 0 in a batch", k);
     mclb_batch b = new (std::nothrow) mclb_batch_s();
     if (!b) return fail(MCLB_ENOMEM, "host allocation failed");
     b->magic = MAGIC;

@@ -12,6 +12,7 @@ namespace mclb {
 constexpr int NMAX = 8;
 constexpr int Q = 9;
 constexpr int ROW_ALIGN = 128;  // data columns per row are padded to a multiple of this
+constexpr int LATTICE_D1Q3 = 1; // Problem::lattice of a D1Q3 lattice (MCLB_D1Q3)
 
 // Everything a launcher needs to know about one simulation, in FP64 as given at
 // the boundary; each precision unit converts it to its own kernel parameters.
@@ -38,6 +39,7 @@ struct Problem {
     int forcing_velocity;   // MCLB_FORCING_COMPONENT (0) or MCLB_FORCING_BARYCENTRIC (1)
     int lattice;            // MCLB_D2Q9 (0) or MCLB_D1Q3 (1: ny = 1, layout [s][i][x], no ghosts)
     int force_form;         // MCLB_FORCE_COMPONENT (0) or MCLB_FORCE_GIBBS_DUHEM (1)
+    int mass_every;         // period of the per-component mass compensation, 0 = off
     int withhold;           // test hook: the single-pass kernel issues no copies
     long long rbytes;       // 16-bit formats: byte offset of the FP32 density lines
                             // ([s][y][pitch], same ghosts) after the deviations; else 0
@@ -53,6 +55,7 @@ struct Scratch {
     size_t partial_cap;     // capacity in doubles
     unsigned int* status;   // device status bits (see STATUS_*)
     void* line_item;        // D1Q3 handles: the device description the resident kernel reads
+    double* mass_ref;       // NMAX FP64 reference masses of the mass compensation
 };
 
 enum : unsigned int {
@@ -139,6 +142,10 @@ struct KernelTable {
                              cudaStream_t st);
     cudaError_t (*set_state)(const Problem&, const Scratch&, const double* in, void* f,
                              cudaStream_t st);
+    // per-component mass compensation of the stored state f, either lattice (mass.cuh):
+    // record != 0 stores each component's FP64 mass in sc.mass_ref; record == 0 adds the
+    // deficit against it, spread over the sites, to the rest populations (16-bit: to R)
+    cudaError_t (*mass)(const Problem&, const Scratch&, void* f, int record, cudaStream_t st);
     // batches: a group of `count` instances with the same N (buffers fa/fb, scratch scs,
     // 8 tensor maps per instance [buffer][load, density load, store, density store] or
     // NULL); one step of the whole group reads buffer `parity` and writes the other, by

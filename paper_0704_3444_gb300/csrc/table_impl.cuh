@@ -7,6 +7,7 @@
 #include "ghosts.cuh"
 #include "line3.cuh"
 #include "march.cuh"
+#include "mass.cuh"
 #include "staged.cuh"
 
 namespace mclb {
@@ -195,6 +196,31 @@ struct Launch {
             k_set_state<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(in, (T*)f, p);
             return cudaGetLastError();
         });
+    }
+
+    // Per-component mass compensation (mass.cuh), either lattice: record != 0 stores the
+    // FP64 mass of every component of f in sc.mass_ref; record == 0 restores it.
+    static cudaError_t mass(const Problem& P, const Scratch& sc, void* f, int record, cudaStream_t st)
+    {
+        MassView v{};
+        v.q = P.lattice == LATTICE_D1Q3 ? 3 : Q;
+        v.lines = P.ny * v.q;
+        v.rlines = Storage<T>::shifted ? P.ny : 0;
+        v.comp_stride = P.plane;
+        v.pitch = P.pitch;
+        v.rbytes = P.rbytes;
+        v.S = P.S;
+        v.first = P.hx;
+        v.nx = P.nx;
+        v.span = P.nx + 2 * P.hx;
+        v.vec = (P.hx * sizeof(T)) % 16 == 0 && (P.pitch * sizeof(T)) % 16 == 0 &&
+                P.rbytes % 16 == 0 && (P.hx * sizeof(float)) % 16 == 0 &&
+                (P.pitch * sizeof(float)) % 16 == 0;
+        k_mass_partials<T><<<dim3(MASS_BLOCKS, P.N), MASS_THREADS, 0, st>>>((const T*)f, v, sc.partial);
+        const unsigned gx = record ? 1u : (unsigned)std::min(P.ny, 1024);
+        k_mass_apply<T><<<dim3(gx, P.N), MASS_THREADS, 0, st>>>((T*)f, v, sc.partial, sc.mass_ref,
+                                                                record);
+        return cudaGetLastError();
     }
 };
 
@@ -456,6 +482,7 @@ inline KernelTable make_table(CUtensorMapDataType tt)
     t.compositions = &Launch<T>::compositions;
     t.get_state = &Launch<T>::get_state;
     t.set_state = &Launch<T>::set_state;
+    t.mass = &Launch<T>::mass;
     t.batch_create = &batch_group_create<T>;
     t.batch_step = &batch_group_step<T>;
     t.batch_launches = &batch_group_launches<T>;

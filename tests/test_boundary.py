@@ -63,6 +63,7 @@ def _params(**kw):
     (dict(force_form=2), "force_form"),
     (dict(force_form=1, kappa=0.01), "kappa = 0"),
     (dict(force_form=1, kernel=1), "staged schedule"),
+    (dict(mass_every=-1), "mass_every"),
 ])
 def test_invalid_parameters_are_rejected(lib, kw, frag):
     p, keep = _params(**kw)
@@ -70,6 +71,18 @@ def test_invalid_parameters_are_rejected(lib, kw, frag):
     rc = lib.mclb_create(ctypes.byref(p), ctypes.byref(h))
     assert rc == -1 and not h.value
     assert frag in lib.mclb_last_error().decode()
+
+
+def test_mass_compensation_is_for_single_handles(lib):
+    """A non-zero mass_every is refused where there is no handle step to follow: in a
+    batch and in the allocation-free single step (checked before any device call)."""
+    p, keep = _params(mass_every=8)
+    b = ctypes.c_void_p()
+    assert lib.mclb_batch_create(ctypes.byref(p), 1, ctypes.byref(b)) == -1 and not b.value
+    assert "mass_every" in lib.mclb_last_error().decode()
+    p, keep = _params(mass_every=8, precision="fp64")
+    assert lib.mclb_step_noalloc(ctypes.byref(p), None, None) == -1
+    assert "mass_every" in lib.mclb_last_error().decode()
 
 
 def test_null_and_foreign_handles(lib):
