@@ -231,7 +231,7 @@ def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=1000):
     # two-phase bulk compositions of the instances that stayed finite and have separated
     # into two phases (fitted phases at least 0.3 apart in some component: below that the
     # two clusters only split the noise of a still mixed state), batch vs handles
-    fit_err, fitted = 0.0, 0
+    diffs = []
     for k in sorted(set(finite) & set(finite_one)):
         try:
             fb = b.fit_equilibrium(k, 2)
@@ -240,8 +240,7 @@ def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=1000):
             continue
         if min(np.max(np.abs(fb[0] - fb[1])), np.max(np.abs(fs[0] - fs[1]))) < 0.3:
             continue
-        fit_err = max(fit_err, float(np.max(np.abs(fb - fs))))
-        fitted += 1
+        diffs.append(float(np.max(np.abs(fb - fs))))
     b.close()
     for sm in sims:
         sm.close()
@@ -253,7 +252,15 @@ def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=1000):
             "diverged_note": "binary instances with chi >= ~1.39 x critical leave the method's "
                              "stability range at kappa = 0.01 (non-finite density) within the "
                              "1000 steps; the same work is timed either way",
-            "fit_max_abs_diff_vs_one_by_one": fit_err, "fit_two_phase_instances_compared": fitted,
+            "fit_vs_one_by_one": {
+                "instances": len(diffs),
+                "within_1e-3": sum(d <= 1e-3 for d in diffs),
+                "median_abs_diff": float(np.median(diffs)) if diffs else None,
+                "max_abs_diff": max(diffs) if diffs else None,
+                "note": "two-phase fits of the same instance from the batch and from its own "
+                        "handle after 1000 steps; the two kernels differ in the last bit, and "
+                        "instances still coarsening amplify that into a different arrangement "
+                        "of domains, which the fit then measures"},
             "sites": sum(p.sites for p in probs), "launches_per_step": launches,
             "one_by_one_fp32_value": vs, "speedup_vs_one_by_one": vb / vs,
             "speedup_vs_fp32": vb / fp32_value}
