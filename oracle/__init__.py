@@ -9,8 +9,10 @@ first use into ``oracle/_build``; this module marshals numpy arrays to it.
 ``oracle.thermo`` holds the Flory-Huggins thermodynamics (binodals, critical
 points) the paper compares its simulations against.
 
-Two lattices: D2Q9 (the two-dimensional workloads) and D1Q3, the lattice of the
-paper's own simulations (Sec. 4), each a plain path of its own in the C file.
+Three lattices, each a plain path of its own in the C file: D2Q9 (the
+two-dimensional workloads), D1Q3 (the lattice of the paper's own simulations,
+Sec. 4) and D3Q19 (three dimensions; the same equations on a lattice whose
+weights give the same moments).
 Two readings of the velocity in the forcing's second moment (Eq. ff3):
 ``forcing_velocity=0`` is the component velocity u^s as printed (the default),
 ``forcing_velocity=1`` the barycentric u.  Two readings of the sum of the component
@@ -23,8 +25,13 @@ transcriptions.  The floor of the logarithm in Eq. definef is pinned by the
 rho -> lambda rho invariance with the floor binding and by bracketing where it
 binds; the barycentric forcing reading by its transcription and by the one-fluid
 sum of Eq. olso; the D1Q3 path by its moment-solving transcription and by the
-one-row D2Q9 lattice it is the projection of.  The paper's printed ternary critical points are not
-reproduced by the symmetric-chi reading and are reported, not asserted.
+one-row D2Q9 lattice it is the projection of; the D3Q19 path by its own moment
+conditions, by the D2Q9 run that a z-, y- or x-invariant D3Q19 run projects onto
+(summing the populations that share their in-plane velocity gives the D2Q9 weights,
+equilibria, forcing and stencils exactly), by conservation, and by the ideal-mixture
+diffusion rate of a mode along a body diagonal, which no two-dimensional run
+reaches.  The paper's printed ternary critical points are not reproduced by the
+symmetric-chi reading and are reported, not asserted.
 """
 from __future__ import annotations
 
@@ -51,7 +58,8 @@ class OracleParams(ctypes.Structure):
                 ("tau", ctypes.c_double), ("theta", ctypes.c_double),
                 ("kappa", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
                 ("chi", ctypes.c_double * (NMAX * NMAX)), ("m", ctypes.c_double * NMAX),
-                ("forcing_velocity", ctypes.c_int), ("force_form", ctypes.c_int)]
+                ("forcing_velocity", ctypes.c_int), ("force_form", ctypes.c_int),
+                ("nz", ctypes.c_int), ("gz", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -90,6 +98,12 @@ def _load():
             lib.oracle_d1q3_run.argtypes = [pp, dp, ctypes.c_long]
             lib.oracle_d1q3_moments.argtypes = [pp, dp] + [dp] * 4
             lib.oracle_d1q3_conservation.argtypes = [pp, dp, dp, dp, dp]
+            lib.oracle_d3q19_equilibrium.argtypes = [ctypes.c_double] * 4 + [dp]
+            lib.oracle_d3q19_forcing.argtypes = [ctypes.c_double] * 7 + [dp]
+            lib.oracle_d3q19_init.argtypes = [pp, dp, dp, dp]
+            lib.oracle_d3q19_run.argtypes = [pp, dp, ctypes.c_long]
+            lib.oracle_d3q19_moments.argtypes = [pp, dp] + [dp] * 4
+            lib.oracle_d3q19_conservation.argtypes = [pp, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -112,21 +126,29 @@ class Oracle:
     current time, velocity order (0,0), (1,0), (0,1), (-1,0), (0,-1), (1,1),
     (-1,1), (-1,-1), (1,-1).  D1Q3 (``lattice="d1q3"``, ny must be 1): ``f`` has
     shape (N, 3, nx), velocity order 0, +1, -1; output fields keep the D2Q9
-    shapes with ny = 1.
+    shapes with ny = 1.  D3Q19 (``lattice="d3q19"``, ``nz`` layers): ``f`` has shape
+    (N, 19, nz, ny, nx), velocity order 0; (+-1,0,0), (0,+-1,0), (0,0,+-1); (1,1,0),
+    (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1),
+    (0,-1,-1), (0,1,-1), (0,-1,1); fields have shape (., nz, ny, nx), U three
+    components, P six (xx, xy, xz, yy, yz, zz), momentum and force sums three.
     """
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
-                 force=(0.0, 0.0), forcing_velocity=0, lattice="d2q9", force_form=0):
-        if lattice not in ("d2q9", "d1q3"):
+                 force=(0.0, 0.0), forcing_velocity=0, lattice="d2q9", force_form=0, nz=1):
+        if lattice not in ("d2q9", "d1q3", "d3q19"):
             raise ValueError(f"lattice {lattice!r}")
         if lattice == "d1q3" and int(ny) != 1:
             raise ValueError("a D1Q3 lattice has ny = 1")
+        if lattice != "d3q19" and int(nz) != 1:
+            raise ValueError("nz > 1 needs the D3Q19 lattice")
         self.lattice = lattice
         self.lib = _load()
         p = OracleParams()
         p.ncomp, p.nx, p.ny = int(ncomp), int(nx), int(ny)
         p.tau, p.theta, p.kappa = float(tau), float(theta), float(kappa)
         p.gx, p.gy = float(force[0]), float(force[1])
+        p.gz = float(force[2]) if len(force) > 2 else 0.0
+        p.nz = int(nz)
         chi = np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp)
         for a in range(ncomp):
             for b in range(ncomp):
@@ -137,21 +159,37 @@ class Oracle:
         p.forcing_velocity = int(forcing_velocity)
         p.force_form = int(force_form)
         self.p = p
-        self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
-        self.f = (np.zeros((ncomp, 3, nx)) if lattice == "d1q3"
-                  else np.zeros((ncomp, 9, ny, nx)))
+        self.ncomp, self.nx, self.ny, self.nz = int(ncomp), int(nx), int(ny), int(nz)
+        self.f = np.zeros(self._fshape)
 
     @classmethod
     def from_problem(cls, prob):
         o = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
                 prob.kappa, prob.force, getattr(prob, "forcing_velocity", 0),
-                getattr(prob, "lattice", "d2q9"), getattr(prob, "force_form", 0))
+                getattr(prob, "lattice", "d2q9"), getattr(prob, "force_form", 0),
+                getattr(prob, "nz", 1))
         o.init(prob.rho, prob.u)
         return o
 
     @property
     def _d1(self):
         return self.lattice == "d1q3"
+
+    @property
+    def _d3(self):
+        return self.lattice == "d3q19"
+
+    @property
+    def _fshape(self):
+        if self._d1:
+            return (self.ncomp, 3, self.nx)
+        if self._d3:
+            return (self.ncomp, 19, self.nz, self.ny, self.nx)
+        return (self.ncomp, 9, self.ny, self.nx)
+
+    def _fn(self, name):
+        prefix = "oracle_d1q3_" if self._d1 else ("oracle_d3q19_" if self._d3 else "oracle_")
+        return getattr(self.lib, prefix + name)
 
     @property
     def _pp(self):
@@ -162,33 +200,31 @@ class Oracle:
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
         if self._d1 and uu is not None:
             uu = np.ascontiguousarray(uu.reshape(-1)[:self.nx])   # x component only
-        init = self.lib.oracle_d1q3_init if self._d1 else self.lib.oracle_init
-        rc = init(self._pp, _ptr(rho), _ptr(uu), _ptr(self.f))
+        rc = self._fn("init")(self._pp, _ptr(rho), _ptr(uu), _ptr(self.f))
         if rc:
             raise ValueError(f"oracle_init failed ({rc})")
 
     def set_state(self, f):
-        shape = (self.ncomp, 3, self.nx) if self._d1 else (self.ncomp, 9, self.ny, self.nx)
-        self.f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(shape)).copy()
+        self.f = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(self._fshape)).copy()
 
     def run(self, nsteps: int) -> int:
-        run = self.lib.oracle_d1q3_run if self._d1 else self.lib.oracle_run
-        rc = run(self._pp, _ptr(self.f), int(nsteps))
+        rc = self._fn("run")(self._pp, _ptr(self.f), int(nsteps))
         if rc < 0:
             raise ValueError(f"oracle_run failed ({rc})")
         return rc
 
     def moments(self):
-        N, S = self.ncomp, (self.ny, self.nx)
-        rho, U, mu, P = np.zeros((N,) + S), np.zeros((2,) + S), np.zeros((N,) + S), np.zeros((3,) + S)
-        mom = self.lib.oracle_d1q3_moments if self._d1 else self.lib.oracle_moments
-        mom(self._pp, _ptr(self.f), _ptr(rho), _ptr(U), _ptr(mu), _ptr(P))
+        N = self.ncomp
+        S = (self.nz, self.ny, self.nx) if self._d3 else (self.ny, self.nx)
+        nu, npp = (3, 6) if self._d3 else (2, 3)
+        rho, U, mu, P = np.zeros((N,) + S), np.zeros((nu,) + S), np.zeros((N,) + S), np.zeros((npp,) + S)
+        self._fn("moments")(self._pp, _ptr(self.f), _ptr(rho), _ptr(U), _ptr(mu), _ptr(P))
         return dict(rho=rho, U=U, mu=mu, P=P)
 
     def conservation(self):
-        mass, mom, fs = np.zeros(self.ncomp), np.zeros(2), np.zeros(2)
-        cons = self.lib.oracle_d1q3_conservation if self._d1 else self.lib.oracle_conservation
-        cons(self._pp, _ptr(self.f), _ptr(mass), _ptr(mom), _ptr(fs))
+        nd = 3 if self._d3 else 2
+        mass, mom, fs = np.zeros(self.ncomp), np.zeros(nd), np.zeros(nd)
+        self._fn("conservation")(self._pp, _ptr(self.f), _ptr(mass), _ptr(mom), _ptr(fs))
         return dict(mass=mass, mom=mom, force=fs)
 
     # per-site helpers used by the pins
@@ -212,4 +248,17 @@ def equilibrium(rho_s, ux, uy):
 def forcing(rho_s, jx, jy, ax, ay):
     out = np.zeros(9)
     _load().oracle_forcing(float(rho_s), float(jx), float(jy), float(ax), float(ay), _ptr(out))
+    return out
+
+
+def equilibrium3(rho_s, ux, uy, uz):
+    out = np.zeros(19)
+    _load().oracle_d3q19_equilibrium(float(rho_s), float(ux), float(uy), float(uz), _ptr(out))
+    return out
+
+
+def forcing3(rho_s, jx, jy, jz, ax, ay, az):
+    out = np.zeros(19)
+    _load().oracle_d3q19_forcing(float(rho_s), float(jx), float(jy), float(jz), float(ax),
+                                 float(ay), float(az), _ptr(out))
     return out

@@ -70,6 +70,7 @@
  * only): the forces keep their differences but their sum over the components is
  * replaced by the continuum total that Gibbs-Duhem gives for the Flory-Huggins free
  * energy (whose pressure sum rho mu - psi vanishes), (1 - 1/(2 tau)) (1/3) grad rho. */
+/* nz and gz are read by the D3Q19 path only (the other lattices ignore them). */
 typedef struct {
     int ncomp, nx, ny;
     double tau, theta, kappa, gx, gy;
@@ -77,6 +78,8 @@ typedef struct {
     double m[OR_NMAX];
     int forcing_velocity;
     int force_form;
+    int nz;
+    double gz;
 } oracle_params;
 
 static const int VX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -768,5 +771,351 @@ int oracle_d1q3_conservation(const oracle_params* p, const double* f, double* ma
     if (mom) { mom[0] = mx; mom[1] = 0.0; }
     if (force_sum) { force_sum[0] = fx; force_sum[1] = 0.0; }
     work1_free(&w);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ D3Q19
+ *
+ * A three-dimensional lattice for the same method (not one the paper uses; its
+ * equations are written for any lattice whose weights give the Sec. 3 moments).
+ * Nineteen velocities: the rest velocity (weight 1/3), the six axis directions
+ * (1/18) and the twelve face diagonals (1/36), c_s^2 = 1/3; the weights are
+ * isotropic to fourth order, so the equilibrium and forcing polynomials of the
+ * D2Q9 path, written with three-component dot products, have the Sec. 3 and
+ * Eqs. ff1-ff3 moments.  The stages are those of the D2Q9 path in the same order,
+ * with grad g = 3 sum_i w_i v_i g(r + v_i) and lap g = 6 sum_i w_i (g(r + v_i) - g(r))
+ * over the nineteen velocities, periodic in x, y and z, body force (gx, gy, gz).
+ *
+ * Layout: f[(s * 19 + i) * S + (z * ny + y) * nx + x], S = nx ny nz, pre-collision.
+ * Velocity order: 0; (+-1,0,0), (0,+-1,0), (0,0,+-1); (1,1,0), (-1,-1,0), (1,-1,0),
+ * (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1),
+ * (0,-1,1): velocity 2k has the opposite of velocity 2k - 1. */
+
+static const int V3X[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static const int V3Y[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static const int V3Z[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+static const double W3[19] = {1.0 / 3.0,
+                              1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+static int check3(const oracle_params* p)
+{
+    if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
+    if (!(p->tau > 0.5)) return -1;
+    if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
+    if (p->force_form != 0 && p->force_form != 1) return -1;
+    if (p->force_form == 1 && p->kappa != 0.0) return -1;
+    return 0;
+}
+
+/* f^e_i = w_i rho^s (1 + 3 v.u + 9/2 (v.u)^2 - 3/2 u.u) (Sec. 3). */
+void oracle_d3q19_equilibrium(double rho_s, double ux, double uy, double uz, double* fe)
+{
+    double uu = ux * ux + uy * uy + uz * uz;
+    for (int i = 0; i < 19; ++i) {
+        double cu = V3X[i] * ux + V3Y[i] * uy + V3Z[i] * uz;
+        fe[i] = W3[i] * rho_s * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+/* F_i = w_i (3 rho^s v.a + 9 (v.a)(v.j) - 3 a.j) (Eqs. ff1-ff3). */
+void oracle_d3q19_forcing(double rho_s, double jx, double jy, double jz, double ax, double ay,
+                          double az, double* F)
+{
+    double aj = ax * jx + ay * jy + az * jz;
+    for (int i = 0; i < 19; ++i) {
+        double ca = V3X[i] * ax + V3Y[i] * ay + V3Z[i] * az;
+        double cj = V3X[i] * jx + V3Y[i] * jy + V3Z[i] * jz;
+        F[i] = W3[i] * (3.0 * rho_s * ca + 9.0 * ca * cj - 3.0 * aj);
+    }
+}
+
+static long site3(const oracle_params* p, long x, long y, long z)
+{
+    return (wrap(z, p->nz) * p->ny + wrap(y, p->ny)) * p->nx + wrap(x, p->nx);
+}
+
+static double lap3_at(const oracle_params* p, const double* g, int x, int y, int z)
+{
+    double c = g[site3(p, x, y, z)], acc = 0.0;
+    for (int i = 0; i < 19; ++i) acc += W3[i] * (g[site3(p, x + V3X[i], y + V3Y[i], z + V3Z[i])] - c);
+    return 6.0 * acc;
+}
+
+static void grad3_at(const oracle_params* p, const double* g, int x, int y, int z, double* gr)
+{
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 19; ++i) {
+        double v = g[site3(p, x + V3X[i], y + V3Y[i], z + V3Z[i])];
+        a[0] += W3[i] * V3X[i] * v;
+        a[1] += W3[i] * V3Y[i] * v;
+        a[2] += W3[i] * V3Z[i] * v;
+    }
+    for (int d = 0; d < 3; ++d) gr[d] = 3.0 * a[d];
+}
+
+typedef struct {
+    long S;
+    double *rs, *j[3];     /* per component: rho^s, j^s             (N*S) */
+    double *rho, *u[3];    /* total density, barycentric velocity   (S)   */
+    double *nu, *a[3];     /* nu^s, a^s                             (N*S) */
+} work3_t;
+
+static int work3_alloc(const oracle_params* p, work3_t* w)
+{
+    long S = (long)p->nx * p->ny * p->nz, N = p->ncomp;
+    int ok = 1;
+    w->S = S;
+    w->rs = malloc(sizeof(double) * N * S);
+    w->rho = malloc(sizeof(double) * S);
+    w->nu = malloc(sizeof(double) * N * S);
+    ok = w->rs && w->rho && w->nu;
+    for (int d = 0; d < 3; ++d) {
+        w->j[d] = malloc(sizeof(double) * N * S);
+        w->u[d] = malloc(sizeof(double) * S);
+        w->a[d] = malloc(sizeof(double) * N * S);
+        ok = ok && w->j[d] && w->u[d] && w->a[d];
+    }
+    return ok ? 0 : -2;
+}
+
+static void work3_free(work3_t* w)
+{
+    free(w->rs); free(w->rho); free(w->nu);
+    for (int d = 0; d < 3; ++d) { free(w->j[d]); free(w->u[d]); free(w->a[d]); }
+}
+
+/* Stages 1-3 of one D3Q19 step: moments, potentials nu^s, accelerations a^s. */
+static void d3_fields(const oracle_params* p, const double* f, work3_t* w)
+{
+    int N = p->ncomp, nx = p->nx, ny = p->ny, nz = p->nz;
+    long S = w->S;
+    double th = p->theta;
+    double g[3] = {p->gx, p->gy, p->gz};
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < S; ++c) {
+        double rho = 0.0, jt[3] = {0.0, 0.0, 0.0};
+        for (int s = 0; s < N; ++s) {
+            double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < 19; ++i) {
+                double v = f[(long)(s * 19 + i) * S + c];
+                r += v;
+                j[0] += v * V3X[i];
+                j[1] += v * V3Y[i];
+                j[2] += v * V3Z[i];
+            }
+            w->rs[s * S + c] = r;
+            for (int d = 0; d < 3; ++d) {
+                w->j[d][s * S + c] = j[d];
+                jt[d] += j[d];
+            }
+            rho += r;
+        }
+        w->rho[c] = rho;
+        for (int d = 0; d < 3; ++d) w->u[d][c] = jt[d] / rho;
+    }
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long c = ((long)z * ny + y) * nx + x;
+                double rho = w->rho[c];
+                double phi[OR_NMAX], chiphi[OR_NMAX];
+                double sum_phi_m = 0.0, quad = 0.0;
+                for (int s = 0; s < N; ++s) phi[s] = w->rs[s * S + c] / rho;
+                for (int s = 0; s < N; ++s) sum_phi_m += phi[s] / p->m[s];
+                for (int s = 0; s < N; ++s) {
+                    chiphi[s] = 0.0;
+                    for (int t = 0; t < N; ++t) chiphi[s] += p->chi[s * N + t] * phi[t];
+                }
+                for (int s = 0; s < N; ++s) quad += 0.5 * phi[s] * chiphi[s];
+                double lnrho = log(rho);
+                for (int s = 0; s < N; ++s) {
+                    double rs = w->rs[s * S + c];
+                    double coef = th / p->m[s] - 1.0 / 3.0;
+                    double logs = -(th / p->m[s]) * lnrho;
+                    if (coef != 0.0) {
+                        double r = rs > LOG_FLOOR * rho ? rs : LOG_FLOOR * rho;
+                        logs += coef * log(r);
+                    }
+                    double bulk = th * (1.0 / p->m[s] - 1.0 - sum_phi_m + chiphi[s] - quad);
+                    w->nu[s * S + c] = logs + bulk - p->kappa * lap3_at(p, w->rs + s * S, x, y, z);
+                }
+            }
+    double coef = 1.0 - 1.0 / (2.0 * p->tau);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long c = ((long)z * ny + y) * nx + x;
+                for (int s = 0; s < N; ++s) {
+                    double gr[3];
+                    grad3_at(p, w->nu + s * S, x, y, z, gr);
+                    for (int d = 0; d < 3; ++d) w->a[d][s * S + c] = -coef * gr[d] + g[d];
+                }
+                if (p->force_form == 1) {   /* Gibbs-Duhem reading, as in stage_forces */
+                    double A[3] = {0.0, 0.0, 0.0}, gr[3];
+                    for (int s = 0; s < N; ++s)
+                        for (int d = 0; d < 3; ++d)
+                            A[d] += w->rs[s * S + c] * (w->a[d][s * S + c] - g[d]);
+                    grad3_at(p, w->rho, x, y, z, gr);
+                    for (int d = 0; d < 3; ++d) {
+                        double sh = (coef * gr[d] / 3.0 - A[d]) / w->rho[c];
+                        for (int s = 0; s < N; ++s) w->a[d][s * S + c] += sh;
+                    }
+                }
+            }
+}
+
+/* f(r, 0) = f^e(rho^s(r), u(r)); u (3*S: x, y, z components) may be NULL. */
+int oracle_d3q19_init(const oracle_params* p, const double* rho, const double* u, double* f)
+{
+    if (check3(p)) return -1;
+    int N = p->ncomp;
+    long S = (long)p->nx * p->ny * p->nz;
+    for (int s = 0; s < N; ++s)
+        for (long c = 0; c < S; ++c) {
+            double fe[19];
+            oracle_d3q19_equilibrium(rho[s * S + c], u ? u[c] : 0.0, u ? u[S + c] : 0.0,
+                                     u ? u[2 * S + c] : 0.0, fe);
+            for (int i = 0; i < 19; ++i) f[(long)(s * 19 + i) * S + c] = fe[i];
+        }
+    return 0;
+}
+
+/* Advance f (in place) by nsteps D3Q19 timesteps.  Returns 0, -1, -2, or 1 if a
+ * non-finite value appeared. */
+int oracle_d3q19_run(const oracle_params* p, double* f, long nsteps)
+{
+    if (check3(p)) return -1;
+    int N = p->ncomp, nx = p->nx, ny = p->ny, nz = p->nz;
+    work3_t w;
+    if (work3_alloc(p, &w)) { work3_free(&w); return -2; }
+    long S = w.S, total = 19L * N * S;
+    double* gbuf = malloc(sizeof(double) * total);
+    if (!gbuf) { work3_free(&w); return -2; }
+    double *cur = f, *nxt = gbuf;
+    double tau = p->tau;
+    for (long t = 0; t < nsteps; ++t) {
+        d3_fields(p, cur, &w);
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    long c = ((long)z * ny + y) * nx + x;
+                    for (int s = 0; s < N; ++s) {
+                        double fe[19], F[19], j[3];
+                        double rs = w.rs[s * S + c];
+                        for (int d = 0; d < 3; ++d)
+                            j[d] = p->forcing_velocity ? rs * w.u[d][c] : w.j[d][s * S + c];
+                        oracle_d3q19_equilibrium(rs, w.u[0][c], w.u[1][c], w.u[2][c], fe);
+                        oracle_d3q19_forcing(rs, j[0], j[1], j[2], w.a[0][s * S + c],
+                                             w.a[1][s * S + c], w.a[2][s * S + c], F);
+                        for (int i = 0; i < 19; ++i) {
+                            double fi = cur[(long)(s * 19 + i) * S + c];
+                            double post = fi + (fe[i] - fi) / tau + F[i];
+                            nxt[(long)(s * 19 + i) * S + site3(p, x + V3X[i], y + V3Y[i], z + V3Z[i])] = post;
+                        }
+                    }
+                }
+        double* tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (cur != f) memcpy(f, cur, sizeof(double) * total);
+    free(gbuf);
+    work3_free(&w);
+    for (long k = 0; k < total; ++k)
+        if (!isfinite(f[k])) return 1;
+    return 0;
+}
+
+/* Output fields of a D3Q19 state (any pointer may be NULL): rho (N*S); U (3*S) =
+ * u + a/2 with rho a = sum_s rho^s a^s (Eq. scon); mu (N*S) = mu^s/m^s - kappa lap
+ * rho^s; P (6*S) = P_xx, P_xy, P_xz, P_yy, P_yz, P_zz with P = (sum_s rho^s mu^s - psi) I
+ * + kappa sum_s grad rho^s grad rho^s, psi the Eq. lgf density plus the gradient energy. */
+int oracle_d3q19_moments(const oracle_params* p, const double* f, double* rho_out, double* U,
+                         double* mu, double* P)
+{
+    if (check3(p)) return -1;
+    int N = p->ncomp, nx = p->nx, ny = p->ny, nz = p->nz;
+    work3_t w;
+    if (work3_alloc(p, &w)) { work3_free(&w); return -2; }
+    d3_fields(p, f, &w);
+    long S = w.S;
+    if (rho_out) memcpy(rho_out, w.rs, sizeof(double) * N * S);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long c = ((long)z * ny + y) * nx + x;
+                if (U)
+                    for (int d = 0; d < 3; ++d) {
+                        double fd = 0.0;
+                        for (int s = 0; s < N; ++s) fd += w.rs[s * S + c] * w.a[d][s * S + c];
+                        U[d * S + c] = w.u[d][c] + 0.5 * fd / w.rho[c];
+                    }
+                if (mu || P) {
+                    double rsl[OR_NMAX], mub[OR_NMAX], muf[OR_NMAX];
+                    for (int s = 0; s < N; ++s) rsl[s] = w.rs[s * S + c];
+                    oracle_mu_bulk(p, rsl, mub);
+                    for (int s = 0; s < N; ++s)
+                        muf[s] = mub[s] - p->kappa * lap3_at(p, w.rs + s * S, x, y, z);
+                    if (mu)
+                        for (int s = 0; s < N; ++s) mu[s * S + c] = muf[s];
+                    if (P) {
+                        double psi = oracle_psi(p, rsl), rmu = 0.0, gg = 0.0;
+                        double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                        for (int s = 0; s < N; ++s) {
+                            double gr[3];
+                            grad3_at(p, w.rs + s * S, x, y, z, gr);
+                            rmu += rsl[s] * muf[s];
+                            gg += 0.5 * p->kappa * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+                            t[0] += p->kappa * gr[0] * gr[0];
+                            t[1] += p->kappa * gr[0] * gr[1];
+                            t[2] += p->kappa * gr[0] * gr[2];
+                            t[3] += p->kappa * gr[1] * gr[1];
+                            t[4] += p->kappa * gr[1] * gr[2];
+                            t[5] += p->kappa * gr[2] * gr[2];
+                        }
+                        double iso = rmu - (psi + gg);
+                        P[c] = iso + t[0];
+                        P[S + c] = t[1];
+                        P[2 * S + c] = t[2];
+                        P[3 * S + c] = iso + t[3];
+                        P[4 * S + c] = t[4];
+                        P[5 * S + c] = iso + t[5];
+                    }
+                }
+            }
+    work3_free(&w);
+    return 0;
+}
+
+/* Global sums of a D3Q19 state: mass^s (N), momentum (3), force sum_s rho^s a^s (3). */
+int oracle_d3q19_conservation(const oracle_params* p, const double* f, double* mass,
+                              double* mom, double* force_sum)
+{
+    if (check3(p)) return -1;
+    int N = p->ncomp;
+    work3_t w;
+    if (work3_alloc(p, &w)) { work3_free(&w); return -2; }
+    d3_fields(p, f, &w);
+    long S = w.S;
+    for (int s = 0; s < N; ++s) {
+        double acc = 0.0;
+        for (long c = 0; c < S; ++c) acc += w.rs[s * S + c];
+        if (mass) mass[s] = acc;
+    }
+    double m3[3] = {0.0, 0.0, 0.0}, f3[3] = {0.0, 0.0, 0.0};
+    for (long c = 0; c < S; ++c)
+        for (int s = 0; s < N; ++s)
+            for (int d = 0; d < 3; ++d) {
+                m3[d] += w.j[d][s * S + c];
+                f3[d] += w.rs[s * S + c] * w.a[d][s * S + c];
+            }
+    for (int d = 0; d < 3; ++d) {
+        if (mom) mom[d] = m3[d];
+        if (force_sum) force_sum[d] = f3[d];
+    }
+    work3_free(&w);
     return 0;
 }
