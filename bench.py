@@ -51,6 +51,8 @@ def workloads():
         "ternary_256x256": lambda: inputs.ternary_gauss(),
         "binary_64x64": lambda: inputs.binary_noise(precision="fp32"),
         "slab_8192x2048": lambda: inputs.slab(),
+        "ternary3d_256": lambda: inputs.ternary3d(256),
+        "ternary3d_128": lambda: inputs.ternary3d(128, name="ternary3d_128"),
     }
 
 
@@ -413,7 +415,8 @@ def main():
         out_rho = torch.empty(prob.rho.shape, dtype=torch.float64).pin_memory().numpy()
         out_u = torch.empty(prob.u.shape, dtype=torch.float64).pin_memory().numpy()
         sim2 = mclb.Simulation(N, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
-                               prob.kappa, prob.force, args.precision, kern, sptr)
+                               prob.kappa, prob.force, args.precision, kern, sptr,
+                               lattice=prob.lattice, nz=prob.nz)
         sim2.init_fields(rho_h, u_h)
         sim2.step(args.warmup)
         sim2.status()
@@ -479,6 +482,19 @@ def main():
                 "hbm_frac_of_measured": v.bytes_per_step / (t / 200) / 1e9 / peak,
                 "speedup_vs_fp32": val / slab_fp32}
             v.close()
+        # the D3Q19 lattice (staged schedule): the paper's ternary chi set on 256^3 in FP32
+        cube = workloads()["ternary3d_256"]()
+        v = mclb.Simulation.from_problem(cube, precision="fp32", stream=sptr)
+        t = time_steps(torch, v, 50, args.warmup, stream)
+        val = cube.sites * cube.ncomp * 50 / t / 1e6
+        variants["d3q19_ternary3d_256_fp32"] = {
+            "value": val, "steps": 50, "status_ok": v.status() == 0,
+            "launches_per_step": v.launches_per_step,
+            "hbm_gbs_algorithmic": v.bytes_per_step / (t / 50) / 1e9,
+            "hbm_frac_of_measured": v.bytes_per_step / (t / 50) / 1e9 / peak,
+            "note": "152 B per site and component (19 loads + 19 stores of f in FP32) per step; "
+                    "three launches (density, potential, collision)"}
+        v.close()
         variants["batched_512"] = run_batched(torch, mclb, sptr, stream, args.warmup, value / world)
     clk.__exit__()
     clocks = clk.summary()

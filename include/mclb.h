@@ -104,8 +104,18 @@ typedef enum {
 /* Lattice. */
 typedef enum {
     MCLB_D2Q9 = 0,   /* two-dimensional, nine velocities (see the conventions above)      */
-    MCLB_D1Q3 = 1    /* the one-dimensional lattice of the paper's simulations (Sec. 4):
+    MCLB_D1Q3 = 1,   /* the one-dimensional lattice of the paper's simulations (Sec. 4):
                         v_0 = 0, v_1 = +1, v_2 = -1, weights 2/3, 1/6, 1/6; ny must be 1   */
+    MCLB_D3Q19 = 2   /* three dimensions, nz layers: the rest velocity (weight 1/3), the six
+                        axis directions (1/18) and the twelve face diagonals (1/36), in the
+                        order 0; (+-1,0,0), (0,+-1,0), (0,0,+-1); (1,1,0), (-1,-1,0),
+                        (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1),
+                        (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).  Not a lattice the paper
+                        uses: its equations hold for any lattice whose weights give the
+                        Sec. 3 moments, which these do.  The staged schedule (three
+                        launches per step), FP64 or FP32 storage, single handles only.
+                        Fields are [.][z][y][x]; U has 3 components, P 6 (xx, xy, xz, yy,
+                        yz, zz), the momentum and force sums 3                             */
 } mclb_lattice;
 
 /* Problem statement (Sec. 3 and Sec. 4 of the paper).
@@ -125,6 +135,8 @@ typedef enum {
  *   forcing_velocity  mclb_forcing_velocity (0: Eq. ff3 as printed)
  *   lattice    mclb_lattice (0: D2Q9)
  *   force_form mclb_force_form (0: Eq. definef as printed)
+ *   nz         layers of a D3Q19 lattice (0 or 1 for the other lattices, which reject more)
+ *   force_z    z component of the body acceleration (D3Q19 only; 0 otherwise)
  *   mass_every 0 (off, the default) or the period, in timesteps, of the per-component
  *              mass compensation.  Eq. ff1 and the collision keep every component's total
  *              mass exactly; stored in FP32 or 16 bits, the rounding of each site's
@@ -156,6 +168,8 @@ typedef struct {
     int lattice;
     int force_form;
     int mass_every;
+    int nz;
+    double force_z;
 } mclb_params;
 
 typedef struct mclb_handle_s* mclb_handle;
@@ -172,7 +186,8 @@ int mclb_create(const mclb_params* params, mclb_handle* out);
 
 /* Set f^s_i(r, 0) to the equilibrium of the given fields (Sec. 3 equilibrium
  * moments with the barycentric u).  rho: N*ny*nx component densities rho^s, each
- * > 0 in total per site; u: 2*ny*nx barycentric velocity or NULL for rest.
+ * > 0 in total per site; u: 2*ny*nx barycentric velocity (D3Q19: N*nz*ny*nx densities,
+ * 3*nz*ny*nx velocity) or NULL for rest.
  * Host pointers; the copy is synchronous.  The values are checked on the device after
  * the upload; on EINVAL the message names the first failing site and the state is
  * left as it was.  Resets the step counter.  Errors: EHANDLE, EINVAL (NULL rho,
@@ -197,6 +212,7 @@ int mclb_status(mclb_handle h);
  * pointers, synchronises.
  *   rho (N*ny*nx)  component densities rho^s = sum_i f^s_i               (Sec. 3)
  *   U   (2*ny*nx)  fluid velocity U = u + a/2 with rho a = sum_s rho^s a^s (Eq. scon)
+ *                  (D3Q19: every field over nz*ny*nx sites, U 3 and P 6 components)
  *   mu  (N*ny*nx)  chemical potential per unit mass mu^s/m^s, gradient term included
  *   P   (3*ny*nx)  pressure tensor P_xx, P_xy, P_yy:
  *                  (sum_s rho^s mu^s/m^s - psi) I + kappa sum_s grad rho^s grad rho^s,
@@ -209,7 +225,8 @@ int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, doubl
 /* FP64 global sums of the current state (any pointer may be NULL), synchronises:
  *   mass (N)       sum over sites of rho^s                (kept by Eq. ff1)
  *   mom (2)        sum over sites of rho u                (Sec. 3 moments)
- *   force_sum (2)  sum over sites of sum_s rho^s a^s      (the next step adds it to mom) */
+ *   force_sum (2)  sum over sites of sum_s rho^s a^s      (the next step adds it to mom)
+ * (D3Q19: mom and force_sum have 3 components.) */
 int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_sum);
 
 /* Mean compositions phi^s = rho^s / rho of the nphase bulk phases of the current
@@ -223,7 +240,8 @@ int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_su
 int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi);
 
 /* Copy the distributions in or out as FP64 pre-collision values f^s_i(r, t), layout
- * [s][i][y][x] (count must equal N*9*ny*nx; on D1Q3 [s][i][x], count N*3*nx).  Host pointers, synchronous.  Getting
+ * [s][i][y][x] (count must equal N*9*ny*nx; on D1Q3 [s][i][x], count N*3*nx; on D3Q19
+ * [s][i][z][y][x], count N*19*nz*ny*nx).  Host pointers, synchronous.  Getting
  * and setting a state is exact in FP64 and FP32; in the shifted modes setting
  * stores the state as R and 16-bit deviations (see mclb_precision), so a state
  * read back differs by the rounding of the deviations.  set_state checks the values
@@ -302,7 +320,8 @@ int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_o
  * Steps are replayed from a CUDA graph in chunks of 32.  D1Q3 instances of one N
  * advance together in one launch per 4096 timesteps (one CTA per line, the line in
  * shared memory; lines too long for that step one launch per timestep).  precision
- * and stream are taken from params[0]; kernel is ignored.  Instances share no data.  Every instance must be initialised
+ * and stream are taken from params[0]; kernel is ignored.  D3Q19 instances are rejected.
+ * Instances share no data.  Every instance must be initialised
  * (mclb_batch_init_fields) before the first mclb_batch_step.  Errors as for the
  * single-simulation calls, and EINVAL for an index outside 0..count-1.
  * ------------------------------------------------------------------------- */

@@ -30,8 +30,8 @@ FP64, FP32, BF16_SHIFTED, FP16_SHIFTED = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_STAGED = 0, 1, 2
 FORCING_COMPONENT, FORCING_BARYCENTRIC = 0, 1
 FORCE_COMPONENT, FORCE_GIBBS_DUHEM = 0, 1
-D2Q9, D1Q3 = 0, 1
-LATTICES = {"d2q9": D2Q9, "d1q3": D1Q3}
+D2Q9, D1Q3, D3Q19 = 0, 1, 2
+LATTICES = {"d2q9": D2Q9, "d1q3": D1Q3, "d3q19": D3Q19}
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16_SHIFTED, "fp16": FP16_SHIFTED}
 NMAX = 8
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "ETIMEOUT",
@@ -55,7 +55,7 @@ class mclb_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("forcing_velocity", ctypes.c_int),
                 ("lattice", ctypes.c_int), ("force_form", ctypes.c_int),
-                ("mass_every", ctypes.c_int)]
+                ("mass_every", ctypes.c_int), ("nz", ctypes.c_int), ("force_z", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -134,12 +134,13 @@ def _tensor_ptr(t) -> Optional[int]:
     return int(t.data_ptr())
 
 
-def _fields(rho, u, ncomp, ny, nx, device=False):
-    """Check the sizes of initial fields (the C call reads N*ny*nx and 2*ny*nx doubles)."""
+def _fields(rho, u, ncomp, ny, nx, device=False, nz=1, ud=2):
+    """Check the sizes of initial fields (the C call reads N*nz*ny*nx and ud*nz*ny*nx
+    doubles; nz = 1 and ud = 2 except on D3Q19)."""
     if not device:
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
-    for name, a, want in (("rho", rho, ncomp * ny * nx), ("u", u, 2 * ny * nx)):
+    for name, a, want in (("rho", rho, ncomp * nz * ny * nx), ("u", u, ud * nz * ny * nx)):
         if a is None:
             continue
         n = a.numel() if device else a.size
@@ -152,8 +153,9 @@ def _fields(rho, u, ncomp, ny, nx, device=False):
 
 def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, force=(0.0, 0.0),
                 precision="fp32", kernel=KERNEL_AUTO, stream=None, forcing_velocity=0,
-                lattice="d2q9", force_form=0, mass_every=0):
-    """Build an mclb_params struct; returns (struct, keep-alive arrays)."""
+                lattice="d2q9", force_form=0, mass_every=0, nz=1):
+    """Build an mclb_params struct; returns (struct, keep-alive arrays).  ``force`` has
+    two components, or three on D3Q19 (the third is force_z)."""
     chi = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp))
     marr = None if m is None else np.ascontiguousarray(np.asarray(m, dtype=np.float64))
     p = mclb_params()
@@ -162,6 +164,8 @@ def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, for
     p.chi = _dp(chi)
     p.m = _dp(marr)
     p.force[0], p.force[1] = float(force[0]), float(force[1])
+    p.force_z = float(force[2]) if len(force) > 2 else 0.0
+    p.nz = int(nz)
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.kernel = int(kernel)
     p.stream = ctypes.c_void_p(stream) if stream else None
@@ -173,16 +177,19 @@ def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, for
 
 
 class Simulation:
-    """One simulation handle (mclb_create ... mclb_destroy)."""
+    """One simulation handle (mclb_create ... mclb_destroy).  Fields are (., ny, nx), or
+    (., nz, ny, nx) with three velocity and six pressure components on D3Q19."""
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
                  force=(0.0, 0.0), precision="fp32", kernel=KERNEL_AUTO, stream=None,
-                 forcing_velocity=0, lattice="d2q9", force_form=0, mass_every=0):
+                 forcing_velocity=0, lattice="d2q9", force_form=0, mass_every=0, nz=1):
         self.lib = load()
         self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
         p, keep = make_params(ncomp, nx, ny, tau, chi, m, theta, kappa, force, precision, kernel,
-                              stream, forcing_velocity, lattice, force_form, mass_every)
-        self.q = 3 if p.lattice == D1Q3 else 9
+                              stream, forcing_velocity, lattice, force_form, mass_every, nz)
+        self.q = {D1Q3: 3, D3Q19: 19}.get(p.lattice, 9)
+        self.nz = max(int(nz), 1) if p.lattice == D3Q19 else 1
+        self.ud = 3 if p.lattice == D3Q19 else 2
         h = ctypes.c_void_p()
         _check(self.lib.mclb_create(ctypes.byref(p), ctypes.byref(h)), "mclb_create")
         self.h = h
@@ -192,7 +199,7 @@ class Simulation:
         s = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta, prob.kappa,
                 prob.force, precision or prob.precision, kernel, stream,
                 getattr(prob, "forcing_velocity", 0), getattr(prob, "lattice", "d2q9"),
-                getattr(prob, "force_form", 0), mass_every)
+                getattr(prob, "force_form", 0), mass_every, getattr(prob, "nz", 1))
         s.init_fields(prob.rho, prob.u)
         return s
 
@@ -215,14 +222,14 @@ class Simulation:
 
     @property
     def shape(self):
-        return (self.ny, self.nx)
+        return (self.nz, self.ny, self.nx) if self.q == 19 else (self.ny, self.nx)
 
     def init_fields(self, rho, u=None):
-        rho, uu = _fields(rho, u, self.ncomp, self.ny, self.nx)
+        rho, uu = _fields(rho, u, self.ncomp, self.ny, self.nx, nz=self.nz, ud=self.ud)
         _check(self.lib.mclb_init_fields(self.h, _dp(rho), _dp(uu)), "mclb_init_fields")
 
     def init_fields_device(self, rho_t, u_t=None):
-        _fields(rho_t, u_t, self.ncomp, self.ny, self.nx, device=True)
+        _fields(rho_t, u_t, self.ncomp, self.ny, self.nx, device=True, nz=self.nz, ud=self.ud)
         _check(self.lib.mclb_init_fields_device(self.h, _tensor_ptr(rho_t), _tensor_ptr(u_t)),
                "mclb_init_fields_device")
 
@@ -237,8 +244,10 @@ class Simulation:
 
     def moments(self, rho=True, U=True, mu=True, P=True):
         N, S = self.ncomp, self.shape
-        out = dict(rho=np.empty((N,) + S) if rho else None, U=np.empty((2,) + S) if U else None,
-                   mu=np.empty((N,) + S) if mu else None, P=np.empty((3,) + S) if P else None)
+        npc = 6 if self.ud == 3 else 3
+        out = dict(rho=np.empty((N,) + S) if rho else None,
+                   U=np.empty((self.ud,) + S) if U else None,
+                   mu=np.empty((N,) + S) if mu else None, P=np.empty((npc,) + S) if P else None)
         _check(self.lib.mclb_moments(self.h, _dp(out["rho"]), _dp(out["U"]), _dp(out["mu"]),
                                      _dp(out["P"])), "mclb_moments")
         return out
@@ -248,7 +257,7 @@ class Simulation:
                                             _tensor_ptr(mu), _tensor_ptr(P)), "mclb_moments_device")
 
     def conservation(self):
-        mass, mom, fs = np.empty(self.ncomp), np.empty(2), np.empty(2)
+        mass, mom, fs = np.empty(self.ncomp), np.empty(self.ud), np.empty(self.ud)
         _check(self.lib.mclb_conservation(self.h, _dp(mass), _dp(mom), _dp(fs)),
                "mclb_conservation")
         return dict(mass=mass, mom=mom, force=fs)
@@ -259,8 +268,12 @@ class Simulation:
         return out
 
     def get_state(self):
-        """Pre-collision populations: (N, 9, ny, nx) on D2Q9, (N, 3, nx) on D1Q3."""
-        f = np.empty((self.ncomp, 3, self.nx) if self.q == 3 else (self.ncomp, 9, self.ny, self.nx))
+        """Pre-collision populations: (N, 9, ny, nx) on D2Q9, (N, 3, nx) on D1Q3,
+        (N, 19, nz, ny, nx) on D3Q19."""
+        if self.q == 3:
+            f = np.empty((self.ncomp, 3, self.nx))
+        else:
+            f = np.empty((self.ncomp, self.q) + self.shape)
         _check(self.lib.mclb_get_state(self.h, _dp(f), f.size), "mclb_get_state")
         return f
 

@@ -70,6 +70,13 @@ const KernelTable& table_for(int precision)
     }
 }
 
+// velocities per site and velocity components of a problem's lattice
+int lattice_q(const Problem& P)
+{
+    return P.lattice == MCLB_D1Q3 ? 3 : (P.lattice == MCLB_D3Q19 ? 19 : Q);
+}
+int vel_dims(const Problem& P) { return P.lattice == MCLB_D3Q19 ? 3 : 2; }
+
 int validate(const mclb_params* p)
 {
     if (!p) return fail(MCLB_EINVAL, "params is NULL");
@@ -104,8 +111,16 @@ int validate(const mclb_params* p)
         return fail(MCLB_EINVAL, "kernel=%d unknown", p->kernel);
     if (p->forcing_velocity != MCLB_FORCING_COMPONENT && p->forcing_velocity != MCLB_FORCING_BARYCENTRIC)
         return fail(MCLB_EINVAL, "forcing_velocity=%d unknown", p->forcing_velocity);
-    if (p->lattice != MCLB_D2Q9 && p->lattice != MCLB_D1Q3)
+    if (p->lattice != MCLB_D2Q9 && p->lattice != MCLB_D1Q3 && p->lattice != MCLB_D3Q19)
         return fail(MCLB_EINVAL, "lattice=%d unknown", p->lattice);
+    if (p->nz < 0) return fail(MCLB_EINVAL, "nz=%d must be >= 0", p->nz);
+    if (p->lattice != MCLB_D3Q19 && p->nz > 1)
+        return fail(MCLB_EINVAL, "nz=%d > 1 needs the D3Q19 lattice", p->nz);
+    if (!std::isfinite(p->force_z)) return fail(MCLB_EINVAL, "force_z not finite");
+    if (p->lattice != MCLB_D3Q19 && p->force_z != 0.0)
+        return fail(MCLB_EINVAL, "force_z != 0 needs the D3Q19 lattice");
+    if ((long long)p->nx * p->ny * (p->nz > 1 ? p->nz : 1) > (1LL << 31))
+        return fail(MCLB_EINVAL, "grid %dx%dx%d exceeds 2^31 sites", p->nx, p->ny, p->nz);
     if (p->force_form != MCLB_FORCE_COMPONENT && p->force_form != MCLB_FORCE_GIBBS_DUHEM)
         return fail(MCLB_EINVAL, "force_form=%d unknown", p->force_form);
     if (p->force_form == MCLB_FORCE_GIBBS_DUHEM) {
@@ -116,6 +131,8 @@ int validate(const mclb_params* p)
                                      "(kernel AUTO or STAGED) on D2Q9");
     }
     if (p->mass_every < 0) return fail(MCLB_EINVAL, "mass_every=%d must be >= 0", p->mass_every);
+    if (p->lattice == MCLB_D3Q19 && p->precision != MCLB_FP64 && p->precision != MCLB_FP32)
+        return fail(MCLB_EINVAL, "lattice D3Q19 stores FP64 or FP32 (precision=%d)", p->precision);
     if (p->lattice == MCLB_D1Q3) {
         if (p->ny != 1) return fail(MCLB_EINVAL, "lattice D1Q3 needs ny = 1 (ny=%d)", p->ny);
         if (p->precision != MCLB_FP64 && p->precision != MCLB_FP32)
@@ -126,12 +143,14 @@ int validate(const mclb_params* p)
 
 void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
 {
-    const int hx = p->lattice == MCLB_D1Q3 ? 0 : tab.hx;
+    // ghost columns only in the D2Q9 layout (the D1Q3 and D3Q19 kernels wrap by index)
+    const int hx = p->lattice == MCLB_D2Q9 ? tab.hx : 0;
     memset(&P, 0, sizeof(P));
     P.N = p->ncomp;
     P.nx = p->nx;
     P.ny = p->ny;
-    P.S = (long long)p->nx * p->ny;
+    P.nz = (p->lattice == MCLB_D3Q19 && p->nz > 1) ? p->nz : 1;
+    P.S = (long long)p->nx * p->ny * P.nz;
     P.hx = hx;
     P.pitch = 2LL * hx + (long long)((p->nx + ROW_ALIGN - 1) / ROW_ALIGN) * ROW_ALIGN;
     P.plane = P.pitch * Q * p->ny;
@@ -140,6 +159,10 @@ void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
         P.pitch = p->nx;
         P.plane = 3LL * p->nx;
     }
+    if (P.lattice == MCLB_D3Q19) {  // compact [s][z][y][19][x], no ghost columns
+        P.pitch = p->nx;
+        P.plane = 19LL * P.S;
+    }
     // 16-bit formats: the FP32 density lines follow the deviations, 256-byte aligned
     P.rbytes = tab.shifted ? (long long)((P.plane * P.N * (long long)tab.storage_bytes + 255) / 256 * 256) : 0;
     P.tau = p->tau;
@@ -147,6 +170,7 @@ void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
     P.kappa = p->kappa;
     P.gx = p->force[0];
     P.gy = p->force[1];
+    P.gz = p->force_z;
     P.forcing_velocity = p->forcing_velocity;
     P.force_form = p->force_form;
     P.mass_every = p->mass_every;
@@ -172,7 +196,7 @@ struct mclb_handle_s {
     Scratch sc;
     FusedPlan plan;
     bool fused;
-    const Line3Table* line3;      // D1Q3 handles: their kernels (null for D2Q9)
+    const LatticeTable* alt;      // D1Q3 and D3Q19 handles: their kernels (null for D2Q9)
     cudaStream_t stream;
     bool own_stream;
     void* f[2];
@@ -350,8 +374,8 @@ int record_mass(mclb_handle h)
 // nsteps timesteps, graph-replayed in GRAPH_STEPS chunks where possible.
 int advance(mclb_handle h, long nsteps)
 {
-    if (h->line3) {
-        CK(h->line3->step(h->P, h->sc, h->f, &h->cur, nsteps, h->stream));
+    if (h->alt) {
+        CK(h->alt->step(h->P, h->sc, h->f, &h->cur, nsteps, h->stream));
         return MCLB_OK;
     }
     long left = nsteps;
@@ -418,8 +442,12 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     h->fbytes = (size_t)P.plane * P.N * h->tab->storage_bytes;
     if (h->tab->shifted) h->fbytes = (size_t)P.rbytes + (size_t)P.N * P.ny * P.pitch * sizeof(float);
     if (P.lattice == MCLB_D1Q3) {
-        h->line3 = h->tab->line3;
-        if (!h->line3) return bail(fail(MCLB_EINVAL, "no D1Q3 kernels for this precision"));
+        h->alt = h->tab->line3;
+        if (!h->alt) return bail(fail(MCLB_EINVAL, "no D1Q3 kernels for this precision"));
+    }
+    if (P.lattice == MCLB_D3Q19) {
+        h->alt = h->tab->d3q19;
+        if (!h->alt) return bail(fail(MCLB_EINVAL, "no D3Q19 kernels for this precision"));
     }
     const size_t cbytes = (h->precision == MCLB_FP64) ? sizeof(double) : sizeof(float);
     for (int b = 0; b < 2; ++b) {
@@ -431,7 +459,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaMalloc(&h->sc.rho_s, (size_t)P.N * P.S * cbytes) != cudaSuccess ||
         cudaMalloc(&h->sc.nu, (size_t)P.N * P.S * cbytes) != cudaSuccess)
         return bail(fail(MCLB_ENOMEM, "scratch fields"));
-    h->sc.partial_cap = (size_t)REDUCE_BLOCKS * (NMAX + 4) + 64;
+    h->sc.partial_cap = (size_t)REDUCE_BLOCKS * (NMAX + 6) + 64;
     if (cudaMalloc(&h->sc.partial, h->sc.partial_cap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->sc.status, sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&h->sc.mass_ref, NMAX * sizeof(double)) != cudaSuccess)
@@ -447,11 +475,11 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaStreamCreateWithFlags(&h->status_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
     h->fused = false;
-    if (P.force_form == MCLB_FORCE_GIBBS_DUHEM && !h->line3) h->kernel = MCLB_KERNEL_STAGED;
-    if (h->line3) {
-        if (cudaMalloc(&h->sc.line_item, h->line3->item_bytes) != cudaSuccess)
+    if (P.force_form == MCLB_FORCE_GIBBS_DUHEM && !h->alt) h->kernel = MCLB_KERNEL_STAGED;
+    if (h->alt) {
+        if (h->alt->item_bytes > 0 && cudaMalloc(&h->sc.line_item, h->alt->item_bytes) != cudaSuccess)
             return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));
-        if (h->line3->prepare(P, h->sc, h->f) != cudaSuccess)
+        if (h->alt->prepare(P, h->sc, h->f) != cudaSuccess)
             return bail(fail(MCLB_ECUDA, "D1Q3 line description upload failed"));
     } else if (h->kernel != MCLB_KERNEL_STAGED) {
         h->plan = h->tab->plan_fused(P, sms);
@@ -498,8 +526,8 @@ static int init_common(mclb_handle h, const double* rho_d, const double* u_d)
     int rc = settle_status(h);
     if (rc) return rc;
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
-    if (h->line3)
-        CK(h->line3->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
+    if (h->alt)
+        CK(h->alt->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
     else
         CK(h->tab->init(h->P, h->sc, rho_d, u_d, h->f[0], h->stream));
     h->cur = 0;
@@ -514,15 +542,16 @@ int mclb_init_fields(mclb_handle h, const double* rho, const double* u)
     if (!rho) return fail(MCLB_EINVAL, "rho is NULL");
     const Problem& P = h->P;
     // upload, then check on the device; the state is touched only if every site passes
-    rc = ensure_dtmp(h, (size_t)(P.N + 2) * P.S + 1);
+    const int ud = vel_dims(P);
+    rc = ensure_dtmp(h, (size_t)(P.N + ud) * P.S + 1);
     if (rc) return rc;
     CK(cudaMemcpyAsync(h->dtmp, rho, sizeof(double) * P.N * P.S, cudaMemcpyHostToDevice,
                        h->stream));
     if (u)
-        CK(cudaMemcpyAsync(h->dtmp + P.N * P.S, u, sizeof(double) * 2 * P.S,
+        CK(cudaMemcpyAsync(h->dtmp + P.N * P.S, u, sizeof(double) * ud * P.S,
                            cudaMemcpyHostToDevice, h->stream));
-    unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(h->dtmp + (P.N + 2) * P.S);
-    CK(check_fields(h->dtmp, u ? h->dtmp + P.N * P.S : nullptr, P.N, P.S, d_bad, h->stream));
+    unsigned long long* d_bad = reinterpret_cast<unsigned long long*>(h->dtmp + (P.N + ud) * P.S);
+    CK(check_fields(h->dtmp, u ? h->dtmp + P.N * P.S : nullptr, P.N, ud, P.S, d_bad, h->stream));
     unsigned long long bad = 0;
     CK(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -605,7 +634,7 @@ int mclb_test_withhold_copies(mclb_handle h, int on)
 double mclb_bytes_per_step(mclb_handle h)
 {
     if (check_handle(h)) return -1.0;
-    const double q = h->line3 ? 3.0 : (double)Q;
+    const double q = (double)lattice_q(h->P);
     const double per = q * (double)h->tab->storage_bytes + (h->tab->shifted ? sizeof(float) : 0.0);
     return 2.0 * h->P.N * (double)h->P.S * per;
 }
@@ -613,7 +642,8 @@ double mclb_bytes_per_step(mclb_handle h)
 int mclb_launches_per_step(mclb_handle h)
 {
     if (check_handle(h)) return -1;
-    if (h->line3) return 1;
+    if (h->P.lattice == MCLB_D1Q3) return 1;
+    if (h->P.lattice == MCLB_D3Q19) return 3;
     return h->fused ? 2 : 3;
 }
 
@@ -622,8 +652,8 @@ int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, doubl
     int rc = check_handle(h);
     if (rc) return rc;
     if (!rho && !U && !mu && !P) return MCLB_OK;
-    if (h->line3)
-        CK(h->line3->moments(h->P, h->sc, h->f[h->cur], rho, U, mu, P, h->stream));
+    if (h->alt)
+        CK(h->alt->moments(h->P, h->sc, h->f[h->cur], rho, U, mu, P, h->stream));
     else
         CK(h->tab->moments(h->P, h->sc, h->f[h->cur], rho, U, mu, P, h->stream));
     return MCLB_OK;
@@ -635,18 +665,19 @@ int mclb_moments(mclb_handle h, double* rho, double* U, double* mu, double* P)
     if (rc) return rc;
     const Problem& Pb = h->P;
     const long long S = Pb.S;
-    rc = ensure_dtmp(h, (size_t)(2 * Pb.N + 5) * S);
+    const int ud = vel_dims(Pb), np = ud == 3 ? 6 : 3;
+    rc = ensure_dtmp(h, (size_t)(2 * Pb.N + ud + np) * S);
     if (rc) return rc;
     double* d_rho = rho ? h->dtmp : nullptr;
     double* d_U = U ? h->dtmp + Pb.N * S : nullptr;
-    double* d_mu = mu ? h->dtmp + (Pb.N + 2) * S : nullptr;
-    double* d_P = P ? h->dtmp + (2 * Pb.N + 2) * S : nullptr;
+    double* d_mu = mu ? h->dtmp + (Pb.N + ud) * S : nullptr;
+    double* d_P = P ? h->dtmp + (2 * Pb.N + ud) * S : nullptr;
     rc = mclb_moments_device(h, d_rho, d_U, d_mu, d_P);
     if (rc) return rc;
     if (rho) CK(cudaMemcpyAsync(rho, d_rho, sizeof(double) * Pb.N * S, cudaMemcpyDeviceToHost, h->stream));
-    if (U) CK(cudaMemcpyAsync(U, d_U, sizeof(double) * 2 * S, cudaMemcpyDeviceToHost, h->stream));
+    if (U) CK(cudaMemcpyAsync(U, d_U, sizeof(double) * ud * S, cudaMemcpyDeviceToHost, h->stream));
     if (mu) CK(cudaMemcpyAsync(mu, d_mu, sizeof(double) * Pb.N * S, cudaMemcpyDeviceToHost, h->stream));
-    if (P) CK(cudaMemcpyAsync(P, d_P, sizeof(double) * 3 * S, cudaMemcpyDeviceToHost, h->stream));
+    if (P) CK(cudaMemcpyAsync(P, d_P, sizeof(double) * np * S, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return MCLB_OK;
 }
@@ -655,19 +686,19 @@ int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_su
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    const int N = h->P.N;
-    rc = ensure_dtmp(h, NMAX + 4);
+    const int N = h->P.N, ud = vel_dims(h->P);
+    rc = ensure_dtmp(h, NMAX + 6);
     if (rc) return rc;
-    if (h->line3)
-        CK(h->line3->conservation(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    if (h->alt)
+        CK(h->alt->conservation(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
     else
         CK(h->tab->conservation(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
-    double out[NMAX + 4];
-    CK(cudaMemcpyAsync(out, h->dtmp, sizeof(double) * (N + 4), cudaMemcpyDeviceToHost, h->stream));
+    double out[NMAX + 6];
+    CK(cudaMemcpyAsync(out, h->dtmp, sizeof(double) * (N + 2 * ud), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (mass) memcpy(mass, out, sizeof(double) * N);
-    if (mom) memcpy(mom, out + N, sizeof(double) * 2);
-    if (force_sum) memcpy(force_sum, out + N + 2, sizeof(double) * 2);
+    if (mom) memcpy(mom, out + N, sizeof(double) * ud);
+    if (force_sum) memcpy(force_sum, out + N + ud, sizeof(double) * ud);
     return MCLB_OK;
 }
 
@@ -675,12 +706,12 @@ int mclb_get_state(mclb_handle h, double* f, size_t count)
 {
     int rc = check_handle(h);
     if (rc) return rc;
-    const size_t want = (size_t)h->P.N * (h->line3 ? 3 : Q) * h->P.S;
+    const size_t want = (size_t)h->P.N * lattice_q(h->P) * h->P.S;
     if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
     rc = ensure_dtmp(h, want);
     if (rc) return rc;
-    if (h->line3)
-        CK(h->line3->get_state(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
+    if (h->alt)
+        CK(h->alt->get_state(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
     else
         CK(h->tab->get_state(h->P, h->sc, h->f[h->cur], h->dtmp, h->stream));
     CK(cudaMemcpyAsync(f, h->dtmp, sizeof(double) * want, cudaMemcpyDeviceToHost, h->stream));
@@ -693,7 +724,7 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
     int rc = check_handle(h);
     if (rc) return rc;
     const Problem& P = h->P;
-    const size_t want = (size_t)P.N * (h->line3 ? 3 : Q) * P.S;
+    const size_t want = (size_t)P.N * lattice_q(P) * P.S;
     if (!f || count != want) return fail(MCLB_EINVAL, "count=%zu, expected %zu", count, want);
     rc = ensure_dtmp(h, want + 1);
     if (rc) return rc;
@@ -707,8 +738,8 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count)
     rc = settle_status(h);
     if (rc) return rc;
     CK(cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream));
-    if (h->line3)
-        CK(h->line3->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
+    if (h->alt)
+        CK(h->alt->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
     else
         CK(h->tab->set_state(P, h->sc, h->dtmp, h->f[0], h->stream));
     h->cur = 0;
@@ -732,8 +763,8 @@ int mclb_fit_equilibrium(mclb_handle h, int nphase, double* phi)
     double* d_phi = h->dtmp;
     double* d_bulk = h->dtmp + P.N * S;
     double* d_work = d_bulk + S;
-    if (h->line3)
-        CK(h->line3->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
+    if (h->alt)
+        CK(h->alt->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
     else
         CK(h->tab->compositions(P, h->sc, h->f[h->cur], d_phi, d_bulk, 1e-3, h->stream));
     // k-means of the bulk sites on the device; only the centroids come back
@@ -800,7 +831,7 @@ int batch_build(mclb_batch b)
         std::vector<Scratch> lscs;
         std::vector<void*> la, lb;
         for (auto h : b->items)
-            if (h->P.N == n && h->line3) {
+            if (h->P.N == n && h->alt) {
                 lprobs.push_back(h->P);
                 lscs.push_back(h->sc);
                 la.push_back(h->f[0]);
@@ -816,7 +847,7 @@ int batch_build(mclb_batch b)
             b->lgroups.push_back(g);
         }
         for (auto h : b->items)
-            if (h->P.N == n && !h->line3) {
+            if (h->P.N == n && !h->alt) {
                 probs.push_back(h->P);
                 scs.push_back(h->sc);
                 fa.push_back(h->f[0]);
@@ -926,9 +957,12 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
     if (!out) return fail(MCLB_EINVAL, "out is NULL");
     *out = nullptr;
     if (!params || count < 1) return fail(MCLB_EINVAL, "count=%d must be >= 1", count);
-    for (int k = 0; k < count; ++k)
+    for (int k = 0; k < count; ++k) {
         if (params[k].mass_every != 0)
             return fail(MCLB_EINVAL, "instance %d: mass_every must be 0 in a batch", k);
+        if (params[k].lattice == MCLB_D3Q19)
+            return fail(MCLB_EINVAL, "instance %d: batches hold D2Q9 and D1Q3 lattices", k);
+    }
     mclb_batch b = new (std::nothrow) mclb_batch_s();
     if (!b) return fail(MCLB_ENOMEM, "host allocation failed");
     b->magic = MAGIC;
@@ -984,7 +1018,7 @@ int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const dou
     if (rc) return rc;
     rc = mclb_init_fields(h, rho, u);  // writes buffer 0
     if (rc) return rc;
-    if ((h->line3 ? b->lparity : b->parity) == 1) {   // the state lives in the batch's buffer
+    if ((h->alt ? b->lparity : b->parity) == 1) {   // the state lives in the batch's buffer
         CK(cudaMemcpyAsync(h->f[1], h->f[0], h->fbytes, cudaMemcpyDeviceToDevice, b->stream));
         CK(cudaStreamSynchronize(b->stream));
         h->cur = 1;
@@ -1025,7 +1059,7 @@ int mclb_batch_step(mclb_batch b, long nsteps)
     }
     CK(batch_join(b));   // later work on the batch's stream sees every ghost refresh
     for (auto h : b->items) {
-        h->cur = h->line3 ? b->lparity : b->parity;
+        h->cur = h->alt ? b->lparity : b->parity;
         h->steps += nsteps;
     }
     return MCLB_OK;

@@ -13,10 +13,10 @@ constexpr int CHECK_THREADS = 256;
 constexpr int CHECK_BLOCKS = 1216;   // 8 per SM on a 152-SM part; grid-stride beyond
 
 // smallest site whose N densities are not all finite, whose total is not positive, or
-// whose velocity (u may be null) is not finite
+// whose velocity (ud components; u may be null) is not finite
 __global__ void __launch_bounds__(CHECK_THREADS)
-k_check_fields(const double* __restrict__ rho, const double* __restrict__ u, int N, long long S,
-               unsigned long long* first_bad)
+k_check_fields(const double* __restrict__ rho, const double* __restrict__ u, int N, int ud,
+               long long S, unsigned long long* first_bad)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < S; c += stride) {
@@ -28,7 +28,8 @@ k_check_fields(const double* __restrict__ rho, const double* __restrict__ u, int
             tot += v;
         }
         ok = ok && tot > 0.0;
-        if (u) ok = ok && isfinite(u[c]) && isfinite(u[S + c]);
+        if (u)
+            for (int d = 0; d < ud; ++d) ok = ok && isfinite(u[d * S + c]);
         if (!ok) atomicMin(first_bad, (unsigned long long)c);
     }
 }
@@ -43,12 +44,12 @@ k_check_finite(const double* __restrict__ a, long long n, unsigned long long* fi
 
 }  // namespace
 
-cudaError_t check_fields(const double* rho, const double* u, int N, long long S,
+cudaError_t check_fields(const double* rho, const double* u, int N, int ud, long long S,
                          unsigned long long* first_bad, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(first_bad, 0xff, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_check_fields<<<CHECK_BLOCKS, CHECK_THREADS, 0, st>>>(rho, u, N, S, first_bad);
+    k_check_fields<<<CHECK_BLOCKS, CHECK_THREADS, 0, st>>>(rho, u, N, ud, S, first_bad);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,489 @@
+// cube.cuh -- the D3Q19 lattice: the staged timestep (three launches) and the diagnostics.
+//
+// The method's equations are written for any lattice whose weights give the Sec. 3
+// moments; D3Q19 (the rest velocity, weight 1/3; six axis directions, 1/18; twelve face
+// diagonals, 1/36; c_s^2 = 1/3) is isotropic to fourth order, so the equilibrium and
+// forcing polynomials of the D2Q9 path, with three-component dot products, keep the
+// Sec. 3 and Eqs. ff1-ff3 moments.  The stages are those of the D2Q9 staged schedule
+// (staged.cuh), with the discrete operators over the nineteen velocities:
+//   k19_density    rho^s = sum_i f^s_i(r - v_i)                     (Eq. ssLB streaming)
+//   k19_potential  nu^s = mu^s/m^s - kappa lap rho^s - (1/3) ln rho^s (Eq. lgf, Eq. definef)
+//   k19_collide    pull again, j^s, u, a^s = -(1 - 1/2tau) grad nu^s + g, f^e, F, BGK
+// lap g = 6 sum_i w_i (g(r + v_i) - g(r)), grad g = 3 sum_i w_i v_i g(r + v_i); periodic
+// in x, y and z; the per-site chemistry (site_nu, site_mu, site_psi) is shared with D2Q9.
+//
+// Layout: component s, layer z, row y, velocity i, column x at
+//   (((s * nz + z) * ny + y) * 19 + i) * nx + x
+// (the nineteen velocity lines of one (z, y) row adjacent; no ghost columns), holding
+// post-collision values: the pre-collision f^s_i(r) is the value stored at r - v_i.
+// Velocity order: 0; (+-1,0,0), (0,+-1,0), (0,0,+-1); (1,1,0), (-1,-1,0), (1,-1,0),
+// (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1),
+// (0,-1,1).  FP64 and FP32 storage.
+#pragma once
+
+#include "staged.cuh"
+
+namespace mclb {
+
+constexpr int Q19 = 19;
+
+// Component d (0: x, 1: y, 2: z) of velocity i.
+__host__ __device__ __forceinline__ constexpr int c19(int i, int d)
+{
+    return d == 0 ? ((i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+                     : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0)
+         : d == 1 ? ((i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+                     : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0)
+                  : ((i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+                     : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+}
+
+// Weights.  FP32: w0 = 2796203 * 2^-23, w1 = 1864135 * 2^-25 (axis), w2 = 1864135 * 2^-26
+// (diagonal), whose sum w0 + 6 w1 + 12 w2 is exactly 1 (with the rounded 1/3, 1/18 and
+// 1/36 it is 1 + 1.5e-8, a fixed-sign bias of every site's equilibrium mass).
+template <typename C>
+__host__ __device__ __forceinline__ constexpr C w19(int i);
+template <>
+__host__ __device__ __forceinline__ constexpr double w19<double>(int i)
+{
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+template <>
+__host__ __device__ __forceinline__ constexpr float w19<float>(int i)
+{
+    return i == 0 ? 2796203.0f * 0x1p-23f : (i <= 6 ? 1864135.0f * 0x1p-25f : 1864135.0f * 0x1p-26f);
+}
+
+// Site coordinates of a linear site index (z * ny + y) * nx + x.
+struct Site3 {
+    int x, y, z;
+};
+template <typename C>
+__device__ __forceinline__ Site3 site3(const StepParams<C>& p, long long site)
+{
+    const long long row = site / p.nx;
+    Site3 c;
+    c.x = (int)(site - row * p.nx);
+    c.y = (int)(row % p.ny);
+    c.z = (int)(row / p.ny);
+    return c;
+}
+
+// Linear index of the neighbour (x + dx, y + dy, z + dz), periodic.
+template <typename C>
+__device__ __forceinline__ long long nbr3(const StepParams<C>& p, const Site3& c, int dx, int dy,
+                                          int dz)
+{
+    const int x = wrap_add(c.x, dx, p.nx), y = wrap_add(c.y, dy, p.ny), z = wrap_add(c.z, dz, p.nz);
+    return ((long long)z * p.ny + y) * p.nx + x;
+}
+
+// Stored element (s, velocity i) of the site with linear index t.
+template <typename C>
+__device__ __forceinline__ long long at19(const StepParams<C>& p, int s, int i, long long t)
+{
+    const long long row = t / p.nx;
+    return (((long long)s * p.ny * p.nz + row) * Q19 + i) * p.nx + (t - row * p.nx);
+}
+
+// Pre-collision f^s_i at site c: the post-collision value stored at c - v_i.
+template <typename T>
+__device__ __forceinline__ typename Storage<T>::C pull19(const T* __restrict__ f,
+                                                         const StepParams<typename Storage<T>::C>& p,
+                                                         int s, int i, const Site3& c)
+{
+    return Storage<T>::load(f + at19(p, s, i, nbr3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2))));
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
+            const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C r = C(0);
+#pragma unroll
+        for (int i = 0; i < Q19; ++i) r += pull19(f, p, s, i, c);
+        rs[s * p.S + site] = r;
+    }
+}
+
+// lap g = 6 sum_i w_i (g(r + v_i) - g(r)) of every component's density field.
+template <typename C, int N>
+__device__ __forceinline__ void laplacians19(const C* __restrict__ rs, const StepParams<C>& p,
+                                             const Site3& c, const C (&r)[N], C (&lap)[N])
+{
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C acc = C(0);
+#pragma unroll
+        for (int i = 1; i < Q19; ++i)
+            acc += w19<C>(i) * (rs[s * p.S + nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2))] - r[s]);
+        lap[s] = C(6) * acc;
+    }
+}
+
+template <typename C, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant__ StepParams<C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+    C r[N], lap[N], out[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) r[s] = rs[s * p.S + site];
+    laplacians19<C, N>(rs, p, c, r, lap);
+    site_nu<C, N>(p, r, lap, out);
+#pragma unroll
+    for (int s = 0; s < N; ++s) nu[s * p.S + site] = out[s];
+}
+
+// grad g = 3 sum_i w_i v_i g(r + v_i) of one scalar field.
+template <typename C>
+__device__ __forceinline__ void grad19(const C* __restrict__ g, const StepParams<C>& p,
+                                       const Site3& c, C (&gr)[3])
+{
+    C a0 = C(0), a1 = C(0), a2 = C(0);
+#pragma unroll
+    for (int i = 1; i < Q19; ++i) {
+        const C v = w19<C>(i) * g[nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2))];
+        if (c19(i, 0)) a0 += C(c19(i, 0)) * v;
+        if (c19(i, 1)) a1 += C(c19(i, 1)) * v;
+        if (c19(i, 2)) a2 += C(c19(i, 2)) * v;
+    }
+    gr[0] = C(3) * a0;
+    gr[1] = C(3) * a1;
+    gr[2] = C(3) * a2;
+}
+
+// Accelerations a^s (Eq. definef plus the body force; with p.gd the Gibbs-Duhem shift
+// (A_c - A)/rho of every component, A = sum_s rho^s (a^s - g), A_c = (1 - 1/2tau)
+// (1/3) grad rho).  r: the site's rho^s, rho their sum.
+template <typename C, int N>
+__device__ __forceinline__ void accel19(const C* __restrict__ rs, const C* __restrict__ nu,
+                                        const StepParams<C>& p, const Site3& c, const C (&r)[N],
+                                        C rho, C (&a)[N][3])
+{
+    const C g[3] = {p.gx, p.gy, p.gz};
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C gr[3];
+        grad19(nu + s * p.S, p, c, gr);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) a[s][d] = -p.fcoef * gr[d] + g[d];
+    }
+    if (p.gd) {
+        C grt[3] = {C(0), C(0), C(0)};
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            C gs[3];
+            grad19(rs + s * p.S, p, c, gs);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) grt[d] += gs[d];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            C A = C(0);
+#pragma unroll
+            for (int s = 0; s < N; ++s) A += r[s] * (a[s][d] - g[d]);
+            const C sh = (p.fcoef * grt[d] / C(3) - A) / rho;
+#pragma unroll
+            for (int s = 0; s < N; ++s) a[s][d] += sh;
+        }
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
+            const typename Storage<T>::C* __restrict__ rs,
+            const typename Storage<T>::C* __restrict__ nu,
+            const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+    // first pass: moments (the populations are pulled again for the collision, from cache)
+    C r[N], j[N][3];
+    C rho = C(0), jt[3] = {C(0), C(0), C(0)};
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        C a = C(0), b[3] = {C(0), C(0), C(0)};
+#pragma unroll
+        for (int i = 0; i < Q19; ++i) {
+            const C v = pull19(fin, p, s, i, c);
+            a += v;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (c19(i, d)) b[d] += C(c19(i, d)) * v;
+        }
+        r[s] = a;
+        rho += a;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            j[s][d] = b[d];
+            jt[d] += b[d];
+        }
+    }
+    const C inv = C(1) / rho;
+    const C u[3] = {jt[0] * inv, jt[1] * inv, jt[2] * inv};
+    const C base = C(-1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    C a[N][3];
+    accel19<C, N>(rs, nu, p, c, r, rho, a);
+    const C keep = C(1) - p.omega;
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        // f* = f (1 - 1/tau) + (rho^s/tau) e_i + w_i [3 rho^s (v.a) + 9 (v.a)(v.J) - 3 a.J
+        // + rho^s/tau], e_i = w_i (3 v.u + 9/2 (v.u)^2 - 3/2 u.u), J = j^s or rho^s u (Eq. ff3)
+        C J[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) J[d] = p.bary ? r[s] * u[d] : j[s][d];
+        const C r3 = C(3) * r[s];
+        const C omr = p.omega * r[s];
+        const C m3aj = fma(C(-3), a[s][0] * J[0] + a[s][1] * J[1] + a[s][2] * J[2], omr);
+#pragma unroll
+        for (int i = 0; i < Q19; ++i) {
+            C cu = C(0), ca = C(0), cj = C(0);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (c19(i, d)) {
+                    cu += C(c19(i, d)) * u[d];
+                    ca += C(c19(i, d)) * a[s][d];
+                    cj += C(c19(i, d)) * J[d];
+                }
+            const C e = (i == 0) ? w19<C>(0) * base : w19<C>(i) * fma(cu, fma(C(4.5), cu, C(3)), base);
+            const C F = (i == 0) ? w19<C>(0) * m3aj : w19<C>(i) * fma(ca, fma(C(9), cj, r3), m3aj);
+            const C v = pull19(fin, p, s, i, c);
+            fout[at19(p, s, i, site)] = T(fma(keep, v, fma(omr, e, F)));
+        }
+    }
+    if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
+}
+
+// ---------------------------------------------------------------- diagnostics
+
+// Stored so that pulling yields f^e_i(rho^s, u) at every site: the value of velocity i at
+// site r is the equilibrium at r + v_i (u: 3 * S values, or null for rest).
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_init(const double* __restrict__ rho, const double* __restrict__ u, T* __restrict__ f,
+         const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+#pragma unroll
+    for (int i = 0; i < Q19; ++i) {
+        const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+        C uu = C(0), cu = C(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const C ud = u ? C(u[d * p.S + t]) : C(0);
+            uu += ud * ud;
+            cu += C(c19(i, d)) * ud;
+        }
+#pragma unroll
+        for (int s = 0; s < N; ++s)
+            f[at19(p, s, i, site)] = T(w19<C>(i) * C(rho[s * p.S + t]) *
+                                       (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_get_state(const T* __restrict__ f, double* __restrict__ out,
+              const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+#pragma unroll
+    for (int s = 0; s < N; ++s)
+#pragma unroll
+        for (int i = 0; i < Q19; ++i) out[(s * Q19 + i) * p.S + site] = (double)pull19(f, p, s, i, c);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_set_state(const double* __restrict__ in, T* __restrict__ f,
+              const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+#pragma unroll
+    for (int i = 0; i < Q19; ++i) {
+        const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+#pragma unroll
+        for (int s = 0; s < N; ++s) f[at19(p, s, i, site)] = T(C(in[(s * Q19 + i) * p.S + t]));
+    }
+}
+
+// Output fields (after k19_density and k19_potential of the same state): rho^s; U (3 * S)
+// = u + (sum_s rho^s a^s)/(2 rho) (Eq. scon); mu^s; P (6 * S: xx, xy, xz, yy, yz, zz) =
+// (sum_s rho^s mu^s - psi) I + kappa sum_s grad rho^s grad rho^s (Eq. ppp, diagnostic).
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_moments(const T* __restrict__ f, const typename Storage<T>::C* __restrict__ rs,
+            const typename Storage<T>::C* __restrict__ nu, double* __restrict__ rho_out,
+            double* __restrict__ U, double* __restrict__ mu_out, double* __restrict__ P,
+            const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+    C r[N];
+    C rho = C(0);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        r[s] = rs[s * p.S + site];
+        rho += r[s];
+    }
+    if (rho_out)
+#pragma unroll
+        for (int s = 0; s < N; ++s) rho_out[s * p.S + site] = (double)r[s];
+    if (U) {
+        C jt[3] = {C(0), C(0), C(0)}, ft[3] = {C(0), C(0), C(0)};
+        C a[N][3];
+        accel19<C, N>(rs, nu, p, c, r, rho, a);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+#pragma unroll
+            for (int i = 0; i < Q19; ++i) {
+                const C v = pull19(f, p, s, i, c);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) jt[d] += v * C(c19(i, d));
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ft[d] += r[s] * a[s][d];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) U[d * p.S + site] = (double)(jt[d] / rho + C(0.5) * ft[d] / rho);
+    }
+    if (mu_out || P) {
+        C lap[N], mu[N];
+        laplacians19<C, N>(rs, p, c, r, lap);
+        site_mu<C, N>(p, r, lap, mu);
+        if (mu_out)
+#pragma unroll
+            for (int s = 0; s < N; ++s) mu_out[s * p.S + site] = (double)mu[s];
+        if (P) {
+            const C psi = site_psi<C, N>(p, r);
+            C rmu = C(0), gg = C(0), t[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
+#pragma unroll
+            for (int s = 0; s < N; ++s) {
+                C g[3];
+                grad19(rs + s * p.S, p, c, g);
+                rmu += r[s] * mu[s];
+                gg += C(0.5) * p.kappa * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+                t[0] += p.kappa * g[0] * g[0];
+                t[1] += p.kappa * g[0] * g[1];
+                t[2] += p.kappa * g[0] * g[2];
+                t[3] += p.kappa * g[1] * g[1];
+                t[4] += p.kappa * g[1] * g[2];
+                t[5] += p.kappa * g[2] * g[2];
+            }
+            const C iso = rmu - (psi + gg);
+            P[site] = (double)(iso + t[0]);
+            P[p.S + site] = (double)t[1];
+            P[2 * p.S + site] = (double)t[2];
+            P[3 * p.S + site] = (double)(iso + t[3]);
+            P[4 * p.S + site] = (double)t[4];
+            P[5 * p.S + site] = (double)(iso + t[5]);
+        }
+    }
+}
+
+// Conservation sums (after k19_density and k19_potential): mass^s, momentum (3), force
+// sum_s rho^s a^s (3), as per-block FP64 partials (fixed grid, fixed tree).
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_conservation(const T* __restrict__ f, const typename Storage<T>::C* __restrict__ rs,
+                 const typename Storage<T>::C* __restrict__ nu, double* __restrict__ partial,
+                 const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    using C = typename Storage<T>::C;
+    constexpr int K = N + 6;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < p.S;
+         site += (long long)gridDim.x * blockDim.x) {
+        const Site3 c = site3(p, site);
+        C rl[N], a[N][3];
+        C rho = C(0);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            rl[s] = rs[s * p.S + site];
+            rho += rl[s];
+        }
+        accel19<C, N>(rs, nu, p, c, rl, rho, a);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            acc[s] += (double)rl[s];
+            double j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int i = 0; i < Q19; ++i) {
+                const double v = (double)pull19(f, p, s, i, c);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) j[d] += v * c19(i, d);
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                acc[N + d] += j[d];
+                acc[N + 3 + d] += (double)rl[s] * (double)a[s][d];
+            }
+        }
+    }
+    block_reduce_store<K>(acc, partial);
+}
+
+// FP64 compositions phi^s = rho^s / rho and a bulk flag (1 where every |grad phi^s| < tol).
+template <typename T, int N>
+__global__ void __launch_bounds__(SITE_THREADS)
+k19_compositions(const typename Storage<T>::C* __restrict__ rs, double* __restrict__ phi,
+                 double* __restrict__ bulk, double tol,
+                 const __grid_constant__ StepParams<typename Storage<T>::C> p)
+{
+    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= p.S) return;
+    const Site3 c = site3(p, site);
+    double g[N][3];
+#pragma unroll
+    for (int s = 0; s < N; ++s) g[s][0] = g[s][1] = g[s][2] = 0.0;
+#pragma unroll
+    for (int i = 1; i < Q19; ++i) {
+        const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+        double rho = 0.0;
+#pragma unroll
+        for (int s = 0; s < N; ++s) rho += (double)rs[s * p.S + t];
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            const double ph = (double)rs[s * p.S + t] / rho;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) g[s][d] += 3.0 * w19<double>(i) * c19(i, d) * ph;
+        }
+    }
+    double rho = 0.0, g2max = 0.0;
+#pragma unroll
+    for (int s = 0; s < N; ++s) rho += (double)rs[s * p.S + site];
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+        phi[s * p.S + site] = (double)rs[s * p.S + site] / rho;
+        const double g2 = g[s][0] * g[s][0] + g[s][1] * g[s][1] + g[s][2] * g[s][2];
+        g2max = g2 > g2max ? g2 : g2max;
+    }
+    bulk[site] = (g2max < tol * tol) ? 1.0 : 0.0;
+}
+
+}  // namespace mclb

@@ -95,6 +95,7 @@ struct Storage<__half> {
 template <typename C>
 struct StepParams {
     int nx, ny;
+    int nz;               // layers (D3Q19), 1 otherwise
     long long S;
     int hx;               // ghost columns per side
     long long pitch;      // elements per (row, velocity) line
@@ -102,7 +103,7 @@ struct StepParams {
     long long rbytes;     // byte offset of the FP32 density lines in a buffer (16-bit formats)
     C omega;              // 1 / tau
     C fcoef;              // 1 - 1/(2 tau), Eq. definef
-    C gx, gy;             // body acceleration
+    C gx, gy, gz;         // body acceleration
     C kappa, theta;
     C log_floor;          // floor of rho^s / rho inside a logarithm
     int bary;             // 1: barycentric u in the forcing's second moment, 0: u^s (Eq. ff3)
@@ -124,6 +125,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
     StepParams<C> p{};
     p.nx = P.nx;
     p.ny = P.ny;
+    p.nz = P.nz > 0 ? P.nz : 1;
     p.S = P.S;
     p.hx = P.hx;
     p.pitch = P.pitch;
@@ -133,6 +135,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
     p.fcoef = C(1.0 - 1.0 / (2.0 * P.tau));
     p.gx = C(P.gx);
     p.gy = C(P.gy);
+    p.gz = C(P.gz);
     p.kappa = C(P.kappa);
     p.theta = C(P.theta);
     p.log_floor = C(1e-12);

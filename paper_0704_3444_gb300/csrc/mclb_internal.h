@@ -13,6 +13,7 @@ constexpr int NMAX = 8;
 constexpr int Q = 9;
 constexpr int ROW_ALIGN = 128;  // data columns per row are padded to a multiple of this
 constexpr int LATTICE_D1Q3 = 1; // Problem::lattice of a D1Q3 lattice (MCLB_D1Q3)
+constexpr int LATTICE_D3Q19 = 2; // Problem::lattice of a D3Q19 lattice (MCLB_D3Q19)
 
 // Everything a launcher needs to know about one simulation, in FP64 as given at
 // the boundary; each precision unit converts it to its own kernel parameters.
@@ -29,15 +30,17 @@ constexpr int LATTICE_D1Q3 = 1; // Problem::lattice of a D1Q3 lattice (MCLB_D1Q3
 // kernel), so that the single-pass kernel moves whole aligned row segments with TMA.
 struct Problem {
     int N, nx, ny;
-    long long S;            // nx * ny sites
+    int nz;                 // layers (D3Q19), 1 otherwise
+    long long S;            // nx * ny * nz sites
     int hx;                 // ghost columns per side
     long long pitch;        // elements per (row, velocity) line
     long long plane;        // elements per component = ny * 9 * pitch
-    double tau, theta, kappa, gx, gy;
+    double tau, theta, kappa, gx, gy, gz;
     double chi[NMAX * NMAX];
     double m[NMAX];
     int forcing_velocity;   // MCLB_FORCING_COMPONENT (0) or MCLB_FORCING_BARYCENTRIC (1)
-    int lattice;            // MCLB_D2Q9 (0) or MCLB_D1Q3 (1: ny = 1, layout [s][i][x], no ghosts)
+    int lattice;            // MCLB_D2Q9 (0), MCLB_D1Q3 (1: ny = 1, layout [s][i][x], no ghosts) or
+                            // MCLB_D3Q19 (2: layout [s][z][y][i][x], no ghosts)
     int force_form;         // MCLB_FORCE_COMPONENT (0) or MCLB_FORCE_GIBBS_DUHEM (1)
     int mass_every;         // period of the per-component mass compensation, 0 = off
     int withhold;           // test hook: the single-pass kernel issues no copies
@@ -75,9 +78,11 @@ struct FusedPlan {
     bool ok;
 };
 
-// Kernels of the D1Q3 lattice (line3.cuh) for one storage type (FP64 and FP32 only).
-// Distributions: post-collision values [s][3][nx]; pre-collision f_i(x) = f*_i(x - v_i).
-struct Line3Table {
+// Kernels of a lattice other than the D2Q9 family -- D1Q3 (line3.cuh) or D3Q19 (cube.cuh)
+// -- for one storage type (FP64 and FP32 only).  Distributions: post-collision values
+// ([s][3][nx] for D1Q3, [s][z][y][19][x] for D3Q19); pre-collision f_i(r) = f*_i(r - v_i).
+// The batch entries are D1Q3 only (null for D3Q19).
+struct LatticeTable {
     int (*max_resident)(int N);   // longest line the resident (shared-memory) kernel holds
     size_t item_bytes;            // size of the device description at Scratch::line_item
     // write the description of buffers f[0], f[1] to sc.line_item (synchronous)
@@ -162,14 +167,15 @@ struct KernelTable {
     cudaError_t (*batch_tune)(void* group, int parity, cudaStream_t st);
     int (*batch_waves)(const void* group);      // waves of the partition in use, 0 if staged
     void (*batch_destroy)(void* group);
-    const Line3Table* line3;    // D1Q3 kernels (null for the 16-bit formats)
+    const LatticeTable* line3;  // D1Q3 kernels (null for the 16-bit formats)
+    const LatticeTable* d3q19;  // D3Q19 kernels (null for the 16-bit formats)
 };
 
 // Device checks of FP64 boundary data (checks.cu).  *first_bad receives the smallest
-// failing site (check_fields: a density not finite, total density not positive, or u,
-// which may be null, not finite) or index (check_finite), and stays ULLONG_MAX when
-// everything passes.  Stream ordered; the caller reads first_bad back.
-cudaError_t check_fields(const double* rho, const double* u, int N, long long S,
+// failing site (check_fields: a density not finite, total density not positive, or one
+// of the ud velocity components, u may be null, not finite) or index (check_finite), and
+// stays ULLONG_MAX when everything passes.  Stream ordered; the caller reads first_bad back.
+cudaError_t check_fields(const double* rho, const double* u, int N, int ud, long long S,
                          unsigned long long* first_bad, cudaStream_t st);
 cudaError_t check_finite(const double* a, long long n, unsigned long long* first_bad,
                          cudaStream_t st);

@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "batch.cuh"
+#include "cube.cuh"
 #include "ghosts.cuh"
 #include "line3.cuh"
 #include "march.cuh"
@@ -203,8 +204,8 @@ struct Launch {
     static cudaError_t mass(const Problem& P, const Scratch& sc, void* f, int record, cudaStream_t st)
     {
         MassView v{};
-        v.q = P.lattice == LATTICE_D1Q3 ? 3 : Q;
-        v.lines = P.ny * v.q;
+        v.q = P.lattice == LATTICE_D1Q3 ? 3 : (P.lattice == LATTICE_D3Q19 ? Q19 : Q);
+        v.lines = (int)(P.S / P.nx) * v.q;   // (layers x) rows x velocities
         v.rlines = Storage<T>::shifted ? P.ny : 0;
         v.comp_stride = P.plane;
         v.pitch = P.pitch;
@@ -441,10 +442,10 @@ struct Line3Launch {
         delete g;
     }
 
-    static const Line3Table* table()
+    static const LatticeTable* table()
     {
-        static const Line3Table t = [] {
-            Line3Table x{};
+        static const LatticeTable t = [] {
+            LatticeTable x{};
             x.max_resident = &max_resident;
             x.item_bytes = sizeof(Line3Item<T>);
             x.prepare = &prepare;
@@ -459,6 +460,134 @@ struct Line3Launch {
             x.batch_step = &batch_step;
             x.batch_launches = &batch_launches;
             x.batch_destroy = &batch_destroy;
+            return x;
+        }();
+        return &t;
+    }
+};
+
+// Launchers of the D3Q19 kernels (cube.cuh) for one storage type: the staged step (three
+// launches) and the diagnostics; no batches.
+template <typename T>
+struct Launch19 {
+    using C = typename Storage<T>::C;
+
+    static int max_resident(int) { return 0; }
+    static cudaError_t prepare(const Problem&, const Scratch&, void* const*) { return cudaSuccess; }
+
+    static cudaError_t init(const Problem& P, const Scratch& sc, const double* rho, const double* u,
+                            void* f, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k19_init<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(rho, u, (T*)f, p);
+            return cudaGetLastError();
+        });
+    }
+
+    // density and potential fields of state f into the scratch
+    template <int N>
+    static cudaError_t fields_n(const StepParams<C>& p, const Scratch& sc, const T* f, cudaStream_t st)
+    {
+        k19_density<T, N><<<site_blocks(p.S), SITE_THREADS, 0, st>>>(f, (C*)sc.rho_s, p);
+        k19_potential<C, N><<<site_blocks(p.S), SITE_THREADS, 0, st>>>((const C*)sc.rho_s,
+                                                                        (C*)sc.nu, p);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t step(const Problem& P, const Scratch& sc, void* const* f, int* cur,
+                            long nsteps, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            for (; nsteps > 0; --nsteps) {
+                cudaError_t e = fields_n<NN>(p, sc, (const T*)f[*cur], st);
+                if (e != cudaSuccess) return e;
+                k19_collide<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(
+                    (const T*)f[*cur], (T*)f[*cur ^ 1], (const C*)sc.rho_s, (const C*)sc.nu, p);
+                e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+                *cur ^= 1;
+            }
+            return cudaSuccess;
+        });
+    }
+
+    static cudaError_t moments(const Problem& P, const Scratch& sc, const void* f, double* rho,
+                               double* U, double* mu, double* Pt, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            cudaError_t e = fields_n<NN>(p, sc, (const T*)f, st);
+            if (e != cudaSuccess) return e;
+            k19_moments<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(
+                (const T*)f, (const C*)sc.rho_s, (const C*)sc.nu, rho, U, mu, Pt, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t conservation(const Problem& P, const Scratch& sc, const void* f, double* out,
+                                    cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            if (sc.partial_cap < (size_t)REDUCE_BLOCKS * (NN + 6)) return cudaErrorInvalidValue;
+            cudaError_t e = fields_n<NN>(p, sc, (const T*)f, st);
+            if (e != cudaSuccess) return e;
+            k19_conservation<T, NN><<<REDUCE_BLOCKS, SITE_THREADS, 0, st>>>(
+                (const T*)f, (const C*)sc.rho_s, (const C*)sc.nu, sc.partial, p);
+            k_reduce_partials<<<1, SITE_THREADS, 0, st>>>(sc.partial, REDUCE_BLOCKS, NN + 6, out);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t compositions(const Problem& P, const Scratch& sc, const void* f, double* phi,
+                                    double* bulk, double tol, cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k19_density<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>((const T*)f,
+                                                                          (C*)sc.rho_s, p);
+            k19_compositions<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(
+                (const C*)sc.rho_s, phi, bulk, tol, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t get_state(const Problem& P, const Scratch& sc, const void* f, double* out,
+                                 cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k19_get_state<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>((const T*)f, out, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static cudaError_t set_state(const Problem& P, const Scratch& sc, const double* in, void* f,
+                                 cudaStream_t st)
+    {
+        const auto p = make_params<C>(P, sc.status);
+        MCLB_DISPATCH_N(P.N, {
+            k19_set_state<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(in, (T*)f, p);
+            return cudaGetLastError();
+        });
+    }
+
+    static const LatticeTable* table()
+    {
+        static const LatticeTable t = [] {
+            LatticeTable x{};
+            x.max_resident = &max_resident;
+            x.item_bytes = 0;
+            x.prepare = &prepare;
+            x.init = &init;
+            x.step = &step;
+            x.moments = &moments;
+            x.conservation = &conservation;
+            x.compositions = &compositions;
+            x.get_state = &get_state;
+            x.set_state = &set_state;
             return x;
         }();
         return &t;
@@ -489,8 +618,13 @@ inline KernelTable make_table(CUtensorMapDataType tt)
     t.batch_tune = &batch_group_tune<T>;
     t.batch_waves = &batch_group_waves<T>;
     t.batch_destroy = &batch_group_destroy<T>;
-    if constexpr (!Storage<T>::shifted) t.line3 = Line3Launch<T>::table();
-    else t.line3 = nullptr;
+    if constexpr (!Storage<T>::shifted) {
+        t.line3 = Line3Launch<T>::table();
+        t.d3q19 = Launch19<T>::table();
+    } else {
+        t.line3 = nullptr;
+        t.d3q19 = nullptr;
+    }
     return t;
 }
 

@@ -77,18 +77,19 @@ class Problem:
     theta: float
     kappa: float
     force: tuple
-    rho: np.ndarray            # (N, ny, nx)
-    u: np.ndarray              # (2, ny, nx)
+    rho: np.ndarray            # (N, ny, nx); (N, nz, ny, nx) on D3Q19
+    u: np.ndarray              # (2, ny, nx); (3, nz, ny, nx) on D3Q19
     steps: int = 0
     precision: str = "fp32"
     meta: dict = field(default_factory=dict)
     forcing_velocity: int = 0      # 0: Eq. ff3 as printed, 1: barycentric reading
-    lattice: str = "d2q9"          # or "d1q3" (ny = 1)
+    lattice: str = "d2q9"          # or "d1q3" (ny = 1) or "d3q19"
     force_form: int = 0            # 0: Eq. definef as printed, 1: Gibbs-Duhem total (kappa = 0)
+    nz: int = 1                    # layers (D3Q19)
 
     @property
     def sites(self) -> int:
-        return self.nx * self.ny
+        return self.nx * self.ny * self.nz
 
 
 def uniform_chi(n: int, value: float) -> np.ndarray:
@@ -254,6 +255,25 @@ def slab(nx=8192, ny=2048, *, tau=1.0 / 0.9, kappa=0.01, amp=0.01, seed=5, steps
     chi[S, NS] = chi[NS, S] = 0.2
     return _problem(name, 3, nx, ny, tau, chi, phi, kappa=kappa, steps=steps,
                     precision=precision)
+
+
+def ternary3d(n=256, *, tau=1.0 / 0.9, kappa=0.01, amp=0.01, seed=6, steps=1000,
+              precision="fp32", name="ternary3d_256") -> Problem:
+    """Three components on an n^3 D3Q19 lattice with the paper's ternary chi set
+    (chi_AB = 3, chi_AC = 0.5, chi_BC = 0.2, Sec. 4) at the mean composition
+    (0.4, 0.4, 0.2), inside the A-B spinodal, plus mass-neutral uniform noise of amplitude
+    `amp`: the mixture separates into A-rich and B-rich domains in three dimensions."""
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    s = n * n * n
+    noise = np.stack([amp * (2.0 * uniform(seed, s, k) - 1.0) for k in range(3)])
+    phi = (np.array([0.4, 0.4, 0.2])[:, None] + _mass_neutral(noise)).reshape(3, n, n, n)
+    return Problem(name=name, ncomp=3, nx=n, ny=n, tau=float(tau), chi=chi, m=np.ones(3),
+                   theta=1.0 / 3.0, kappa=float(kappa), force=(0.0, 0.0, 0.0),
+                   rho=np.ascontiguousarray(phi), u=np.zeros((3, n, n, n)), steps=steps,
+                   precision=precision, lattice="d3q19", nz=n)
 
 
 def flat_interface(phi0, *, chi, nx=128, ny=1, m=None, tau=1.0 / 0.9, kappa=0.0, amp=0.1,

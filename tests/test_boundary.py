@@ -57,13 +57,18 @@ def _params(**kw):
     (dict(precision=7), "precision"),
     (dict(kernel=5), "kernel"),
     (dict(forcing_velocity=2), "forcing_velocity"),
-    (dict(lattice=2), "lattice"),
     (dict(lattice="d1q3", ny=2), "ny = 1"),
     (dict(lattice="d1q3", ny=1, precision="bf16"), "FP64 or FP32"),
     (dict(force_form=2), "force_form"),
     (dict(force_form=1, kappa=0.01), "kappa = 0"),
     (dict(force_form=1, kernel=1), "staged schedule"),
     (dict(mass_every=-1), "mass_every"),
+    (dict(lattice=3), "lattice"),
+    (dict(lattice="d3q19", nz=2, precision="bf16"), "FP64 or FP32"),
+    (dict(nz=2), "D3Q19"),
+    (dict(nz=-1), "nz"),
+    (dict(force=(0.0, 0.0, 1e-5)), "force_z"),
+    (dict(lattice="d3q19", nz=4, force=(0.0, 0.0, float("inf"))), "force_z"),
 ])
 def test_invalid_parameters_are_rejected(lib, kw, frag):
     p, keep = _params(**kw)
@@ -71,6 +76,13 @@ def test_invalid_parameters_are_rejected(lib, kw, frag):
     rc = lib.mclb_create(ctypes.byref(p), ctypes.byref(h))
     assert rc == -1 and not h.value
     assert frag in lib.mclb_last_error().decode()
+
+
+def test_batches_reject_d3q19(lib):
+    p, keep = _params(lattice="d3q19", nz=3)
+    b = ctypes.c_void_p()
+    assert lib.mclb_batch_create(ctypes.byref(p), 1, ctypes.byref(b)) == -1 and not b.value
+    assert "D2Q9 and D1Q3" in lib.mclb_last_error().decode()
 
 
 def test_mass_compensation_is_for_single_handles(lib):

@@ -1,4 +1,6 @@
 """GPU: batched simulations and the equilibrium fit, against the FP64 oracle."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -269,18 +271,28 @@ def test_batch_ternary_sweep_matches_oracle():
     b.close()
 
 
-def _fit_by_definition(rho, nphase):
+def _fit_by_definition(rho, nphase, lattice="d2q9"):
     """mclb_fit_equilibrium written out in numpy: compositions; bulk sites where every
-    component's D2Q9 gradient 3 sum_i w_i v_i phi(x + v_i) is below 1e-3 in magnitude;
-    k-means seeded at the bulk site richest in component c (first on ties), nearest
-    centroid by squared distance (lower phase on ties), until the centroids stop moving."""
+    component's lattice gradient 3 sum_i w_i v_i phi(x + v_i) (D2Q9, or D3Q19 for fields
+    (N, nz, ny, nx)) is below 1e-3 in magnitude; k-means seeded at the bulk site richest
+    in component c (first on ties), nearest centroid by squared distance (lower phase on
+    ties), until the centroids stop moving."""
     phi = rho / rho.sum(0)
-    cx = [0, 1, 0, -1, 0, 1, -1, -1, 1]
-    cy = [0, 0, 1, 0, -1, 1, 1, -1, -1]
-    w = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
-    gx = sum(3 * w[i] * cx[i] * np.roll(phi, (-cy[i], -cx[i]), axis=(1, 2)) for i in range(9))
-    gy = sum(3 * w[i] * cy[i] * np.roll(phi, (-cy[i], -cx[i]), axis=(1, 2)) for i in range(9))
-    bulk = np.all(gx * gx + gy * gy < 1e-6, axis=0).ravel()
+    if lattice == "d3q19":
+        vel = [c for c in itertools.product((-1, 0, 1), repeat=3) if 0 < sum(x * x for x in c) <= 2]
+        g2 = 0.0
+        for d in range(3):
+            g = sum(3 * (1 / 18 if sum(x * x for x in c) == 1 else 1 / 36) * c[d]
+                    * np.roll(phi, (-c[2], -c[1], -c[0]), axis=(1, 2, 3)) for c in vel)
+            g2 = g2 + g * g
+        bulk = np.all(g2 < 1e-6, axis=0).ravel()
+    else:
+        cx = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+        cy = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+        w = [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4
+        gx = sum(3 * w[i] * cx[i] * np.roll(phi, (-cy[i], -cx[i]), axis=(1, 2)) for i in range(9))
+        gy = sum(3 * w[i] * cy[i] * np.roll(phi, (-cy[i], -cx[i]), axis=(1, 2)) for i in range(9))
+        bulk = np.all(gx * gx + gy * gy < 1e-6, axis=0).ravel()
     pts = phi.reshape(phi.shape[0], -1)[:, bulk].T
     cen = np.stack([pts[np.argmax(pts[:, c])] for c in range(nphase)])
     for _ in range(100):
