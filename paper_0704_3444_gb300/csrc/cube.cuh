@@ -54,36 +54,51 @@ __host__ __device__ __forceinline__ constexpr float w19<float>(int i)
     return i == 0 ? 2796203.0f * 0x1p-23f : (i <= 6 ? 1864135.0f * 0x1p-25f : 1864135.0f * 0x1p-26f);
 }
 
-// Site coordinates of a linear site index (z * ny + y) * nx + x.
+// Site coordinates of a linear site index (z * ny + y) * nx + x (< 2^31: one 32-bit
+// division per thread, none per neighbour).
 struct Site3 {
     int x, y, z;
 };
 template <typename C>
 __device__ __forceinline__ Site3 site3(const StepParams<C>& p, long long site)
 {
-    const long long row = site / p.nx;
+    const unsigned t = (unsigned)site, nx = (unsigned)p.nx, ny = (unsigned)p.ny;
+    const unsigned row = t / nx;
     Site3 c;
-    c.x = (int)(site - row * p.nx);
-    c.y = (int)(row % p.ny);
-    c.z = (int)(row / p.ny);
+    c.x = (int)(t - row * nx);
+    c.z = (int)(row / ny);
+    c.y = (int)(row - (unsigned)c.z * ny);
     return c;
 }
 
-// Linear index of the neighbour (x + dx, y + dy, z + dz), periodic.
+// A neighbour (x + dx, y + dy, z + dz), periodic, as its row z * ny + y and column x.
+struct Nb3 {
+    int row, x;
+};
+template <typename C>
+__device__ __forceinline__ Nb3 nb3(const StepParams<C>& p, const Site3& c, int dx, int dy, int dz)
+{
+    Nb3 n;
+    n.x = wrap_add(c.x, dx, p.nx);
+    n.row = wrap_add(c.z, dz, p.nz) * p.ny + wrap_add(c.y, dy, p.ny);
+    return n;
+}
+
+// Linear site index of a neighbour (index into an N * S field: s * S + nbr3(...)).
 template <typename C>
 __device__ __forceinline__ long long nbr3(const StepParams<C>& p, const Site3& c, int dx, int dy,
                                           int dz)
 {
-    const int x = wrap_add(c.x, dx, p.nx), y = wrap_add(c.y, dy, p.ny), z = wrap_add(c.z, dz, p.nz);
-    return ((long long)z * p.ny + y) * p.nx + x;
+    const Nb3 n = nb3(p, c, dx, dy, dz);
+    return (long long)n.row * p.nx + n.x;
 }
 
-// Stored element (s, velocity i) of the site with linear index t.
+// Stored element (component 0, velocity i) of the site at (row, x); component s is
+// s * 19 * S further.
 template <typename C>
-__device__ __forceinline__ long long at19(const StepParams<C>& p, int s, int i, long long t)
+__device__ __forceinline__ long long at19(const StepParams<C>& p, int i, int row, int x)
 {
-    const long long row = t / p.nx;
-    return (((long long)s * p.ny * p.nz + row) * Q19 + i) * p.nx + (t - row * p.nx);
+    return ((long long)row * Q19 + i) * p.nx + x;
 }
 
 // Pre-collision f^s_i at site c: the post-collision value stored at c - v_i.
@@ -92,7 +107,8 @@ __device__ __forceinline__ typename Storage<T>::C pull19(const T* __restrict__ f
                                                          const StepParams<typename Storage<T>::C>& p,
                                                          int s, int i, const Site3& c)
 {
-    return Storage<T>::load(f + at19(p, s, i, nbr3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2))));
+    const Nb3 n = nb3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2));
+    return Storage<T>::load(f + (long long)s * Q19 * p.S + at19(p, i, n.row, n.x));
 }
 
 template <typename T, int N>
@@ -104,28 +120,37 @@ k19_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
     const Site3 c = site3(p, site);
+    C r[N];
 #pragma unroll
-    for (int s = 0; s < N; ++s) {
-        C r = C(0);
+    for (int s = 0; s < N; ++s) r[s] = C(0);
 #pragma unroll
-        for (int i = 0; i < Q19; ++i) r += pull19(f, p, s, i, c);
-        rs[s * p.S + site] = r;
+    for (int i = 0; i < Q19; ++i) {
+        const Nb3 n = nb3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2));
+        const T* src = f + at19(p, i, n.row, n.x);
+#pragma unroll
+        for (int s = 0; s < N; ++s) r[s] += Storage<T>::load(src + (long long)s * Q19 * p.S);
     }
+#pragma unroll
+    for (int s = 0; s < N; ++s) rs[s * p.S + site] = r[s];
 }
 
-// lap g = 6 sum_i w_i (g(r + v_i) - g(r)) of every component's density field.
+// lap g = 6 sum_i w_i (g(r + v_i) - g(r)) of every component's density field (each
+// neighbour's index formed once for all components).
 template <typename C, int N>
 __device__ __forceinline__ void laplacians19(const C* __restrict__ rs, const StepParams<C>& p,
                                              const Site3& c, const C (&r)[N], C (&lap)[N])
 {
+    C acc[N];
 #pragma unroll
-    for (int s = 0; s < N; ++s) {
-        C acc = C(0);
+    for (int s = 0; s < N; ++s) acc[s] = C(0);
 #pragma unroll
-        for (int i = 1; i < Q19; ++i)
-            acc += w19<C>(i) * (rs[s * p.S + nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2))] - r[s]);
-        lap[s] = C(6) * acc;
+    for (int i = 1; i < Q19; ++i) {
+        const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+#pragma unroll
+        for (int s = 0; s < N; ++s) acc[s] += w19<C>(i) * (rs[s * p.S + t] - r[s]);
     }
+#pragma unroll
+    for (int s = 0; s < N; ++s) lap[s] = C(6) * acc[s];
 }
 
 template <typename C, int N>
@@ -162,6 +187,30 @@ __device__ __forceinline__ void grad19(const C* __restrict__ g, const StepParams
     gr[2] = C(3) * a2;
 }
 
+// grad g = 3 sum_i w_i v_i g(r + v_i) of N fields g + s * S at once.
+template <typename C, int N>
+__device__ __forceinline__ void grads19(const C* __restrict__ g, const StepParams<C>& p,
+                                        const Site3& c, C (&gr)[N][3])
+{
+#pragma unroll
+    for (int s = 0; s < N; ++s) gr[s][0] = gr[s][1] = gr[s][2] = C(0);
+#pragma unroll
+    for (int i = 1; i < Q19; ++i) {
+        const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            const C v = w19<C>(i) * g[s * p.S + t];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (c19(i, d)) gr[s][d] += C(c19(i, d)) * v;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < N; ++s)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gr[s][d] *= C(3);
+}
+
 // Accelerations a^s (Eq. definef plus the body force; with p.gd the Gibbs-Duhem shift
 // (A_c - A)/rho of every component, A = sum_s rho^s (a^s - g), A_c = (1 - 1/2tau)
 // (1/3) grad rho).  r: the site's rho^s, rho their sum.
@@ -171,22 +220,19 @@ __device__ __forceinline__ void accel19(const C* __restrict__ rs, const C* __res
                                         C rho, C (&a)[N][3])
 {
     const C g[3] = {p.gx, p.gy, p.gz};
+    grads19<C, N>(nu, p, c, a);
 #pragma unroll
-    for (int s = 0; s < N; ++s) {
-        C gr[3];
-        grad19(nu + s * p.S, p, c, gr);
+    for (int s = 0; s < N; ++s)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) a[s][d] = -p.fcoef * gr[d] + g[d];
-    }
+        for (int d = 0; d < 3; ++d) a[s][d] = -p.fcoef * a[s][d] + g[d];
     if (p.gd) {
         C grt[3] = {C(0), C(0), C(0)};
+        C gs[N][3];
+        grads19<C, N>(rs, p, c, gs);
 #pragma unroll
-        for (int s = 0; s < N; ++s) {
-            C gs[3];
-            grad19(rs + s * p.S, p, c, gs);
+        for (int s = 0; s < N; ++s)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) grt[d] += gs[d];
-        }
+            for (int d = 0; d < 3; ++d) grt[d] += gs[s][d];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             C A = C(0);
@@ -200,7 +246,7 @@ __device__ __forceinline__ void accel19(const C* __restrict__ rs, const C* __res
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(SITE_THREADS)
+__global__ void __launch_bounds__(SITE_THREADS, 2)
 k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
             const typename Storage<T>::C* __restrict__ rs,
             const typename Storage<T>::C* __restrict__ nu,
@@ -210,58 +256,74 @@ k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
     const Site3 c = site3(p, site);
+    const long long cstride = (long long)Q19 * p.S;   // one component's stored values
     // first pass: moments (the populations are pulled again for the collision, from cache)
     C r[N], j[N][3];
+#pragma unroll
+    for (int s = 0; s < N; ++s) r[s] = j[s][0] = j[s][1] = j[s][2] = C(0);
+#pragma unroll
+    for (int i = 0; i < Q19; ++i) {
+        const Nb3 n = nb3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2));
+        const T* src = fin + at19(p, i, n.row, n.x);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            const C v = Storage<T>::load(src + s * cstride);
+            r[s] += v;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (c19(i, d)) j[s][d] += C(c19(i, d)) * v;
+        }
+    }
     C rho = C(0), jt[3] = {C(0), C(0), C(0)};
 #pragma unroll
     for (int s = 0; s < N; ++s) {
-        C a = C(0), b[3] = {C(0), C(0), C(0)};
+        rho += r[s];
 #pragma unroll
-        for (int i = 0; i < Q19; ++i) {
-            const C v = pull19(fin, p, s, i, c);
-            a += v;
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                if (c19(i, d)) b[d] += C(c19(i, d)) * v;
-        }
-        r[s] = a;
-        rho += a;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            j[s][d] = b[d];
-            jt[d] += b[d];
-        }
+        for (int d = 0; d < 3; ++d) jt[d] += j[s][d];
     }
     const C inv = C(1) / rho;
     const C u[3] = {jt[0] * inv, jt[1] * inv, jt[2] * inv};
     const C base = C(-1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     C a[N][3];
     accel19<C, N>(rs, nu, p, c, r, rho, a);
-    const C keep = C(1) - p.omega;
+    // f* = f (1 - 1/tau) + (rho^s/tau) e_i + w_i [3 rho^s (v.a) + 9 (v.a)(v.J) - 3 a.J
+    // + rho^s/tau], e_i = w_i (3 v.u + 9/2 (v.u)^2 - 3/2 u.u), J = j^s or rho^s u (Eq. ff3);
+    // J is kept in j, and the per-component constants are formed once
+    C r3[N], omr[N], m3aj[N];
 #pragma unroll
     for (int s = 0; s < N; ++s) {
-        // f* = f (1 - 1/tau) + (rho^s/tau) e_i + w_i [3 rho^s (v.a) + 9 (v.a)(v.J) - 3 a.J
-        // + rho^s/tau], e_i = w_i (3 v.u + 9/2 (v.u)^2 - 3/2 u.u), J = j^s or rho^s u (Eq. ff3)
-        C J[3];
+        if (p.bary)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) J[d] = p.bary ? r[s] * u[d] : j[s][d];
-        const C r3 = C(3) * r[s];
-        const C omr = p.omega * r[s];
-        const C m3aj = fma(C(-3), a[s][0] * J[0] + a[s][1] * J[1] + a[s][2] * J[2], omr);
+            for (int d = 0; d < 3; ++d) j[s][d] = r[s] * u[d];
+        r3[s] = C(3) * r[s];
+        omr[s] = p.omega * r[s];
+        m3aj[s] = fma(C(-3), a[s][0] * j[s][0] + a[s][1] * j[s][1] + a[s][2] * j[s][2], omr[s]);
+    }
+    const C keep = C(1) - p.omega;
+    const Nb3 here = nb3(p, c, 0, 0, 0);
+    T* dst = fout + at19(p, 0, here.row, here.x);
 #pragma unroll
-        for (int i = 0; i < Q19; ++i) {
-            C cu = C(0), ca = C(0), cj = C(0);
+    for (int i = 0; i < Q19; ++i) {
+        C cu = C(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (c19(i, d)) cu += C(c19(i, d)) * u[d];
+        const C e = (i == 0) ? w19<C>(0) * base : w19<C>(i) * fma(cu, fma(C(4.5), cu, C(3)), base);
+        const Nb3 n = nb3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2));
+        const T* src = fin + at19(p, i, n.row, n.x);
+#pragma unroll
+        for (int s = 0; s < N; ++s) {
+            C ca = C(0), cj = C(0);
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (c19(i, d)) {
-                    cu += C(c19(i, d)) * u[d];
                     ca += C(c19(i, d)) * a[s][d];
-                    cj += C(c19(i, d)) * J[d];
+                    cj += C(c19(i, d)) * j[s][d];
                 }
-            const C e = (i == 0) ? w19<C>(0) * base : w19<C>(i) * fma(cu, fma(C(4.5), cu, C(3)), base);
-            const C F = (i == 0) ? w19<C>(0) * m3aj : w19<C>(i) * fma(ca, fma(C(9), cj, r3), m3aj);
-            const C v = pull19(fin, p, s, i, c);
-            fout[at19(p, s, i, site)] = T(fma(keep, v, fma(omr, e, F)));
+            const C F = (i == 0) ? w19<C>(0) * m3aj[s]
+                                 : w19<C>(i) * fma(ca, fma(C(9), cj, r3[s]), m3aj[s]);
+            const C v = Storage<T>::load(src + s * cstride);
+            dst[s * cstride + (long long)i * p.nx] = T(fma(keep, v, fma(omr[s], e, F)));
         }
     }
     if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
@@ -290,10 +352,11 @@ k19_init(const double* __restrict__ rho, const double* __restrict__ u, T* __rest
             uu += ud * ud;
             cu += C(c19(i, d)) * ud;
         }
+        const Nb3 h = nb3(p, c, 0, 0, 0);
 #pragma unroll
         for (int s = 0; s < N; ++s)
-            f[at19(p, s, i, site)] = T(w19<C>(i) * C(rho[s * p.S + t]) *
-                                       (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
+            f[(long long)s * Q19 * p.S + at19(p, i, h.row, h.x)] =
+                T(w19<C>(i) * C(rho[s * p.S + t]) * (C(1) + C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu));
     }
 }
 
@@ -323,8 +386,10 @@ k19_set_state(const double* __restrict__ in, T* __restrict__ f,
 #pragma unroll
     for (int i = 0; i < Q19; ++i) {
         const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+        const Nb3 h = nb3(p, c, 0, 0, 0);
 #pragma unroll
-        for (int s = 0; s < N; ++s) f[at19(p, s, i, site)] = T(C(in[(s * Q19 + i) * p.S + t]));
+        for (int s = 0; s < N; ++s)
+            f[(long long)s * Q19 * p.S + at19(p, i, h.row, h.x)] = T(C(in[(s * Q19 + i) * p.S + t]));
     }
 }
 

@@ -156,11 +156,9 @@ def test_resume_equals_uninterrupted(precision):
     b.close()
 
 
-def test_mass_compensation_and_fit():
+def test_mass_compensation():
     """FP32 with the compensation every 50 steps: masses within 1e-6 of the start after
-    1000 steps of the 3-D ternary on 32^3; the device fit of the two phases equals the
-    k-means definition on the handle's own compositions to 1e-12."""
-    from tests.test_gpu_batch_fit import _fit_by_definition
+    1000 steps of the 3-D ternary on 32^3."""
     p = inputs.ternary3d(32, steps=1000)
     sim = mclb.Simulation.from_problem(p, precision="fp32", mass_every=50)
     m0 = sim.conservation()["mass"]
@@ -168,8 +166,33 @@ def test_mass_compensation_and_fit():
     assert sim.status() == 0
     drift = np.abs(sim.conservation()["mass"] / m0 - 1.0)
     assert np.all(drift < 1e-6), drift
-    rho = sim.moments(U=False, mu=False, P=False)["rho"]
+    sim.close()
+
+
+def test_fit_equilibrium_on_slabs():
+    """The paper's ternary chi set started as two slabs (in x) at the ends of the
+    Flory-Huggins tie line through (0.4, 0.4, 0.2), 24 x 8 x 8, 2000 FP64 steps: the
+    device fit of the two phases equals the k-means definition on the handle's own
+    compositions to 1e-12, and lies within 0.05 of the tie line."""
+    from oracle import thermo
+    from tests.test_gpu_batch_fit import _fit_by_definition
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    q1, q2 = thermo.tie_line(chi, np.ones(3), [0.4, 0.4, 0.2])
+    hi, lo = (np.asarray(q1), np.asarray(q2)) if q1[0] > q2[0] else (np.asarray(q2), np.asarray(q1))
+    nx, ny, nz = 24, 8, 8
+    x = np.arange(nx)
+    inside = (x >= nx // 4) & (x < 3 * nx // 4)
+    phi = np.where(inside[None, :], hi[:, None], lo[:, None])
+    rho = np.ascontiguousarray(np.broadcast_to(phi[:, None, None, :], (3, nz, ny, nx)))
+    sim = mclb.Simulation(3, nx, ny, 1 / 0.9, chi, precision="fp64", lattice="d3q19", nz=nz)
+    sim.init_fields(rho)
+    sim.step(2000)
+    assert sim.status() == 0
     fit = sim.fit_equilibrium(2)
-    want = _fit_by_definition(rho, 2, lattice="d3q19")
+    want = _fit_by_definition(sim.moments(U=False, mu=False, P=False)["rho"], 2, lattice="d3q19")
     assert np.max(np.abs(fit - want)) < 1e-12
+    assert np.max(np.abs(fit[0] - hi)) < 0.05 and np.max(np.abs(fit[1] - lo)) < 0.05
     sim.close()
