@@ -13,6 +13,8 @@ Three lattices, each a plain path of its own in the C file: D2Q9 (the
 two-dimensional workloads), D1Q3 (the lattice of the paper's own simulations,
 Sec. 4) and D3Q19 (three dimensions; the same equations on a lattice whose
 weights give the same moments).
+Optional solid walls in y on D2Q9 (``walls=1``; the paper has none): halfway
+bounce-back of the populations and mirrored rows in the stencils.
 Two readings of the velocity in the forcing's second moment (Eq. ff3):
 ``forcing_velocity=0`` is the component velocity u^s as printed (the default),
 ``forcing_velocity=1`` the barycentric u.  Two readings of the sum of the component
@@ -59,7 +61,7 @@ class OracleParams(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
                 ("chi", ctypes.c_double * (NMAX * NMAX)), ("m", ctypes.c_double * NMAX),
                 ("forcing_velocity", ctypes.c_int), ("force_form", ctypes.c_int),
-                ("nz", ctypes.c_int), ("gz", ctypes.c_double)]
+                ("nz", ctypes.c_int), ("gz", ctypes.c_double), ("walls", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -134,13 +136,16 @@ class Oracle:
     """
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
-                 force=(0.0, 0.0), forcing_velocity=0, lattice="d2q9", force_form=0, nz=1):
+                 force=(0.0, 0.0), forcing_velocity=0, lattice="d2q9", force_form=0, nz=1,
+                 walls=0):
         if lattice not in ("d2q9", "d1q3", "d3q19"):
             raise ValueError(f"lattice {lattice!r}")
         if lattice == "d1q3" and int(ny) != 1:
             raise ValueError("a D1Q3 lattice has ny = 1")
         if lattice != "d3q19" and int(nz) != 1:
             raise ValueError("nz > 1 needs the D3Q19 lattice")
+        if walls and lattice != "d2q9":
+            raise ValueError("walls are a D2Q9 option")
         self.lattice = lattice
         self.lib = _load()
         p = OracleParams()
@@ -149,6 +154,7 @@ class Oracle:
         p.gx, p.gy = float(force[0]), float(force[1])
         p.gz = float(force[2]) if len(force) > 2 else 0.0
         p.nz = int(nz)
+        p.walls = int(walls)
         chi = np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp)
         for a in range(ncomp):
             for b in range(ncomp):
@@ -167,7 +173,7 @@ class Oracle:
         o = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta,
                 prob.kappa, prob.force, getattr(prob, "forcing_velocity", 0),
                 getattr(prob, "lattice", "d2q9"), getattr(prob, "force_form", 0),
-                getattr(prob, "nz", 1))
+                getattr(prob, "nz", 1), getattr(prob, "walls", 0))
         o.init(prob.rho, prob.u)
         return o
 

@@ -44,7 +44,9 @@
  *     force_form = 1 and kappa = 0, shifted so that their sum is the Gibbs-Duhem
  *     total (1 - 1/(2 tau)) (1/3) grad rho);
  *     the output velocity is U = u + a/2 with rho a = sum_s rho^s a^s;
- *   - initial distributions are the equilibria of the given fields.
+ *   - initial distributions are the equilibria of the given fields;
+ *   - optional solid walls in y (walls = 1; the paper has none): halfway bounce-back
+ *     of the populations, mirrored rows in the stencils (see oracle_params).
  *
  * Layout: f[((s * 9 + i) * ny + y) * nx + x], the pre-collision distribution
  * of component s, velocity i at site (x, y) at the current time.
@@ -70,7 +72,13 @@
  * only): the forces keep their differences but their sum over the components is
  * replaced by the continuum total that Gibbs-Duhem gives for the Flory-Huggins free
  * energy (whose pressure sum rho mu - psi vanishes), (1 - 1/(2 tau)) (1/3) grad rho. */
-/* nz and gz are read by the D3Q19 path only (the other lattices ignore them). */
+/* nz and gz are read by the D3Q19 path only (the other lattices ignore them).
+ * walls (D2Q9 only): 0 = periodic in y; 1 = stationary solid walls halfway between
+ * rows, below row 0 and above row ny - 1 (the paper has no walls: a reading for the
+ * membrane-formation set-up its introduction motivates).  A population that would
+ * stream across a wall returns to its site with the opposite velocity (halfway
+ * bounce-back), and the stencils of rho^s, nu^s and rho see the wall rows as mirror
+ * images of the rows next to them (zero normal gradient: neutral wetting). */
 typedef struct {
     int ncomp, nx, ny;
     double tau, theta, kappa, gx, gy;
@@ -80,12 +88,14 @@ typedef struct {
     int force_form;
     int nz;
     double gz;
+    int walls;
 } oracle_params;
 
 static const int VX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int VY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double WT[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};   /* v_OPP[i] = -v_i */
 static const double LOG_FLOOR = 1e-12;
 
 int oracle_nthreads(void)
@@ -104,6 +114,7 @@ static int check(const oracle_params* p)
     if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
     if (p->force_form != 0 && p->force_form != 1) return -1;
     if (p->force_form == 1 && p->kappa != 0.0) return -1;
+    if (p->walls != 0 && p->walls != 1) return -1;
     return 0;
 }
 
@@ -208,23 +219,33 @@ static void work_free(work_t* w)
     free(w->nu); free(w->ax); free(w->ay);
 }
 
+/* Row of the neighbour y + dy seen by a stencil: periodic, or with walls the mirror
+ * image of the row next to the wall (rows -1 and ny read rows 0 and ny - 1). */
+static long stencil_row(long y, int dy, int ny, int walls)
+{
+    long yy = y + dy;
+    if (!walls) return wrap(yy, ny);
+    return yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy);
+}
+
 /* Discrete lap g = 6 sum_i w_i (g(r + v_i) - g(r)) of one scalar field. */
-static double lap_at(const double* g, int nx, int ny, int x, int y)
+static double lap_at(const double* g, int nx, int ny, int walls, int x, int y)
 {
     double c = g[(long)y * nx + x], acc = 0.0;
     for (int i = 0; i < 9; ++i) {
-        long xx = wrap(x + VX[i], nx), yy = wrap(y + VY[i], ny);
+        long xx = wrap(x + VX[i], nx), yy = stencil_row(y, VY[i], ny, walls);
         acc += WT[i] * (g[yy * nx + xx] - c);
     }
     return 6.0 * acc;
 }
 
 /* Discrete grad g = 3 sum_i w_i v_i g(r + v_i). */
-static void grad_at(const double* g, int nx, int ny, int x, int y, double* gx, double* gy)
+static void grad_at(const double* g, int nx, int ny, int walls, int x, int y, double* gx,
+                    double* gy)
 {
     double ax = 0.0, ay = 0.0;
     for (int i = 0; i < 9; ++i) {
-        long xx = wrap(x + VX[i], nx), yy = wrap(y + VY[i], ny);
+        long xx = wrap(x + VX[i], nx), yy = stencil_row(y, VY[i], ny, walls);
         double v = g[yy * nx + xx];
         ax += WT[i] * VX[i] * v;
         ay += WT[i] * VY[i] * v;
@@ -296,7 +317,7 @@ static void stage_potentials(const oracle_params* p, work_t* w)
                     logs += coef * log(r);
                 }
                 double bulk = th * (1.0 / p->m[s] - 1.0 - sum_phi_m + chiphi[s] - quad);
-                double grad_term = -p->kappa * lap_at(w->rs + s * S, nx, ny, x, y);
+                double grad_term = -p->kappa * lap_at(w->rs + s * S, nx, ny, p->walls, x, y);
                 w->nu[s * S + c] = logs + bulk + grad_term;
             }
         }
@@ -315,7 +336,7 @@ static void stage_forces(const oracle_params* p, work_t* w)
             long c = (long)y * nx + x;
             for (int s = 0; s < N; ++s) {
                 double gx, gy;
-                grad_at(w->nu + s * S, nx, ny, x, y, &gx, &gy);
+                grad_at(w->nu + s * S, nx, ny, p->walls, x, y, &gx, &gy);
                 w->ax[s * S + c] = -coef * gx + p->gx;
                 w->ay[s * S + c] = -coef * gy + p->gy;
             }
@@ -334,7 +355,7 @@ static void stage_forces(const oracle_params* p, work_t* w)
                     Ax += w->rs[s * S + c] * (w->ax[s * S + c] - p->gx);
                     Ay += w->rs[s * S + c] * (w->ay[s * S + c] - p->gy);
                 }
-                grad_at(w->rho, nx, ny, x, y, &gx, &gy);
+                grad_at(w->rho, nx, ny, p->walls, x, y, &gx, &gy);
                 double dx = (coef * gx / 3.0 - Ax) / w->rho[c];
                 double dy = (coef * gy / 3.0 - Ay) / w->rho[c];
                 for (int s = 0; s < N; ++s) {
@@ -367,8 +388,14 @@ static void stage_collide_stream(const oracle_params* p, const double* f, const 
                 for (int i = 0; i < 9; ++i) {
                     double fi = f[(long)(s * 9 + i) * S + c];
                     double post = fi + (fe[i] - fi) / tau + F[i];
-                    long xx = wrap(x + VX[i], nx), yy = wrap(y + VY[i], ny);
-                    fnew[(long)(s * 9 + i) * S + yy * nx + xx] = post;
+                    long yy = y + VY[i];
+                    if (p->walls && (yy < 0 || yy >= ny)) {
+                        /* halfway bounce-back: back to this site, opposite velocity */
+                        fnew[(long)(s * 9 + OPP[i]) * S + c] = post;
+                    } else {
+                        long xx = wrap(x + VX[i], nx);
+                        fnew[(long)(s * 9 + i) * S + wrap(yy, ny) * nx + xx] = post;
+                    }
                 }
             }
         }
@@ -455,7 +482,7 @@ int oracle_moments(const oracle_params* p, const double* f, double* rho_out, dou
                 for (int s = 0; s < N; ++s) rsl[s] = w.rs[s * S + c];
                 oracle_mu_bulk(p, rsl, mub);
                 for (int s = 0; s < N; ++s)
-                    muf[s] = mub[s] - p->kappa * lap_at(w.rs + s * S, nx, ny, x, y);
+                    muf[s] = mub[s] - p->kappa * lap_at(w.rs + s * S, nx, ny, p->walls, x, y);
                 if (mu)
                     for (int s = 0; s < N; ++s) mu[s * S + c] = muf[s];
                 if (P) {
@@ -463,7 +490,7 @@ int oracle_moments(const oracle_params* p, const double* f, double* rho_out, dou
                     double pxx = 0.0, pxy = 0.0, pyy = 0.0;
                     for (int s = 0; s < N; ++s) {
                         double gx, gy;
-                        grad_at(w.rs + s * S, nx, ny, x, y, &gx, &gy);
+                        grad_at(w.rs + s * S, nx, ny, p->walls, x, y, &gx, &gy);
                         rmu += rsl[s] * muf[s];
                         gg += 0.5 * p->kappa * (gx * gx + gy * gy);
                         pxx += p->kappa * gx * gx;
@@ -527,7 +554,7 @@ static const double W1[3] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0};
 
 static int check1(const oracle_params* p)
 {
-    if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1) return -1;
+    if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1 || p->walls != 0) return -1;
     if (!(p->tau > 0.5)) return -1;
     if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
     if (p->force_form != 0 && p->force_form != 1) return -1;
@@ -802,6 +829,7 @@ static const double W3[19] = {1.0 / 3.0,
 static int check3(const oracle_params* p)
 {
     if (!p || p->ncomp < 1 || p->ncomp > OR_NMAX || p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
+    if (p->walls != 0) return -1;
     if (!(p->tau > 0.5)) return -1;
     if (p->forcing_velocity != 0 && p->forcing_velocity != 1) return -1;
     if (p->force_form != 0 && p->force_form != 1) return -1;
