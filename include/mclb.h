@@ -137,6 +137,15 @@ typedef enum {
  *   force_form mclb_force_form (0: Eq. definef as printed)
  *   nz         layers of a D3Q19 lattice (0 or 1 for the other lattices, which reject more)
  *   force_z    z component of the body acceleration (D3Q19 only; 0 otherwise)
+ *   walls      0: periodic in y (the paper's setting); 1: stationary solid walls halfway
+ *              between rows, below row 0 and above row ny - 1 (the paper has no walls:
+ *              a reading for non-periodic set-ups such as a slab in contact with a solid).
+ *              A population that would stream across a wall returns to its site with
+ *              the opposite velocity (halfway bounce-back), which keeps every component's
+ *              mass; the stencils of rho^s and nu^s see the rows beyond a wall as mirror
+ *              images of the rows next to it (zero normal gradient: neutral wetting).
+ *              x stays periodic.  D2Q9 on the staged schedule only (kernel AUTO or
+ *              STAGED); single handles only (batches and mclb_step_noalloc reject it)
  *   mass_every 0 (off, the default) or the period, in timesteps, of the per-component
  *              mass compensation.  Eq. ff1 and the collision keep every component's total
  *              mass exactly; stored in FP32 or 16 bits, the rounding of each site's
@@ -170,6 +179,7 @@ typedef struct {
     int mass_every;
     int nz;
     double force_z;
+    int walls;
 } mclb_params;
 
 typedef struct mclb_handle_s* mclb_handle;

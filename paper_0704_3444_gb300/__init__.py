@@ -55,7 +55,8 @@ class mclb_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("forcing_velocity", ctypes.c_int),
                 ("lattice", ctypes.c_int), ("force_form", ctypes.c_int),
-                ("mass_every", ctypes.c_int), ("nz", ctypes.c_int), ("force_z", ctypes.c_double)]
+                ("mass_every", ctypes.c_int), ("nz", ctypes.c_int), ("force_z", ctypes.c_double),
+                ("walls", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -153,7 +154,7 @@ def _fields(rho, u, ncomp, ny, nx, device=False, nz=1, ud=2):
 
 def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, force=(0.0, 0.0),
                 precision="fp32", kernel=KERNEL_AUTO, stream=None, forcing_velocity=0,
-                lattice="d2q9", force_form=0, mass_every=0, nz=1):
+                lattice="d2q9", force_form=0, mass_every=0, nz=1, walls=0):
     """Build an mclb_params struct; returns (struct, keep-alive arrays).  ``force`` has
     two components, or three on D3Q19 (the third is force_z)."""
     chi = np.ascontiguousarray(np.asarray(chi, dtype=np.float64).reshape(ncomp, ncomp))
@@ -166,6 +167,7 @@ def make_params(ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0, for
     p.force[0], p.force[1] = float(force[0]), float(force[1])
     p.force_z = float(force[2]) if len(force) > 2 else 0.0
     p.nz = int(nz)
+    p.walls = int(walls)
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.kernel = int(kernel)
     p.stream = ctypes.c_void_p(stream) if stream else None
@@ -182,11 +184,11 @@ class Simulation:
 
     def __init__(self, ncomp, nx, ny, tau, chi, m=None, theta=1.0 / 3.0, kappa=0.0,
                  force=(0.0, 0.0), precision="fp32", kernel=KERNEL_AUTO, stream=None,
-                 forcing_velocity=0, lattice="d2q9", force_form=0, mass_every=0, nz=1):
+                 forcing_velocity=0, lattice="d2q9", force_form=0, mass_every=0, nz=1, walls=0):
         self.lib = load()
         self.ncomp, self.nx, self.ny = int(ncomp), int(nx), int(ny)
         p, keep = make_params(ncomp, nx, ny, tau, chi, m, theta, kappa, force, precision, kernel,
-                              stream, forcing_velocity, lattice, force_form, mass_every, nz)
+                              stream, forcing_velocity, lattice, force_form, mass_every, nz, walls)
         self.q = {D1Q3: 3, D3Q19: 19}.get(p.lattice, 9)
         self.nz = max(int(nz), 1) if p.lattice == D3Q19 else 1
         self.ud = 3 if p.lattice == D3Q19 else 2
@@ -199,7 +201,8 @@ class Simulation:
         s = cls(prob.ncomp, prob.nx, prob.ny, prob.tau, prob.chi, prob.m, prob.theta, prob.kappa,
                 prob.force, precision or prob.precision, kernel, stream,
                 getattr(prob, "forcing_velocity", 0), getattr(prob, "lattice", "d2q9"),
-                getattr(prob, "force_form", 0), mass_every, getattr(prob, "nz", 1))
+                getattr(prob, "force_form", 0), mass_every, getattr(prob, "nz", 1),
+                getattr(prob, "walls", 0))
         s.init_fields(prob.rho, prob.u)
         return s
 

@@ -131,6 +131,11 @@ int validate(const mclb_params* p)
                                      "(kernel AUTO or STAGED) on D2Q9");
     }
     if (p->mass_every < 0) return fail(MCLB_EINVAL, "mass_every=%d must be >= 0", p->mass_every);
+    if (p->walls != 0 && p->walls != 1) return fail(MCLB_EINVAL, "walls=%d unknown", p->walls);
+    if (p->walls && p->lattice != MCLB_D2Q9)
+        return fail(MCLB_EINVAL, "walls are a D2Q9 option (lattice=%d)", p->lattice);
+    if (p->walls && p->kernel == MCLB_KERNEL_FUSED)
+        return fail(MCLB_EINVAL, "walls run on the staged schedule (kernel AUTO or STAGED)");
     if (p->lattice == MCLB_D3Q19 && p->precision != MCLB_FP64 && p->precision != MCLB_FP32)
         return fail(MCLB_EINVAL, "lattice D3Q19 stores FP64 or FP32 (precision=%d)", p->precision);
     if (p->lattice == MCLB_D1Q3) {
@@ -174,6 +179,7 @@ void fill_problem(const mclb_params* p, const KernelTable& tab, Problem& P)
     P.forcing_velocity = p->forcing_velocity;
     P.force_form = p->force_form;
     P.mass_every = p->mass_every;
+    P.walls = p->walls;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) P.chi[a * P.N + b] = p->chi[a * P.N + b];
         P.m[a] = p->m ? p->m[a] : 1.0;
@@ -475,7 +481,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaStreamCreateWithFlags(&h->status_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
     h->fused = false;
-    if (P.force_form == MCLB_FORCE_GIBBS_DUHEM && !h->alt) h->kernel = MCLB_KERNEL_STAGED;
+    if ((P.force_form == MCLB_FORCE_GIBBS_DUHEM || P.walls) && !h->alt) h->kernel = MCLB_KERNEL_STAGED;
     if (h->alt) {
         if (h->alt->item_bytes > 0 && cudaMalloc(&h->sc.line_item, h->alt->item_bytes) != cudaSuccess)
             return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));
@@ -962,6 +968,8 @@ int mclb_batch_create(const mclb_params* params, int count, mclb_batch* out)
             return fail(MCLB_EINVAL, "instance %d: mass_every must be 0 in a batch", k);
         if (params[k].lattice == MCLB_D3Q19)
             return fail(MCLB_EINVAL, "instance %d: batches hold D2Q9 and D1Q3 lattices", k);
+        if (params[k].walls)
+            return fail(MCLB_EINVAL, "instance %d: batches are periodic (walls must be 0)", k);
     }
     mclb_batch b = new (std::nothrow) mclb_batch_s();
     if (!b) return fail(MCLB_ENOMEM, "host allocation failed");

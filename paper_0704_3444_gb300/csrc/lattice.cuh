@@ -17,6 +17,12 @@ __host__ __device__ __forceinline__ constexpr int vx(int i)
 {
     return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
 }
+// Index of the opposite velocity, v_opp9(i) = -v_i.
+__host__ __device__ __forceinline__ constexpr int opp9(int i)
+{
+    return i == 0 ? 0 : (i <= 4 ? (i <= 2 ? i + 2 : i - 2) : (i <= 6 ? i + 2 : i - 2));
+}
+
 __host__ __device__ __forceinline__ constexpr int vy(int i)
 {
     return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
@@ -108,6 +114,7 @@ struct StepParams {
     C log_floor;          // floor of rho^s / rho inside a logarithm
     int bary;             // 1: barycentric u in the forcing's second moment, 0: u^s (Eq. ff3)
     int gd;               // 1: Gibbs-Duhem total force (kappa = 0), 0: Eq. definef as printed
+    int walls;            // 1: solid walls below row 0 and above row ny - 1 (staged D2Q9)
     C chi[NMAX * NMAX];
     C th_m[NMAX];         // theta / m^s
     C logc[NMAX];         // theta / m^s - 1/3: coefficient of ln rho^s in nu^s
@@ -141,6 +148,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
     p.log_floor = C(1e-12);
     p.bary = P.forcing_velocity;
     p.gd = P.force_form;
+    p.walls = P.walls;
     p.log_mask = 0;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) p.chi[a * P.N + b] = C(P.chi[a * P.N + b]);

@@ -42,6 +42,7 @@ struct Problem {
     int lattice;            // MCLB_D2Q9 (0), MCLB_D1Q3 (1: ny = 1, layout [s][i][x], no ghosts) or
                             // MCLB_D3Q19 (2: layout [s][z][y][i][x], no ghosts)
     int force_form;         // MCLB_FORCE_COMPONENT (0) or MCLB_FORCE_GIBBS_DUHEM (1)
+    int walls;              // 1: solid walls in y (D2Q9, staged schedule), 0: periodic
     int mass_every;         // period of the per-component mass compensation, 0 = off
     int withhold;           // test hook: the single-pass kernel issues no copies
     long long rbytes;       // 16-bit formats: byte offset of the FP32 density lines

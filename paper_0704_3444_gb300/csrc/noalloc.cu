@@ -153,6 +153,8 @@ extern "C" int mclb_step_noalloc(const mclb_params* params, const double* f_in, 
     if (rc) return rc;
     if (params->precision != MCLB_FP64)
         return report(MCLB_EINVAL, "mclb_step_noalloc: only precision MCLB_FP64 is supported");
+    if (params->walls != 0)
+        return report(MCLB_EINVAL, "mclb_step_noalloc: the lattice must be periodic (walls = 0)");
     if (params->mass_every != 0)
         return report(MCLB_EINVAL, "mclb_step_noalloc: mass_every must be 0 (one step, no handle)");
     if (params->lattice != MCLB_D2Q9)

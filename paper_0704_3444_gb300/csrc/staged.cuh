@@ -15,17 +15,45 @@ namespace mclb {
 constexpr int SITE_THREADS = 256;
 
 // Pre-collision value f^s_i(x, y) = post-collision value stored at (x - v_i, y - v_i).
+// With walls (p.walls), a population whose source row lies beyond a wall is the site's
+// own post-collision value of the opposite velocity (halfway bounce-back).
 template <typename T>
 __device__ __forceinline__ typename Storage<T>::C pull(const T* __restrict__ f,
                                                        const StepParams<typename Storage<T>::C>& p,
                                                        int s, int i, int x, int y)
 {
     using C = typename Storage<T>::C;
-    const int xs = wrap_add(x, -vx(i), p.nx);
-    const int ys = wrap_add(y, -vy(i), p.ny);
-    C v = Storage<T>::load(f + fidx(p, s, i, ys, xs));
+    int xs, ys = y - vy(i), is = i;
+    if (p.walls && (ys < 0 || ys >= p.ny)) {
+        xs = x;
+        ys = y;
+        is = opp9(i);
+    } else {
+        xs = wrap_add(x, -vx(i), p.nx);
+        ys = wrap_add(y, -vy(i), p.ny);
+    }
+    C v = Storage<T>::load(f + fidx(p, s, is, ys, xs));
     if constexpr (Storage<T>::shifted) v += wq<C>(i) * __ldg(rho_line(f, p, s, ys) + p.hx + xs);
     return v;
+}
+
+// Row y + dy as a stencil sees it: periodic, or with walls the mirror image of the row
+// next to the wall (rows -1 and ny read rows 0 and ny - 1: zero normal gradient).
+template <typename C>
+__device__ __forceinline__ int stencil_row(const StepParams<C>& p, int y, int dy)
+{
+    if (!p.walls) return wrap_add(y, dy, p.ny);
+    const int yy = y + dy;
+    return yy < 0 ? 0 : (yy >= p.ny ? p.ny - 1 : yy);
+}
+
+// Velocity whose stored value at (x, y) the site (x + v_i, y + v_i) pulls as f_i, or,
+// when that site lies beyond a wall, the velocity the site (x, y) itself pulls it as.
+template <typename C>
+__device__ __forceinline__ bool bounced(const StepParams<C>& p, int y, int i)
+{
+    const int yy = y + vy(i);
+    return p.walls && (yy < 0 || yy >= p.ny);
 }
 
 // rho^s at one site (pull streaming + zeroth moment).
@@ -66,7 +94,7 @@ __device__ __forceinline__ void neighbour_laplacians(const C* __restrict__ rs,
         C acc = C(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+            const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row(p, y, vy(i));
             acc += wq<C>(i) * (rs[s * p.S + (long long)yy * p.nx + xx] - r[s]);
         }
         lap[s] = C(6) * acc;
@@ -105,7 +133,7 @@ __device__ __forceinline__ void field_grad(const C* __restrict__ g, const StepPa
     C ax = C(0), ay = C(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row(p, y, vy(i));
         const C v = g[(long long)yy * p.nx + xx];
         ax += wq<C>(i) * C(vx(i)) * v;
         ay += wq<C>(i) * C(vy(i)) * v;
@@ -122,7 +150,7 @@ __device__ __forceinline__ void rho_grad(const C* __restrict__ rs, const StepPar
     C ax = C(0), ay = C(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row(p, y, vy(i));
         C r = C(0);
 #pragma unroll
         for (int s = 0; s < N; ++s) r += rs[s * p.S + (long long)yy * p.nx + xx];
@@ -228,11 +256,15 @@ k_init(const double* __restrict__ rho, const double* __restrict__ u, T* __restri
     C v[N][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        // the site that pulls this value, and as which velocity (itself, as the opposite
+        // velocity, when the value is bounced back from a wall)
+        const bool bb = bounced(p, y, i);
+        const int ie = bb ? opp9(i) : i;
+        const int xx = bb ? x : wrap_add(x, vx(i), p.nx), yy = bb ? y : wrap_add(y, vy(i), p.ny);
         const long long t = (long long)yy * p.nx + xx;
         const C ux = u ? C(u[t]) : C(0), uy = u ? C(u[p.S + t]) : C(0);
         const C uu = ux * ux + uy * uy;
-        const C cu = C(vx(i)) * ux + C(vy(i)) * uy;
+        const C cu = C(vx(ie)) * ux + C(vy(ie)) * uy;
 #pragma unroll
         for (int s = 0; s < N; ++s)
             v[s][i] = wq<C>(i) * C(rho[s * p.S + t]) *
@@ -268,10 +300,12 @@ k_set_state(const double* __restrict__ in, T* __restrict__ f,
     C v[N][Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const bool bb = bounced(p, y, i);
+        const int ie = bb ? opp9(i) : i;
+        const int xx = bb ? x : wrap_add(x, vx(i), p.nx), yy = bb ? y : wrap_add(y, vy(i), p.ny);
         const long long t = (long long)yy * p.nx + xx;
 #pragma unroll
-        for (int s = 0; s < N; ++s) v[s][i] = C(in[(s * Q + i) * p.S + t]);
+        for (int s = 0; s < N; ++s) v[s][i] = C(in[(s * Q + ie) * p.S + t]);
     }
 #pragma unroll
     for (int s = 0; s < N; ++s) store_site(f, p, s, y, x, v[s]);
@@ -449,7 +483,7 @@ k_compositions(const typename Storage<T>::C* __restrict__ rs, double* __restrict
     for (int s = 0; s < N; ++s) gx[s] = gy[s] = 0.0;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int xx = wrap_add(x, vx(i), p.nx), yy = wrap_add(y, vy(i), p.ny);
+        const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row(p, y, vy(i));
         const long long t = (long long)yy * p.nx + xx;
         double rho = 0.0;
 #pragma unroll

@@ -86,6 +86,7 @@ class Problem:
     lattice: str = "d2q9"          # or "d1q3" (ny = 1) or "d3q19"
     force_form: int = 0            # 0: Eq. definef as printed, 1: Gibbs-Duhem total (kappa = 0)
     nz: int = 1                    # layers (D3Q19)
+    walls: int = 0                 # 1: solid walls in y (D2Q9)
 
     @property
     def sites(self) -> int:

@@ -64,6 +64,9 @@ def _params(**kw):
     (dict(force_form=1, kernel=1), "staged schedule"),
     (dict(mass_every=-1), "mass_every"),
     (dict(lattice=3), "lattice"),
+    (dict(walls=2), "walls"),
+    (dict(walls=1, lattice="d1q3", ny=1), "D2Q9 option"),
+    (dict(walls=1, kernel=1), "staged schedule"),
     (dict(lattice="d3q19", nz=2, precision="bf16"), "FP64 or FP32"),
     (dict(nz=2), "D3Q19"),
     (dict(nz=-1), "nz"),
@@ -76,6 +79,16 @@ def test_invalid_parameters_are_rejected(lib, kw, frag):
     rc = lib.mclb_create(ctypes.byref(p), ctypes.byref(h))
     assert rc == -1 and not h.value
     assert frag in lib.mclb_last_error().decode()
+
+
+def test_batches_and_noalloc_reject_walls(lib):
+    p, keep = _params(walls=1)
+    b = ctypes.c_void_p()
+    assert lib.mclb_batch_create(ctypes.byref(p), 1, ctypes.byref(b)) == -1 and not b.value
+    assert "periodic" in lib.mclb_last_error().decode()
+    p, keep = _params(walls=1, precision="fp64")
+    assert lib.mclb_step_noalloc(ctypes.byref(p), None, None) == -1
+    assert "periodic" in lib.mclb_last_error().decode()
 
 
 def test_batches_reject_d3q19(lib):

@@ -1,0 +1,154 @@
+"""GPU: solid walls in y (walls = 1, D2Q9 staged schedule) against the FP64 oracle's walls.
+
+Halfway bounce-back of the populations and mirrored stencil rows (neutral wetting); x
+stays periodic.  Tolerances as elsewhere: FP64 1e-12 of the field's max-norm (P
+absolute), FP32 1e-5 per field after 100 steps, 16-bit formats 2e-3 of the density
+scale after 20 steps.
+"""
+import numpy as np
+import pytest
+
+import paper_0704_3444_gb300 as mclb
+from oracle import Oracle
+from paper_0704_3444_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mclb.build()
+    mclb.load()
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.mark.parametrize("fv", [0, 1])
+@pytest.mark.parametrize("shape", [(5, 3, 2), (40, 33, 3), (130, 37, 4), (9, 1, 2)],
+                         ids=lambda s: f"{s[0]}x{s[1]}N{s[2]}")
+def test_fp64_parity(shape, fv):
+    """20 FP64 steps with every term on (m != 1, theta != 1/3, kappa > 0, a body force
+    toward a wall): state, rho, U, mu within 1e-12, P to 1e-12 absolute, the sums."""
+    nx, ny, n = shape
+    rho, u = inputs.random_state(n, nx, ny, seed=500 + nx + n, amp=0.3, umax=0.03)
+    chi = inputs.uniform_chi(n, 1.6)
+    kw = dict(m=[1.0 + (k % 3) for k in range(n)], theta=0.4, kappa=0.02,
+              force=(1e-5, -2e-5), forcing_velocity=fv, walls=1)
+    sim = mclb.Simulation(n, nx, ny, 0.9, chi, precision="fp64", **kw)
+    assert sim.launches_per_step == 3
+    orc = Oracle(n, nx, ny, 0.9, chi, **kw)
+    sim.init_fields(rho, u)
+    orc.init(rho, u)
+    sim.step(20)
+    assert orc.run(20) == 0
+    assert sim.status() == 0
+    assert _rel(sim.get_state(), orc.f) < 1e-12
+    gm, om = sim.moments(), orc.moments()
+    for k in ("rho", "U", "mu"):
+        assert _rel(gm[k], om[k]) < 1e-12, k
+    assert np.max(np.abs(gm["P"] - om["P"])) < 1e-12
+    gc, oc = sim.conservation(), orc.conservation()
+    np.testing.assert_allclose(gc["mass"], oc["mass"], rtol=1e-13)
+    np.testing.assert_allclose(gc["force"], oc["force"], rtol=1e-9, atol=1e-15)
+    sim.close()
+
+
+def test_fp64_gibbs_duhem_and_mass():
+    """The Gibbs-Duhem reading (kappa = 0) between walls: 50 FP64 steps within 1e-12 of
+    the oracle, and each component's mass kept to 1e-13 over 1000 steps."""
+    n, nx, ny = 3, 40, 24
+    rho, u = inputs.random_state(n, nx, ny, seed=61, amp=0.3, umax=0.03)
+    chi = inputs.uniform_chi(n, 1.6)
+    kw = dict(m=[1.0, 2.0, 1.0], theta=0.4, forcing_velocity=1, force_form=1, walls=1)
+    sim = mclb.Simulation(n, nx, ny, 0.9, chi, precision="fp64", **kw)
+    orc = Oracle(n, nx, ny, 0.9, chi, **kw)
+    sim.init_fields(rho, u)
+    orc.init(rho, u)
+    m0 = sim.conservation()["mass"]
+    sim.step(50)
+    assert orc.run(50) == 0
+    assert _rel(sim.get_state(), orc.f) < 1e-12
+    sim.step(950)
+    assert sim.status() == 0
+    assert np.all(np.abs(sim.conservation()["mass"] / m0 - 1.0) < 1e-13)
+    sim.close()
+
+
+def test_fp32_slab_in_a_channel():
+    """The polymer/solvent | non-solvent slab between walls (256 x 64, interfaces meeting
+    the walls): rho, U, mu and P within 1e-5 of the oracle after 100 FP32 steps."""
+    p = inputs.slab(256, 64, steps=100)
+    p.walls = 1
+    sim = mclb.Simulation.from_problem(p, precision="fp32")
+    orc = Oracle.from_problem(p)
+    sim.step(100)
+    assert orc.run(100) == 0
+    assert sim.status() == 0
+    gm, om = sim.moments(), orc.moments()
+    err = {k: float(np.max(np.abs(gm[k] - om[k]))) for k in ("rho", "U", "mu", "P")}
+    assert all(e < 1e-5 for e in err.values()), err
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_shifted_storage_between_walls(precision):
+    """16-bit storage between walls, 130 x 37, N = 3: densities within 2e-3 of the
+    density scale of the oracle's after 20 steps, each component's mass to 1e-6."""
+    n, nx, ny = 3, 130, 37
+    rho, u = inputs.random_state(n, nx, ny, seed=77, amp=0.3, umax=0.03)
+    chi = inputs.uniform_chi(n, 1.5)
+    kw = dict(kappa=0.01, walls=1)
+    sim = mclb.Simulation(n, nx, ny, 0.9, chi, precision=precision, **kw)
+    sim.init_fields(rho, u)
+    m0 = sim.conservation()["mass"]
+    sim.step(20)
+    assert sim.status() == 0
+    orc = Oracle(n, nx, ny, 0.9, chi, **kw)
+    orc.init(rho, u)
+    orc.run(20)
+    got, want = sim.moments(mu=False, P=False)["rho"], orc.moments()["rho"]
+    assert np.max(np.abs(got - want)) < 2e-3 * np.abs(want).max()
+    np.testing.assert_allclose(sim.conservation()["mass"], m0, rtol=1e-6)
+    sim.close()
+
+
+def test_poiseuille_fp32():
+    """Plane Poiseuille flow (one component, body force along x, channel width 32):
+    the steady FP32 profile equals the oracle's steady profile to 1e-4 of its maximum,
+    and that one is within 1e-3 of the parabola g/(2 nu) (y + 1/2)(H - y - 1/2)."""
+    H, tau, g = 32, 1.0, 1e-5
+    rho = np.ones((1, H, 4))
+    nu = (tau - 0.5) / 3.0
+    steps = int(12 * H * H / nu / np.pi ** 2) + 1000
+    sim = mclb.Simulation(1, 4, H, tau, np.zeros((1, 1)), force=(g, 0.0), precision="fp32", walls=1)
+    sim.init_fields(rho)
+    sim.step(steps)
+    assert sim.status() == 0
+    orc = Oracle(1, 4, H, tau, np.zeros((1, 1)), force=(g, 0.0), walls=1)
+    orc.init(rho)
+    assert orc.run(steps) == 0
+    Ug, Uo = sim.moments()["U"][0], orc.moments()["U"][0]
+    assert np.max(np.abs(Ug - Uo)) < 1e-4 * np.abs(Uo).max()
+    y = np.arange(H) + 0.5
+    want = g / (2.0 * nu) * y * (H - y)
+    assert np.max(np.abs(Uo[:, 0] - want)) < 1e-3 * want.max()
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_resume_equals_uninterrupted(precision):
+    p = inputs.slab(128, 48)
+    p.walls = 1
+    a = mclb.Simulation.from_problem(p, precision=precision)
+    a.step(21)
+    b = mclb.Simulation(p.ncomp, p.nx, p.ny, p.tau, p.chi, p.m, p.theta, p.kappa, p.force,
+                        precision, walls=1)
+    b.set_state(a.get_state())
+    a.step(33)
+    b.step(33)
+    assert a.status() == 0 and b.status() == 0
+    assert np.array_equal(a.get_state(), b.get_state())
+    a.close()
+    b.close()
