@@ -482,6 +482,18 @@ def main():
                 "hbm_frac_of_measured": v.bytes_per_step / (t / 200) / 1e9 / peak,
                 "speedup_vs_fp32": val / slab_fp32}
             v.close()
+        # the same slab between solid walls in y (staged schedule, FP32)
+        slab.walls = 1
+        v = mclb.Simulation.from_problem(slab, precision="fp32", stream=sptr)
+        t = time_steps(torch, v, 100, args.warmup, stream)
+        val = slab.sites * slab.ncomp * 100 / t / 1e6
+        variants["slab_8192x2048_fp32_walls"] = {
+            "value": val, "steps": 100, "status_ok": v.status() == 0,
+            "launches_per_step": v.launches_per_step,
+            "hbm_gbs_algorithmic": v.bytes_per_step / (t / 100) / 1e9,
+            "hbm_frac_of_measured": v.bytes_per_step / (t / 100) / 1e9 / peak,
+            "speedup_vs_fp32": val / slab_fp32}
+        v.close()
         # the D3Q19 lattice (staged schedule): the paper's ternary chi set on 256^3 in FP32
         cube = workloads()["ternary3d_256"]()
         v = mclb.Simulation.from_problem(cube, precision="fp32", stream=sptr)

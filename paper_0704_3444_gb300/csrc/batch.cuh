@@ -32,7 +32,7 @@ kb_density(const BatchItem<T>* __restrict__ items, const int* __restrict__ blk2i
     const BatchItem<T>& it = items[blk2inst[blockIdx.x]];
     const long long site = (long long)(blockIdx.x - it.block0) * SITE_THREADS + threadIdx.x;
     if (site >= it.p.S) return;
-    density_site<T, N>(it.f[parity], it.rs, it.p, site);
+    density_site<T, N, false>(it.f[parity], it.rs, it.p, site);   // batches are periodic
 }
 
 template <typename T, int N>
@@ -42,7 +42,7 @@ kb_potential(const BatchItem<T>* __restrict__ items, const int* __restrict__ blk
     const BatchItem<T>& it = items[blk2inst[blockIdx.x]];
     const long long site = (long long)(blockIdx.x - it.block0) * SITE_THREADS + threadIdx.x;
     if (site >= it.p.S) return;
-    potential_site<typename Storage<T>::C, N>(it.rs, it.nu, it.p, site);
+    potential_site<typename Storage<T>::C, N, false>(it.rs, it.nu, it.p, site);
 }
 
 template <typename T, int N>
@@ -52,7 +52,7 @@ kb_collide(const BatchItem<T>* __restrict__ items, const int* __restrict__ blk2i
     const BatchItem<T>& it = items[blk2inst[blockIdx.x]];
     const long long site = (long long)(blockIdx.x - it.block0) * SITE_THREADS + threadIdx.x;
     if (site >= it.p.S) return;
-    collide_site<T, N>(it.f[parity], it.f[parity ^ 1], it.rs, it.nu, it.p, site);
+    collide_site<T, N, false>(it.f[parity], it.f[parity ^ 1], it.rs, it.nu, it.p, site);
 }
 
 // Device-side description of one instance for the batched march: its tensor maps

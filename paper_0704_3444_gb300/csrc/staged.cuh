@@ -14,23 +14,28 @@ namespace mclb {
 
 constexpr int SITE_THREADS = 256;
 
+// The site functions below take a compile-time flag E: with E = true they handle solid
+// walls in y (p.walls), with E = false they assume a periodic neighbourhood.  The timestep
+// kernels use E = false on every row that no wall touches (all rows of a periodic
+// lattice, rows 1 .. ny - 2 between walls), so the periodic path is free of wall tests.
+
 // Pre-collision value f^s_i(x, y) = post-collision value stored at (x - v_i, y - v_i).
 // With walls (p.walls), a population whose source row lies beyond a wall is the site's
 // own post-collision value of the opposite velocity (halfway bounce-back).
-template <typename T>
+template <bool E = true, typename T>
 __device__ __forceinline__ typename Storage<T>::C pull(const T* __restrict__ f,
                                                        const StepParams<typename Storage<T>::C>& p,
                                                        int s, int i, int x, int y)
 {
     using C = typename Storage<T>::C;
-    int xs, ys = y - vy(i), is = i;
-    if (p.walls && (ys < 0 || ys >= p.ny)) {
-        xs = x;
-        ys = y;
-        is = opp9(i);
-    } else {
-        xs = wrap_add(x, -vx(i), p.nx);
-        ys = wrap_add(y, -vy(i), p.ny);
+    int xs = wrap_add(x, -vx(i), p.nx), ys = wrap_add(y, -vy(i), p.ny), is = i;
+    if constexpr (E) {
+        const int yb = y - vy(i);
+        if (p.walls && (yb < 0 || yb >= p.ny)) {
+            xs = x;
+            ys = y;
+            is = opp9(i);
+        }
     }
     C v = Storage<T>::load(f + fidx(p, s, is, ys, xs));
     if constexpr (Storage<T>::shifted) v += wq<C>(i) * __ldg(rho_line(f, p, s, ys) + p.hx + xs);
@@ -39,12 +44,25 @@ __device__ __forceinline__ typename Storage<T>::C pull(const T* __restrict__ f,
 
 // Row y + dy as a stencil sees it: periodic, or with walls the mirror image of the row
 // next to the wall (rows -1 and ny read rows 0 and ny - 1: zero normal gradient).
-template <typename C>
+template <bool E = true, typename C>
 __device__ __forceinline__ int stencil_row(const StepParams<C>& p, int y, int dy)
 {
-    if (!p.walls) return wrap_add(y, dy, p.ny);
-    const int yy = y + dy;
-    return yy < 0 ? 0 : (yy >= p.ny ? p.ny - 1 : yy);
+    if constexpr (E) {
+        if (p.walls) {
+            const int yy = y + dy;
+            return yy < 0 ? 0 : (yy >= p.ny ? p.ny - 1 : yy);
+        }
+    }
+    return wrap_add(y, dy, p.ny);
+}
+
+// True where a timestep kernel must take the wall-aware (E = true) path.
+template <typename C>
+__device__ __forceinline__ bool wall_row(const StepParams<C>& p, long long site)
+{
+    if (!p.walls) return false;
+    const int y = (int)(site / p.nx);
+    return y == 0 || y == p.ny - 1;
 }
 
 // Velocity whose stored value at (x, y) the site (x + v_i, y + v_i) pulls as f_i, or,
@@ -57,7 +75,7 @@ __device__ __forceinline__ bool bounced(const StepParams<C>& p, int y, int i)
 }
 
 // rho^s at one site (pull streaming + zeroth moment).
-template <typename T, int N>
+template <typename T, int N, bool E = true>
 __device__ __forceinline__ void density_site(const T* __restrict__ f,
                                              typename Storage<T>::C* __restrict__ rs,
                                              const StepParams<typename Storage<T>::C>& p, long long site)
@@ -68,7 +86,7 @@ __device__ __forceinline__ void density_site(const T* __restrict__ f,
     for (int s = 0; s < N; ++s) {
         C r = C(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) r += pull(f, p, s, i, x, y);
+        for (int i = 0; i < Q; ++i) r += pull<E>(f, p, s, i, x, y);
         rs[s * p.S + site] = r;
     }
 }
@@ -80,10 +98,13 @@ k_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
 {
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
-    density_site<T, N>(f, rs, p, site);
+    if (wall_row(p, site))
+        density_site<T, N, true>(f, rs, p, site);
+    else
+        density_site<T, N, false>(f, rs, p, site);
 }
 
-template <typename C, int N>
+template <typename C, int N, bool E = true>
 __device__ __forceinline__ void neighbour_laplacians(const C* __restrict__ rs,
                                                      const StepParams<C>& p, int x, int y,
                                                      const C (&r)[N], C (&lap)[N])
@@ -94,7 +115,7 @@ __device__ __forceinline__ void neighbour_laplacians(const C* __restrict__ rs,
         C acc = C(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row(p, y, vy(i));
+            const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row<E>(p, y, vy(i));
             acc += wq<C>(i) * (rs[s * p.S + (long long)yy * p.nx + xx] - r[s]);
         }
         lap[s] = C(6) * acc;
@@ -102,7 +123,7 @@ __device__ __forceinline__ void neighbour_laplacians(const C* __restrict__ rs,
 }
 
 // nu^s at one site from the density fields.
-template <typename C, int N>
+template <typename C, int N, bool E = true>
 __device__ __forceinline__ void potential_site(const C* __restrict__ rs, C* __restrict__ nu,
                                                const StepParams<C>& p, long long site)
 {
@@ -110,7 +131,7 @@ __device__ __forceinline__ void potential_site(const C* __restrict__ rs, C* __re
     C r[N], lap[N], out[N];
 #pragma unroll
     for (int s = 0; s < N; ++s) r[s] = rs[s * p.S + site];
-    neighbour_laplacians<C, N>(rs, p, x, y, r, lap);
+    neighbour_laplacians<C, N, E>(rs, p, x, y, r, lap);
     site_nu<C, N>(p, r, lap, out);
 #pragma unroll
     for (int s = 0; s < N; ++s) nu[s * p.S + site] = out[s];
@@ -122,18 +143,21 @@ k_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant_
 {
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
-    potential_site<C, N>(rs, nu, p, site);
+    if (wall_row(p, site))
+        potential_site<C, N, true>(rs, nu, p, site);
+    else
+        potential_site<C, N, false>(rs, nu, p, site);
 }
 
 // grad g = 3 sum_i w_i v_i g(r + v_i) of one component's field
-template <typename C>
+template <bool E = true, typename C>
 __device__ __forceinline__ void field_grad(const C* __restrict__ g, const StepParams<C>& p, int x,
                                            int y, C& gx, C& gy)
 {
     C ax = C(0), ay = C(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row(p, y, vy(i));
+        const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row<E>(p, y, vy(i));
         const C v = g[(long long)yy * p.nx + xx];
         ax += wq<C>(i) * C(vx(i)) * v;
         ay += wq<C>(i) * C(vy(i)) * v;
@@ -143,14 +167,14 @@ __device__ __forceinline__ void field_grad(const C* __restrict__ g, const StepPa
 }
 
 // grad rho = 3 sum_i w_i v_i rho(r + v_i) of the total density, from the N density fields
-template <typename C, int N>
+template <typename C, int N, bool E = true>
 __device__ __forceinline__ void rho_grad(const C* __restrict__ rs, const StepParams<C>& p, int x,
                                          int y, C& gx, C& gy)
 {
     C ax = C(0), ay = C(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row(p, y, vy(i));
+        const int xx = wrap_add(x, vx(i), p.nx), yy = stencil_row<E>(p, y, vy(i));
         C r = C(0);
 #pragma unroll
         for (int s = 0; s < N; ++s) r += rs[s * p.S + (long long)yy * p.nx + xx];
@@ -163,7 +187,7 @@ __device__ __forceinline__ void rho_grad(const C* __restrict__ rs, const StepPar
 
 // Accelerations a^s at (x, y) from the potential fields (Eq. definef plus the body force;
 // with p.gd the Gibbs-Duhem shift).  r: the site's rho^s, rho their sum.
-template <typename C, int N>
+template <typename C, int N, bool E = true>
 __device__ __forceinline__ void site_accel(const C* __restrict__ rs, const C* __restrict__ nu,
                                            const StepParams<C>& p, int x, int y, const C (&r)[N],
                                            C rho, C (&ax)[N], C (&ay)[N])
@@ -171,20 +195,20 @@ __device__ __forceinline__ void site_accel(const C* __restrict__ rs, const C* __
 #pragma unroll
     for (int s = 0; s < N; ++s) {
         C gx, gy;
-        field_grad(nu + s * p.S, p, x, y, gx, gy);
+        field_grad<E>(nu + s * p.S, p, x, y, gx, gy);
         ax[s] = -p.fcoef * gx + p.gx;
         ay[s] = -p.fcoef * gy + p.gy;
     }
     if (p.gd) {
         C grx, gry;
-        rho_grad<C, N>(rs, p, x, y, grx, gry);
+        rho_grad<C, N, E>(rs, p, x, y, grx, gry);
         gibbs_duhem_shift<C, N>(p, r, rho, grx, gry, ax, ay);
     }
 }
 
 // Collision at one site from the pulled populations and the potential fields; the
 // post-collision values are stored in place (pull scheme), ghosts included.
-template <typename T, int N>
+template <typename T, int N, bool E = true>
 __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __restrict__ fout,
                                              const typename Storage<T>::C* __restrict__ rs,
                                              const typename Storage<T>::C* __restrict__ nu,
@@ -201,7 +225,7 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
         C a = C(0), bx = C(0), by = C(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const C v = pull(fin, p, s, i, x, y);
+            const C v = pull<E>(fin, p, s, i, x, y);
             f[s][i] = v;
             a += v;
             bx += v * C(vx(i));
@@ -218,7 +242,7 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
     C e[Q];
     eq_weights(ux, uy, e);
     C ax[N], ay[N];
-    site_accel<C, N>(rs, nu, p, x, y, r, rho, ax, ay);
+    site_accel<C, N, E>(rs, nu, p, x, y, r, rho, ax, ay);
 #pragma unroll
     for (int s = 0; s < N; ++s) {
         C out[Q], fjx, fjy;
@@ -238,7 +262,10 @@ k_collide(const T* __restrict__ fin, T* __restrict__ fout,
 {
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
-    collide_site<T, N>(fin, fout, rs, nu, p, site);
+    if (wall_row(p, site))
+        collide_site<T, N, true>(fin, fout, rs, nu, p, site);
+    else
+        collide_site<T, N, false>(fin, fout, rs, nu, p, site);
 }
 
 // ---------------------------------------------------------------- diagnostics
