@@ -594,17 +594,33 @@ struct Launch19 {
     }
 };
 
+// The kernel table of one storage type is assembled from three parts, each instantiated
+// in a translation unit of its own (prec_<type>_<part>.cu) so that
+// the build compiles them in parallel; prec_<type>.cu puts the table together.
 template <typename T>
-inline KernelTable make_table(CUtensorMapDataType tt)
+inline void table_base(KernelTable& t, CUtensorMapDataType tt)
 {
-    KernelTable t{};
     t.storage_bytes = sizeof(T);
     t.shifted = Storage<T>::shifted;
     t.tma_type = tt;
     t.hx = (int)std::max<size_t>(4, 16 / sizeof(T));
+    t.line3 = nullptr;
+    t.d3q19 = nullptr;
+}
+
+// single handles on D2Q9: the single pass
+template <typename T>
+inline void fill_march(KernelTable& t)
+{
     t.plan_fused = &Launch<T>::plan_fused;
-    t.init = &Launch<T>::init;
     t.step_fused = &Launch<T>::step_fused;
+}
+
+// single handles on D2Q9: the staged schedule and the diagnostics
+template <typename T>
+inline void fill_staged(KernelTable& t)
+{
+    t.init = &Launch<T>::init;
     t.step_staged = &Launch<T>::step_staged;
     t.moments = &Launch<T>::moments;
     t.conservation = &Launch<T>::conservation;
@@ -612,20 +628,34 @@ inline KernelTable make_table(CUtensorMapDataType tt)
     t.get_state = &Launch<T>::get_state;
     t.set_state = &Launch<T>::set_state;
     t.mass = &Launch<T>::mass;
+}
+
+// batches of D2Q9 instances
+template <typename T>
+inline void fill_batch(KernelTable& t)
+{
     t.batch_create = &batch_group_create<T>;
     t.batch_step = &batch_group_step<T>;
     t.batch_launches = &batch_group_launches<T>;
     t.batch_tune = &batch_group_tune<T>;
     t.batch_waves = &batch_group_waves<T>;
     t.batch_destroy = &batch_group_destroy<T>;
-    if constexpr (!Storage<T>::shifted) {
-        t.line3 = Line3Launch<T>::table();
-        t.d3q19 = Launch19<T>::table();
-    } else {
-        t.line3 = nullptr;
-        t.d3q19 = nullptr;
-    }
-    return t;
+}
+
+// the D1Q3 lattice (FP64 and FP32 storage)
+template <typename T>
+inline void fill_line3(KernelTable& t)
+{
+    static_assert(!Storage<T>::shifted, "D1Q3 stores FP64 or FP32");
+    t.line3 = Line3Launch<T>::table();
+}
+
+// the D3Q19 lattice (FP64 and FP32 storage)
+template <typename T>
+inline void fill_cube(KernelTable& t)
+{
+    static_assert(!Storage<T>::shifted, "D3Q19 stores FP64 or FP32");
+    t.d3q19 = Launch19<T>::table();
 }
 
 }  // namespace mclb
