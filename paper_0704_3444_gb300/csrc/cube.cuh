@@ -84,6 +84,43 @@ __device__ __forceinline__ Nb3 nb3(const StepParams<C>& p, const Site3& c, int d
     return n;
 }
 
+// Per-thread neighbourhood: the three wrapped columns x - 1, x, x + 1 and, for a (dy, dz)
+// row offset, the start of that row in the stored layout (in units of elements: row *
+// 19 * nx) and in an N * S field (row * nx).  Each (dy, dz) pair is shared by one to
+// three velocities, so the compiler forms each row base once.
+struct Hood3 {
+    int xw[3];
+};
+template <typename C>
+__device__ __forceinline__ Hood3 hood3(const StepParams<C>& p, const Site3& c)
+{
+    Hood3 h;
+    h.xw[0] = wrap_add(c.x, -1, p.nx);
+    h.xw[1] = c.x;
+    h.xw[2] = wrap_add(c.x, 1, p.nx);
+    return h;
+}
+template <typename C>
+__device__ __forceinline__ int row3(const StepParams<C>& p, const Site3& c, int dy, int dz)
+{
+    return wrap_add(c.z, dz, p.nz) * p.ny + wrap_add(c.y, dy, p.ny);
+}
+// stored element (component 0) of velocity i pulled by the site: (row, x) of r - v_i
+template <typename C>
+__device__ __forceinline__ long long src19(const StepParams<C>& p, const Site3& c, const Hood3& h,
+                                           int i)
+{
+    const long long rb = (long long)row3(p, c, -c19(i, 1), -c19(i, 2)) * (Q19 * (long long)p.nx);
+    return rb + (long long)i * p.nx + h.xw[1 - c19(i, 0)];
+}
+// field index of the neighbour r + v_i
+template <typename C>
+__device__ __forceinline__ long long fnb3(const StepParams<C>& p, const Site3& c, const Hood3& h,
+                                         int i)
+{
+    return (long long)row3(p, c, c19(i, 1), c19(i, 2)) * p.nx + h.xw[1 + c19(i, 0)];
+}
+
 // Linear site index of a neighbour (index into an N * S field: s * S + nbr3(...)).
 template <typename C>
 __device__ __forceinline__ long long nbr3(const StepParams<C>& p, const Site3& c, int dx, int dy,
@@ -120,13 +157,13 @@ k19_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
     const Site3 c = site3(p, site);
+    const Hood3 h = hood3(p, c);
     C r[N];
 #pragma unroll
     for (int s = 0; s < N; ++s) r[s] = C(0);
 #pragma unroll
     for (int i = 0; i < Q19; ++i) {
-        const Nb3 n = nb3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2));
-        const T* src = f + at19(p, i, n.row, n.x);
+        const T* src = f + src19(p, c, h, i);
 #pragma unroll
         for (int s = 0; s < N; ++s) r[s] += Storage<T>::load(src + (long long)s * Q19 * p.S);
     }
@@ -141,11 +178,12 @@ __device__ __forceinline__ void laplacians19(const C* __restrict__ rs, const Ste
                                              const Site3& c, const C (&r)[N], C (&lap)[N])
 {
     C acc[N];
+    const Hood3 h = hood3(p, c);
 #pragma unroll
     for (int s = 0; s < N; ++s) acc[s] = C(0);
 #pragma unroll
     for (int i = 1; i < Q19; ++i) {
-        const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+        const long long t = fnb3(p, c, h, i);
 #pragma unroll
         for (int s = 0; s < N; ++s) acc[s] += w19<C>(i) * (rs[s * p.S + t] - r[s]);
     }
@@ -192,11 +230,12 @@ template <typename C, int N>
 __device__ __forceinline__ void grads19(const C* __restrict__ g, const StepParams<C>& p,
                                         const Site3& c, C (&gr)[N][3])
 {
+    const Hood3 h = hood3(p, c);
 #pragma unroll
     for (int s = 0; s < N; ++s) gr[s][0] = gr[s][1] = gr[s][2] = C(0);
 #pragma unroll
     for (int i = 1; i < Q19; ++i) {
-        const long long t = nbr3(p, c, c19(i, 0), c19(i, 1), c19(i, 2));
+        const long long t = fnb3(p, c, h, i);
 #pragma unroll
         for (int s = 0; s < N; ++s) {
             const C v = w19<C>(i) * g[s * p.S + t];
@@ -256,6 +295,7 @@ k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
     const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (site >= p.S) return;
     const Site3 c = site3(p, site);
+    const Hood3 h = hood3(p, c);
     const long long cstride = (long long)Q19 * p.S;   // one component's stored values
     // first pass: moments (the populations are pulled again for the collision, from cache)
     C r[N], j[N][3];
@@ -263,8 +303,7 @@ k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
     for (int s = 0; s < N; ++s) r[s] = j[s][0] = j[s][1] = j[s][2] = C(0);
 #pragma unroll
     for (int i = 0; i < Q19; ++i) {
-        const Nb3 n = nb3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2));
-        const T* src = fin + at19(p, i, n.row, n.x);
+        const T* src = fin + src19(p, c, h, i);
 #pragma unroll
         for (int s = 0; s < N; ++s) {
             const C v = Storage<T>::load(src + s * cstride);
@@ -309,8 +348,7 @@ k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
         for (int d = 0; d < 3; ++d)
             if (c19(i, d)) cu += C(c19(i, d)) * u[d];
         const C e = (i == 0) ? w19<C>(0) * base : w19<C>(i) * fma(cu, fma(C(4.5), cu, C(3)), base);
-        const Nb3 n = nb3(p, c, -c19(i, 0), -c19(i, 1), -c19(i, 2));
-        const T* src = fin + at19(p, i, n.row, n.x);
+        const T* src = fin + src19(p, c, h, i);
 #pragma unroll
         for (int s = 0; s < N; ++s) {
             C ca = C(0), cj = C(0);
