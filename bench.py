@@ -218,6 +218,7 @@ def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=1000):
     per = b.status()[1]
     finite = [k for k, v in enumerate(per) if v == 0]
     launches = b.launches_per_step
+    tuning = [{"narrow_strips": nar, "waves": w} for nar, w in b.tuning()]
     sims = [mclb.Simulation.from_problem(p, precision="fp32", kernel=mclb.KERNEL_FUSED, stream=sptr)
             for p in probs]
     for sm in sims:
@@ -264,6 +265,7 @@ def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=1000):
                         "instances still coarsening amplify that into a different arrangement "
                         "of domains, which the fit then measures"},
             "sites": sum(p.sites for p in probs), "launches_per_step": launches,
+            "autotuned_partition": tuning,
             "one_by_one_fp32_value": vs, "speedup_vs_one_by_one": vb / vs,
             "speedup_vs_fp32": vb / fp32_value}
 

@@ -325,8 +325,10 @@ int mclb_step_noalloc(const mclb_params* params, const double* f_in, double* f_o
  * instance, column strip and row segment in a table built at the first step) and one
  * launch refreshes their ghost columns; where that kernel cannot be set up the group
  * falls back to the staged schedule (three launches).  The first step after the batch
- * is (re)built picks each group's partition into row segments by timing a few
- * candidates on the current state (the state is not changed; the call synchronises).
+ * is (re)built picks each group's work partition -- the strip shape (the single-lattice
+ * kernel's, or a narrow one with two compute warps and 56 columns per CTA) and the segment
+ * height (2, 4, 8 or 16 waves of resident CTAs) -- by timing every candidate on the current
+ * state (the state is not changed; the call synchronises; mclb_batch_tuning reports it).
  * Steps are replayed from a CUDA graph in chunks of 32.  D1Q3 instances of one N
  * advance together in one launch per 4096 timesteps (one CTA per line, the line in
  * shared memory; lines too long for that step one launch per timestep).  precision
@@ -345,6 +347,24 @@ int mclb_batch_step(mclb_batch b, long nsteps);
  * staged schedule; D1Q3 lines: 1 per distinct N, plus 1 per line too long for shared
  * memory). */
 int mclb_batch_launches_per_step(mclb_batch b);
+
+/* The work partition the autotuner picked for each group of D2Q9 instances that share N
+ * (groups in ascending N; D1Q3 lines are not included): narrow[g] = 1 where it picked the
+ * narrow strip shape (two compute warps, 56 written columns per CTA) over the wide one (the
+ * single-lattice kernel's, 112 columns where it has four compute warps), waves[g] = how many
+ * waves of resident CTAs its segment height makes (2, 4, 8 or 16), or 0 where the group
+ * runs the staged schedule.  The pick is made by timing every candidate on the first step
+ * after the batch is (re)built; before that the defaults are reported.  Host arrays of cap
+ * entries; returns the number of groups (entries beyond cap are not written), or -1 on an
+ * invalid batch.  Synchronises only if the batch's tables have to be built. */
+int mclb_batch_tuning(mclb_batch b, int* narrow, int* waves, int cap);
+
+/* Test hook (no counterpart in the paper): make every group of D2Q9 instances use the
+ * candidate partition (narrow strips or not, waves 2, 4, 8 or 16) instead of the timed
+ * pick, so that each candidate's results can be checked.  Groups without that candidate
+ * (no narrow shape for their N, the staged schedule) keep theirs.  Returns the number of
+ * groups that switched, or -1 on an invalid batch or argument. */
+int mclb_test_batch_partition(mclb_batch b, int narrow, int waves);
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P);
 /* mclb_fit_equilibrium of one instance (Sec. 4 coexisting compositions). */
 int mclb_batch_fit_equilibrium(mclb_batch b, int index, int nphase, double* phi);

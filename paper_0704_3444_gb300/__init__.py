@@ -103,6 +103,9 @@ def load():
             "mclb_batch_status": ([H, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
             "mclb_batch_bytes_per_step": ([H], ctypes.c_double),
             "mclb_batch_launches_per_step": ([H], ctypes.c_int),
+            "mclb_batch_tuning": ([H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.c_int], ctypes.c_int),
+            "mclb_test_batch_partition": ([H, ctypes.c_int, ctypes.c_int], ctypes.c_int),
             "mclb_batch_destroy": ([H], ctypes.c_int),
             "mclb_step_noalloc": ([ctypes.POINTER(mclb_params), ctypes.c_void_p, ctypes.c_void_p],
                                   ctypes.c_int),
@@ -379,3 +382,19 @@ class Batch:
     @property
     def launches_per_step(self):
         return self.lib.mclb_batch_launches_per_step(self.h)
+
+    def tuning(self):
+        """Per group of D2Q9 instances (ascending N): (narrow strips picked, waves)."""
+        cap = 16
+        nar, wav = (ctypes.c_int * cap)(), (ctypes.c_int * cap)()
+        n = self.lib.mclb_batch_tuning(self.h, nar, wav, cap)
+        if n < 0:
+            raise MclbError(n, "mclb_batch_tuning")
+        return [(bool(nar[k]), int(wav[k])) for k in range(min(n, cap))]
+
+    def test_force_partition(self, narrow: bool, waves: int) -> int:
+        """Test hook (mclb_test_batch_partition): groups that switched to the candidate."""
+        n = self.lib.mclb_test_batch_partition(self.h, int(bool(narrow)), int(waves))
+        if n < 0:
+            raise MclbError(n, "mclb_test_batch_partition")
+        return n

@@ -56,11 +56,14 @@ kb_collide(const BatchItem<T>* __restrict__ items, const int* __restrict__ blk2i
 }
 
 // Device-side description of one instance for the batched march: its tensor maps
-// ([buffer][load view, density-line load view, store view, density-line store view]),
-// parameters and buffers.  Tensor maps in global memory must be 64-byte aligned.
+// ([buffer][load view, density-line load view, store view, density-line store view]) for
+// the wide geometry (maps) and the narrow one (maps2: the same views with that geometry's
+// box widths), parameters and buffers.  Tensor maps in global memory must be 64-byte
+// aligned.
 template <typename T>
 struct alignas(64) MarchItem {
     CUtensorMap maps[2][4];
+    CUtensorMap maps2[2][4];
     StepParams<typename Storage<T>::C> p;
     T* f[2];
 };
@@ -70,8 +73,10 @@ struct MarchCta {
     int inst, x0, y0, H;
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(MarchGeom<T, N>::THREADS) __maxnreg__((MarchGeom<T, N>::MAXREG))
+// G: the march geometry of this launch (MarchGeom, or MarchNarrow with NARROW = true, which
+// selects the instance's maps2)
+template <typename T, int N, typename G, bool NARROW>
+__global__ void __launch_bounds__(G::THREADS) __maxnreg__((G::MAXREG))
 kb_march(const MarchItem<T>* __restrict__ items, const MarchCta* __restrict__ ctas, int parity)
 {
     using C = typename Storage<T>::C;
@@ -79,6 +84,7 @@ kb_march(const MarchItem<T>* __restrict__ items, const MarchCta* __restrict__ ct
     __shared__ StepParams<C> ps;
     const MarchCta c = ctas[blockIdx.x];
     const MarchItem<T>& it = items[c.inst];
+    const CUtensorMap (&maps)[2][4] = NARROW ? it.maps2 : it.maps;
     static_assert(sizeof(StepParams<C>) % sizeof(int) == 0, "parameter copy by words");
     const int* src = reinterpret_cast<const int*>(&it.p);
     int* dst = reinterpret_cast<int*>(&ps);
@@ -88,12 +94,12 @@ kb_march(const MarchItem<T>* __restrict__ items, const MarchCta* __restrict__ ct
         // visible to the tensor-map proxy before the first copy uses them
         for (int b = 0; b < 2; ++b)
             for (int j = 0; j < 4; ++j)
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&it.maps[b][j])
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps[b][j])
                              : "memory");
     }
     __syncthreads();
-    march_cta<T, N>(&it.maps[parity][0], &it.maps[parity][1], &it.maps[parity ^ 1][2],
-                    &it.maps[parity ^ 1][3], it.f[parity ^ 1], ps, c.x0, c.y0, c.H, smem);
+    march_cta<T, N, G>(&maps[parity][0], &maps[parity][1], &maps[parity ^ 1][2], &maps[parity ^ 1][3],
+                       it.f[parity ^ 1], ps, c.x0, c.y0, c.H, smem);
 }
 
 // Ghost columns of every instance's new buffer (parity ^ 1), laid out per instance as in
@@ -133,8 +139,9 @@ struct BatchGroup {
     int nblocks = 0;
     BatchItem<T>* items = nullptr;
     int* blk2inst = nullptr;
-    // batched march: candidate CTA tables (segment heights for different wave counts),
-    // the one in use picked by timing them at the first step
+    // batched march: candidate CTA tables (the wide and, where it exists, the narrow strip
+    // geometry, each with segment heights for different wave counts), the one in use picked
+    // by timing them at the first step
     bool march = false;
     bool tuned = false;
     int count = 0;
@@ -142,6 +149,7 @@ struct BatchGroup {
     std::vector<MarchCta*> cand;
     std::vector<int> cand_n;
     std::vector<int> cand_waves;
+    std::vector<int> cand_geo;   // 0: MarchGeom (wide strips), 1: MarchNarrow
     int pick = 0;
     long long* gstart = nullptr;
     int* gfirst = nullptr;      // first ghost block of each instance
@@ -153,10 +161,9 @@ constexpr int MARCH_WAVES[] = {2, 4, 8, 16};
 
 // Table of the batched march's CTAs: strips of WOUT columns, segments of about the same
 // height everywhere (chosen so that the launch is about `waves` waves deep), tallest first.
-template <typename T, int N>
+template <typename T, int N, typename G = MarchGeom<T, N>>
 std::vector<MarchCta> march_ctas(int count, const Problem* probs, int slots, int waves)
 {
-    using G = MarchGeom<T, N>;
     long long rows = 0;
     for (int k = 0; k < count; ++k) rows += (long long)((probs[k].nx + G::WOUT - 1) / G::WOUT) * probs[k].ny;
     const int target = (int)std::max<long long>(8, rows / std::max(1, waves * slots));
@@ -172,33 +179,68 @@ std::vector<MarchCta> march_ctas(int count, const Problem* probs, int slots, int
     return v;
 }
 
+// Kernel attributes of one geometry's batched march; *per_sm receives its resident CTAs.
+template <typename T, int N, typename G, bool NARROW>
+bool march_geometry_ready(int* per_sm)
+{
+    auto kern = kb_march<T, N, G, NARROW>;
+    if (!G::FITS ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, G::THREADS, G::SMEM) != cudaSuccess ||
+        *per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// The candidate CTA tables of one geometry (one per wave count) appended to the group.
+template <typename T, int N, typename G>
+bool march_add_candidates(BatchGroup<T>* g, int geo, int count, const Problem* probs, int slots,
+                          cudaStream_t st)
+{
+    for (int waves : MARCH_WAVES) {
+        const std::vector<MarchCta> ctas = march_ctas<T, N, G>(count, probs, slots, waves);
+        if (ctas.empty() || ctas.size() > (size_t)INT32_MAX) return false;
+        MarchCta* d = nullptr;
+        if (cudaMalloc(&d, sizeof(MarchCta) * ctas.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        g->cand.push_back(d);
+        g->cand_n.push_back((int)ctas.size());
+        g->cand_waves.push_back(waves);
+        g->cand_geo.push_back(geo);
+        if (cudaMemcpyAsync(d, ctas.data(), sizeof(MarchCta) * ctas.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    return true;
+}
+
 template <typename T, int N>
 bool march_group_create(BatchGroup<T>* g, int count, const Problem* probs, const Scratch* scs,
-                        void* const* fa, void* const* fb, const CUtensorMap* maps, int sm_count,
-                        cudaStream_t st)
+                        void* const* fa, void* const* fb, const CUtensorMap* maps,
+                        const CUtensorMap* maps2, int sm_count, cudaStream_t st)
 {
-    using G = MarchGeom<T, N>;
     using C = typename Storage<T>::C;
-    if (!G::FITS) return false;
-    const size_t smem = G::SMEM;
-    if (cudaFuncSetAttribute(kb_march<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(kb_march<T, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb_march<T, N>, G::THREADS, smem) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        return false;
-    }
+    int per_sm = 0, per_sm2 = 0;
+    if (!march_geometry_ready<T, N, MarchGeom<T, N>, false>(&per_sm)) return false;
+    bool narrow = false;
+    if constexpr (has_narrow<T, N>())
+        narrow = maps2 && march_geometry_ready<T, N, MarchNarrow<T, N>, true>(&per_sm2);
     std::vector<MarchItem<T>> items(count);
     std::vector<long long> gstart(count + 1, 0);
     std::vector<int> gfirst(count + 1, 0), gmap;
     for (int k = 0; k < count; ++k) {
         for (int b = 0; b < 2; ++b)
-            for (int j = 0; j < 4; ++j) items[k].maps[b][j] = maps[(size_t)k * 8 + b * 4 + j];
+            for (int j = 0; j < 4; ++j) {
+                items[k].maps[b][j] = maps[(size_t)k * 8 + b * 4 + j];
+                items[k].maps2[b][j] = narrow ? maps2[(size_t)k * 8 + b * 4 + j] : maps[(size_t)k * 8 + b * 4 + j];
+            }
         items[k].p = make_params<C>(probs[k], scs[k].status);
         items[k].f[0] = static_cast<T*>(fa[k]);
         items[k].f[1] = static_cast<T*>(fb[k]);
@@ -221,51 +263,55 @@ bool march_group_create(BatchGroup<T>* g, int count, const Problem* probs, const
         cudaGetLastError();
         return false;
     }
-    for (int waves : MARCH_WAVES) {
-        const std::vector<MarchCta> ctas = march_ctas<T, N>(count, probs, per_sm * std::max(1, sm_count), waves);
-        if (ctas.empty() || ctas.size() > (size_t)INT32_MAX) return false;
-        MarchCta* d = nullptr;
-        if (cudaMalloc(&d, sizeof(MarchCta) * ctas.size()) != cudaSuccess) {
-            cudaGetLastError();
+    const int slots = per_sm * std::max(1, sm_count);
+    if (!march_add_candidates<T, N, MarchGeom<T, N>>(g, 0, count, probs, slots, st)) return false;
+    if constexpr (has_narrow<T, N>())
+        if (narrow && !march_add_candidates<T, N, MarchNarrow<T, N>>(g, 1, count, probs,
+                                                                   per_sm2 * std::max(1, sm_count), st))
             return false;
-        }
-        g->cand.push_back(d);
-        g->cand_n.push_back((int)ctas.size());
-        g->cand_waves.push_back(waves);
-        if (cudaMemcpyAsync(d, ctas.data(), sizeof(MarchCta) * ctas.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-    }
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     g->march = true;
     g->count = count;
-    g->pick = 1;   // six waves' worth until tuned
+    g->pick = 1;   // wide strips, four waves, until tuned
     g->gblocks = (int)gmap.size();
     return true;
 }
 
-// Time every candidate CTA table on the current state (each run reads buffer `parity`
-// and rewrites the other buffer with the same values, so the state is unchanged) and
-// keep the fastest.  Synchronises the stream.
+// One launch of the batched march with candidate table c.
+template <typename T, int N>
+cudaError_t march_launch(const BatchGroup<T>* g, int c, int parity, cudaStream_t st)
+{
+    if (g->cand_geo[c] == 0) {
+        using G = MarchGeom<T, N>;
+        kb_march<T, N, G, false><<<g->cand_n[c], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[c], parity);
+    } else {
+        if constexpr (has_narrow<T, N>()) {
+            using G = MarchNarrow<T, N>;
+            kb_march<T, N, G, true><<<g->cand_n[c], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[c], parity);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+// Time every candidate CTA table -- both strip geometries, every wave count -- on the
+// current state (each run reads buffer `parity` and rewrites the other buffer with the
+// same values, so the state is unchanged) and keep the fastest.  Synchronises the stream.
 template <typename T, int N>
 cudaError_t march_group_tune(BatchGroup<T>* g, int parity, cudaStream_t st)
 {
-    using G = MarchGeom<T, N>;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t err = cudaEventCreate(&e0);
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     float best = 1e30f;
     for (size_t c = 0; c < g->cand.size() && err == cudaSuccess; ++c) {
-        kb_march<T, N><<<g->cand_n[c], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[c], parity);
-        err = cudaEventRecord(e0, st);
-        for (int r = 0; r < 3 && err == cudaSuccess; ++r) {
-            kb_march<T, N><<<g->cand_n[c], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[c], parity);
-            err = cudaGetLastError();
-        }
+        err = march_launch<T, N>(g, (int)c, parity, st);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = march_launch<T, N>(g, (int)c, parity, st);
         if (err == cudaSuccess) err = cudaEventRecord(e1, st);
         if (err == cudaSuccess) err = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -286,8 +332,8 @@ void batch_group_destroy(void* group);
 
 template <typename T>
 void* batch_group_create(int N, int count, const Problem* probs, const Scratch* scs,
-                         void* const* fa, void* const* fb, const CUtensorMap* maps, int sm_count,
-                         cudaStream_t st)
+                         void* const* fa, void* const* fb, const CUtensorMap* maps,
+                         const CUtensorMap* maps2, int sm_count, cudaStream_t st)
 {
     using C = typename Storage<T>::C;
     if (maps) {
@@ -295,14 +341,14 @@ void* batch_group_create(int N, int count, const Problem* probs, const Scratch* 
         g->N = N;
         bool ok = false;
         switch (N) {
-            case 1: ok = march_group_create<T, 1>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
-            case 2: ok = march_group_create<T, 2>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
-            case 3: ok = march_group_create<T, 3>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
-            case 4: ok = march_group_create<T, 4>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
-            case 5: ok = march_group_create<T, 5>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
-            case 6: ok = march_group_create<T, 6>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
-            case 7: ok = march_group_create<T, 7>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
-            case 8: ok = march_group_create<T, 8>(g, count, probs, scs, fa, fb, maps, sm_count, st); break;
+            case 1: ok = march_group_create<T, 1>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
+            case 2: ok = march_group_create<T, 2>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
+            case 3: ok = march_group_create<T, 3>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
+            case 4: ok = march_group_create<T, 4>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
+            case 5: ok = march_group_create<T, 5>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
+            case 6: ok = march_group_create<T, 6>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
+            case 7: ok = march_group_create<T, 7>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
+            case 8: ok = march_group_create<T, 8>(g, count, probs, scs, fa, fb, maps, maps2, sm_count, st); break;
             default: break;
         }
         if (ok) return g;
@@ -347,11 +393,8 @@ template <typename T, int N>
 cudaError_t batch_group_step_n(const BatchGroup<T>* g, int parity, cudaStream_t st, int part)
 {
     if (g->march) {
-        using G = MarchGeom<T, N>;
-        if (part == 0)
-            kb_march<T, N><<<g->cand_n[g->pick], G::THREADS, G::SMEM, st>>>(g->mitems, g->cand[g->pick], parity);
-        else
-            kb_ghosts<T><<<g->gblocks, 256, 0, st>>>(g->mitems, g->gstart, g->gfirst, g->gblk2inst, parity, N);
+        if (part == 0) return march_launch<T, N>(g, g->pick, parity, st);
+        kb_ghosts<T><<<g->gblocks, 256, 0, st>>>(g->mitems, g->gstart, g->gfirst, g->gblk2inst, parity, N);
         return cudaGetLastError();
     }
     if (part != 0) return cudaSuccess;
@@ -396,12 +439,57 @@ cudaError_t batch_group_tune(void* group, int parity, cudaStream_t st)
     }
 }
 
-// waves of the CTA table in use (0 for the staged schedule)
+// Test hook: use candidate (narrow, waves) from now on, untimed.
+template <typename T>
+bool batch_group_force(void* group, int narrow, int waves)
+{
+    auto* g = static_cast<BatchGroup<T>*>(group);
+    if (!g->march) return false;
+    for (size_t c = 0; c < g->cand.size(); ++c)
+        if (g->cand_geo[c] == (narrow ? 1 : 0) && g->cand_waves[c] == waves) {
+            g->pick = (int)c;
+            g->tuned = true;
+            return true;
+        }
+    return false;
+}
+
+// waves of the CTA table in use (0 for the staged schedule), plus 1000 when the narrow
+// strip geometry was picked
 template <typename T>
 int batch_group_waves(const void* group)
 {
     const auto* g = static_cast<const BatchGroup<T>*>(group);
-    return g->march ? g->cand_waves[g->pick] : 0;
+    return g->march ? g->cand_waves[g->pick] + 1000 * g->cand_geo[g->pick] : 0;
+}
+
+// Box widths of the narrow geometry's views for N components (load boxes, store boxes);
+// false where the group has no narrow candidate.
+template <typename T, int N>
+bool narrow_boxes_n(int* box_w, int* out_w)
+{
+    if constexpr (has_narrow<T, N>()) {
+        using G = MarchNarrow<T, N>;
+        *box_w = G::WI;
+        *out_w = G::TMA_STORE ? MARCH_OUT : (G::CTA_STORE ? G::WOUT : 0);
+        return true;
+    }
+    return false;
+}
+template <typename T>
+bool batch_narrow_boxes(int N, int* box_w, int* out_w)
+{
+    switch (N) {
+        case 1: return narrow_boxes_n<T, 1>(box_w, out_w);
+        case 2: return narrow_boxes_n<T, 2>(box_w, out_w);
+        case 3: return narrow_boxes_n<T, 3>(box_w, out_w);
+        case 4: return narrow_boxes_n<T, 4>(box_w, out_w);
+        case 5: return narrow_boxes_n<T, 5>(box_w, out_w);
+        case 6: return narrow_boxes_n<T, 6>(box_w, out_w);
+        case 7: return narrow_boxes_n<T, 7>(box_w, out_w);
+        case 8: return narrow_boxes_n<T, 8>(box_w, out_w);
+        default: return false;
+    }
 }
 
 template <typename T>

@@ -256,7 +256,10 @@ int ensure_dtmp(mclb_handle h, size_t doubles)
     return MCLB_OK;
 }
 
-int make_tmap(mclb_handle h, int b)
+// The four views of buffer b with load boxes of box_w columns and store boxes of out_w
+// columns (0: no store views): v[0] load, v[1] density-line load (16-bit formats), v[2]
+// store, v[3] density-line store (16-bit formats).
+int encode_views(mclb_handle h, int b, int box_w, int out_w, CUtensorMap* const* v)
 {
     auto fn = encode_fn();
     if (!fn) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled unavailable");
@@ -268,18 +271,18 @@ int make_tmap(mclb_handle h, int b)
     cuuint64_t dims[4] = {(cuuint64_t)(P.nx + 2 * P.hx), (cuuint64_t)Q, (cuuint64_t)P.ny, (cuuint64_t)P.N};
     cuuint64_t strides[3] = {(cuuint64_t)(P.pitch * sz), (cuuint64_t)(Q * P.pitch * sz),
                              (cuuint64_t)(P.plane * sz)};
-    cuuint32_t box[4] = {(cuuint32_t)h->plan.box_w, 1u, 1u, (cuuint32_t)P.N};
+    cuuint32_t box[4] = {(cuuint32_t)box_w, 1u, 1u, (cuuint32_t)P.N};
     cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
-    CUresult r = fn(&h->tmap[b], h->tab->tma_type, 4, h->f[b], dims, strides, box, estr,
+    CUresult r = fn(v[0], h->tab->tma_type, 4, h->f[b], dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    if (h->plan.out_w > 0) {
+    if (out_w > 0) {
         // the same 4-D view ending at column nx (boxes that reach past it are clipped):
         // one box = out_w columns of the 9 lines of one row, all components
         cuuint64_t wdims[4] = {(cuuint64_t)(P.nx + P.hx), (cuuint64_t)Q, (cuuint64_t)P.ny, (cuuint64_t)P.N};
-        cuuint32_t wbox[4] = {(cuuint32_t)h->plan.out_w, (cuuint32_t)Q, 1u, (cuuint32_t)P.N};
-        r = fn(&h->tmapw[b], h->tab->tma_type, 4, h->f[b], wdims, strides, wbox, estr,
+        cuuint32_t wbox[4] = {(cuuint32_t)out_w, (cuuint32_t)Q, 1u, (cuuint32_t)P.N};
+        r = fn(v[2], h->tab->tma_type, 4, h->f[b], wdims, strides, wbox, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS)
@@ -288,8 +291,8 @@ int make_tmap(mclb_handle h, int b)
             cuuint64_t rdims[3] = {(cuuint64_t)(P.nx + P.hx), (cuuint64_t)P.ny, (cuuint64_t)P.N};
             cuuint64_t rstrides[2] = {(cuuint64_t)(P.pitch * sizeof(float)),
                                       (cuuint64_t)(P.ny * P.pitch * sizeof(float))};
-            cuuint32_t rbox[3] = {(cuuint32_t)h->plan.out_w, 1u, (cuuint32_t)P.N};
-            r = fn(&h->tmapwr[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+            cuuint32_t rbox[3] = {(cuuint32_t)out_w, 1u, (cuuint32_t)P.N};
+            r = fn(v[3], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                    static_cast<char*>(h->f[b]) + P.rbytes, rdims, rstrides, rbox, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -302,8 +305,8 @@ int make_tmap(mclb_handle h, int b)
         cuuint64_t rdims[3] = {(cuuint64_t)(P.nx + 2 * P.hx), (cuuint64_t)P.ny, (cuuint64_t)P.N};
         cuuint64_t rstrides[2] = {(cuuint64_t)(P.pitch * sizeof(float)),
                                   (cuuint64_t)(P.ny * P.pitch * sizeof(float))};
-        cuuint32_t rbox[3] = {(cuuint32_t)h->plan.box_w, 1u, (cuuint32_t)P.N};
-        r = fn(&h->tmapr[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+        cuuint32_t rbox[3] = {(cuuint32_t)box_w, 1u, (cuuint32_t)P.N};
+        r = fn(v[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                static_cast<char*>(h->f[b]) + P.rbytes, rdims, rstrides, rbox, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -311,6 +314,12 @@ int make_tmap(mclb_handle h, int b)
             return fail(MCLB_ECUDA, "cuTensorMapEncodeTiled (density lines) failed (%d)", (int)r);
     }
     return MCLB_OK;
+}
+
+int make_tmap(mclb_handle h, int b)
+{
+    CUtensorMap* const v[4] = {&h->tmap[b], &h->tmapr[b], &h->tmapw[b], &h->tmapwr[b]};
+    return encode_views(h, b, h->plan.box_w, h->plan.out_w, v);
 }
 
 cudaError_t launch_one_step(mclb_handle h, int from)
@@ -831,8 +840,11 @@ int batch_build(mclb_batch b)
         std::vector<Problem> probs;
         std::vector<Scratch> scs;
         std::vector<void*> fa, fb;
-        std::vector<CUtensorMap> maps;
+        std::vector<CUtensorMap> maps, maps2;
         bool fused = true;
+        // the narrow strip geometry's views, a second candidate for the autotuner
+        int nbox = 0, nout = 0;
+        bool narrow = b->tab->narrow_boxes(n, &nbox, &nout);
         std::vector<Problem> lprobs;
         std::vector<Scratch> lscs;
         std::vector<void*> la, lb;
@@ -864,6 +876,16 @@ int batch_build(mclb_batch b)
                     maps.push_back(h->tmapr[k]);
                     maps.push_back(h->tmapw[k]);
                     maps.push_back(h->tmapwr[k]);
+                    if (narrow && h->fused) {
+                        CUtensorMap m[4] = {};
+                        CUtensorMap* const v[4] = {&m[0], &m[1], &m[2], &m[3]};
+                        if (encode_views(h, k, nbox, nout, v) == MCLB_OK) {
+                            maps2.insert(maps2.end(), m, m + 4);
+                        } else {
+                            narrow = false;
+                            cudaGetLastError();
+                        }
+                    }
                 }
             }
         if (probs.empty()) continue;
@@ -871,8 +893,10 @@ int batch_build(mclb_batch b)
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             cudaGetLastError();
+        narrow = narrow && fused && maps2.size() == maps.size();
         void* g = b->tab->batch_create(n, (int)probs.size(), probs.data(), scs.data(), fa.data(),
-                                       fb.data(), fused ? maps.data() : nullptr, sms, b->stream);
+                                       fb.data(), fused ? maps.data() : nullptr,
+                                       narrow ? maps2.data() : nullptr, sms, b->stream);
         if (!g) {
             batch_drop(b);
             return fail(MCLB_ENOMEM, "batched launch tables for N=%d could not be built", n);
@@ -1080,6 +1104,42 @@ int mclb_batch_launches_per_step(mclb_batch b)
     int n = 0;
     for (const void* g : b->groups) n += b->tab->batch_launches(g);
     for (const void* g : b->lgroups) n += b->tab->line3->batch_launches(g);
+    return n;
+}
+
+int mclb_batch_tuning(mclb_batch b, int* narrow, int* waves, int cap)
+{
+    if (!b || b->magic != MAGIC || cap < 0) return -1;
+    if (b->dirty && batch_build(b)) return -1;
+    int n = 0;
+    for (const void* g : b->groups) {
+        const int w = b->tab->batch_waves(g);
+        if (n < cap) {
+            if (narrow) narrow[n] = w >= 1000 ? 1 : 0;
+            if (waves) waves[n] = w % 1000;
+        }
+        ++n;
+    }
+    return n;
+}
+
+int mclb_test_batch_partition(mclb_batch b, int narrow, int waves)
+{
+    if (!b || b->magic != MAGIC) return -1;
+    if (waves != 2 && waves != 4 && waves != 8 && waves != 16) return -1;
+    if (b->dirty && batch_build(b)) return -1;
+    int n = 0;
+    for (void* g : b->groups) n += b->tab->batch_force(g, narrow, waves) ? 1 : 0;
+    // graphs captured with the previous pick would replay it (let queued replays finish)
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+        b->graph[k] = nullptr;
+        b->graph_tried[k] = false;
+    }
     return n;
 }
 

@@ -122,11 +122,19 @@ struct MarchPick {
 template <typename T, int N>
 using MarchGeom = typename MarchPick<T, N>::G;
 
+// The narrow alternative the batch's autotuner may pick: two compute warps (56-column
+// strips) with the same ring depth, for groups of narrow instances whose last strip would
+// leave many of a wide strip's lanes idle.  Only where the pick above has four warps.
+template <typename T, int N>
+using MarchNarrow = MarchGeomT<T, N, 2, MarchPick<T, N>::NS>;
+template <typename T, int N>
+constexpr bool has_narrow() { return MarchPick<T, N>::NW == 4 && MarchNarrow<T, N>::FITS; }
+
 
 // The march of one CTA over the strip starting at column x0 and the segment of H rows
 // starting at row y0 (tmap/tmapr: load views of the input buffer; tmapw/tmapwr: store
-// views of fout; p may live in parameter or shared memory).
-template <typename T, int N>
+// views of fout; p may live in parameter or shared memory; G: the geometry).
+template <typename T, int N, typename G = MarchGeom<T, N>>
 __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtensorMap* tmapr,
                                           const CUtensorMap* tmapw, const CUtensorMap* tmapwr,
                                           T* __restrict__ fout,
@@ -134,7 +142,6 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                                           const int x0, const int y0, const int H,
                                           unsigned char* smem)
 {
-    using G = MarchGeom<T, N>;
     using C = typename Storage<T>::C;
     constexpr int NS = G::STAGES, WI = G::WI, NCW = G::NCW;
     const int Hc = min(H, p.ny - y0);

@@ -156,9 +156,12 @@ struct KernelTable {
     // 8 tensor maps per instance [buffer][load, density load, store, density store] or
     // NULL); one step of the whole group reads buffer `parity` and writes the other, by
     // the batched march when the maps are given and it fits, else by the staged schedule
+    // maps2 (or NULL): the same 8 maps per instance with the narrow geometry's box widths
+    // (narrow_boxes), a second strip shape for the autotuner
     void* (*batch_create)(int N, int count, const Problem* probs, const Scratch* scs,
-                          void* const* fa, void* const* fb, const CUtensorMap* maps, int sm_count,
-                          cudaStream_t st);
+                          void* const* fa, void* const* fb, const CUtensorMap* maps,
+                          const CUtensorMap* maps2, int sm_count, cudaStream_t st);
+    bool (*narrow_boxes)(int N, int* box_w, int* out_w);
     // part 0: the batched march (or the whole staged step); part 1: the ghost refresh of
     // the buffer part 0 wrote (nothing for the staged schedule)
     cudaError_t (*batch_step)(void* group, int parity, cudaStream_t st, int part);
@@ -166,6 +169,8 @@ struct KernelTable {
     // pick the group's work partition by timing the candidates on the current state
     // (reads buffer `parity`, rewrites the other with the same values; synchronises)
     cudaError_t (*batch_tune)(void* group, int parity, cudaStream_t st);
+    // test hook: use the candidate (narrow, waves) instead of the timed pick; false if absent
+    bool (*batch_force)(void* group, int narrow, int waves);
     int (*batch_waves)(const void* group);      // waves of the partition in use, 0 if staged
     void (*batch_destroy)(void* group);
     const LatticeTable* line3;  // D1Q3 kernels (null for the 16-bit formats)

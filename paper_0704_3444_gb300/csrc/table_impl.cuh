@@ -640,6 +640,8 @@ inline void fill_batch(KernelTable& t)
     t.batch_tune = &batch_group_tune<T>;
     t.batch_waves = &batch_group_waves<T>;
     t.batch_destroy = &batch_group_destroy<T>;
+    t.narrow_boxes = &batch_narrow_boxes<T>;
+    t.batch_force = &batch_group_force<T>;
 }
 
 // the D1Q3 lattice (FP64 and FP32 storage)

@@ -20,10 +20,18 @@ PROBE = r'''
 #include "march.cuh"
 #include <cstdio>
 using namespace mclb;
-template <typename T, int N> void pr(const char* nm) {
-    using G = MarchGeom<T, N>;
+template <typename G, typename T, int N> void pg(const char* nm) {
     printf("%s %d %d %d %d %zu %d %d %d %d %d %d %d\n", nm, N, G::NWC, G::STAGES, G::NB, G::SMEM,
            G::MIN_CTAS, G::MAXREG, G::THREADS, G::WI, G::WOUT, (int)sizeof(T), (int)G::FITS);
+}
+template <typename T, int N> void pr(const char* nm) {
+    pg<MarchGeom<T, N>, T, N>(nm);
+    // the batch's narrow alternative, where it exists
+    if (has_narrow<T, N>()) {
+        char buf[32];
+        snprintf(buf, sizeof(buf), "%s-narrow", nm);
+        pg<MarchNarrow<T, N>, T, N>(buf);
+    }
 }
 template <typename T> void all(const char* nm) {
     pr<T, 1>(nm); pr<T, 2>(nm); pr<T, 3>(nm); pr<T, 4>(nm);
@@ -52,7 +60,7 @@ def geometry():
         n, nw, ns, nb, smem, ctas, maxreg, threads, wi, wout, size, fits = map(int, v)
         g[(name, n)] = dict(nw=nw, ns=ns, nb=nb, smem=smem, ctas=ctas, maxreg=maxreg,
                             threads=threads, wi=wi, wout=wout, size=size, fits=fits)
-    assert len(g) == 32
+    assert sum(1 for (name, _) in g if "narrow" not in name) == 32
     return g
 
 
@@ -77,6 +85,21 @@ def test_tma_boxes(geometry):
             assert (c["wout"] * 2) % 16 == 0
         else:                                       # per-warp 28-column box stores
             assert (28 * c["size"]) % 16 == 0
+
+
+def test_narrow_alternative(geometry):
+    """The batch's second strip shape: two compute warps (56 columns) wherever the pick has
+    four, the same ring depth, and never fewer resident CTAs than the wide one."""
+    for (name, n), c in geometry.items():
+        if "narrow" in name:
+            continue
+        nar = geometry.get((name + "-narrow", n))
+        if c["nw"] == 4:
+            assert nar is not None, (name, n)
+            assert nar["nw"] == 2 and nar["wout"] == 56 and nar["ns"] == c["ns"]
+            assert nar["ctas"] >= c["ctas"], (name, n)
+        else:
+            assert nar is None
 
 
 def test_measured_picks(geometry):

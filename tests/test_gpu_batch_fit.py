@@ -319,3 +319,41 @@ def test_fit_equilibrium_matches_its_definition(nphase):
     want = _fit_by_definition(sim.moments(U=False, mu=False, P=False)["rho"], nphase)
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-12)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_every_autotuner_candidate_matches_single_handles(precision):
+    """The autotuner times every partition (wide and narrow strips, segment heights for 2,
+    4, 8 and 16 waves) and keeps the fastest; each one must compute the same step.  With
+    each candidate forced in turn, 23 steps of the mixed batch equal the instances' own
+    handles to the storage format's rounding (FP32 2e-5, BF16 3e-3 of the density scale);
+    the tuner's own pick is reported as a valid candidate."""
+    probs = _instances()
+    tol = {"fp32": 2e-5, "bf16": 3e-3}[precision]
+    want = []
+    for p in probs:
+        sim = mclb.Simulation.from_problem(p, precision=precision, kernel=mclb.KERNEL_FUSED)
+        sim.step(23)
+        assert sim.status() == 0
+        want.append(sim.moments(U=False, mu=False, P=False)["rho"])
+        sim.close()
+    b = mclb.Batch(probs, precision=precision)
+    b.init_all()
+    b.step(1)
+    for nar, w in b.tuning():
+        assert w in (2, 4, 8, 16)
+    b.close()
+    switched = 0
+    for narrow in (False, True):
+        for waves in (2, 4, 8, 16):
+            b = mclb.Batch(probs, precision=precision)
+            b.init_all()
+            switched += b.test_force_partition(narrow, waves)
+            b.step(23)
+            rc, per = b.status()
+            assert rc == 0 and all(v == 0 for v in per)
+            for k in range(len(probs)):
+                got = b.moments(k)["rho"]
+                assert np.max(np.abs(got - want[k])) <= tol * np.abs(want[k]).max(), (narrow, waves, k)
+            b.close()
+    assert switched >= 2 * 4          # every candidate of at least one group, both shapes
