@@ -464,6 +464,11 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
         h->alt = h->tab->d3q19;
         if (!h->alt) return bail(fail(MCLB_EINVAL, "no D3Q19 kernels for this precision"));
     }
+    const size_t jbytes = (P.lattice == MCLB_D3Q19)
+                              ? (size_t)3 * P.N * P.S * ((h->precision == MCLB_FP64) ? sizeof(double) : sizeof(float))
+                              : 0;
+    if (jbytes && cudaMalloc(&h->sc.js, jbytes) != cudaSuccess)
+        return bail(fail(MCLB_ENOMEM, "D3Q19 momentum scratch"));
     const size_t cbytes = (h->precision == MCLB_FP64) ? sizeof(double) : sizeof(float);
     for (int b = 0; b < 2; ++b) {
         if (cudaMalloc(&h->f[b], h->fbytes) != cudaSuccess)
@@ -525,6 +530,7 @@ int mclb_destroy(mclb_handle h)
     if (h->sc.status) cudaFree(h->sc.status);
     if (h->sc.line_item) cudaFree(h->sc.line_item);
     if (h->sc.mass_ref) cudaFree(h->sc.mass_ref);
+    if (h->sc.js) cudaFree(h->sc.js);
     if (h->dtmp) cudaFree(h->dtmp);
     if (h->status_host) cudaFreeHost(h->status_host);
     if (h->status_event) cudaEventDestroy(h->status_event);

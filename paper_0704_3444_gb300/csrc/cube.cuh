@@ -148,9 +148,12 @@ __device__ __forceinline__ typename Storage<T>::C pull19(const T* __restrict__ f
     return Storage<T>::load(f + (long long)s * Q19 * p.S + at19(p, i, n.row, n.x));
 }
 
+// rho^s and, when js is given, the momenta j^s = sum_i f^s_i v_i ([s][d][site]) that the
+// collision would otherwise pull the populations a second time to form.
 template <typename T, int N>
 __global__ void __launch_bounds__(SITE_THREADS)
 k19_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
+            typename Storage<T>::C* __restrict__ js,
             const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
     using C = typename Storage<T>::C;
@@ -158,17 +161,28 @@ k19_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
     if (site >= p.S) return;
     const Site3 c = site3(p, site);
     const Hood3 h = hood3(p, c);
-    C r[N];
+    C r[N], j[N][3];
 #pragma unroll
-    for (int s = 0; s < N; ++s) r[s] = C(0);
+    for (int s = 0; s < N; ++s) r[s] = j[s][0] = j[s][1] = j[s][2] = C(0);
 #pragma unroll
     for (int i = 0; i < Q19; ++i) {
         const T* src = f + src19(p, c, h, i);
 #pragma unroll
-        for (int s = 0; s < N; ++s) r[s] += Storage<T>::load(src + (long long)s * Q19 * p.S);
+        for (int s = 0; s < N; ++s) {
+            const C v = Storage<T>::load(src + (long long)s * Q19 * p.S);
+            r[s] += v;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (c19(i, d)) j[s][d] += C(c19(i, d)) * v;
+        }
     }
 #pragma unroll
     for (int s = 0; s < N; ++s) rs[s * p.S + site] = r[s];
+    if (js)
+#pragma unroll
+        for (int s = 0; s < N; ++s)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) js[(s * 3 + d) * p.S + site] = j[s][d];
 }
 
 // lap g = 6 sum_i w_i (g(r + v_i) - g(r)) of every component's density field (each
@@ -284,10 +298,13 @@ __device__ __forceinline__ void accel19(const C* __restrict__ rs, const C* __res
     }
 }
 
+// rs, js: the densities and momenta k19_density wrote for fin (the same sums, in the same
+// order, as pulling the populations here would form)
 template <typename T, int N>
 __global__ void __launch_bounds__(SITE_THREADS, 2)
 k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
             const typename Storage<T>::C* __restrict__ rs,
+            const typename Storage<T>::C* __restrict__ js,
             const typename Storage<T>::C* __restrict__ nu,
             const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
@@ -297,21 +314,12 @@ k19_collide(const T* __restrict__ fin, T* __restrict__ fout,
     const Site3 c = site3(p, site);
     const Hood3 h = hood3(p, c);
     const long long cstride = (long long)Q19 * p.S;   // one component's stored values
-    // first pass: moments (the populations are pulled again for the collision, from cache)
     C r[N], j[N][3];
 #pragma unroll
-    for (int s = 0; s < N; ++s) r[s] = j[s][0] = j[s][1] = j[s][2] = C(0);
+    for (int s = 0; s < N; ++s) {
+        r[s] = rs[s * p.S + site];
 #pragma unroll
-    for (int i = 0; i < Q19; ++i) {
-        const T* src = fin + src19(p, c, h, i);
-#pragma unroll
-        for (int s = 0; s < N; ++s) {
-            const C v = Storage<T>::load(src + s * cstride);
-            r[s] += v;
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                if (c19(i, d)) j[s][d] += C(c19(i, d)) * v;
-        }
+        for (int d = 0; d < 3; ++d) j[s][d] = js[(s * 3 + d) * p.S + site];
     }
     C rho = C(0), jt[3] = {C(0), C(0), C(0)};
 #pragma unroll

@@ -60,6 +60,7 @@ struct Scratch {
     unsigned int* status;   // device status bits (see STATUS_*)
     void* line_item;        // D1Q3 handles: the device description the resident kernel reads
     double* mass_ref;       // NMAX FP64 reference masses of the mass compensation
+    void* js;               // D3Q19 handles: momenta j^s, 3 N S compute-type values ([s][d][site])
 };
 
 enum : unsigned int {

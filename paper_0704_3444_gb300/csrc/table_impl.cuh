@@ -489,7 +489,7 @@ struct Launch19 {
     template <int N>
     static cudaError_t fields_n(const StepParams<C>& p, const Scratch& sc, const T* f, cudaStream_t st)
     {
-        k19_density<T, N><<<site_blocks(p.S), SITE_THREADS, 0, st>>>(f, (C*)sc.rho_s, p);
+        k19_density<T, N><<<site_blocks(p.S), SITE_THREADS, 0, st>>>(f, (C*)sc.rho_s, (C*)sc.js, p);
         k19_potential<C, N><<<site_blocks(p.S), SITE_THREADS, 0, st>>>((const C*)sc.rho_s,
                                                                         (C*)sc.nu, p);
         return cudaGetLastError();
@@ -504,7 +504,8 @@ struct Launch19 {
                 cudaError_t e = fields_n<NN>(p, sc, (const T*)f[*cur], st);
                 if (e != cudaSuccess) return e;
                 k19_collide<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(
-                    (const T*)f[*cur], (T*)f[*cur ^ 1], (const C*)sc.rho_s, (const C*)sc.nu, p);
+                    (const T*)f[*cur], (T*)f[*cur ^ 1], (const C*)sc.rho_s, (const C*)sc.js,
+                    (const C*)sc.nu, p);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) return e;
                 *cur ^= 1;
@@ -547,7 +548,7 @@ struct Launch19 {
         const auto p = make_params<C>(P, sc.status);
         MCLB_DISPATCH_N(P.N, {
             k19_density<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>((const T*)f,
-                                                                          (C*)sc.rho_s, p);
+                                                                          (C*)sc.rho_s, nullptr, p);
             k19_compositions<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(
                 (const C*)sc.rho_s, phi, bulk, tol, p);
             return cudaGetLastError();
