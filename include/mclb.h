@@ -144,8 +144,10 @@ typedef enum {
  *              the opposite velocity (halfway bounce-back), which keeps every component's
  *              mass; the stencils of rho^s and nu^s see the rows beyond a wall as mirror
  *              images of the rows next to it (zero normal gradient: neutral wetting).
- *              x stays periodic.  D2Q9 on the staged schedule only (kernel AUTO or
- *              STAGED); single handles only (batches and mclb_step_noalloc reject it)
+ *              x stays periodic.  D2Q9 only; both schedules: the single pass computes
+ *              every row at least three rows from a wall (their update reaches no row
+ *              beyond one) and three staged launches then redo the rows next to the
+ *              walls.  Single handles only (batches and mclb_step_noalloc reject it)
  *   mass_every 0 (off, the default) or the period, in timesteps, of the per-component
  *              mass compensation.  Eq. ff1 and the collision keep every component's total
  *              mass exactly; stored in FP32 or 16 bits, the rounding of each site's

@@ -134,8 +134,6 @@ int validate(const mclb_params* p)
     if (p->walls != 0 && p->walls != 1) return fail(MCLB_EINVAL, "walls=%d unknown", p->walls);
     if (p->walls && p->lattice != MCLB_D2Q9)
         return fail(MCLB_EINVAL, "walls are a D2Q9 option (lattice=%d)", p->lattice);
-    if (p->walls && p->kernel == MCLB_KERNEL_FUSED)
-        return fail(MCLB_EINVAL, "walls run on the staged schedule (kernel AUTO or STAGED)");
     if (p->lattice == MCLB_D3Q19 && p->precision != MCLB_FP64 && p->precision != MCLB_FP32)
         return fail(MCLB_EINVAL, "lattice D3Q19 stores FP64 or FP32 (precision=%d)", p->precision);
     if (p->lattice == MCLB_D1Q3) {
@@ -327,8 +325,8 @@ cudaError_t launch_one_step(mclb_handle h, int from)
     const Problem& P = h->P;
     if (h->fused)
         return h->tab->step_fused(P, h->sc, h->plan, &h->tmap[from], &h->tmapr[from],
-                                  &h->tmapw[from ^ 1], &h->tmapwr[from ^ 1], h->f[from ^ 1],
-                                  h->stream);
+                                  &h->tmapw[from ^ 1], &h->tmapwr[from ^ 1], h->f[from],
+                                  h->f[from ^ 1], h->stream);
     return h->tab->step_staged(P, h->sc, h->f[from], h->f[from ^ 1], h->stream);
 }
 
@@ -495,7 +493,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaStreamCreateWithFlags(&h->status_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
     h->fused = false;
-    if ((P.force_form == MCLB_FORCE_GIBBS_DUHEM || P.walls) && !h->alt) h->kernel = MCLB_KERNEL_STAGED;
+    if (P.force_form == MCLB_FORCE_GIBBS_DUHEM && !h->alt) h->kernel = MCLB_KERNEL_STAGED;
     if (h->alt) {
         if (h->alt->item_bytes > 0 && cudaMalloc(&h->sc.line_item, h->alt->item_bytes) != cudaSuccess)
             return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));
@@ -665,7 +663,8 @@ int mclb_launches_per_step(mclb_handle h)
     if (check_handle(h)) return -1;
     if (h->P.lattice == MCLB_D1Q3) return 1;
     if (h->P.lattice == MCLB_D3Q19) return 3;
-    return h->fused ? 2 : 3;
+    if (h->fused) return h->P.walls ? 5 : 2;   // k_march, k_ghosts (+ three wall-row launches)
+    return 3;
 }
 
 int mclb_moments_device(mclb_handle h, double* rho, double* U, double* mu, double* P)

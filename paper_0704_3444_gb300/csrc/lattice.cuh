@@ -114,7 +114,9 @@ struct StepParams {
     C log_floor;          // floor of rho^s / rho inside a logarithm
     int bary;             // 1: barycentric u in the forcing's second moment, 0: u^s (Eq. ff3)
     int gd;               // 1: Gibbs-Duhem total force (kappa = 0), 0: Eq. definef as printed
-    int walls;            // 1: solid walls below row 0 and above row ny - 1 (staged D2Q9)
+    int walls;            // 1: solid walls below row 0 and above row ny - 1 (D2Q9)
+    long long band;       // staged launches: 0 = every site; > 0 = the first and the last
+                          // `band` sites only (the rows next to the walls)
     C chi[NMAX * NMAX];
     C th_m[NMAX];         // theta / m^s
     C logc[NMAX];         // theta / m^s - 1/3: coefficient of ln rho^s in nu^s
@@ -149,6 +151,7 @@ inline StepParams<C> make_params(const Problem& P, unsigned int* status)
     p.bary = P.forcing_velocity;
     p.gd = P.force_form;
     p.walls = P.walls;
+    p.band = 0;
     p.log_mask = 0;
     for (int a = 0; a < P.N; ++a) {
         for (int b = 0; b < P.N; ++b) p.chi[a * P.N + b] = C(P.chi[a * P.N + b]);

@@ -147,6 +147,11 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     const int Hc = min(H, p.ny - y0);
     const int nk = Hc + 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // rows whose density the status word checks: with walls, the three rows next to each
+    // wall are written here with periodic neighbours and then rewritten by the wall-aware
+    // staged launches, so only those launches check them
+    const int ychk0 = p.walls ? max(y0, 3) : y0;
+    const int ychk1 = p.walls ? min(y0 + Hc, p.ny - 3) : y0 + Hc;
 
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + MARCH_MAX_NS;
@@ -305,7 +310,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             for (int t = 0; t < N; ++t) rho += R0[t];
             const C inv = C(1) / rho;
             const C ux0 = jxp * inv, uy0 = jyp * inv;
-            if (out_lane && m >= y0 && m < y0 + Hc && (!(rho > C(0)) || !isfinite(rho)))
+            if (out_lane && m >= ychk0 && m < ychk1 && (!(rho > C(0)) || !isfinite(rho)))
                 atomicOr(p.status, STATUS_NONFINITE);
             const C lnr = dev_log(rho);
             C acc[N];

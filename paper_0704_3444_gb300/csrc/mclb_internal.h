@@ -127,11 +127,11 @@ struct KernelTable {
                         void* f, cudaStream_t st);
     // one fused timestep fin -> fout (tmap_in describes fin's lines, tmapr_in its density
     // lines in the 16-bit formats, tmapw_out / tmapwr_out the columns [0, nx) of fout's
-    // lines / density lines)
+    // lines / density lines; with walls the rows next to them are redone from fin)
     cudaError_t (*step_fused)(const Problem&, const Scratch&, const FusedPlan&,
                               const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in,
                               const CUtensorMap* tmapw_out, const CUtensorMap* tmapwr_out,
-                              void* fout, cudaStream_t st);
+                              const void* fin, void* fout, cudaStream_t st);
     // one staged timestep fin -> fout (three launches through scratch)
     cudaError_t (*step_staged)(const Problem&, const Scratch&, const void* fin, void* fout,
                                cudaStream_t st);

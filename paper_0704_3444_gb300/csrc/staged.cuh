@@ -56,6 +56,15 @@ __device__ __forceinline__ int stencil_row(const StepParams<C>& p, int y, int dy
     return wrap_add(y, dy, p.ny);
 }
 
+// Site of thread t in a staged launch: every site, or with p.band > 0 the first and the
+// last p.band sites (rows next to the walls); -1 for a thread beyond them.
+template <typename C>
+__device__ __forceinline__ long long site_of(const StepParams<C>& p, long long t)
+{
+    if (p.band == 0) return t < p.S ? t : -1;
+    return t < p.band ? t : (t < 2 * p.band ? p.S - 2 * p.band + t : -1);
+}
+
 // True where a timestep kernel must take the wall-aware (E = true) path.
 template <typename C>
 __device__ __forceinline__ bool wall_row(const StepParams<C>& p, long long site)
@@ -96,8 +105,8 @@ __global__ void __launch_bounds__(SITE_THREADS)
 k_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
           const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
-    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= p.S) return;
+    const long long site = site_of(p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (site < 0) return;
     if (wall_row(p, site))
         density_site<T, N, true>(f, rs, p, site);
     else
@@ -141,8 +150,8 @@ template <typename C, int N>
 __global__ void __launch_bounds__(SITE_THREADS)
 k_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant__ StepParams<C> p)
 {
-    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= p.S) return;
+    const long long site = site_of(p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (site < 0) return;
     if (wall_row(p, site))
         potential_site<C, N, true>(rs, nu, p, site);
     else
@@ -260,8 +269,8 @@ k_collide(const T* __restrict__ fin, T* __restrict__ fout,
           const typename Storage<T>::C* __restrict__ nu,
           const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
-    const long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (site >= p.S) return;
+    const long long site = site_of(p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (site < 0) return;
     if (wall_row(p, site))
         collide_site<T, N, true>(fin, fout, rs, nu, p, site);
     else

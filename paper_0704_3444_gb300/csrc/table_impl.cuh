@@ -120,10 +120,31 @@ struct Launch {
         }
     }
 
+    // Walls on the single pass.  A row's new state reaches three rows of the old one (the
+    // pull of rho^s two rows away, which nu^s one row away needs), so rows 3 .. ny - 4 of
+    // k_march, which treats y as periodic, are already those of the walled lattice.  The
+    // wall-aware staged kernels then rewrite the three rows next to each wall, from the
+    // bands of fields they need (rho^s on five rows, nu^s on four); ghosts included.
+    template <int N>
+    static cudaError_t wall_rows(StepParams<C> p, const Scratch& sc, const T* fin, T* fout,
+                                 cudaStream_t st)
+    {
+        const auto band = [&](int rows) { return 2 * rows >= p.ny ? 0LL : (long long)rows * p.nx; };
+        const auto blocks = [&]() { return site_blocks(p.band ? 2 * p.band : p.S); };
+        p.band = band(5);
+        k_density<T, N><<<blocks(), SITE_THREADS, 0, st>>>(fin, (C*)sc.rho_s, p);
+        p.band = band(4);
+        k_potential<C, N><<<blocks(), SITE_THREADS, 0, st>>>((const C*)sc.rho_s, (C*)sc.nu, p);
+        p.band = band(3);
+        k_collide<T, N><<<blocks(), SITE_THREADS, 0, st>>>(fin, fout, (const C*)sc.rho_s,
+                                                            (const C*)sc.nu, p);
+        return cudaGetLastError();
+    }
+
     static cudaError_t step_fused(const Problem& P, const Scratch& sc, const FusedPlan& pl,
                                   const CUtensorMap* tmap_in, const CUtensorMap* tmapr_in,
                                   const CUtensorMap* tmapw_out, const CUtensorMap* tmapwr_out,
-                                  void* fout, cudaStream_t st)
+                                  const void* fin, void* fout, cudaStream_t st)
     {
         const auto p = make_params<C>(P, sc.status);
         const dim3 grid(pl.nstrips, pl.nsegs);
@@ -134,6 +155,7 @@ struct Launch {
             k_march<T, NN><<<grid, pl.threads, pl.smem, st>>>(*tmap_in, tr, tw, twr, (T*)fout, p, pl.H);
             const long long ghosts = (long long)NN * P.ny * (Q + (Storage<T>::shifted ? 1 : 0)) * 2 * P.hx;
             k_ghosts<T><<<(unsigned)((ghosts + 255) / 256), 256, 0, st>>>((T*)fout, p, NN);
+            if (P.walls) return wall_rows<NN>(p, sc, (const T*)fin, (T*)fout, st);
             return cudaGetLastError();
         });
     }

@@ -66,7 +66,6 @@ def _params(**kw):
     (dict(lattice=3), "lattice"),
     (dict(walls=2), "walls"),
     (dict(walls=1, lattice="d1q3", ny=1), "D2Q9 option"),
-    (dict(walls=1, kernel=1), "staged schedule"),
     (dict(lattice="d3q19", nz=2, precision="bf16"), "FP64 or FP32"),
     (dict(nz=2), "D3Q19"),
     (dict(nz=-1), "nz"),
