@@ -543,19 +543,25 @@ def main():
                 "hbm_frac_of_measured": v.bytes_per_step / (t / 100) / 1e9 / peak,
                 "speedup_vs_fp32": val / slab_fp32}
             v.close()
-        # the D3Q19 lattice (staged schedule): the paper's ternary chi set on 256^3 in FP32
+        # the D3Q19 lattice: the paper's ternary chi set on 256^3 in FP32, the density pass
+        # + z-plane march and the staged schedule
         cube = workloads()["ternary3d_256"]()
-        v = mclb.Simulation.from_problem(cube, precision="fp32", stream=sptr)
-        t = time_steps(torch, v, 50, args.warmup, stream)
-        val = cube.sites * cube.ncomp * 50 / t / 1e6
-        variants["d3q19_ternary3d_256_fp32"] = {
-            "value": val, "steps": 50, "status_ok": v.status() == 0,
-            "launches_per_step": v.launches_per_step,
-            "hbm_gbs_algorithmic": v.bytes_per_step / (t / 50) / 1e9,
-            "hbm_frac_of_measured": v.bytes_per_step / (t / 50) / 1e9 / peak,
-            "note": "152 B per site and component (19 loads + 19 stores of f in FP32) per step; "
-                    "three launches (density, potential, collision)"}
-        v.close()
+        for kern_c, key, what in (
+                (mclb.KERNEL_FUSED, "d3q19_ternary3d_256_fp32",
+                 "two launches (density pass, z-plane march with the potentials on chip)"),
+                (mclb.KERNEL_STAGED, "d3q19_ternary3d_256_fp32_staged",
+                 "three launches (density, potential, collision)")):
+            v = mclb.Simulation.from_problem(cube, precision="fp32", kernel=kern_c, stream=sptr)
+            t = time_steps(torch, v, 50, args.warmup, stream)
+            val = cube.sites * cube.ncomp * 50 / t / 1e6
+            variants[key] = {
+                "value": val, "steps": 50, "status_ok": v.status() == 0,
+                "launches_per_step": v.launches_per_step,
+                "hbm_gbs_algorithmic": v.bytes_per_step / (t / 50) / 1e9,
+                "hbm_frac_of_measured": v.bytes_per_step / (t / 50) / 1e9 / peak,
+                "note": "152 B per site and component (19 loads + 19 stores of f in FP32) per "
+                        "step; " + what}
+            v.close()
         for prec in ("fp64", "fp32"):
             variants[f"d1q3_lines_512x1024_{prec}"] = run_lines(torch, mclb, sptr, stream,
                                                                 precision=prec)

@@ -112,8 +112,12 @@ typedef enum {
                         (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1),
                         (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).  Not a lattice the paper
                         uses: its equations hold for any lattice whose weights give the
-                        Sec. 3 moments, which these do.  The staged schedule (three
-                        launches per step), FP64 or FP32 storage, single handles only.
+                        Sec. 3 moments, which these do.  FP64 or FP32 storage, single
+                        handles only.  Kernel AUTO or FUSED: a density pass and a march
+                        over z planes that forms the potentials on chip and collides (two
+                        launches per step; N <= 4, Eq. definef as printed; FUSED fails
+                        with MCLB_EINVAL otherwise, AUTO falls back); STAGED: three
+                        launches.  The two schedules give the same values bit for bit.
                         Fields are [.][z][y][x]; U has 3 components, P 6 (xx, xy, xz, yy,
                         yz, zz), the momentum and force sums 3                             */
 } mclb_lattice;

@@ -499,6 +499,13 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
             return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));
         if (h->alt->prepare(P, h->sc, h->f) != cudaSuccess)
             return bail(fail(MCLB_ECUDA, "D1Q3 line description upload failed"));
+        if (h->alt->plan && h->kernel != MCLB_KERNEL_STAGED) {
+            const int r = h->alt->plan(h->P, sms);
+            if (r < 0) return bail(fail(MCLB_ECUDA, "single-pass kernel set-up failed"));
+            h->fused = r == 1;
+            if (!h->fused && h->kernel == MCLB_KERNEL_FUSED)
+                return bail(fail(MCLB_EINVAL, "fused kernel unavailable for this problem"));
+        }
     } else if (h->kernel != MCLB_KERNEL_STAGED) {
         h->plan = h->tab->plan_fused(P, sms);
         if (h->plan.ok && make_tmap(h, 0) == MCLB_OK && make_tmap(h, 1) == MCLB_OK) h->fused = true;
@@ -662,7 +669,7 @@ int mclb_launches_per_step(mclb_handle h)
 {
     if (check_handle(h)) return -1;
     if (h->P.lattice == MCLB_D1Q3) return 1;
-    if (h->P.lattice == MCLB_D3Q19) return 3;
+    if (h->P.lattice == MCLB_D3Q19) return h->fused ? 2 : 3;   // density + march, or staged
     if (h->fused) return h->P.walls ? 5 : 2;   // k_march, k_ghosts (+ three wall-row launches)
     return 3;
 }

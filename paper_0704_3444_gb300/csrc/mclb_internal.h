@@ -42,11 +42,13 @@ struct Problem {
     int lattice;            // MCLB_D2Q9 (0), MCLB_D1Q3 (1: ny = 1, layout [s][i][x], no ghosts) or
                             // MCLB_D3Q19 (2: layout [s][z][y][i][x], no ghosts)
     int force_form;         // MCLB_FORCE_COMPONENT (0) or MCLB_FORCE_GIBBS_DUHEM (1)
-    int walls;              // 1: solid walls in y (D2Q9, staged schedule), 0: periodic
+    int walls;              // 1: solid walls in y (D2Q9), 0: periodic
     int mass_every;         // period of the per-component mass compensation, 0 = off
     int withhold;           // test hook: the single-pass kernel issues no copies
     long long rbytes;       // 16-bit formats: byte offset of the FP32 density lines
                             // ([s][y][pitch], same ghosts) after the deviations; else 0
+    int seg3;               // D3Q19: > 0 = density pass + march, z segments of seg3 planes
+    int grid3[3];           // over grid3 CTAs (x tiles, y tiles, segments); 0 = staged
 };
 
 // Device scratch owned by a handle: component densities and the potentials
@@ -86,6 +88,9 @@ struct FusedPlan {
 // The batch entries are D1Q3 only (null for D3Q19).
 struct LatticeTable {
     int (*max_resident)(int N);   // longest line the resident (shared-memory) kernel holds
+    // set up the single-pass step where it applies (P.seg3, P.grid3): 1 = set up, 0 = the
+    // staged step, -1 = CUDA error; null for lattices with one step kernel
+    int (*plan)(Problem& P, int sm_count);
     size_t item_bytes;            // size of the device description at Scratch::line_item
     // write the description of buffers f[0], f[1] to sc.line_item (synchronous)
     cudaError_t (*prepare)(const Problem&, const Scratch&, void* const* f);

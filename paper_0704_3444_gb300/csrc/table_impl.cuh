@@ -5,6 +5,7 @@
 
 #include "batch.cuh"
 #include "cube.cuh"
+#include "cube_march.cuh"
 #include "ghosts.cuh"
 #include "line3.cuh"
 #include "march.cuh"
@@ -497,6 +498,61 @@ struct Launch19 {
     static int max_resident(int) { return 0; }
     static cudaError_t prepare(const Problem&, const Scratch&, void* const*) { return cudaSuccess; }
 
+    // The march (cube_march.cuh) after a density pass: tiles of M3_OUT_X x M3_OUT_Y, z
+    // segments of H planes.  The CTAs are latency bound, so more of them than one wave
+    // of resident slots helps; a segment of H planes costs about H + 4 plane iterations (four
+    // warm-up planes) and the launch about waves x (H + 4) of them, so the segment count
+    // that minimises that product is taken.  Not for N > M3_NMAX, the Gibbs-Duhem reading
+    // (it needs grad rho on the density planes the next iteration overwrites) or
+    // 19 S >= 2^31 (32-bit offsets).
+    template <int N>
+    static int plan_n(Problem& P, int sm_count)
+    {
+        if constexpr (N > M3_NMAX) {
+            return 0;
+        } else {
+            if (P.force_form != 0 || 19.0 * (double)P.S >= 2147483647.0) return 0;
+            const int smem = (int)m3_smem_bytes<C, N>();
+            if (cudaFuncSetAttribute(k19_march<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem) != cudaSuccess)
+                return -1;
+            int ctas = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k19_march<T, N>, M3_THREADS,
+                                                              smem) != cudaSuccess)
+                return -1;
+            if (ctas < 1) return 0;
+            const long long tx = (P.nx + M3_OUT_X - 1) / M3_OUT_X, ty = (P.ny + M3_OUT_Y - 1) / M3_OUT_Y;
+            const long long slots = (long long)ctas * std::max(1, sm_count);
+            int best = 1;
+            long long best_cost = -1;
+            for (int nseg = 1; nseg <= std::max(1, P.nz / 4); ++nseg) {
+                const long long H = (P.nz + nseg - 1) / nseg, segs = (P.nz + H - 1) / H;
+                const long long waves = (tx * ty * segs + slots - 1) / slots;
+                const long long cost = waves * (H + 4);
+                if (best_cost < 0 || cost < best_cost) {
+                    best_cost = cost;
+                    best = nseg;
+                }
+            }
+            const int H = (P.nz + best - 1) / best;
+            P.grid3[0] = (int)tx;
+            P.grid3[1] = (int)ty;
+            P.grid3[2] = (P.nz + H - 1) / H;
+            P.seg3 = H;
+            return 1;
+        }
+    }
+    static int plan(Problem& P, int sm_count)
+    {
+        switch (P.N) {
+            case 1: return plan_n<1>(P, sm_count);
+            case 2: return plan_n<2>(P, sm_count);
+            case 3: return plan_n<3>(P, sm_count);
+            case 4: return plan_n<4>(P, sm_count);
+            default: return 0;
+        }
+    }
+
     static cudaError_t init(const Problem& P, const Scratch& sc, const double* rho, const double* u,
                             void* f, cudaStream_t st)
     {
@@ -522,6 +578,22 @@ struct Launch19 {
     {
         const auto p = make_params<C>(P, sc.status);
         MCLB_DISPATCH_N(P.N, {
+            if constexpr (NN <= M3_NMAX) {
+                if (P.seg3 > 0) {
+                    const dim3 grid(P.grid3[0], P.grid3[1], P.grid3[2]);
+                    for (; nsteps > 0; --nsteps) {
+                        const T* fi = (const T*)f[*cur];
+                        k19_density<T, NN><<<site_blocks(P.S), SITE_THREADS, 0, st>>>(
+                            fi, (C*)sc.rho_s, nullptr, p);
+                        k19_march<T, NN><<<grid, M3_THREADS, m3_smem_bytes<C, NN>(), st>>>(
+                            fi, (T*)f[*cur ^ 1], (const C*)sc.rho_s, p, P.seg3);
+                        const cudaError_t e = cudaGetLastError();
+                        if (e != cudaSuccess) return e;
+                        *cur ^= 1;
+                    }
+                    return cudaSuccess;
+                }
+            }
             for (; nsteps > 0; --nsteps) {
                 cudaError_t e = fields_n<NN>(p, sc, (const T*)f[*cur], st);
                 if (e != cudaSuccess) return e;
@@ -602,6 +674,7 @@ struct Launch19 {
         static const LatticeTable t = [] {
             LatticeTable x{};
             x.max_resident = &max_resident;
+            x.plan = &plan;
             x.item_bytes = 0;
             x.prepare = &prepare;
             x.init = &init;

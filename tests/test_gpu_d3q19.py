@@ -1,4 +1,5 @@
-"""GPU: the D3Q19 lattice (cube.cuh, staged schedule) against the FP64 oracle's D3Q19 path.
+"""GPU: the D3Q19 lattice against the FP64 oracle's D3Q19 path, on both schedules: the
+density pass + z-plane march (cube_march.cuh, N <= 4) and the staged one (cube.cuh).
 
 Tolerances as on D2Q9: FP64 1e-12 of the field's max-norm (P absolute), FP32 1e-5 per
 field after 100 steps.  Plus the projection property on the GPU (a z-invariant D3Q19 run
@@ -38,12 +39,18 @@ def _state(n, nx, ny, nz, seed, amp=0.3, umax=0.03):
     return phi, u
 
 
-CASES = [(5, 4, 3, 2), (17, 6, 5, 3), (33, 9, 4, 4), (7, 3, 11, 5)]
+# (nx, ny, nz, N): lattices smaller than the march's 28 x 8 tiles, several tiles in x and y
+# with ragged last ones and several z segments (60 x 37 x 20), one component, and N = 5,
+# which only the staged schedule takes
+CASES = [(5, 4, 3, 2), (17, 6, 5, 3), (33, 9, 4, 4), (60, 37, 20, 3), (9, 5, 6, 1), (7, 3, 11, 5)]
+KERNELS = [mclb.KERNEL_FUSED, mclb.KERNEL_STAGED]
+MARCH_NMAX = 4
 
 
 @pytest.mark.parametrize("fv", [0, 1])
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}N{c[3]}")
-def test_fp64_parity(case, fv):
+def test_fp64_parity(case, kernel, fv):
     """10 FP64 steps with every term on (m != 1, theta != 1/3, kappa > 0, a 3-D body
     force): the state, rho, U, mu within 1e-12 of the oracle (relative to the field's
     max), P to 1e-12 absolute, and the conservation sums."""
@@ -52,8 +59,12 @@ def test_fp64_parity(case, fv):
     chi = inputs.uniform_chi(n, 1.6)
     kw = dict(m=[1.0 + (k % 3) for k in range(n)], theta=0.4, kappa=0.02,
               force=(1e-5, -2e-5, 3e-5), forcing_velocity=fv, lattice="d3q19", nz=nz)
-    sim = mclb.Simulation(n, nx, ny, 0.9, chi, precision="fp64", **kw)
-    assert sim.launches_per_step == 3
+    if kernel == mclb.KERNEL_FUSED and n > MARCH_NMAX:
+        with pytest.raises(mclb.MclbError, match="fused kernel unavailable"):
+            mclb.Simulation(n, nx, ny, 0.9, chi, precision="fp64", kernel=kernel, **kw)
+        return
+    sim = mclb.Simulation(n, nx, ny, 0.9, chi, precision="fp64", kernel=kernel, **kw)
+    assert sim.launches_per_step == (2 if kernel == mclb.KERNEL_FUSED else 3)
     orc = Oracle(n, nx, ny, 0.9, chi, **kw)
     sim.init_fields(rho, u)
     orc.init(rho, u)
@@ -70,6 +81,28 @@ def test_fp64_parity(case, fv):
     np.testing.assert_allclose(gc["mom"], oc["mom"], rtol=1e-10, atol=1e-14)
     np.testing.assert_allclose(gc["force"], oc["force"], rtol=1e-9, atol=1e-15)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(60, 37, 20), (100, 17, 40)], ids=lambda s: "x".join(map(str, s)))
+def test_march_equals_staged_bitwise(shape, precision):
+    """The march forms the same sums in the same order as the three staged kernels, so
+    after 25 steps of the 3-D ternary (every term on, a body force) the two schedules'
+    states are identical bit for bit, on lattices of several tiles and z segments."""
+    nx, ny, nz = shape
+    chi = np.array([[0.0, 3.0, 0.5], [3.0, 0.0, 0.2], [0.5, 0.2, 0.0]])  # the paper's ternary set
+    rho, u = _state(3, nx, ny, nz, seed=nx + nz)
+    kw = dict(m=[1.0, 2.0, 1.0], theta=0.4, kappa=0.02, force=(1e-5, -2e-5, 3e-5),
+              lattice="d3q19", nz=nz, precision=precision)
+    sims = [mclb.Simulation(3, nx, ny, 0.9, chi, kernel=k, **kw) for k in KERNELS]
+    for s in sims:
+        s.init_fields(rho, u)
+        s.step(25)
+        assert s.status() == 0
+    assert sims[0].launches_per_step == 2 and sims[1].launches_per_step == 3
+    assert np.array_equal(sims[0].get_state(), sims[1].get_state())
+    for s in sims:
+        s.close()
 
 
 def test_fp64_gibbs_duhem():
@@ -93,11 +126,12 @@ def test_fp64_gibbs_duhem():
     sim.close()
 
 
-def test_fp32_four_fields():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_fp32_four_fields(kernel):
     """The 3-D ternary recipe (paper's chi set at (0.4, 0.4, 0.2), inside the A-B
     spinodal) on 24^3: rho, U, mu and P within 1e-5 of the oracle after 100 FP32 steps."""
     p = inputs.ternary3d(24, steps=100)
-    sim = mclb.Simulation.from_problem(p, precision="fp32")
+    sim = mclb.Simulation.from_problem(p, precision="fp32", kernel=kernel)
     orc = Oracle.from_problem(p)
     sim.step(100)
     assert orc.run(100) == 0
@@ -108,7 +142,8 @@ def test_fp32_four_fields():
     sim.close()
 
 
-def test_z_invariant_run_equals_d2q9_handle():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_z_invariant_run_equals_d2q9_handle(kernel):
     """A D3Q19 handle whose fields do not depend on z (4 layers), after 30 FP64 steps and
     a sum over v_z, equals the D2Q9 staged handle of the plane to 1e-12."""
     n, nx, ny, nz = 3, 19, 13, 4
@@ -121,8 +156,8 @@ def test_z_invariant_run_equals_d2q9_handle():
     rho3 = np.repeat(rho2[:, None], nz, axis=1)
     u3 = np.zeros((3, nz, ny, nx))
     u3[0], u3[1] = u2[0][None], u2[1][None]
-    s3 = mclb.Simulation(n, nx, ny, 0.85, chi, force=(2e-5, -1e-5, 0.0), lattice="d3q19", nz=nz,
-                         **common)
+    s3 = mclb.Simulation(n, nx, ny, 0.85, chi, force=(2e-5, -1e-5, 0.0), kernel=kernel,
+                         lattice="d3q19", nz=nz, **common)
     s3.init_fields(rho3, u3)
     s2.step(30)
     s3.step(30)
@@ -138,15 +173,16 @@ def test_z_invariant_run_equals_d2q9_handle():
     s3.close()
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_resume_equals_uninterrupted(precision):
+def test_resume_equals_uninterrupted(precision, kernel):
     """get_state after 13 steps, set_state into a new handle, 17 more steps there equal
     17 more steps of the original, bitwise."""
     p = inputs.ternary3d(20)
-    a = mclb.Simulation.from_problem(p, precision=precision)
+    a = mclb.Simulation.from_problem(p, precision=precision, kernel=kernel)
     a.step(13)
     b = mclb.Simulation(p.ncomp, p.nx, p.ny, p.tau, p.chi, p.m, p.theta, p.kappa, p.force,
-                        precision, lattice="d3q19", nz=p.nz)
+                        precision, kernel, lattice="d3q19", nz=p.nz)
     b.set_state(a.get_state())
     a.step(17)
     b.step(17)
