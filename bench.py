@@ -577,23 +577,42 @@ def main():
         torch.cuda.synchronize()
         cpu = run_cpu_baseline(prob)
 
+    d3 = getattr(prob, "lattice", "d2q9") == "d3q19"
+    walls = getattr(prob, "walls", 0)
+    if args.kernel == "staged":
+        schedule, timed = "staged, 3 launches", "the three staged kernels"
+    elif d3:
+        schedule, timed = ("density pass + z-plane march, 2 launches",
+                           "k19_density + k19_march (the march about 3/4 of it)")
+    elif walls:
+        schedule, timed = ("fused single pass + the rows next to the walls by 3 staged launches",
+                           "k_march, the ghost-column refresh and the wall-row launches (about "
+                           "5 % of it)")
+    else:
+        schedule, timed = ("fused single pass",
+                           "k_march plus the ghost-column refresh, about 3 % of it")
+    per = bytes_step / (S * N)
+    config = {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "ncomp": N,
+              "precision": args.precision, "schedule": schedule,
+              "l2": "distributions (2 x %.0f MB) exceed the 129 MB L2; no flush" %
+                    (bytes_step / 2 / 1e6)}
+    if d3:
+        config["nz"] = prob.nz
+    if walls:
+        config["walls"] = walls
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16-storage/f32", "fp16": "f16-storage/f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": args.workload, "nx": prob.nx, "ny": prob.ny, "ncomp": N,
-                   "precision": args.precision,
-                   "schedule": "fused single pass" if args.kernel == "fused" else "staged, 3 launches",
-                   "l2": "distributions (2 x %.0f MB) exceed the 129 MB L2; no flush" %
-                         (bytes_step / 2 / 1e6)},
+        "config": config,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "note": f"k_march: 72*N B per site (9 loads + 9 stores of f in FP32) per "
-                             f"launch / CUDA-event time per step (k_march plus the ghost-column "
-                             f"refresh, about 3 % of it); peak = {peak_src} copy bandwidth; traffic "
-                             f"= ncu dram bytes per k_march launch from profiles/"},
+                     "note": f"{per:.0f} B per site and component (every stored value read once "
+                             f"and written once) x sites x N / CUDA-event time per step ({timed}); "
+                             f"peak = {peak_src} copy bandwidth; traffic = ncu dram bytes per "
+                             f"k_march launch from profiles/ (the FP32 N = 5 2048^2 workload only)"},
         "mlups": world * S * args.steps / elapsed / 1e6,
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
