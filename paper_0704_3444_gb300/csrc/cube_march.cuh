@@ -30,9 +30,10 @@
 namespace mclb {
 
 constexpr int M3_WARPS = 4;
+constexpr int M3_RC = 2;                     // rows each warp collides (one at a time)
 constexpr int M3_THREADS = 32 * M3_WARPS;
 constexpr int M3_OUT_X = 28;                 // written columns of the 32 a warp holds
-constexpr int M3_OUT_Y = 2 * M3_WARPS;       // written rows: two per warp in C
+constexpr int M3_OUT_Y = M3_RC * M3_WARPS;   // written rows
 constexpr int M3_ROWS = M3_OUT_Y + 4;        // rows with the two-row halo each side
 constexpr int M3_NMAX = 4;                   // components the march takes
 
@@ -114,7 +115,7 @@ __device__ __forceinline__ void m3_pull(const T* __restrict__ f, unsigned cst, c
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(M3_THREADS, 4)
+__global__ void __launch_bounds__(M3_THREADS, 512 / M3_THREADS)
 k19_march(const T* __restrict__ fin, T* __restrict__ fout,
           const typename Storage<T>::C* __restrict__ rs,
           const __grid_constant__ StepParams<typename Storage<T>::C> p, int H)
@@ -137,7 +138,7 @@ k19_march(const T* __restrict__ fin, T* __restrict__ fout,
     xw[2] = inc_wrap(xw[1], nx);
 
     // rows of phase A and B: r = warp + M3_WARPS j while r < M3_ROWS; of phase C: r = warp +
-    // 2 + M3_WARPS j, j = 0, 1 (one row at a time: a site's 19 N pulled values fill the
+    // 2 + M3_WARPS j, j < M3_RC (one row at a time: a site's 19 N pulled values fill the
     // registers)
     constexpr int NA = (M3_ROWS + M3_WARPS - 1) / M3_WARPS;
     const bool xout = lane >= 2 && lane < 30 && x0 + lane - 2 < nx;
@@ -201,7 +202,7 @@ k19_march(const T* __restrict__ fin, T* __restrict__ fout,
             zz[2] = inc_wrap(zz[1], nz);
             const int qn[3] = {(k + 1) % 3, (k + 2) % 3, k % 3};   // nu planes m - 3 .. m - 1
 #pragma unroll 1
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < M3_RC; ++j) {
                 const int r = warp + 2 + M3_WARPS * j;
                 if (!xout || y0 + r - 2 >= ny) continue;
                 const M3Rows rw = m3_rows(y0 - 2 + r, ny);
