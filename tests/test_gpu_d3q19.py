@@ -40,9 +40,11 @@ def _state(n, nx, ny, nz, seed, amp=0.3, umax=0.03):
 
 
 # (nx, ny, nz, N): lattices smaller than the march's 28 x 8 tiles, several tiles in x and y
-# with ragged last ones and several z segments (60 x 37 x 20), one component, and N = 5,
-# which only the staged schedule takes
-CASES = [(5, 4, 3, 2), (17, 6, 5, 3), (33, 9, 4, 4), (60, 37, 20, 3), (9, 5, 6, 1), (7, 3, 11, 5)]
+# with ragged last ones and several z segments (60 x 37 x 20), one and two layers (every
+# z neighbour the layer itself or the other one), one component, and N = 5, which only the
+# staged schedule takes
+CASES = [(5, 4, 3, 2), (17, 6, 5, 3), (33, 9, 4, 4), (60, 37, 20, 3), (9, 7, 1, 2), (6, 5, 2, 3),
+         (9, 5, 6, 1), (7, 3, 11, 5)]
 KERNELS = [mclb.KERNEL_FUSED, mclb.KERNEL_STAGED]
 MARCH_NMAX = 4
 
