@@ -305,8 +305,9 @@ def run_lines(torch, mclb, sptr, stream, count=512, nx=1024, steps=4096, precisi
     t = start.elapsed_time(stop) / 1e3
     rc, per = b.status()
     out = {"value": count * nx * 2 * steps / t / 1e6, "steps": steps, "lines": count, "sites": nx,
+           "precision": precision,
            "launches_per_step_chunk": b.launches_per_step, "status_ok": rc == 0,
-           "note": "MLUPS x N of 512 D1Q3 lines advanced 4096 steps by one resident "
+           "note": f"MLUPS x N of {count} D1Q3 lines advanced {steps} steps by one resident "
                    "launch (one CTA per line, the line in shared memory): bound by the "
                    "per-site arithmetic (FP64 runs at a small fraction of the FP32 rate on "
                    "this GPU), not by HBM"}
@@ -393,6 +394,10 @@ def main():
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the 512-instance batch variant and print its record")
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--only-lines", action="store_true",
+                    help="run only the D1Q3 lines variant (512 lines x 1024 sites, --precision "
+                         "fp32 or fp64, --lines-steps steps per resident launch) and print it")
+    ap.add_argument("--lines-steps", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -417,6 +422,10 @@ def main():
     if args.only_batch:
         print(json.dumps(run_batched(torch, mclb, sptr, stream, args.warmup, float("nan"),
                                      args.batch_steps)), flush=True)
+        return
+    if args.only_lines:
+        print(json.dumps(run_lines(torch, mclb, sptr, stream, steps=args.lines_steps,
+                                   precision=args.precision)), flush=True)
         return
     prob = workloads()[args.workload]()
     N, S = prob.ncomp, prob.sites
