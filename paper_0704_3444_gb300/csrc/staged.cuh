@@ -56,8 +56,9 @@ __device__ __forceinline__ int stencil_row(const StepParams<C>& p, int y, int dy
     return wrap_add(y, dy, p.ny);
 }
 
-// Site of thread t in a staged launch: every site, or with p.band > 0 the first and the
-// last p.band sites (rows next to the walls); -1 for a thread beyond them.
+// Site of thread t in a band launch (BAND = true): every site, or with p.band > 0 the first
+// and the last p.band sites (rows next to the walls); -1 for a thread beyond them.  The
+// full-lattice launches (BAND = false) index sites directly.
 template <typename C>
 __device__ __forceinline__ long long site_of(const StepParams<C>& p, long long t)
 {
@@ -100,13 +101,18 @@ __device__ __forceinline__ void density_site(const T* __restrict__ f,
     }
 }
 
-template <typename T, int N>
+template <typename T, int N, bool BAND = false>
 __global__ void __launch_bounds__(SITE_THREADS)
 k_density(const T* __restrict__ f, typename Storage<T>::C* __restrict__ rs,
           const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
-    const long long site = site_of(p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-    if (site < 0) return;
+    long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (BAND) {
+        site = site_of(p, site);
+        if (site < 0) return;
+    } else if (site >= p.S) {
+        return;
+    }
     if (wall_row(p, site))
         density_site<T, N, true>(f, rs, p, site);
     else
@@ -146,12 +152,17 @@ __device__ __forceinline__ void potential_site(const C* __restrict__ rs, C* __re
     for (int s = 0; s < N; ++s) nu[s * p.S + site] = out[s];
 }
 
-template <typename C, int N>
+template <typename C, int N, bool BAND = false>
 __global__ void __launch_bounds__(SITE_THREADS)
 k_potential(const C* __restrict__ rs, C* __restrict__ nu, const __grid_constant__ StepParams<C> p)
 {
-    const long long site = site_of(p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-    if (site < 0) return;
+    long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (BAND) {
+        site = site_of(p, site);
+        if (site < 0) return;
+    } else if (site >= p.S) {
+        return;
+    }
     if (wall_row(p, site))
         potential_site<C, N, true>(rs, nu, p, site);
     else
@@ -262,15 +273,20 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
     if (!(rho > C(0)) || !isfinite(rho)) atomicOr(p.status, STATUS_NONFINITE);
 }
 
-template <typename T, int N>
+template <typename T, int N, bool BAND = false>
 __global__ void __launch_bounds__(SITE_THREADS)
 k_collide(const T* __restrict__ fin, T* __restrict__ fout,
           const typename Storage<T>::C* __restrict__ rs,
           const typename Storage<T>::C* __restrict__ nu,
           const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
-    const long long site = site_of(p, (long long)blockIdx.x * blockDim.x + threadIdx.x);
-    if (site < 0) return;
+    long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (BAND) {
+        site = site_of(p, site);
+        if (site < 0) return;
+    } else if (site >= p.S) {
+        return;
+    }
     if (wall_row(p, site))
         collide_site<T, N, true>(fin, fout, rs, nu, p, site);
     else

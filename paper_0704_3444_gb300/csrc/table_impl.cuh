@@ -133,11 +133,11 @@ struct Launch {
         const auto band = [&](int rows) { return 2 * rows >= p.ny ? 0LL : (long long)rows * p.nx; };
         const auto blocks = [&]() { return site_blocks(p.band ? 2 * p.band : p.S); };
         p.band = band(5);
-        k_density<T, N><<<blocks(), SITE_THREADS, 0, st>>>(fin, (C*)sc.rho_s, p);
+        k_density<T, N, true><<<blocks(), SITE_THREADS, 0, st>>>(fin, (C*)sc.rho_s, p);
         p.band = band(4);
-        k_potential<C, N><<<blocks(), SITE_THREADS, 0, st>>>((const C*)sc.rho_s, (C*)sc.nu, p);
+        k_potential<C, N, true><<<blocks(), SITE_THREADS, 0, st>>>((const C*)sc.rho_s, (C*)sc.nu, p);
         p.band = band(3);
-        k_collide<T, N><<<blocks(), SITE_THREADS, 0, st>>>(fin, fout, (const C*)sc.rho_s,
+        k_collide<T, N, true><<<blocks(), SITE_THREADS, 0, st>>>(fin, fout, (const C*)sc.rho_s,
                                                             (const C*)sc.nu, p);
         return cudaGetLastError();
     }
