@@ -3,8 +3,8 @@
 //
 // The march does what k19_potential and k19_collide do, with the same per-site arithmetic
 // in the same order (the result equals the staged schedule's bit for bit), without writing
-// nu^s to HBM or reading it back: 2 x 4 N B fewer per site, and the 18-neighbour gradient
-// gathers come from shared memory.  A CTA owns a tile of M3_OUT_X columns x M3_OUT_Y rows
+// nu^s and j^s to HBM and reading them back (2 x 16 N B fewer per site in FP32), and with
+// the 18-neighbour Laplacian and gradient gathers from shared memory.  A CTA owns a tile of M3_OUT_X columns x M3_OUT_Y rows
 // and a segment of z planes.  Lane l of every warp holds column x0 - 2 + l (two halo
 // columns each side); the tile's rows carry two halo rows each side.  Iteration k of the
 // march, lead plane m = z0 - 2 + k:
@@ -49,8 +49,9 @@ __device__ __forceinline__ int pmod(int a, int n)
 __device__ __forceinline__ int dec_wrap(int a, int n) { return a == 0 ? n - 1 : a - 1; }
 __device__ __forceinline__ int inc_wrap(int a, int n) { return a == n - 1 ? 0 : a + 1; }
 
-// The wrapped rows y - 1, y, y + 1 and planes z - 1, z, z + 1 of a site; the start of the
-// stored row (z', y') of component 0 is ((z' ny + y') * 19) nx (32-bit: 19 S < 2^31).
+// The wrapped rows y - 1, y, y + 1 of a site (its planes z - 1, z, z + 1 travel as zz[3]);
+// the start of the stored row (z', y') of component 0 is ((z' ny + y') * 19) nx (32-bit:
+// 19 S < 2^31).
 struct M3Rows {
     int y[3];
 };
