@@ -552,6 +552,22 @@ def main():
                 "hbm_frac_of_measured": v.bytes_per_step / (t / 100) / 1e9 / peak,
                 "speedup_vs_fp32": val / slab_fp32}
             v.close()
+        # the periodic slab under the Gibbs-Duhem force reading (kappa = 0), FP32: the
+        # single pass with its total-density gradient, and the staged schedule
+        slab.walls = 0
+        slab.kappa = 0.0
+        slab.force_form = 1
+        for kern_g, key in ((mclb.KERNEL_FUSED, "slab_8192x2048_fp32_gibbs_duhem"),
+                            (mclb.KERNEL_STAGED, "slab_8192x2048_fp32_gibbs_duhem_staged")):
+            v = mclb.Simulation.from_problem(slab, precision="fp32", kernel=kern_g, stream=sptr)
+            t = time_steps(torch, v, 100, args.warmup, stream)
+            val = slab.sites * slab.ncomp * 100 / t / 1e6
+            variants[key] = {
+                "value": val, "steps": 100, "status_ok": v.status() == 0,
+                "launches_per_step": v.launches_per_step,
+                "hbm_frac_of_measured": v.bytes_per_step / (t / 100) / 1e9 / peak,
+                "speedup_vs_fp32": val / slab_fp32}
+            v.close()
         # the D3Q19 lattice: the paper's ternary chi set on 256^3 in FP32, the density pass
         # + z-plane march and the staged schedule
         cube = workloads()["ternary3d_256"]()

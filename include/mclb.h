@@ -98,7 +98,9 @@ typedef enum {
                                      that Gibbs-Duhem gives for the Flory-Huggins free energy
                                      (its pressure sum rho mu - psi vanishes); the total force
                                      is then a discrete gradient and total momentum is kept.
-                                     Runs on the staged schedule (D2Q9) and on D1Q3          */
+                                     D2Q9: the single pass for FP64/FP32 and N <= 3 (kernel
+                                     AUTO or FUSED; FUSED fails with MCLB_EINVAL otherwise),
+                                     else the staged schedule; D1Q3; D3Q19 staged only      */
 } mclb_force_form;
 
 /* Lattice. */

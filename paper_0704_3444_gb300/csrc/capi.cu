@@ -126,9 +126,6 @@ int validate(const mclb_params* p)
     if (p->force_form == MCLB_FORCE_GIBBS_DUHEM) {
         if (p->kappa != 0.0)
             return fail(MCLB_EINVAL, "the Gibbs-Duhem force form is defined for kappa = 0");
-        if (p->lattice == MCLB_D2Q9 && p->kernel == MCLB_KERNEL_FUSED)
-            return fail(MCLB_EINVAL, "the Gibbs-Duhem force form runs on the staged schedule "
-                                     "(kernel AUTO or STAGED) on D2Q9");
     }
     if (p->mass_every < 0) return fail(MCLB_EINVAL, "mass_every=%d must be >= 0", p->mass_every);
     if (p->walls != 0 && p->walls != 1) return fail(MCLB_EINVAL, "walls=%d unknown", p->walls);
@@ -493,7 +490,6 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (cudaStreamCreateWithFlags(&h->status_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaStreamCreate failed"));
     h->fused = false;
-    if (P.force_form == MCLB_FORCE_GIBBS_DUHEM && !h->alt) h->kernel = MCLB_KERNEL_STAGED;
     if (h->alt) {
         if (h->alt->item_bytes > 0 && cudaMalloc(&h->sc.line_item, h->alt->item_bytes) != cudaSuccess)
             return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));
@@ -882,7 +878,8 @@ int batch_build(mclb_batch b)
                 scs.push_back(h->sc);
                 fa.push_back(h->f[0]);
                 fb.push_back(h->f[1]);
-                fused = fused && h->fused;
+                // the batched march has no Gibbs-Duhem instance: such a group runs staged
+                fused = fused && h->fused && h->P.force_form != FORCE_GIBBS_DUHEM;
                 for (int k = 0; k < 2; ++k) {
                     maps.push_back(h->tmap[k]);
                     maps.push_back(h->tmapr[k]);

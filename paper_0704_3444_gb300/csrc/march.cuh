@@ -134,7 +134,7 @@ constexpr bool has_narrow() { return MarchPick<T, N>::NW == 4 && MarchNarrow<T, 
 // The march of one CTA over the strip starting at column x0 and the segment of H rows
 // starting at row y0 (tmap/tmapr: load views of the input buffer; tmapw/tmapwr: store
 // views of fout; p may live in parameter or shared memory; G: the geometry).
-template <typename T, int N, typename G = MarchGeom<T, N>>
+template <typename T, int N, typename G = MarchGeom<T, N>, bool GD = false>
 __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtensorMap* tmapr,
                                           const CUtensorMap* tmapw, const CUtensorMap* tmapwr,
                                           T* __restrict__ fout,
@@ -271,6 +271,10 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
         C Q1[N], Q0[N], GX[N], Dp[N], T2[N], T1[N];
         C R2[N], X2[N], Y2[N], R1[N], X1[N], Y1[N];
         C ux2 = C(0), uy2 = C(0), ux1 = C(0), uy1 = C(0);
+        // GD (the Gibbs-Duhem total force): the same D and T sums of the total density for
+        // rows m - 1, m - 2, m - 3, and the total density of rows m - 1, m - 2
+        [[maybe_unused]] C Dr1 = C(0), Dr2 = C(0), Dr3 = C(0), Tr1 = C(0), Tr3 = C(0), Tr2 = C(0);
+        [[maybe_unused]] C rt1 = C(0), rt2 = C(0);
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             Q1[c] = Q0[c] = GX[c] = Dp[c] = T2[c] = T1[c] = C(0);
@@ -325,6 +329,13 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                 quad += R0[t] * a;
             }
             const C Gs = -theta * (sm * inv + C(0.5) * quad * inv * inv);
+            [[maybe_unused]] C Drn = C(0), Trn = C(0);
+            if constexpr (GD) {
+                const C rl = __shfl_up_sync(0xffffffffu, rho, 1);
+                const C rr = __shfl_down_sync(0xffffffffu, rho, 1);
+                Drn = rr - rl;
+                Trn = rho * c9 + (rr + rl) * c36;
+            }
 
             // ---- nu of row m - 1, partial nu of rows m and m + 1
             C Dn[N], Tn[N];
@@ -419,11 +430,29 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                     }
                 };
                 // acceleration a^s of row r (Eq. definef plus the body force)
-                auto accel = [&](const int c, C& ax, C& ay) {
+                auto accel0 = [&](const int c, C& ax, C& ay) {
                     const C gx = GX[c] + Dn[c] * c36;
                     const C gy = Tn[c] - T2[c];
                     ax = -p.fcoef * (C(3) * gx) + p.gx;
                     ay = -p.fcoef * (C(3) * gy) + p.gy;
+                };
+                // GD: every component's a^s first, then the shift (A_c - A)/rho with A_c =
+                // (1 - 1/2tau) (1/3) grad rho from the total-density sums of rows r - 1 .. r + 1
+                [[maybe_unused]] C axg[N], ayg[N];
+                if constexpr (GD) {
+#pragma unroll
+                    for (int c = 0; c < N; ++c) accel0(c, axg[c], ayg[c]);
+                    const C grx = C(3) * (Dr2 * c9 + (Dr3 + Dr1) * c36);
+                    const C gry = C(3) * (Tr1 - Tr3);
+                    gibbs_duhem_shift<C, N>(p, R2, rt2, grx, gry, axg, ayg);
+                }
+                auto accel = [&](const int c, C& ax, C& ay) {
+                    if constexpr (GD) {
+                        ax = axg[c];
+                        ay = ayg[c];
+                    } else {
+                        accel0(c, ax, ay);
+                    }
                 };
                 // 16-bit formats: out_i is already the deviation f*_i - w_i M, with M the
                 // site's pre-collision mass rho^s, which the collision conserves
@@ -537,6 +566,16 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
             uy2 = uy1;
             ux1 = ux0;
             uy1 = uy0;
+            if constexpr (GD) {
+                Dr3 = Dr2;
+                Dr2 = Dr1;
+                Dr1 = Drn;
+                Tr3 = Tr2;
+                Tr2 = Tr1;
+                Tr1 = Trn;
+                rt2 = rt1;
+                rt1 = rho;
+            }
         }
     };
 
@@ -550,7 +589,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
     __syncthreads();
 }
 
-template <typename T, int N>
+template <typename T, int N, bool GD = false>
 __global__ void __launch_bounds__(MarchGeom<T, N>::THREADS) __maxnreg__((MarchGeom<T, N>::MAXREG))
 k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapr,
         const __grid_constant__ CUtensorMap tmapw, const __grid_constant__ CUtensorMap tmapwr,
@@ -558,8 +597,9 @@ k_march(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtens
         const int H)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    march_cta<T, N>(&tmap, &tmapr, &tmapw, &tmapwr, fout, p, blockIdx.x * MarchGeom<T, N>::WOUT,
-                    blockIdx.y * H, H, smem);
+    march_cta<T, N, MarchGeom<T, N>, GD>(&tmap, &tmapr, &tmapw, &tmapwr, fout, p,
+                                         blockIdx.x * MarchGeom<T, N>::WOUT, blockIdx.y * H, H,
+                                         smem);
 }
 
 }  // namespace mclb

@@ -14,6 +14,7 @@ constexpr int Q = 9;
 constexpr int ROW_ALIGN = 128;  // data columns per row are padded to a multiple of this
 constexpr int LATTICE_D1Q3 = 1; // Problem::lattice of a D1Q3 lattice (MCLB_D1Q3)
 constexpr int LATTICE_D3Q19 = 2; // Problem::lattice of a D3Q19 lattice (MCLB_D3Q19)
+constexpr int FORCE_GIBBS_DUHEM = 1; // Problem::force_form of the Gibbs-Duhem total force
 
 // Everything a launcher needs to know about one simulation, in FP64 as given at
 // the boundary; each precision unit converts it to its own kernel parameters.

@@ -69,23 +69,23 @@ struct Launch {
     // Strips of WOUT columns, segments of H rows: one wave of CTAs, each segment as
     // tall as the resident CTAs allow (every segment re-reads 4 halo rows and spends 4
     // warm-up iterations), at least 8 rows.
-    template <int N>
-    static FusedPlan plan_n(const Problem& P, int sm_count)
+    template <int N, bool GD>
+    static FusedPlan plan_k(const Problem& P, int sm_count)
     {
         using G = MarchGeom<T, N>;
         FusedPlan pl{};
         pl.ok = false;
         if (!G::FITS) return pl;
-        if (cudaFuncSetAttribute(k_march<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_march<T, N, GD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)G::SMEM) != cudaSuccess)
             return pl;
         // the largest shared-memory carveout, so that the resident CTAs the occupancy
         // query counts (it assumes the largest) are the ones the launch gets
-        if (cudaFuncSetAttribute(k_march<T, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        if (cudaFuncSetAttribute(k_march<T, N, GD>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return pl;
         int ctas = 0;  // resident CTAs per SM as the runtime computes them (smem, registers)
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_march<T, N>, G::THREADS,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_march<T, N, GD>, G::THREADS,
                                                           G::SMEM) != cudaSuccess || ctas < 1)
             return pl;
         pl.W = G::WOUT;
@@ -102,6 +102,25 @@ struct Launch {
         pl.nsegs = (P.ny + pl.H - 1) / pl.H;
         pl.ok = true;
         return pl;
+    }
+
+    // The Gibbs-Duhem force form has its own single-pass instance for FP64 and FP32 storage
+    // and N <= 3 (the paper's polymer binary and ternary); elsewhere it runs staged.
+    template <int N>
+    static constexpr bool gd_single_pass()
+    {
+        return (std::is_same<T, float>::value || std::is_same<T, double>::value) && N <= 3;
+    }
+    template <int N>
+    static FusedPlan plan_n(const Problem& P, int sm_count)
+    {
+        if (P.force_form == FORCE_GIBBS_DUHEM) {
+            if constexpr (gd_single_pass<N>()) return plan_k<N, true>(P, sm_count);
+            FusedPlan none{};
+            none.ok = false;
+            return none;
+        }
+        return plan_k<N, false>(P, sm_count);
     }
 
     static FusedPlan plan_fused(const Problem& P, int sm_count)
@@ -153,7 +172,16 @@ struct Launch {
         const CUtensorMap& tw = pl.out_w > 0 ? *tmapw_out : *tmap_in;
         const CUtensorMap& twr = (pl.out_w > 0 && Storage<T>::shifted) ? *tmapwr_out : *tmap_in;
         MCLB_DISPATCH_N(P.N, {
-            k_march<T, NN><<<grid, pl.threads, pl.smem, st>>>(*tmap_in, tr, tw, twr, (T*)fout, p, pl.H);
+            bool launched = false;
+            if constexpr (gd_single_pass<NN>()) {
+                if (P.force_form == FORCE_GIBBS_DUHEM) {
+                    k_march<T, NN, true><<<grid, pl.threads, pl.smem, st>>>(*tmap_in, tr, tw, twr,
+                                                                          (T*)fout, p, pl.H);
+                    launched = true;
+                }
+            }
+            if (!launched)
+                k_march<T, NN><<<grid, pl.threads, pl.smem, st>>>(*tmap_in, tr, tw, twr, (T*)fout, p, pl.H);
             const long long ghosts = (long long)NN * P.ny * (Q + (Storage<T>::shifted ? 1 : 0)) * 2 * P.hx;
             k_ghosts<T><<<(unsigned)((ghosts + 255) / 256), 256, 0, st>>>((T*)fout, p, NN);
             if (P.walls) return wall_rows<NN>(p, sc, (const T*)fin, (T*)fout, st);

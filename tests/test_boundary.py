@@ -61,7 +61,6 @@ def _params(**kw):
     (dict(lattice="d1q3", ny=1, precision="bf16"), "FP64 or FP32"),
     (dict(force_form=2), "force_form"),
     (dict(force_form=1, kappa=0.01), "kappa = 0"),
-    (dict(force_form=1, kernel=1), "staged schedule"),
     (dict(mass_every=-1), "mass_every"),
     (dict(lattice=3), "lattice"),
     (dict(walls=2), "walls"),

@@ -1,6 +1,7 @@
 """GPU: the Gibbs-Duhem reading of the sum of the component forces (force_form = 1,
-kappa = 0) against the FP64 oracle, on the D2Q9 staged schedule and on D1Q3, and the
-paper's polymer binary (Sec. 4) run with it.
+kappa = 0) against the FP64 oracle, on the D2Q9 single pass (FP64/FP32, N <= 3) and
+staged schedule, in D2Q9 batches and on D1Q3, and the paper's polymer binary (Sec. 4) run
+with it.
 
 Tolerances as elsewhere: FP64 1e-12 of the field's max-norm, FP32 1e-5 absolute.
 """
@@ -31,18 +32,31 @@ def _chi(n, seed):
     return c
 
 
+KERNELS = [mclb.KERNEL_AUTO, mclb.KERNEL_FUSED, mclb.KERNEL_STAGED]
+
+
 @pytest.mark.parametrize("fv", [0, 1])
-@pytest.mark.parametrize("shape", [(5, 3, 3), (40, 33, 2), (130, 37, 4)],
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(5, 3, 3), (40, 33, 2), (300, 170, 3), (130, 37, 4), (9, 1, 2)],
                          ids=lambda s: f"{s[0]}x{s[1]}N{s[2]}")
-def test_d2q9_staged_fp64(shape, fv):
-    """D2Q9 (the handle picks the staged schedule): 20 FP64 steps, state, rho, U and mu
-    within 1e-12 of the oracle, with m != 1, theta != 1/3 and a body force."""
+def test_d2q9_fp64(shape, kernel, fv):
+    """D2Q9, 20 FP64 steps: state, rho, U and mu within 1e-12 of the oracle, with m != 1,
+    theta != 1/3 and a body force.  The single pass carries the total-density gradient
+    sums like the potential's and takes N <= 3; AUTO falls back to the staged schedule for
+    N = 4, where a FUSED request fails."""
     nx, ny, n = shape
     rho, u = inputs.random_state(n, nx, ny, seed=810 + nx + n, amp=0.3, umax=0.03)
     m = [1.0 + (k % 3) for k in range(n)]
     kw = dict(m=m, theta=0.4, kappa=0.0, force=(1e-5, -2e-5), forcing_velocity=fv)
-    sim = mclb.Simulation(n, nx, ny, 0.9, _chi(n, 81), precision="fp64", force_form=1, **kw)
-    assert sim.launches_per_step == 3
+    if kernel == mclb.KERNEL_FUSED and n > 3:
+        with pytest.raises(mclb.MclbError, match="fused kernel unavailable"):
+            mclb.Simulation(n, nx, ny, 0.9, _chi(n, 81), precision="fp64", force_form=1,
+                            kernel=kernel, **kw)
+        return
+    sim = mclb.Simulation(n, nx, ny, 0.9, _chi(n, 81), precision="fp64", force_form=1,
+                          kernel=kernel, **kw)
+    single = kernel == mclb.KERNEL_FUSED or (kernel == mclb.KERNEL_AUTO and n <= 3)
+    assert sim.launches_per_step == (2 if single else 3)
     orc = Oracle(n, nx, ny, 0.9, _chi(n, 81), force_form=1, **kw)
     sim.init_fields(rho, u)
     orc.init(rho, u)
@@ -58,14 +72,15 @@ def test_d2q9_staged_fp64(shape, fv):
     sim.close()
 
 
-def test_d2q9_staged_fp32_and_momentum():
+@pytest.mark.parametrize("kernel", [mclb.KERNEL_FUSED, mclb.KERNEL_STAGED])
+def test_d2q9_fp32_and_momentum(kernel):
     """FP32 storage: densities and velocity within 1e-5 of the oracle after 100 steps of
     the ternary droplet state (kappa = 0).  In FP64 on the GPU, with g = 0, the total
     momentum stays at its start to rounding over 200 steps (the reading's exact
     property), while Eq. definef's component forces as printed change it."""
     p = inputs.ternary_droplets(128, 96, kappa=0.0)
     p.force_form = 1
-    sim = mclb.Simulation.from_problem(p, precision="fp32")
+    sim = mclb.Simulation.from_problem(p, precision="fp32", kernel=kernel)
     orc = Oracle.from_problem(p)
     sim.step(100)
     assert orc.run(100) == 0
@@ -77,13 +92,49 @@ def test_d2q9_staged_fp32_and_momentum():
     drift = {}
     for ff in (1, 0):
         p.force_form = ff
-        sim = mclb.Simulation.from_problem(p, precision="fp64", kernel=mclb.KERNEL_STAGED)
+        sim = mclb.Simulation.from_problem(p, precision="fp64", kernel=kernel)
         m0 = sim.conservation()["mom"]
         sim.step(200)
         drift[ff] = np.max(np.abs(sim.conservation()["mom"] - m0))
         sim.close()
     assert drift[1] < 1e-12, drift
     assert drift[0] > 1e-8, drift
+
+
+def test_single_pass_unavailable_in_16_bit():
+    """The 16-bit formats have no single-pass instance of the reading: FUSED fails, AUTO
+    runs staged."""
+    chi = _chi(2, 81)
+    with pytest.raises(mclb.MclbError, match="fused kernel unavailable"):
+        mclb.Simulation(2, 64, 32, 0.9, chi, kappa=0.0, precision="bf16", force_form=1,
+                        kernel=mclb.KERNEL_FUSED)
+    sim = mclb.Simulation(2, 64, 32, 0.9, chi, kappa=0.0, precision="bf16", force_form=1)
+    assert sim.launches_per_step == 3
+    sim.close()
+
+
+def test_d2q9_batch_equals_single_handles():
+    """A D2Q9 batch of instances with the reading runs the staged batch kernels (the
+    batched march has no instance of it) and equals each instance's own handle to 1e-12
+    after 30 FP64 steps."""
+    probs = []
+    for k, (nx, ny) in enumerate(((40, 24), (33, 17), (64, 9))):
+        n = 2 + (k % 2)
+        rho, u = inputs.random_state(n, nx, ny, seed=830 + k, amp=0.3, umax=0.03)
+        probs.append(inputs.Problem(
+            name=f"gd{k}", ncomp=n, nx=nx, ny=ny, tau=0.9, chi=_chi(n, 81 + k),
+            m=np.array([1.0 + (j % 3) for j in range(n)]), theta=0.4, kappa=0.0,
+            force=(1e-5, -2e-5), rho=rho, u=u, force_form=1, precision="fp64"))
+    b = mclb.Batch(probs, precision="fp64")
+    b.init_all()
+    b.step(30)
+    assert b.status()[0] == 0
+    for k, p in enumerate(probs):
+        sim = mclb.Simulation.from_problem(p, precision="fp64", kernel=mclb.KERNEL_STAGED)
+        sim.step(30)
+        assert _rel(b.get_state(k), sim.get_state()) < 1e-12
+        sim.close()
+    b.close()
 
 
 @pytest.mark.parametrize("nx", [96, 3001])
