@@ -274,7 +274,7 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
         // GD (the Gibbs-Duhem total force): the same D and T sums of the total density for
         // rows m - 1, m - 2, m - 3, and the total density of rows m - 1, m - 2
         [[maybe_unused]] C Dr1 = C(0), Dr2 = C(0), Dr3 = C(0), Tr1 = C(0), Tr3 = C(0), Tr2 = C(0);
-        [[maybe_unused]] C rt1 = C(0), rt2 = C(0);
+        [[maybe_unused]] C it1 = C(0), it2 = C(0);   // 1 / rho of rows m - 1, m - 2
 #pragma unroll
         for (int c = 0; c < N; ++c) {
             Q1[c] = Q0[c] = GX[c] = Dp[c] = T2[c] = T1[c] = C(0);
@@ -438,13 +438,24 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                 };
                 // GD: every component's a^s first, then the shift (A_c - A)/rho with A_c =
                 // (1 - 1/2tau) (1/3) grad rho from the total-density sums of rows r - 1 .. r + 1
+                // (gibbs_duhem_shift's terms, with the row's 1/rho and (1 - 1/2tau)/3 * 3
+                // folded: no division per site)
                 [[maybe_unused]] C axg[N], ayg[N];
                 if constexpr (GD) {
+                    C Ax = C(0), Ay = C(0);
 #pragma unroll
-                    for (int c = 0; c < N; ++c) accel0(c, axg[c], ayg[c]);
-                    const C grx = C(3) * (Dr2 * c9 + (Dr3 + Dr1) * c36);
-                    const C gry = C(3) * (Tr1 - Tr3);
-                    gibbs_duhem_shift<C, N>(p, R2, rt2, grx, gry, axg, ayg);
+                    for (int c = 0; c < N; ++c) {
+                        accel0(c, axg[c], ayg[c]);
+                        Ax += R2[c] * (axg[c] - p.gx);
+                        Ay += R2[c] * (ayg[c] - p.gy);
+                    }
+                    const C dx = (p.fcoef * (Dr2 * c9 + (Dr3 + Dr1) * c36) - Ax) * it2;
+                    const C dy = (p.fcoef * (Tr1 - Tr3) - Ay) * it2;
+#pragma unroll
+                    for (int c = 0; c < N; ++c) {
+                        axg[c] += dx;
+                        ayg[c] += dy;
+                    }
                 }
                 auto accel = [&](const int c, C& ax, C& ay) {
                     if constexpr (GD) {
@@ -573,8 +584,8 @@ __device__ __forceinline__ void march_cta(const CUtensorMap* tmap, const CUtenso
                 Tr3 = Tr2;
                 Tr2 = Tr1;
                 Tr1 = Trn;
-                rt2 = rt1;
-                rt1 = rho;
+                it2 = it1;
+                it1 = inv;
             }
         }
     };
