@@ -176,8 +176,9 @@ __device__ __forceinline__ void gibbs_duhem_shift(const StepParams<C>& p, const 
         Ax += r[s] * (ax[s] - p.gx);
         Ay += r[s] * (ay[s] - p.gy);
     }
-    const C dx = (p.fcoef * grx / C(3) - Ax) / rho;
-    const C dy = (p.fcoef * gry / C(3) - Ay) / rho;
+    const C k = p.fcoef * C(1.0 / 3.0), inv = C(1) / rho;
+    const C dx = (k * grx - Ax) * inv;
+    const C dy = (k * gry - Ay) * inv;
 #pragma unroll
     for (int s = 0; s < N; ++s) {
         ax[s] += dx;

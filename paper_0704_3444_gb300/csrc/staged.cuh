@@ -258,7 +258,8 @@ __device__ __forceinline__ void collide_site(const T* __restrict__ fin, T* __res
         jxt += bx;
         jyt += by;
     }
-    const C ux = jxt / rho, uy = jyt / rho;
+    const C inv = C(1) / rho;
+    const C ux = jxt * inv, uy = jyt * inv;
     C e[Q];
     eq_weights(ux, uy, e);
     C ax[N], ay[N];
