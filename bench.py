@@ -200,6 +200,35 @@ def job_rate(torch, dist, work, elapsed, world, device):
     return world * work / elapsed / 1e6, elapsed
 
 
+def run_slabs(torch, mclb, prob, warmup, fp32_value, parts=2, steps=200):
+    """The workload's lattice cut into ``parts`` y slabs held by separate handles on this
+    GPU (paper_0704_3444_gb300.slabs.LocalSlabs), every slab padded by 3 * period rows
+    on each side and refreshed from its neighbours' bands every ``period`` steps: the cost
+    of the decomposition a multi-GPU split of one lattice uses, measured without the
+    interconnect (extra rows, band copies, twice the launches)."""
+    from paper_0704_3444_gb300 import slabs as slabs_mod
+
+    out = {}
+    kw = dict(ncomp=prob.ncomp, tau=prob.tau, chi=prob.chi, m=prob.m, theta=prob.theta,
+              kappa=prob.kappa, force=prob.force, precision="fp32", kernel=mclb.KERNEL_FUSED)
+    ts = torch.cuda.Stream()   # one stream for every slab handle, its copies and the events
+    for period in (1, 4):
+        ls = slabs_mod.LocalSlabs(prob.nx, prob.ny, parts, period, stream=ts.cuda_stream, **kw)
+        ls.init_fields(prob.rho, prob.u)
+        t = time_steps(torch, ls, steps, warmup, ts)
+        val = prob.sites * prob.ncomp * steps / t / 1e6
+        band = ls.slabs[0].handle.rows_bytes(ls.slabs[0].G)
+        out[f"slabs_{parts}_{prob.name}_fp32_period{period}"] = {
+            "value": val, "steps": steps, "status_ok": all(v == 0 for v in ls.status()),
+            "slab_rows": [s.h for s in ls.slabs], "outer_rows_per_side": ls.slabs[0].G,
+            "band_bytes": band, "speedup_vs_fp32": val / fp32_value,
+            "note": "MLUPS x N of the lattice's own sites; every slab also computes its outer "
+                    "rows, and every period steps 2 bands per slab are packed and unpacked "
+                    "(device copies on the same stream)"}
+        ls.close()
+    return out
+
+
 def run_batched(torch, mclb, sptr, stream, warmup, fp32_value, steps=1000):
     """512 independent binary/ternary FP32 simulations of uneven size advanced together
     for the workload's 1000 steps (one batch handle, graph-replayed launches) against the
@@ -398,6 +427,9 @@ def main():
                     help="run only the D1Q3 lines variant (512 lines x 1024 sites, --precision "
                          "fp32 or fp64, --lines-steps steps per resident launch) and print it")
     ap.add_argument("--lines-steps", type=int, default=4096)
+    ap.add_argument("--only-slabs", action="store_true",
+                    help="run only the slab-decomposition variant of the workload (two slabs "
+                         "on this GPU) and print its record")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -429,6 +461,10 @@ def main():
         return
     prob = workloads()[args.workload]()
     N, S = prob.ncomp, prob.sites
+    if args.only_slabs:
+        print(json.dumps(run_slabs(torch, mclb, prob, args.warmup, float("nan"))),
+              flush=True)
+        return
 
     kern = mclb.KERNEL_FUSED if args.kernel == "fused" else mclb.KERNEL_STAGED
     sim = mclb.Simulation.from_problem(prob, precision=args.precision, kernel=kern, stream=sptr)
@@ -590,6 +626,7 @@ def main():
         for prec in ("fp64", "fp32"):
             variants[f"d1q3_lines_512x1024_{prec}"] = run_lines(torch, mclb, sptr, stream,
                                                                 precision=prec)
+        variants.update(run_slabs(torch, mclb, prob, args.warmup, value / world))
         variants["batched_512"] = run_batched(torch, mclb, sptr, stream, args.warmup, value / world)
     clk.__exit__()
     clocks = clk.summary()

@@ -30,8 +30,9 @@
  *     w_1,2 of D1Q3 sit one unit in the last place below the nearest float), so that
  *     the equilibria keep every site's mass to rounding.
  *   - All device work of a handle is ordered on the stream given at creation
- *     (NULL: the legacy default stream).  Calls that return host data
- *     synchronise that stream.  Handles are not thread-safe.
+ *     (NULL: a stream the handle creates with cudaStreamCreate and owns, which is
+ *     ordered with the legacy default stream but not with other streams).  Calls that
+ *     return host data synchronise that stream.  Handles are not thread-safe.
  */
 #ifndef MCLB_H
 #define MCLB_H
@@ -137,7 +138,7 @@ typedef enum {
  *   force      body acceleration g (Eq. NSEeq), added to every a^s
  *   precision  mclb_precision
  *   kernel     mclb_kernel
- *   stream     cudaStream_t to order all work on, or NULL
+ *   stream     cudaStream_t to order all work on, or NULL (the handle creates its own)
  *   forcing_velocity  mclb_forcing_velocity (0: Eq. ff3 as printed)
  *   lattice    mclb_lattice (0: D2Q9)
  *   force_form mclb_force_form (0: Eq. definef as printed)
@@ -270,6 +271,44 @@ int mclb_set_state(mclb_handle h, const double* f, size_t count);
 
 /* Timesteps taken since the last init / set_state. */
 long mclb_step_count(mclb_handle h);
+
+/* ----------------------------------------------------------------------------
+ * Bands of rows, for splitting one periodic D2Q9 lattice into y slabs (one handle per
+ * slab, on one or several GPUs).  The paper has one periodic lattice; the split rests on
+ * how far one timestep reaches.  A site's post-collision values depend on the stored
+ * values at most 3 rows away: the pull of Eq. ssLB reaches 1 row, the force of Eq.
+ * definef takes a centred gradient of mu^s (1 row more), and mu^s holds the Laplacian
+ * -kappa lap rho^s (1 row more).  So a slab of h rows stored in a handle of h + 2G rows,
+ * whose G rows on each side are copies of the neighbouring slabs' rows, advances its own
+ * h rows exactly as the whole lattice would for G / 3 timesteps, whatever the handle does
+ * beyond its edges (the paper_0704_3444_gb300 package gives it walls = 1); then the G
+ * outer rows are refreshed from the neighbours' bands.  The package's SlabDecomposition
+ * and LocalSlabs do this.
+ *
+ * A band is the stored (post-collision, pull-scheme) representation itself, copied
+ * byte for byte: per component, the nine velocity lines of each row with their ghost
+ * columns, then in the 16-bit formats each row's FP32 density line.  Packing a band of
+ * one handle and unpacking it into another handle with the same N, nx and precision is
+ * exact in every format.  Rows are [y0, y0 + nrows), 0 <= y0, y0 + nrows <= ny.
+ *
+ * mclb_rows_bytes: bytes of a band of nrows rows (0 on a bad handle, a lattice other than
+ *   D2Q9, or nrows < 0).
+ * mclb_pack_rows_device / mclb_unpack_rows_device: copy the band between the current
+ *   state and buf, a buffer of mclb_rows_bytes(h, nrows) bytes in device memory (or host
+ *   memory pinned for the device), in stream order, without synchronising.  The caller
+ *   owns buf and keeps it alive until the stream has passed the copy.  Unpacking does not
+ *   check the values, leaves the step counter alone and is not seen by the mass
+ *   compensation (mass_every), whose reference is the whole handle.
+ *   Errors: EHANDLE, EINVAL (lattice not D2Q9, rows out of range, NULL buffer with
+ *   nrows > 0), ECUDA.
+ * mclb_conservation_rows: the sums of mclb_conservation over the rows [y0, y0 + nrows)
+ *   only (mass N, mom 2, force_sum 2; zeros for nrows = 0).  Host pointers, any may be
+ *   NULL; synchronises.  Errors: EHANDLE, EINVAL, ECUDA. */
+size_t mclb_rows_bytes(mclb_handle h, int nrows);
+int mclb_pack_rows_device(mclb_handle h, int y0, int nrows, void* buf);
+int mclb_unpack_rows_device(mclb_handle h, int y0, int nrows, const void* buf);
+int mclb_conservation_rows(mclb_handle h, int y0, int nrows, double* mass, double* mom,
+                           double* force_sum);
 
 /* Test hook for the failure path of the single-pass kernel (no counterpart in the
  * paper): while on != 0, its steps issue no copies, so every CTA's first bounded wait

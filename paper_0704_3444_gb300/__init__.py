@@ -109,6 +109,11 @@ def load():
             "mclb_batch_destroy": ([H], ctypes.c_int),
             "mclb_step_noalloc": ([ctypes.POINTER(mclb_params), ctypes.c_void_p, ctypes.c_void_p],
                                   ctypes.c_int),
+            "mclb_rows_bytes": ([H, ctypes.c_int], ctypes.c_size_t),
+            "mclb_pack_rows_device": ([H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+            "mclb_unpack_rows_device": ([H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+                                        ctypes.c_int),
+            "mclb_conservation_rows": ([H, ctypes.c_int, ctypes.c_int, dp, dp, dp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -136,6 +141,11 @@ def _tensor_ptr(t) -> Optional[int]:
     if t is None:
         return None
     return int(t.data_ptr())
+
+
+def _check_buf(buf, nbytes: int):
+    if not buf.is_contiguous() or buf.numel() * buf.element_size() < nbytes:
+        raise ValueError(f"band buffer must be contiguous with at least {nbytes} bytes")
 
 
 def _fields(rho, u, ncomp, ny, nx, device=False, nz=1, ud=2):
@@ -272,6 +282,29 @@ class Simulation:
         out = np.empty((nphase, self.ncomp))
         _check(self.lib.mclb_fit_equilibrium(self.h, int(nphase), _dp(out)), "mclb_fit_equilibrium")
         return out
+
+    # bands of rows (mclb_rows_bytes, mclb_pack_rows_device, ...): D2Q9 only
+    def rows_bytes(self, nrows: int) -> int:
+        return int(self.lib.mclb_rows_bytes(self.h, int(nrows)))
+
+    def pack_rows(self, y0: int, nrows: int, buf):
+        """Copy the stored rows [y0, y0 + nrows) into ``buf`` (a contiguous torch tensor of
+        at least rows_bytes(nrows) bytes on the handle's device), in stream order."""
+        _check_buf(buf, self.rows_bytes(nrows))
+        _check(self.lib.mclb_pack_rows_device(self.h, int(y0), int(nrows), _tensor_ptr(buf)),
+               "mclb_pack_rows_device")
+
+    def unpack_rows(self, y0: int, nrows: int, buf):
+        """Overwrite the stored rows [y0, y0 + nrows) from ``buf`` (as pack_rows)."""
+        _check_buf(buf, self.rows_bytes(nrows))
+        _check(self.lib.mclb_unpack_rows_device(self.h, int(y0), int(nrows), _tensor_ptr(buf)),
+               "mclb_unpack_rows_device")
+
+    def conservation_rows(self, y0: int, nrows: int):
+        mass, mom, fs = np.empty(self.ncomp), np.empty(2), np.empty(2)
+        _check(self.lib.mclb_conservation_rows(self.h, int(y0), int(nrows), _dp(mass), _dp(mom),
+                                               _dp(fs)), "mclb_conservation_rows")
+        return dict(mass=mass, mom=mom, force=fs)
 
     def get_state(self):
         """Pre-collision populations: (N, 9, ny, nx) on D2Q9, (N, 3, nx) on D1Q3,

@@ -468,7 +468,9 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     for (int b = 0; b < 2; ++b) {
         if (cudaMalloc(&h->f[b], h->fbytes) != cudaSuccess)
             return bail(fail(MCLB_ENOMEM, "distribution buffer of %zu bytes", h->fbytes));
-        if (cudaMemset(h->f[b], 0, h->fbytes) != cudaSuccess)
+        // on the handle's stream: a stream created non-blocking is not ordered with the
+        // legacy default stream, so a plain cudaMemset could land after the first init
+        if (cudaMemsetAsync(h->f[b], 0, h->fbytes, h->stream) != cudaSuccess)
             return bail(fail(MCLB_ECUDA, "cudaMemset failed"));
     }
     if (cudaMalloc(&h->sc.rho_s, (size_t)P.N * P.S * cbytes) != cudaSuccess ||
@@ -479,7 +481,7 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
         cudaMalloc(&h->sc.status, sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&h->sc.mass_ref, NMAX * sizeof(double)) != cudaSuccess)
         return bail(fail(MCLB_ENOMEM, "reduction scratch"));
-    if (cudaMemset(h->sc.status, 0, sizeof(unsigned int)) != cudaSuccess)
+    if (cudaMemsetAsync(h->sc.status, 0, sizeof(unsigned int), h->stream) != cudaSuccess)
         return bail(fail(MCLB_ECUDA, "cudaMemset failed"));
     if (cudaMallocHost(&h->status_host, sizeof(unsigned int)) != cudaSuccess)
         return bail(fail(MCLB_ENOMEM, "pinned status word"));
@@ -493,7 +495,10 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
     if (h->alt) {
         if (h->alt->item_bytes > 0 && cudaMalloc(&h->sc.line_item, h->alt->item_bytes) != cudaSuccess)
             return bail(fail(MCLB_ENOMEM, "D1Q3 line description"));
-        if (h->alt->prepare(P, h->sc, h->f) != cudaSuccess)
+        // the upload is a plain cudaMemcpy (legacy default stream), which may return before
+        // the copy lands: wait for it, since the handle's stream need not be ordered with it
+        if (h->alt->prepare(P, h->sc, h->f) != cudaSuccess ||
+            cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess)
             return bail(fail(MCLB_ECUDA, "D1Q3 line description upload failed"));
         if (h->alt->plan && h->kernel != MCLB_KERNEL_STAGED) {
             const int r = h->alt->plan(h->P, sms);
@@ -509,6 +514,8 @@ int mclb_create(const mclb_params* params, mclb_handle* out)
             return bail(fail(MCLB_EINVAL, "fused kernel unavailable for this problem"));
     }
     cudaGetLastError();
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)   // the zeroed buffers and status
+        return bail(fail(MCLB_ECUDA, "stream synchronisation after set-up failed"));
     h->magic = MAGIC;
     *out = h;
     return MCLB_OK;
@@ -722,6 +729,115 @@ int mclb_conservation(mclb_handle h, double* mass, double* mom, double* force_su
     if (mass) memcpy(mass, out, sizeof(double) * N);
     if (mom) memcpy(mom, out + N, sizeof(double) * ud);
     if (force_sum) memcpy(force_sum, out + N + ud, sizeof(double) * ud);
+    return MCLB_OK;
+}
+
+namespace {
+
+// Bytes of nrows stored rows of every component of a D2Q9 handle: per component the nine
+// velocity lines of each row (ghost columns included) and, in the 16-bit formats, the
+// row's FP32 density line.  Rows [y0, y0 + n) of one component are contiguous in both
+// arrays, so a band is N (or 2N) contiguous pieces.
+size_t band_bytes(const mclb_handle_s* h, int nrows)
+{
+    const Problem& P = h->P;
+    size_t b = (size_t)P.N * nrows * Q * P.pitch * h->tab->storage_bytes;
+    if (h->tab->shifted) b += (size_t)P.N * nrows * P.pitch * sizeof(float);
+    return b;
+}
+
+int check_band(mclb_handle h, int y0, int nrows, const char* what)
+{
+    int rc = check_handle(h);
+    if (rc) return rc;
+    if (h->P.lattice != MCLB_D2Q9) return fail(MCLB_EINVAL, "%s: D2Q9 handles only", what);
+    if (y0 < 0 || nrows < 0 || (long long)y0 + nrows > h->P.ny)
+        return fail(MCLB_EINVAL, "%s: rows [%d, %d + %d) outside [0, %d)", what, y0, y0, nrows,
+                    h->P.ny);
+    return MCLB_OK;
+}
+
+// Copy N pieces of `width` bytes, one per component, between the state (component s at
+// state + s * stride) and a packed buffer (at buf + s * width): one 2-D copy, or one copy
+// per component where the stride is beyond a 2-D copy's pitch limit.
+int copy_pieces(mclb_handle h, char* state, size_t stride, char* buf, size_t width, bool pack)
+{
+    const int N = h->P.N;
+    int dev = 0, max_pitch = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxPitch, dev));
+    if (stride <= (size_t)max_pitch) {
+        if (pack)
+            CK(cudaMemcpy2DAsync(buf, width, state, stride, width, N, cudaMemcpyDefault, h->stream));
+        else
+            CK(cudaMemcpy2DAsync(state, stride, buf, width, width, N, cudaMemcpyDefault, h->stream));
+        return MCLB_OK;
+    }
+    for (int s = 0; s < N; ++s) {
+        char* a = state + (size_t)s * stride;
+        char* b = buf + (size_t)s * width;
+        CK(cudaMemcpyAsync(pack ? b : a, pack ? a : b, width, cudaMemcpyDefault, h->stream));
+    }
+    return MCLB_OK;
+}
+
+// Copy the band [y0, y0 + nrows) of the current state to (pack) or from (!pack) buf.
+int copy_band(mclb_handle h, int y0, int nrows, char* buf, bool pack)
+{
+    const Problem& P = h->P;
+    const size_t line = (size_t)Q * P.pitch * h->tab->storage_bytes;   // one row, one component
+    char* base = static_cast<char*>(h->f[h->cur]);
+    int rc = copy_pieces(h, base + (size_t)y0 * line, (size_t)P.ny * line, buf, nrows * line, pack);
+    if (rc || !h->tab->shifted) return rc;
+    const size_t rl = (size_t)P.pitch * sizeof(float);
+    return copy_pieces(h, base + P.rbytes + (size_t)y0 * rl, (size_t)P.ny * rl,
+                       buf + (size_t)P.N * nrows * line, nrows * rl, pack);
+}
+
+}  // namespace
+
+size_t mclb_rows_bytes(mclb_handle h, int nrows)
+{
+    if (check_handle(h) || h->P.lattice != MCLB_D2Q9 || nrows < 0) return 0;
+    return band_bytes(h, nrows);
+}
+
+int mclb_pack_rows_device(mclb_handle h, int y0, int nrows, void* buf)
+{
+    int rc = check_band(h, y0, nrows, "mclb_pack_rows_device");
+    if (rc) return rc;
+    if (nrows == 0) return MCLB_OK;
+    if (!buf) return fail(MCLB_EINVAL, "mclb_pack_rows_device: buf is NULL");
+    return copy_band(h, y0, nrows, static_cast<char*>(buf), true);
+}
+
+int mclb_unpack_rows_device(mclb_handle h, int y0, int nrows, const void* buf)
+{
+    int rc = check_band(h, y0, nrows, "mclb_unpack_rows_device");
+    if (rc) return rc;
+    if (nrows == 0) return MCLB_OK;
+    if (!buf) return fail(MCLB_EINVAL, "mclb_unpack_rows_device: buf is NULL");
+    return copy_band(h, y0, nrows, const_cast<char*>(static_cast<const char*>(buf)), false);
+}
+
+int mclb_conservation_rows(mclb_handle h, int y0, int nrows, double* mass, double* mom,
+                           double* force_sum)
+{
+    int rc = check_band(h, y0, nrows, "mclb_conservation_rows");
+    if (rc) return rc;
+    const int N = h->P.N;
+    rc = ensure_dtmp(h, NMAX + 6);
+    if (rc) return rc;
+    double out[NMAX + 6] = {0.0};
+    if (nrows > 0) {
+        CK(h->tab->conservation_rows(h->P, h->sc, h->f[h->cur], y0, nrows, h->dtmp, h->stream));
+        CK(cudaMemcpyAsync(out, h->dtmp, sizeof(double) * (N + 4), cudaMemcpyDeviceToHost,
+                           h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    if (mass) memcpy(mass, out, sizeof(double) * N);
+    if (mom) memcpy(mom, out + N, sizeof(double) * 2);
+    if (force_sum) memcpy(force_sum, out + N + 2, sizeof(double) * 2);
     return MCLB_OK;
 }
 

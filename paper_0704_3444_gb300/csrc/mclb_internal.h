@@ -147,6 +147,9 @@ struct KernelTable {
     // FP64 sums into out: [0, N) mass, [N, N+2) momentum, [N+2, N+4) force
     cudaError_t (*conservation)(const Problem&, const Scratch&, const void* f, double* out,
                                 cudaStream_t st);
+    // the same sums over the rows [y0, y0 + nrows) only
+    cudaError_t (*conservation_rows)(const Problem&, const Scratch&, const void* f, int y0,
+                                     int nrows, double* out, cudaStream_t st);
     // FP64 compositions phi (N * S) and bulk flags (S, 1.0 where max |grad phi| < tol)
     cudaError_t (*compositions)(const Problem&, const Scratch&, const void* f, double* phi,
                                 double* bulk, double tol, cudaStream_t st);

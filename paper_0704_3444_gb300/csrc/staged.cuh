@@ -450,11 +450,13 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[K], double* parti
     }
 }
 
-// Conservation sums: mass^s, total momentum sum_s j^s, force sum_s rho^s a^s.
+// Conservation sums over the sites [s0, s1) (row-major, so a range of whole rows is a
+// y band): mass^s, total momentum sum_s j^s, force sum_s rho^s a^s.
 template <typename T, int N>
 __global__ void __launch_bounds__(SITE_THREADS)
 k_conservation(const T* __restrict__ f, const typename Storage<T>::C* __restrict__ rs,
                const typename Storage<T>::C* __restrict__ nu, double* __restrict__ partial,
+               long long s0, long long s1,
                const __grid_constant__ StepParams<typename Storage<T>::C> p)
 {
     using C = typename Storage<T>::C;
@@ -462,7 +464,7 @@ k_conservation(const T* __restrict__ f, const typename Storage<T>::C* __restrict
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < p.S;
+    for (long long site = s0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; site < s1;
          site += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(site / p.nx), x = (int)(site - (long long)y * p.nx);
         C rl[N], ax[N], ay[N];

@@ -205,13 +205,20 @@ struct Launch {
     static cudaError_t conservation(const Problem& P, const Scratch& sc, const void* f, double* out,
                                     cudaStream_t st)
     {
+        return conservation_rows(P, sc, f, 0, P.ny, out, st);
+    }
+
+    static cudaError_t conservation_rows(const Problem& P, const Scratch& sc, const void* f,
+                                         int y0, int nrows, double* out, cudaStream_t st)
+    {
         const auto p = make_params<C>(P, sc.status);
+        const long long s0 = (long long)y0 * P.nx, s1 = (long long)(y0 + nrows) * P.nx;
         MCLB_DISPATCH_N(P.N, {
             cudaError_t e = fields_n<NN>(p, sc, (const T*)f, st);
             if (e != cudaSuccess) return e;
             if (sc.partial_cap < (size_t)REDUCE_BLOCKS * (NN + 4)) return cudaErrorInvalidValue;
             k_conservation<T, NN><<<REDUCE_BLOCKS, SITE_THREADS, 0, st>>>(
-                (const T*)f, (const C*)sc.rho_s, (const C*)sc.nu, sc.partial, p);
+                (const T*)f, (const C*)sc.rho_s, (const C*)sc.nu, sc.partial, s0, s1, p);
             k_reduce_partials<<<1, SITE_THREADS, 0, st>>>(sc.partial, REDUCE_BLOCKS, NN + 4, out);
             return cudaGetLastError();
         });
@@ -748,6 +755,7 @@ inline void fill_staged(KernelTable& t)
     t.step_staged = &Launch<T>::step_staged;
     t.moments = &Launch<T>::moments;
     t.conservation = &Launch<T>::conservation;
+    t.conservation_rows = &Launch<T>::conservation_rows;
     t.compositions = &Launch<T>::compositions;
     t.get_state = &Launch<T>::get_state;
     t.set_state = &Launch<T>::set_state;
