@@ -212,20 +212,26 @@ def run_slabs(torch, mclb, prob, warmup, fp32_value, parts=2, steps=200):
     kw = dict(ncomp=prob.ncomp, tau=prob.tau, chi=prob.chi, m=prob.m, theta=prob.theta,
               kappa=prob.kappa, force=prob.force, precision="fp32", kernel=mclb.KERNEL_FUSED)
     ts = torch.cuda.Stream()   # one stream for every slab handle, its copies and the events
-    for period in (1, 4):
-        ls = slabs_mod.LocalSlabs(prob.nx, prob.ny, parts, period, stream=ts.cuda_stream, **kw)
-        ls.init_fields(prob.rho, prob.u)
-        t = time_steps(torch, ls, steps, warmup, ts)
-        val = prob.sites * prob.ncomp * steps / t / 1e6
-        band = ls.slabs[0].handle.rows_bytes(ls.slabs[0].G)
-        out[f"slabs_{parts}_{prob.name}_fp32_period{period}"] = {
-            "value": val, "steps": steps, "status_ok": all(v == 0 for v in ls.status()),
-            "slab_rows": [s.h for s in ls.slabs], "outer_rows_per_side": ls.slabs[0].G,
-            "band_bytes": band, "speedup_vs_fp32": val / fp32_value,
-            "note": "MLUPS x N of the lattice's own sites; every slab also computes its outer "
-                    "rows, and every period steps 2 bands per slab are packed and unpacked "
-                    "(device copies on the same stream)"}
-        ls.close()
+    for edges in ("walls", "periodic"):
+        for period in (1, 4):
+            ls = slabs_mod.LocalSlabs(prob.nx, prob.ny, parts, period, stream=ts.cuda_stream,
+                                      edges=edges, **kw)
+            ls.init_fields(prob.rho, prob.u)
+            t = time_steps(torch, ls, steps, warmup, ts)
+            val = prob.sites * prob.ncomp * steps / t / 1e6
+            band = ls.slabs[0].handle.rows_bytes(ls.slabs[0].G)
+            key = f"slabs_{parts}_{prob.name}_fp32_period{period}" + (
+                "" if edges == "walls" else "_periodic_edges")
+            out[key] = {
+                "value": val, "steps": steps, "status_ok": all(v == 0 for v in ls.status()),
+                "edges": edges, "slab_rows": [s.h for s in ls.slabs],
+                "outer_rows_per_side": ls.slabs[0].G, "band_bytes": band,
+                "launches_per_slab_step": ls.slabs[0].handle.launches_per_step,
+                "speedup_vs_fp32": val / fp32_value,
+                "note": "MLUPS x N of the lattice's own sites; every slab also computes its "
+                        "outer rows, and every period steps 2 bands per slab are packed and "
+                        "unpacked (device copies on the same stream)"}
+            ls.close()
     return out
 
 

@@ -35,7 +35,7 @@ Every slab needs h >= G rows, so that the G rows it sends are its own.
 from __future__ import annotations
 
 import contextlib
-from typing import Callable, List, Optional, Sequence, Tuple
+from typing import Callable, List, Optional, Tuple
 
 import numpy as np
 

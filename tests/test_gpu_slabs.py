@@ -120,16 +120,20 @@ def test_band_arguments_are_checked():
         line.conservation_rows(0, 1)
 
 
-@pytest.mark.parametrize("kernel", [mclb.KERNEL_FUSED, mclb.KERNEL_STAGED])
-@pytest.mark.parametrize("parts,period", [(2, 1), (3, 2), (1, 1)])
-def test_fp64_slabs_match_the_oracle(parts, period, kernel):
+@pytest.mark.parametrize("kernel,parts,period,edges", [
+    (mclb.KERNEL_FUSED, 2, 1, "walls"), (mclb.KERNEL_FUSED, 3, 2, "walls"),
+    (mclb.KERNEL_FUSED, 1, 1, "walls"), (mclb.KERNEL_STAGED, 2, 1, "walls"),
+    (mclb.KERNEL_STAGED, 3, 2, "walls"), (mclb.KERNEL_STAGED, 1, 1, "walls"),
+    (mclb.KERNEL_FUSED, 3, 2, "periodic"), (mclb.KERNEL_STAGED, 2, 1, "periodic")])
+def test_fp64_slabs_match_the_oracle(parts, period, kernel, edges):
     nx, ny, steps = 130, 61, 30
     rho, u = inputs.random_state(3, nx, ny, seed=11, amp=0.2, umax=0.03)
     orc = Oracle(KW["ncomp"], nx, ny, KW["tau"], KW["chi"], KW["m"], KW["theta"], KW["kappa"],
                  KW["force"])
     orc.init(rho, u)
     orc.run(steps)
-    ls = slabs.LocalSlabs(nx, ny, parts, period, precision="fp64", kernel=kernel, **KW)
+    ls = slabs.LocalSlabs(nx, ny, parts, period, precision="fp64", kernel=kernel, edges=edges,
+                          **KW)
     ls.init_fields(rho, u)
     ls.step(11)
     ls.step(steps - 11)
@@ -148,7 +152,8 @@ def test_fp64_slabs_match_the_oracle(parts, period, kernel):
     ls.close()
 
 
-def test_fp32_slabs_match_the_whole_handle():
+@pytest.mark.parametrize("edges", ["walls", "periodic"])
+def test_fp32_slabs_match_the_whole_handle(edges):
     nx, ny, steps = 256, 256, 100
     prob = inputs.ternary_droplets(nx, ny, precision="fp32")
     kw = dict(ncomp=prob.ncomp, tau=prob.tau, chi=prob.chi, m=prob.m, theta=prob.theta,
@@ -156,7 +161,7 @@ def test_fp32_slabs_match_the_whole_handle():
     whole = mclb.Simulation(nx=nx, ny=ny, precision="fp32", **kw)
     whole.init_fields(prob.rho, prob.u)
     whole.step(steps)
-    ls = slabs.LocalSlabs(nx, ny, 2, 1, precision="fp32", **kw)
+    ls = slabs.LocalSlabs(nx, ny, 2, 1, precision="fp32", edges=edges, **kw)
     ls.init_fields(prob.rho, prob.u)
     ls.step(steps)
     assert all(s == 0 for s in ls.status()) and whole.status() == 0
