@@ -117,6 +117,11 @@ def test_null_and_foreign_handles(lib):
     h = ctypes.c_void_p()
     assert lib.mclb_create(None, ctypes.byref(h)) == -1
     assert lib.mclb_create(ctypes.byref(_params()[0]), None) == -1
+    # the band calls check the handle before anything else
+    assert lib.mclb_rows_bytes(None, 3) == 0
+    assert lib.mclb_pack_rows_device(None, 0, 3, None) == -6
+    assert lib.mclb_unpack_rows_device(None, 0, 3, None) == -6
+    assert lib.mclb_conservation_rows(None, 0, 3, None, None, None) == -6
 
 
 def test_binding_checks_field_sizes():
