@@ -24,7 +24,12 @@ Two ways to connect the slabs:
 * ``SlabDecomposition`` -- one slab per rank of a ``torch.distributed`` process group
   (NCCL between GPUs, gloo on CPU): the bands move by point-to-point sends and receives,
   the FP64 conservation sums by an all-reduce.  Every method that exchanges or reduces
-  (``step``, ``moments``, ``conservation``, ``init_fields``, ``set_state``) is collective.
+  (``step``, ``moments``, ``conservation``, ``init_fields``, ``set_state``, ``status``) is
+  collective.  A device status (a non-finite density) does not stop ``step`` on one rank
+  and leave the others waiting: every rank keeps stepping and exchanging, and ``status``
+  reports the worst code on all of them.  A rank that dies (an exception, a lost process)
+  is seen by the others only when their next exchange fails, so give the process group a
+  short ``timeout``.
 * ``LocalSlabs`` -- every slab in this process (for instance several slabs on one GPU):
   the bands move by copies on the handles' common stream.
 
@@ -167,6 +172,9 @@ class _Stepper:
     period: int
     _fresh: int = 0
 
+    def _advance(self, hd, c: int):
+        hd.step(c)   # the library binding raises on a non-zero status
+
     def step(self, n: int = 1):
         n = int(n)
         if n < 0:
@@ -174,7 +182,7 @@ class _Stepper:
         while n > 0:
             c = min(n, self.period - self._fresh)
             for hd in self._handles():
-                hd.step(c)
+                self._advance(hd, c)
             self._fresh += c
             n -= c
             if self._fresh == self.period:
@@ -313,6 +321,16 @@ class SlabDecomposition(_Stepper):
         y0, h = split[self.rank]
         self.slab = Slab(make_handle(h + 2 * G), nx, ny, y0, h, period, new_buffer)
         self._fresh = 0
+        self._error = 0
+
+    def _advance(self, hd, c: int):
+        """Steps do not raise between exchanges: a rank that stopped here would leave its
+        neighbours waiting for its bands.  The first non-zero status (the binding's
+        step_nocheck returns it) is kept, and status() reports it on every rank."""
+        nocheck = getattr(hd, "step_nocheck", None)
+        rc = nocheck(c) if nocheck else hd.step(c)
+        if rc and not self._error:
+            self._error = int(rc)
 
     def _peer(self, r: int) -> int:
         r %= self.world
@@ -381,7 +399,13 @@ class SlabDecomposition(_Stepper):
         return dict(mass=v[:n], mom=v[n:n + 2], force=v[n + 2:n + 4])
 
     def status(self) -> int:
-        return self.slab.handle.status()
+        """Device status over the whole group (collective): 0, or the smallest (negative)
+        MCLB_E* code any rank's handle has reported since it was created."""
+        local = min(int(self.slab.handle.status() or 0), self._error)
+        with _on(self.stream):
+            t = self.torch.tensor([local], dtype=self.torch.int64, device=self.reduce_device)
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MIN, group=self.group)
+            return int(t.item())
 
     def close(self):
         close = getattr(self.slab.handle, "close", None)

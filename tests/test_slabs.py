@@ -218,3 +218,97 @@ def test_slab_decomposition_over_gloo_ranks(world, period):
         _, _, state_ok, moments_ok, sums_err = res[r]
         assert state_ok and moments_ok, r
         assert sums_err < 1e-11, (r, sums_err)
+
+
+class FailingSlabHandle(OracleSlabHandle):
+    """A stand-in whose device status turns ENONFINITE (-4) after `after` timesteps, as the
+    library's step_nocheck would report it (the failure is made on the host)."""
+
+    def __init__(self, nx, rows, kw, after):
+        super().__init__(nx, rows, kw)
+        self.after, self.done = after, 0
+
+    def step_nocheck(self, n):
+        self.o.run(n)
+        self.done += n
+        return -4 if self.done > self.after else 0
+
+
+def _failing_rank(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    os.environ["OMP_NUM_THREADS"] = "1"
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        kw, rho, u = problem()
+        make = ((lambda rows: FailingSlabHandle(NX, rows, kw, after=5)) if rank == 1
+                else (lambda rows: OracleSlabHandle(NX, rows, kw)))
+        sd = slabs.SlabDecomposition(NX, NY, 1, make_handle=make, new_buffer=cpu_buffer)
+        sd.init_fields(rho, u)
+        sd.step(12)           # rank 1's status turns bad at step 6; nobody stops early
+        out[rank] = (sd._fresh, sd.status())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_a_device_status_on_one_rank_reaches_every_rank():
+    """A non-finite status on one rank neither stops its steps nor leaves its neighbour
+    waiting for bands: both ranks finish the steps, and the collective status() reports the
+    code on both."""
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        procs = [ctx.Process(target=_failing_rank, args=(r, world, port, out))
+                 for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(300)
+            assert p.exitcode == 0
+        res = dict(out)
+    assert res == {0: (0, -4), 1: (0, -4)}
+
+
+def _dying_rank(rank, world, port, out):
+    import datetime
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    os.environ["OMP_NUM_THREADS"] = "1"
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    kw, rho, u = problem()
+    sd = slabs.SlabDecomposition(NX, NY, 1, make_handle=lambda rows: OracleSlabHandle(NX, rows, kw),
+                                 new_buffer=cpu_buffer)
+    sd.init_fields(rho, u)
+    if rank == 1:
+        os._exit(3)           # the rank is lost between steps, none of its exchanges in flight
+    import time
+
+    t0 = time.time()
+    try:
+        sd.step(4)
+        out[rank] = ("no error", time.time() - t0)
+    except Exception as e:    # the next exchange with the lost rank fails
+        out[rank] = (type(e).__name__, time.time() - t0)
+    os._exit(0)               # no teardown with a lost peer
+
+
+def test_a_lost_rank_ends_the_next_exchange_with_an_error():
+    """A rank that leaves between steps: its neighbour's next exchange fails within the
+    process group's timeout instead of waiting for ever (failure made on the host)."""
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        procs = [ctx.Process(target=_dying_rank, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+        codes = [p.exitcode for p in procs]
+        res = dict(out)
+    assert codes == [0, 3]
+    kind, seconds = res[0]
+    assert kind != "no error" and seconds < 60, res
