@@ -385,6 +385,19 @@ class SlabDecomposition(_Stepper):
         m = self.slab.handle.moments()
         return {k: np.ascontiguousarray(self.slab.own(v)) for k, v in m.items()}
 
+    def gather_moments(self, root: int = 0) -> Optional[dict]:
+        """The whole lattice's macroscopic fields on rank ``root`` of the group, None on the
+        other ranks (collective; the slabs' rows are sent as pickled host arrays, for output;
+        with NCCL the current CUDA device must be this rank's)."""
+        mine = (self.slab.y0, self.moments())
+        parts = [None] * self.world if self.rank == root else None
+        dst = root if self.group is None else self.dist.get_global_rank(self.group, root)
+        self.dist.gather_object(mine, parts, dst=dst, group=self.group)
+        if self.rank != root:
+            return None
+        parts.sort(key=lambda p: p[0])
+        return {k: np.concatenate([p[1][k] for p in parts], axis=-2) for k in parts[0][1]}
+
     def conservation(self) -> dict:
         """FP64 sums over the whole lattice (collective): each rank's own rows, all-reduced."""
         self.refresh()

@@ -194,7 +194,10 @@ def _rank(rank, world, port, period, out):
         c, cr = sd.conservation(), rows_sums(ref, 0, NY)
         sums_err = max(float(np.max(np.abs(c[k] - cr[k]) / (np.abs(cr[k]) + 1e-12)))
                        for k in ("mass", "mom", "force"))
-        out[rank] = (y0, h, state_ok, moments_ok, sums_err)
+        g = sd.gather_moments(root=world - 1)
+        gathered_ok = (g is None) if rank != world - 1 else all(
+            np.array_equal(g[k], mr[k]) for k in ("rho", "U", "mu", "P"))
+        out[rank] = (y0, h, state_ok, moments_ok and gathered_ok, sums_err)
     finally:
         dist.destroy_process_group()
 
