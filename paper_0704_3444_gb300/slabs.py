@@ -123,7 +123,8 @@ class Slab:
     """Rows [y0, y0 + h) of an ny-row periodic lattice, stored in a handle of h + 2G rows
     (G = REACH * period): stored row e holds lattice row (y0 - G + e) mod ny."""
 
-    def __init__(self, handle, nx: int, ny: int, y0: int, h: int, period: int, new_buffer):
+    def __init__(self, handle, nx: int, ny: int, y0: int, h: int, period: int, new_buffer,
+                 receive: bool = False):
         self.nx, self.ny, self.y0, self.h = int(nx), int(ny), int(y0), int(h)
         self.period = int(period)
         self.G = REACH * self.period
@@ -133,9 +134,13 @@ class Slab:
         self.rows = self.h + 2 * self.G
         self.handle = handle
         nb = handle.rows_bytes(self.G)
-        # outgoing bands: the top G own rows (to the slab above) and the bottom G (below)
+        # outgoing bands: the top G own rows (to the slab above) and the bottom G (below);
+        # incoming ones only where the bands arrive by messages (slabs in one process read
+        # their neighbours' outgoing buffers directly)
         self.send_up, self.send_down = new_buffer(nb), new_buffer(nb)
-        self.recv_below, self.recv_above = new_buffer(nb), new_buffer(nb)
+        self.recv_below = self.recv_above = None
+        if receive:
+            self.recv_below, self.recv_above = new_buffer(nb), new_buffer(nb)
 
     @property
     def lattice_rows(self) -> np.ndarray:
@@ -319,7 +324,8 @@ class SlabDecomposition(_Stepper):
             raise ValueError(f"slabs of ranks {short} have fewer than {G} rows (period "
                              f"{self.period}): use fewer ranks or a shorter period")
         y0, h = split[self.rank]
-        self.slab = Slab(make_handle(h + 2 * G), nx, ny, y0, h, period, new_buffer)
+        self.slab = Slab(make_handle(h + 2 * G), nx, ny, y0, h, period, new_buffer,
+                         receive=self.world > 1)
         self._fresh = 0
         self._error = 0
 
