@@ -226,3 +226,33 @@ def spinodal_det(phi, chi, m) -> float:
         B[k, k] = 1.0
         B[N - 1, k] = -1.0
     return float(np.linalg.det(B.T @ H @ B))
+
+
+def critical_ternary(chi, m, guess) -> np.ndarray:
+    """A critical point of a ternary mixture (N = 3) near `guess`.
+
+    Two conditions on the composition phi: the Hessian of f restricted to the simplex is
+    singular (the spinodal, det = 0), and the third derivative of f along its null
+    direction v vanishes (the two coexisting phases merge there).  f's third derivatives
+    are diagonal, d^3 f / d phi^s^3 = -1 / (m^s phi^s^2), so the second condition reads
+    sum_s v_s^3 / (m^s phi_s^2) = 0 with v = (w_0, w_1, -w_0 - w_1), w the null vector of
+    the 2 x 2 restricted Hessian."""
+    chi = np.asarray(chi, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    B = np.array([[1.0, 0.0], [0.0, 1.0], [-1.0, -1.0]])
+
+    def eqs(x):
+        phi = np.array([x[0], x[1], 1.0 - x[0] - x[1]])
+        if phi.min() <= 0:
+            return np.full(2, 1e3)
+        H = B.T @ (np.diag(1.0 / (m * phi)) + chi) @ B
+        # null direction of the singular 2 x 2 matrix (the row with the larger entries)
+        w = np.array([-H[0, 1], H[0, 0]]) if abs(H[0, 0]) + abs(H[0, 1]) >= abs(H[1, 0]) + abs(H[1, 1]) \
+            else np.array([H[1, 1], -H[1, 0]])
+        v = B @ (w / np.linalg.norm(w))
+        return np.array([np.linalg.det(H), np.sum(v ** 3 / (m * phi ** 2))])
+
+    sol = optimize.root(eqs, np.asarray(guess, dtype=np.float64)[:2], method="hybr", tol=1e-14)
+    if np.max(np.abs(eqs(sol.x))) > 1e-10:
+        raise RuntimeError(f"critical point failed: {sol.message}")
+    return np.array([sol.x[0], sol.x[1], 1.0 - sol.x[0] - sol.x[1]])

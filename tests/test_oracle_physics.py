@@ -437,3 +437,44 @@ def test_ternary_polymer_near_the_critical_point():
     assert np.abs(rich - tl[np.argmax(tl[:, 0])]).max() < 0.03
     assert np.abs(poor - tl[np.argmin(tl[:, 0])]).max() < 0.03
     assert rich[0] - poor[0] > 0.3   # separated, not relaxed to the mean
+
+
+@pytest.mark.parametrize("chi_ab", [2.5, 3.0, 4.0])
+def test_ternary_critical_point_closed_form(chi_ab):
+    """A symmetric A-B pair in an ideal third component (chi_AC = chi_BC = 0, m = 1): by the
+    A <-> B symmetry the critical point lies on phi_A = phi_B = x, the null direction is
+    (1, -1, 0), the third-order condition holds there identically, and the spinodal along it,
+    2 / x - 2 chi = 0, gives x = 1 / chi."""
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = chi_ab
+    x = 1.0 / chi_ab
+    c = thermo.critical_ternary(chi, np.ones(3), (x + 0.03, x - 0.02))
+    np.testing.assert_allclose(c, [x, x, 1 - 2 * x], atol=1e-10)
+
+
+def test_paper_ternary_critical_points():
+    """The paper's ternary systems (Sec. 4: chi_AB = 3, chi_AC = 0.5, chi_BC = 0.2; m = (1, 1, 1)
+    and (10, 1, 1)).  Under the symmetric-chi reading their critical points are (0.3568,
+    0.3078, 0.3354) and (0.1659, 0.0752, 0.7589); the printed ones, (0.32, 0.32, 0.36) and
+    (0.14, 0.11, 0.75), lie within 0.04 (the printed values are not reproduced exactly:
+    parity unpinned).  Tie lines through mean compositions a fraction s of the way from the
+    critical point toward (0.5, 0.5, 0) shrink to it as sqrt(s) (the mean-field order
+    parameter exponent 1/2): their width doubles from s = 0.0025 to s = 0.01, and their
+    ends lie on either side of the critical point."""
+    chi = np.zeros((3, 3))
+    chi[0, 1] = chi[1, 0] = 3.0
+    chi[0, 2] = chi[2, 0] = 0.5
+    chi[1, 2] = chi[2, 1] = 0.2
+    end = np.array([0.5, 0.5, 0.0])
+    for m, printed, want in (([1.0, 1.0, 1.0], (0.32, 0.32, 0.36), (0.3568, 0.3078, 0.3354)),
+                             ([10.0, 1.0, 1.0], (0.14, 0.11, 0.75), (0.1659, 0.0752, 0.7589))):
+        m = np.array(m)
+        c = thermo.critical_ternary(chi, m, printed)
+        np.testing.assert_allclose(c, want, atol=1e-4)
+        assert np.max(np.abs(c - np.array(printed))) < 0.04
+        widths = []
+        for s in (0.0025, 0.01):
+            p1, p2 = thermo.tie_line(chi, m, c + s * (end - c))
+            widths.append(np.max(np.abs(p1 - p2)))
+            assert (p1[0] - c[0]) * (p2[0] - c[0]) < 0
+        assert abs(widths[1] / widths[0] - 2.0) < 0.02, widths
