@@ -461,13 +461,15 @@ def test_paper_ternary_critical_points():
     critical point toward (0.5, 0.5, 0) shrink to it as sqrt(s) (the mean-field order
     parameter exponent 1/2): their width doubles from s = 0.0025 to s = 0.01, and their
     ends lie on either side of the critical point."""
+    gold = json.load(open(GOLDEN))
+    tc, printed_pts = gold["ternary_chi"], gold["ternary_critical_printed"]
     chi = np.zeros((3, 3))
-    chi[0, 1] = chi[1, 0] = 3.0
-    chi[0, 2] = chi[2, 0] = 0.5
-    chi[1, 2] = chi[2, 1] = 0.2
+    chi[0, 1] = chi[1, 0] = tc["AB"]
+    chi[0, 2] = chi[2, 0] = tc["AC"]
+    chi[1, 2] = chi[2, 1] = tc["BC"]
     end = np.array([0.5, 0.5, 0.0])
-    for m, printed, want in (([1.0, 1.0, 1.0], (0.32, 0.32, 0.36), (0.3568, 0.3078, 0.3354)),
-                             ([10.0, 1.0, 1.0], (0.14, 0.11, 0.75), (0.1659, 0.0752, 0.7589))):
+    for m, printed, want in (([1.0, 1.0, 1.0], printed_pts["monomer"], (0.3568, 0.3078, 0.3354)),
+                             ([10.0, 1.0, 1.0], printed_pts["polymer"], (0.1659, 0.0752, 0.7589))):
         m = np.array(m)
         c = thermo.critical_ternary(chi, m, printed)
         np.testing.assert_allclose(c, want, atol=1e-4)
