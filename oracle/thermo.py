@@ -22,7 +22,7 @@ sampled on a fine grid.
 from __future__ import annotations
 
 import math
-from typing import Sequence, Tuple
+from typing import Tuple
 
 import numpy as np
 from scipy import optimize

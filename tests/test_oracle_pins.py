@@ -6,7 +6,6 @@ from them, an independent transcription (complex-step chemical potentials,
 generic Hermite populations, the paper's D1Q3 lattice), a closed-form rate
 from Eq. woche, or a symmetry of the method.
 """
-import math
 
 import numpy as np
 import pytest
