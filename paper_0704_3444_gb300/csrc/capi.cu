@@ -1170,7 +1170,7 @@ static int batch_item(mclb_batch b, int index, mclb_handle* h)
 
 int mclb_batch_init_fields(mclb_batch b, int index, const double* rho, const double* u)
 {
-    mclb_handle h;
+    mclb_handle h = nullptr;
     int rc = batch_item(b, index, &h);
     if (rc) return rc;
     rc = mclb_init_fields(h, rho, u);  // writes buffer 0
@@ -1270,21 +1270,21 @@ int mclb_test_batch_partition(mclb_batch b, int narrow, int waves)
 
 int mclb_batch_moments(mclb_batch b, int index, double* rho, double* U, double* mu, double* P)
 {
-    mclb_handle h;
+    mclb_handle h = nullptr;
     int rc = batch_item(b, index, &h);
     return rc ? rc : mclb_moments(h, rho, U, mu, P);
 }
 
 int mclb_batch_fit_equilibrium(mclb_batch b, int index, int nphase, double* phi)
 {
-    mclb_handle h;
+    mclb_handle h = nullptr;
     int rc = batch_item(b, index, &h);
     return rc ? rc : mclb_fit_equilibrium(h, nphase, phi);
 }
 
 int mclb_batch_get_state(mclb_batch b, int index, double* f, size_t count)
 {
-    mclb_handle h;
+    mclb_handle h = nullptr;
     int rc = batch_item(b, index, &h);
     return rc ? rc : mclb_get_state(h, f, count);
 }
